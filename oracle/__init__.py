@@ -1,0 +1,224 @@
+"""ctypes front end of the plain FP64 CPU oracle (oracle/sl_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and
+by the CPU-baseline leg of bench.py.  The library path never imports it.
+
+Every function follows the paper's definitions (arXiv 1801.10233): see the
+header of sl_oracle.c for the equation each part implements.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+
+ORC_OK, ORC_ERR_ARG, ORC_ERR_BOX, ORC_ERR_SPIN_NORM, ORC_ERR_SKIN, ORC_ERR_OOM = 0, -1, -3, -4, -5, -8
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int32), ("rotation", ctypes.c_int32), ("fix_lattice", ctypes.c_int32),
+        ("rebuild_every", ctypes.c_int32), ("morse_shift", ctypes.c_int32), ("brute_force", ctypes.c_int32),
+        ("box", ctypes.c_double * 3), ("mass", ctypes.c_double), ("mu_s", ctypes.c_double),
+        ("H", ctypes.c_double * 3), ("dt", ctypes.c_double),
+        ("ex_alpha", ctypes.c_double), ("ex_gamma", ctypes.c_double), ("ex_delta", ctypes.c_double),
+        ("ex_rc", ctypes.c_double),
+        ("m_D0", ctypes.c_double), ("m_alpha", ctypes.c_double), ("m_r0", ctypes.c_double),
+        ("m_rc", ctypes.c_double), ("skin", ctypes.c_double),
+        ("lam", ctypes.c_double), ("temperature", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32), ("pad", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        L.orc_create.restype = ctypes.c_void_p
+        L.orc_create.argtypes = [ctypes.POINTER(_Params), _c_double_p, _c_double_p, _c_double_p, _c_int_p]
+        L.orc_destroy.argtypes = [ctypes.c_void_p]
+        L.orc_step.restype = ctypes.c_int
+        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_set_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.orc_get_state.argtypes = [ctypes.c_void_p, _c_double_p, _c_double_p, _c_double_p]
+        L.orc_get_forces.argtypes = [ctypes.c_void_p, _c_double_p]
+        L.orc_get_omega.argtypes = [ctypes.c_void_p, _c_double_p]
+        L.orc_get_order.argtypes = [ctypes.c_void_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p]
+        L.orc_get_step.restype = ctypes.c_long
+        L.orc_get_step.argtypes = [ctypes.c_void_p]
+        L.orc_get_rebuilds.restype = ctypes.c_int
+        L.orc_get_rebuilds.argtypes = [ctypes.c_void_p]
+        L.orc_get_error.restype = ctypes.c_int
+        L.orc_get_error.argtypes = [ctypes.c_void_p]
+        L.orc_count_pairs.restype = ctypes.c_int
+        L.orc_count_pairs.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.orc_energy.argtypes = [ctypes.c_void_p, _c_double_p]
+        L.orc_magnetization.argtypes = [ctypes.c_void_p, _c_double_p]
+        L.orc_potential_energy.restype = ctypes.c_int
+        L.orc_potential_energy.argtypes = [ctypes.POINTER(_Params), _c_double_p, _c_double_p, _c_double_p]
+        L.orc_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32 * 4), ctypes.POINTER(ctypes.c_uint32 * 2),
+                                        ctypes.POINTER(ctypes.c_uint32 * 4)]
+        L.orc_gauss3.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_long, ctypes.c_int, ctypes.c_int,
+                                 _c_double_p]
+        L.orc_params_size.restype = ctypes.c_int
+        if L.orc_params_size() != ctypes.sizeof(_Params):
+            raise RuntimeError("oracle parameter struct layout mismatch")
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_c_double_p)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_c_int_p)
+
+
+def make_params(p: dict, brute_force=False, lam=0.0, temperature=0.0, seed=0, replica=0) -> _Params:
+    q = _Params()
+    q.n_atoms = int(p["n_atoms"])
+    q.rotation = int(p.get("rotation", 0))
+    q.fix_lattice = int(p.get("fix_lattice", 0))
+    q.rebuild_every = int(p.get("rebuild_every", 0))
+    q.morse_shift = int(p.get("morse_shift_energy", 1))
+    q.brute_force = int(bool(brute_force))
+    for a in range(3):
+        q.box[a] = float(p["box"][a])
+        q.H[a] = float(p["H_tesla"][a])
+    q.mass = float(p["mass_amu"])
+    q.mu_s = float(p["mu_s_muB"])
+    q.dt = float(p["dt_ps"])
+    q.ex_alpha, q.ex_gamma = float(p["ex_alpha_eV"]), float(p["ex_gamma"])
+    q.ex_delta, q.ex_rc = float(p["ex_delta_A"]), float(p["ex_rc_A"])
+    q.m_D0, q.m_alpha = float(p["morse_D0_eV"]), float(p["morse_alpha_invA"])
+    q.m_r0, q.m_rc = float(p["morse_r0_A"]), float(p["morse_rc_A"])
+    q.skin = float(p["skin_A"])
+    q.lam = float(lam)
+    q.temperature = float(temperature)
+    q.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    q.replica = int(replica)
+    return q
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"oracle error {code}")
+        self.code = code
+
+
+class Oracle:
+    """Plain FP64 reference of one coupled spin-lattice system."""
+
+    def __init__(self, params: dict, r, v, s, brute_force=False, lam=0.0, temperature=0.0, seed=0, replica=0):
+        self._L = lib()
+        self.params = dict(params)
+        self.n = int(params["n_atoms"])
+        self._p = make_params(params, brute_force, lam, temperature, seed, replica)
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(self.n, 3)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(self.n, 3)
+        s = np.ascontiguousarray(s, dtype=np.float64).reshape(self.n, 3)
+        err = ctypes.c_int(0)
+        h = self._L.orc_create(ctypes.byref(self._p), _dp(r), _dp(v), _dp(s), ctypes.byref(err))
+        if not h:
+            raise OracleError(err.value)
+        self._h = ctypes.c_void_p(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and self._L is not None:
+            self._L.orc_destroy(h)
+            self._h = None
+
+    def step(self, n=1):
+        return int(self._L.orc_step(self._h, int(n)))
+
+    def set_dt(self, dt):
+        self._L.orc_set_dt(self._h, float(dt))
+
+    def state(self):
+        r = np.empty((self.n, 3)); v = np.empty((self.n, 3)); s = np.empty((self.n, 3))
+        self._L.orc_get_state(self._h, _dp(r), _dp(v), _dp(s))
+        return r, v, s
+
+    def forces(self):
+        F = np.empty((self.n, 3))
+        self._L.orc_get_forces(self._h, _dp(F))
+        return F
+
+    def omega(self):
+        w = np.empty((self.n, 3))
+        self._L.orc_get_omega(self._h, _dp(w))
+        return w
+
+    def order(self):
+        order = np.empty(self.n, dtype=np.int32)
+        cs = np.empty(9, dtype=np.int32)
+        sec = np.empty(self.n, dtype=np.int32)
+        col = np.empty(self.n, dtype=np.int32)
+        ns = np.empty(3, dtype=np.int32)
+        self._L.orc_get_order(self._h, _ip(order), _ip(cs), _ip(sec), _ip(col), _ip(ns))
+        return dict(order=order, colour_start=cs, sector=sec, colour=col, nsec=ns)
+
+    @property
+    def steps_done(self):
+        return int(self._L.orc_get_step(self._h))
+
+    @property
+    def rebuilds(self):
+        return int(self._L.orc_get_rebuilds(self._h))
+
+    @property
+    def error(self):
+        return int(self._L.orc_get_error(self._h))
+
+    def pair_count(self, which="exchange"):
+        return int(self._L.orc_count_pairs(self._h, 0 if which == "exchange" else 1))
+
+    def energy(self):
+        out = np.empty(8)
+        self._L.orc_energy(self._h, _dp(out))
+        return out
+
+    def magnetization(self):
+        out = np.empty(4)
+        self._L.orc_magnetization(self._h, _dp(out))
+        return out
+
+
+def potential_energy(params: dict, r, s):
+    """(E_morse, E_exch, E_zeeman, sum) of arbitrary positions and spin
+    vectors (spins need not be unit length), brute-force pairs."""
+    L = lib()
+    p = make_params(params)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    out = np.empty(4)
+    L.orc_potential_energy(ctypes.byref(p), _dp(r), _dp(s), _dp(out))
+    return out
+
+
+def philox4x32_10(ctr, key):
+    L = lib()
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    L.orc_philox4x32_10(ctypes.byref(c), ctypes.byref(k), ctypes.byref(o))
+    return [int(x) for x in o]
+
+
+def gauss3(seed, replica, step, subpass, atom):
+    L = lib()
+    g = np.empty(3)
+    L.orc_gauss3(int(seed) & 0xFFFFFFFFFFFFFFFF, int(replica), int(step), int(subpass), int(atom), _dp(g))
+    return g

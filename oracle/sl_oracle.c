@@ -1,0 +1,683 @@
+/*
+ * Plain FP64 CPU oracle for the coupled spin-lattice timestep of
+ * Tranchida, Plimpton, Thibaudeau, Thompson (arXiv 1801.10233).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * reference that the CUDA library is checked against.  It shares no code,
+ * header, table or constant generator with the CUDA path; only the tests,
+ * the smoke check and the CPU-baseline leg of the benchmark load it.
+ *
+ * What it computes, in the paper's order:
+ *   Hamiltonian   H = -mu_s mu_B sum_i H.s_i - sum_{i<j} J(r_ij) s_i.s_j
+ *                     + sum_i p_i^2/2m + sum_{i<j} V(r_ij)
+ *                 (Eq. s_hamiltonian and Eq. sl_hamiltonian, Sec. 2; every
+ *                 unordered pair counted once), J(r) the Bethe-Slater form of
+ *                 Eq. BSfunction (App. A.1), V(r) a Morse pair potential.
+ *   Precession    omega_i = -(1/hbar) dH/ds_i                 (Sec. 2.1)
+ *   EOM           dr/dt = p/m, dp/dt = -dH/dr, ds/dt = omega x s
+ *                 (Eqs. r_advance, p_advance, s_advance, Sec. 2.2)
+ *   Step          e^{Lp dt/2} e^{Ls dt/2} e^{Lr dt} e^{Ls dt/2} e^{Lp dt/2}
+ *                 (Eq. general_ST_decomposition, Sec. 3)
+ *   Spin half-op  prod_{k=1..N} e^{Ls_k dt/4} prod_{k=N..1} e^{Ls_k dt/4}
+ *                 with omega_k recomputed right before each single-spin
+ *                 update (Eq. spin_ST_decomposition, Sec. 3), the spins
+ *                 numbered by (colour, sector, atom id) as in the sectored
+ *                 form Eq. spin_ST_sectoring (Sec. 5.1).
+ *   Single spin   exact rotation of s about omega by |omega| tau (default) or
+ *                 the Cayley-type propagator printed in Sec. 3 (mode 1).
+ *   Thermostat    stochastic precession vector of Eq. sLLG (Sec. 4.1) with
+ *                 noise variance 2 D_S / tau per component.
+ *   Observables   kinetic, Morse, exchange, Zeeman energies; T_L
+ *                 (Eq. lattice_temperature), T_S (Eq. spin_temperature),
+ *                 magnetisation M = (1/N) sum_i s_i.
+ *
+ * Pair lists are rebuilt from scratch at the exact cutoffs whenever the
+ * positions change (brute force, or a plain cell list that the tests check
+ * against brute force); there is no Verlet skin here.  The skin only enters
+ * through the sector assignment, which is redone when an atom has moved more
+ * than skin/2 since the last assignment (or on a fixed schedule), because the
+ * colour order of the sweep depends on it.
+ *
+ * Compiled with -ffp-contract=off so that every a*b+c rounds twice, as written.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Physical constants in the paper's "metal" unit set (A, ps, eV, amu, K, T). */
+#define ORC_HBAR 6.582119569e-4   /* eV ps / rad (Sec. 2.1 prints 1e3 too small) */
+#define ORC_KB 8.617333262e-5     /* eV / K */
+#define ORC_MUB 5.7883818060e-5   /* eV / T */
+#define ORC_FTOA 9648.533212      /* (eV/A)/amu -> A/ps^2 */
+
+enum { ORC_OK = 0, ORC_ERR_ARG = -1, ORC_ERR_BOX = -3, ORC_ERR_SPIN_NORM = -4,
+       ORC_ERR_SKIN = -5, ORC_ERR_OOM = -8 };
+
+typedef struct {
+  int32_t n_atoms;
+  int32_t rotation;      /* 0 exact (Rodrigues) rotation, 1 Cayley propagator of Sec. 3 */
+  int32_t fix_lattice;   /* 1: positions and velocities frozen, spins only */
+  int32_t rebuild_every; /* 0: re-sector when max displacement > skin/2; K>0: every K steps */
+  int32_t morse_shift;   /* 1: report V(r)-V(rc) in the energy (dynamics unchanged) */
+  int32_t brute_force;   /* 1: O(N^2) pair search instead of the cell list */
+  double box[3];
+  double mass;           /* amu */
+  double mu_s;           /* magnetic moment in units of mu_B */
+  double H[3];           /* applied field, T */
+  double dt;             /* ps */
+  double ex_alpha, ex_gamma, ex_delta, ex_rc;   /* Eq. BSfunction */
+  double m_D0, m_alpha, m_r0, m_rc;             /* Morse */
+  double skin;
+  double lambda;         /* transverse damping of Eq. sLLG (0: none) */
+  double temperature;    /* spin bath temperature, K (0: no noise) */
+  uint64_t seed;
+  int32_t replica;
+  int32_t pad;
+} orc_params;
+
+typedef struct {
+  int n;
+  int *off;    /* CSR offsets, n+1 */
+  int *j;      /* neighbour ids, ascending within each row */
+  int cap;
+} orc_list;
+
+typedef struct {
+  orc_params p;
+  int n;
+  double *r, *v, *s, *F;   /* [n][3], indexed by atom id */
+  double *rb;              /* positions at the last sector assignment */
+  int nsec[3];
+  double edge[3];
+  int *sector;             /* linear sector index per atom */
+  int *colour;             /* colour 0..7 per atom */
+  int *order;              /* atom ids in sweep order: colour, sector, id */
+  int colour_start[9];
+  orc_list ex, mo;         /* exchange pairs (r < ex_rc), Morse pairs (r < m_rc) */
+  double *exJ, *exdJ;      /* J(r_ij), J'(r_ij) per exchange list entry */
+  long step;               /* completed steps */
+  int err;
+  int rebuilds;
+} orc_state;
+
+/* ------------------------------------------------------------------ */
+/* Counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11).              */
+/* ------------------------------------------------------------------ */
+static void philox_round(uint32_t c[4], const uint32_t k[2]) {
+  uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c[0];
+  uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c[2];
+  uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+  uint32_t n0 = hi1 ^ c[1] ^ k[0];
+  uint32_t n2 = hi0 ^ c[3] ^ k[1];
+  c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+  uint32_t k[2] = {key[0], key[1]};
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k[0] += 0x9E3779B9u; k[1] += 0xBB67AE85u; }
+    philox_round(c, k);
+  }
+  out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* Three standard normal deviates for (seed, replica, step, sub-pass, atom):
+ * Box-Muller on the four 32-bit words, u = (x + 1/2) / 2^32 in (0,1). */
+void orc_gauss3(uint64_t seed, int replica, long step, int subpass, int atom, double g[3]) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t ctr[4] = {(uint32_t)atom, (uint32_t)step, (uint32_t)subpass, (uint32_t)replica};
+  uint32_t x[4];
+  orc_philox4x32_10(ctr, key, x);
+  const double two32 = 4294967296.0;
+  const double twopi = 6.283185307179586476925286766559;
+  double u0 = ((double)x[0] + 0.5) / two32, u1 = ((double)x[1] + 0.5) / two32;
+  double u2 = ((double)x[2] + 0.5) / two32, u3 = ((double)x[3] + 0.5) / two32;
+  double ra = sqrt(-2.0 * log(u0)), rb = sqrt(-2.0 * log(u2));
+  g[0] = ra * cos(twopi * u1);
+  g[1] = ra * sin(twopi * u1);
+  g[2] = rb * cos(twopi * u3);
+}
+
+/* ------------------------------------------------------------------ */
+/* Pair functions                                                      */
+/* ------------------------------------------------------------------ */
+
+/* Bethe-Slater exchange, Eq. BSfunction (App. A.1), without the cutoff step. */
+static double bs_J(const orc_params* p, double r) {
+  double x = (r / p->ex_delta) * (r / p->ex_delta);
+  return 4.0 * p->ex_alpha * x * (1.0 - p->ex_gamma * x) * exp(-x);
+}
+/* dJ/dr of the same expression. */
+static double bs_dJ(const orc_params* p, double r) {
+  double x = (r / p->ex_delta) * (r / p->ex_delta);
+  double dxdr = 2.0 * r / (p->ex_delta * p->ex_delta);
+  /* d/dx [x (1 - g x) e^{-x}] = e^{-x} (1 - 2 g x - x + g x^2) */
+  return 4.0 * p->ex_alpha * exp(-x) * (1.0 - 2.0 * p->ex_gamma * x - x + p->ex_gamma * x * x) * dxdr;
+}
+/* Morse pair energy V(r) = D0 (e^{-2a(r-r0)} - 2 e^{-a(r-r0)}). */
+static double morse_V(const orc_params* p, double r) {
+  double e = exp(-p->m_alpha * (r - p->m_r0));
+  return p->m_D0 * (e * e - 2.0 * e);
+}
+/* dV/dr. */
+static double morse_dV(const orc_params* p, double r) {
+  double e = exp(-p->m_alpha * (r - p->m_r0));
+  return p->m_D0 * (-2.0 * p->m_alpha * e * e + 2.0 * p->m_alpha * e);
+}
+
+/* Minimum-image separation d = r_j - r_i. */
+static void min_image(const orc_state* st, int i, int j, double d[3]) {
+  for (int a = 0; a < 3; ++a) {
+    double L = st->p.box[a];
+    double x = st->r[3 * j + a] - st->r[3 * i + a];
+    d[a] = x - L * nearbyint(x / L);
+  }
+}
+
+static double wrap1(double x, double L) { return x - L * floor(x / L); }
+
+/* ------------------------------------------------------------------ */
+/* Pair search at an exact cutoff                                      */
+/* ------------------------------------------------------------------ */
+static int cmp_int(const void* a, const void* b) {
+  int x = *(const int*)a, y = *(const int*)b;
+  return (x > y) - (x < y);
+}
+
+static int list_push(orc_list* L, int* cnt, int j) {
+  if (*cnt >= L->cap) {
+    int nc = L->cap ? 2 * L->cap : 1024;
+    int* nj = (int*)realloc(L->j, (size_t)nc * sizeof(int));
+    if (!nj) return ORC_ERR_OOM;
+    L->j = nj; L->cap = nc;
+  }
+  L->j[(*cnt)++] = j;
+  return ORC_OK;
+}
+
+/* All j != i with |min_image(r_j - r_i)| < rc, rows sorted by j. */
+static int build_list(orc_state* st, double rc, orc_list* L) {
+  int n = st->n;
+  double rc2 = rc * rc;
+  if (!L->off) { L->off = (int*)malloc((size_t)(n + 1) * sizeof(int)); if (!L->off) return ORC_ERR_OOM; }
+  int cnt = 0;
+  int nc[3];
+  int use_cells = !st->p.brute_force;
+  for (int a = 0; a < 3; ++a) {
+    nc[a] = (int)floor(st->p.box[a] / rc);
+    if (nc[a] < 3) use_cells = 0;
+  }
+  if (!use_cells) {
+    for (int i = 0; i < n; ++i) {
+      L->off[i] = cnt;
+      for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        double d[3];
+        min_image(st, i, j, d);
+        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2)
+          if (list_push(L, &cnt, j)) return ORC_ERR_OOM;
+      }
+    }
+    L->off[n] = cnt;
+    return ORC_OK;
+  }
+  /* cell list: cell edge >= rc, at least 3 cells per dimension */
+  int ncell = nc[0] * nc[1] * nc[2];
+  int* head = (int*)malloc((size_t)ncell * sizeof(int));
+  int* next = (int*)malloc((size_t)n * sizeof(int));
+  int* cellof = (int*)malloc((size_t)n * 3 * sizeof(int));
+  if (!head || !next || !cellof) { free(head); free(next); free(cellof); return ORC_ERR_OOM; }
+  for (int c = 0; c < ncell; ++c) head[c] = -1;
+  for (int i = n - 1; i >= 0; --i) {
+    int cc[3];
+    for (int a = 0; a < 3; ++a) {
+      double L_ = st->p.box[a];
+      int k = (int)floor(wrap1(st->r[3 * i + a], L_) / (L_ / nc[a]));
+      if (k < 0) k = 0;
+      if (k >= nc[a]) k = nc[a] - 1;
+      cc[a] = k;
+      cellof[3 * i + a] = k;
+    }
+    int c = cc[0] + nc[0] * (cc[1] + nc[1] * cc[2]);
+    next[i] = head[c];
+    head[c] = i;
+  }
+  for (int i = 0; i < n; ++i) {
+    L->off[i] = cnt;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int x = (cellof[3 * i] + dx + nc[0]) % nc[0];
+          int y = (cellof[3 * i + 1] + dy + nc[1]) % nc[1];
+          int z = (cellof[3 * i + 2] + dz + nc[2]) % nc[2];
+          for (int j = head[x + nc[0] * (y + nc[1] * z)]; j >= 0; j = next[j]) {
+            if (j == i) continue;
+            double d[3];
+            min_image(st, i, j, d);
+            if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2)
+              if (list_push(L, &cnt, j)) { free(head); free(next); free(cellof); return ORC_ERR_OOM; }
+          }
+        }
+    qsort(L->j + L->off[i], (size_t)(cnt - L->off[i]), sizeof(int), cmp_int);
+  }
+  L->off[n] = cnt;
+  free(head); free(next); free(cellof);
+  return ORC_OK;
+}
+
+/* Pair lists and the exchange coefficients at the current positions
+ * (J is recomputed after every drift, Sec. 3). */
+static int refresh_pairs(orc_state* st) {
+  int e = build_list(st, st->p.ex_rc, &st->ex);
+  if (e) return e;
+  e = build_list(st, st->p.m_rc, &st->mo);
+  if (e) return e;
+  int np = st->ex.off[st->n];
+  free(st->exJ); free(st->exdJ);
+  st->exJ = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
+  st->exdJ = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
+  if (!st->exJ || !st->exdJ) return ORC_ERR_OOM;
+  for (int i = 0; i < st->n; ++i)
+    for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
+      double d[3];
+      min_image(st, i, st->ex.j[k], d);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      st->exJ[k] = bs_J(&st->p, r);
+      st->exdJ[k] = bs_dJ(&st->p, r);
+    }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sector assignment (Sec. 5.1) and the sweep order                   */
+/* ------------------------------------------------------------------ */
+static int sector_grid(const orc_params* p, int nsec[3], double edge[3]) {
+  double w = p->ex_rc + p->skin;
+  for (int a = 0; a < 3; ++a) {
+    int n = (int)floor(p->box[a] / w);
+    if (n % 2) n -= 1;
+    if (n < 2) return ORC_ERR_BOX;
+    nsec[a] = n;
+    edge[a] = p->box[a] / (double)n;
+  }
+  return ORC_OK;
+}
+
+typedef struct { int colour, sector, id; } orc_key;
+static int cmp_key(const void* a, const void* b) {
+  const orc_key* x = (const orc_key*)a; const orc_key* y = (const orc_key*)b;
+  if (x->colour != y->colour) return x->colour < y->colour ? -1 : 1;
+  if (x->sector != y->sector) return x->sector < y->sector ? -1 : 1;
+  return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Wrap positions into the box, assign each atom to its sector and colour,
+ * order the atoms by (colour, sector, id), remember the positions. */
+static int assign_sectors(orc_state* st) {
+  int n = st->n;
+  orc_key* keys = (orc_key*)malloc((size_t)(n ? n : 1) * sizeof(orc_key));
+  if (!keys) return ORC_ERR_OOM;
+  for (int i = 0; i < n; ++i) {
+    int sx[3];
+    for (int a = 0; a < 3; ++a) {
+      double x = wrap1(st->r[3 * i + a], st->p.box[a]);
+      st->r[3 * i + a] = x;
+      int k = (int)floor(x / st->edge[a]);
+      if (k < 0) k = 0;
+      if (k >= st->nsec[a]) k = st->nsec[a] - 1;
+      sx[a] = k;
+    }
+    st->sector[i] = sx[0] + st->nsec[0] * (sx[1] + st->nsec[1] * sx[2]);
+    st->colour[i] = (sx[0] & 1) + 2 * (sx[1] & 1) + 4 * (sx[2] & 1);
+    keys[i].colour = st->colour[i];
+    keys[i].sector = st->sector[i];
+    keys[i].id = i;
+  }
+  qsort(keys, (size_t)n, sizeof(orc_key), cmp_key);
+  for (int c = 0; c <= 8; ++c) st->colour_start[c] = n;
+  for (int k = n - 1; k >= 0; --k) {
+    st->order[k] = keys[k].id;
+    st->colour_start[keys[k].colour] = k;
+  }
+  for (int c = 7; c >= 0; --c)
+    if (st->colour_start[c] > st->colour_start[c + 1]) st->colour_start[c] = st->colour_start[c + 1];
+  memcpy(st->rb, st->r, (size_t)n * 3 * sizeof(double));
+  free(keys);
+  st->rebuilds += 1;
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Precession vector and single-spin propagators                      */
+/* ------------------------------------------------------------------ */
+
+/* omega_i = (1/hbar) (mu_s mu_B H + sum_j J_ij s_j)  (= -(1/hbar) dH/ds_i). */
+static void omega_of(const orc_state* st, int i, double w[3]) {
+  double zf = st->p.mu_s * ORC_MUB;
+  double h[3] = {zf * st->p.H[0], zf * st->p.H[1], zf * st->p.H[2]};
+  for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
+    const double* sj = st->s + 3 * st->ex.j[k];
+    h[0] += st->exJ[k] * sj[0];
+    h[1] += st->exJ[k] * sj[1];
+    h[2] += st->exJ[k] * sj[2];
+  }
+  w[0] = h[0] / ORC_HBAR; w[1] = h[1] / ORC_HBAR; w[2] = h[2] / ORC_HBAR;
+}
+
+static void cross(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Update spin i over time tau (one factor e^{L_si tau} of Eq. spin_ST_decomposition). */
+static void rotate(orc_state* st, int i, double tau, int subpass) {
+  double w[3];
+  omega_of(st, i, w);
+  double* s = st->s + 3 * i;
+  if (st->p.lambda != 0.0 || st->p.temperature != 0.0) {
+    /* Eq. sLLG written as ds/dt = Om x s with
+     * Om = (omega + eta + lambda s x omega) / (1 + lambda^2);
+     * eta ~ N(0, 2 D_S / |tau|) per component, D_S = lambda (1+lambda^2) k_B T / hbar. */
+    double lam = st->p.lambda;
+    double eta[3] = {0, 0, 0};
+    if (st->p.temperature > 0.0) {
+      double g[3];
+      orc_gauss3(st->p.seed, st->p.replica, st->step, subpass, i, g);
+      double DS = lam * (1.0 + lam * lam) * ORC_KB * st->p.temperature / ORC_HBAR;
+      double sig = sqrt(2.0 * DS / fabs(tau));
+      eta[0] = sig * g[0]; eta[1] = sig * g[1]; eta[2] = sig * g[2];
+    }
+    double sxw[3];
+    cross(s, w, sxw);
+    double den = 1.0 + lam * lam;
+    for (int a = 0; a < 3; ++a) w[a] = (w[a] + eta[a] + lam * sxw[a]) / den;
+  }
+  double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  if (st->p.rotation == 0) {
+    /* exact rotation about omega by theta = |omega| tau (Rodrigues) */
+    double wn = sqrt(w2);
+    double th = wn * tau;
+    if (wn == 0.0 || th == 0.0) return;
+    double nv[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+    double c = cos(th), sn = sin(th), h = sin(0.5 * th);
+    double omc = 2.0 * h * h;
+    double nxs[3];
+    cross(nv, s, nxs);
+    double ns = nv[0] * s[0] + nv[1] * s[1] + nv[2] * s[2];
+    double out[3];
+    for (int a = 0; a < 3; ++a) out[a] = s[a] * c + nxs[a] * sn + nv[a] * ns * omc;
+    s[0] = out[0]; s[1] = out[1]; s[2] = out[2];
+  } else {
+    /* Cayley-type propagator of Sec. 3 over time tau */
+    double wxs[3];
+    cross(w, s, wxs);
+    double ws = w[0] * s[0] + w[1] * s[1] + w[2] * s[2];
+    double q = tau * tau / 4.0;
+    double den = 1.0 + q * w2;
+    double out[3];
+    for (int a = 0; a < 3; ++a) out[a] = (s[a] + tau * wxs[a] + q * (2.0 * w[a] * ws - w2 * s[a])) / den;
+    s[0] = out[0]; s[1] = out[1]; s[2] = out[2];
+  }
+}
+
+/* e^{L_s h}: forward over the sweep order with h/2 per spin, then backward. */
+static void spin_half_op(orc_state* st, double h, int subpass0) {
+  int n = st->n;
+  for (int k = 0; k < n; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
+  for (int k = n - 1; k >= 0; --k) rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
+}
+
+/* ------------------------------------------------------------------ */
+/* Forces (Eq. p_advance derived from the energy)                     */
+/* ------------------------------------------------------------------ */
+static void compute_forces(orc_state* st) {
+  int n = st->n;
+  memset(st->F, 0, (size_t)n * 3 * sizeof(double));
+  for (int i = 0; i < n; ++i) {
+    double* f = st->F + 3 * i;
+    for (int k = st->mo.off[i]; k < st->mo.off[i + 1]; ++k) {
+      double d[3];
+      min_image(st, i, st->mo.j[k], d);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      double c = morse_dV(&st->p, r) / r;       /* F_i += V'(r) (r_j - r_i)/r */
+      f[0] += c * d[0]; f[1] += c * d[1]; f[2] += c * d[2];
+    }
+    const double* si = st->s + 3 * i;
+    for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
+      int j = st->ex.j[k];
+      double d[3];
+      min_image(st, i, j, d);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      const double* sj = st->s + 3 * j;
+      double sij = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
+      double c = -st->exdJ[k] * sij / r;        /* F_i -= J'(r) s_i.s_j (r_j - r_i)/r */
+      f[0] += c * d[0]; f[1] += c * d[1]; f[2] += c * d[2];
+    }
+  }
+}
+
+static void kick(orc_state* st, double h) {
+  double c = h * ORC_FTOA / st->p.mass;
+  for (int k = 0; k < 3 * st->n; ++k) st->v[k] += c * st->F[k];
+}
+
+static double max_disp2(const orc_state* st) {
+  double m = 0.0;
+  for (int i = 0; i < st->n; ++i) {
+    double d0 = st->r[3 * i] - st->rb[3 * i];
+    double d1 = st->r[3 * i + 1] - st->rb[3 * i + 1];
+    double d2 = st->r[3 * i + 2] - st->rb[3 * i + 2];
+    double q = d0 * d0 + d1 * d1 + d2 * d2;
+    if (q > m) m = q;
+  }
+  return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Public interface                                                    */
+/* ------------------------------------------------------------------ */
+void orc_destroy(orc_state* st) {
+  if (!st) return;
+  free(st->r); free(st->v); free(st->s); free(st->F); free(st->rb);
+  free(st->sector); free(st->colour); free(st->order);
+  free(st->ex.off); free(st->ex.j); free(st->mo.off); free(st->mo.j);
+  free(st->exJ); free(st->exdJ);
+  free(st);
+}
+
+int orc_params_size(void) { return (int)sizeof(orc_params); }
+
+/* r, v, s: [n][3] in atom-id order.  Returns NULL and sets *err on failure. */
+orc_state* orc_create(const orc_params* p, const double* r, const double* v, const double* s, int* err) {
+  *err = ORC_OK;
+  if (!p || p->n_atoms < 0 || p->mass <= 0.0) { *err = ORC_ERR_ARG; return NULL; }
+  double need = 2.0 * ((p->m_rc > p->ex_rc ? p->m_rc : p->ex_rc) + p->skin);
+  for (int a = 0; a < 3; ++a)
+    if (!(p->box[a] >= need)) { *err = ORC_ERR_BOX; return NULL; }
+  orc_state* st = (orc_state*)calloc(1, sizeof(orc_state));
+  if (!st) { *err = ORC_ERR_OOM; return NULL; }
+  st->p = *p;
+  int n = p->n_atoms;
+  st->n = n;
+  size_t b3 = (size_t)(n ? n : 1) * 3 * sizeof(double);
+  st->r = (double*)malloc(b3); st->v = (double*)malloc(b3); st->s = (double*)malloc(b3);
+  st->F = (double*)malloc(b3); st->rb = (double*)malloc(b3);
+  st->sector = (int*)malloc((size_t)(n ? n : 1) * sizeof(int));
+  st->colour = (int*)malloc((size_t)(n ? n : 1) * sizeof(int));
+  st->order = (int*)malloc((size_t)(n ? n : 1) * sizeof(int));
+  if (!st->r || !st->v || !st->s || !st->F || !st->rb || !st->sector || !st->colour || !st->order) {
+    orc_destroy(st); *err = ORC_ERR_OOM; return NULL;
+  }
+  memcpy(st->r, r, (size_t)n * 3 * sizeof(double));
+  memcpy(st->v, v, (size_t)n * 3 * sizeof(double));
+  memcpy(st->s, s, (size_t)n * 3 * sizeof(double));
+  for (int i = 0; i < n; ++i) {
+    const double* si = s + 3 * i;
+    double nn = sqrt(si[0] * si[0] + si[1] * si[1] + si[2] * si[2]);
+    if (!(fabs(nn - 1.0) <= 1e-12)) { orc_destroy(st); *err = ORC_ERR_SPIN_NORM; return NULL; }
+  }
+  int e = sector_grid(p, st->nsec, st->edge);
+  if (!e) e = assign_sectors(st);
+  if (!e) e = refresh_pairs(st);
+  if (e) { orc_destroy(st); *err = e; return NULL; }
+  compute_forces(st);
+  return st;
+}
+
+/* One or more timesteps of Eq. general_ST_decomposition. */
+int orc_step(orc_state* st, int nsteps) {
+  for (int it = 0; it < nsteps; ++it) {
+    double dt = st->p.dt;
+    int lat = !st->p.fix_lattice;
+    if (lat) kick(st, 0.5 * dt);
+    spin_half_op(st, 0.5 * dt, 0);
+    if (lat) {
+      for (int k = 0; k < 3 * st->n; ++k) st->r[k] += dt * st->v[k];
+      double h = 0.5 * st->p.skin;
+      double md2 = max_disp2(st);
+      int resector;
+      if (st->p.rebuild_every > 0) {
+        resector = ((st->step + 1) % st->p.rebuild_every) == 0;
+        if (!resector && md2 > h * h && st->err == ORC_OK) st->err = ORC_ERR_SKIN;
+      } else {
+        resector = md2 > h * h;
+      }
+      if (resector) {
+        int e = assign_sectors(st);
+        if (e) return e;
+      }
+      int e = refresh_pairs(st);
+      if (e) return e;
+    }
+    spin_half_op(st, 0.5 * dt, 2);
+    if (lat) {
+      compute_forces(st);
+      kick(st, 0.5 * dt);
+    }
+    st->step += 1;
+  }
+  return st->err;
+}
+
+void orc_set_dt(orc_state* st, double dt) { st->p.dt = dt; }
+
+void orc_get_state(const orc_state* st, double* r, double* v, double* s) {
+  size_t b = (size_t)st->n * 3 * sizeof(double);
+  if (r) memcpy(r, st->r, b);
+  if (v) memcpy(v, st->v, b);
+  if (s) memcpy(s, st->s, b);
+}
+
+void orc_get_forces(const orc_state* st, double* F) {
+  memcpy(F, st->F, (size_t)st->n * 3 * sizeof(double));
+}
+
+/* omega_i of the current state, [n][3], rad/ps (no noise, no damping). */
+void orc_get_omega(const orc_state* st, double* w) {
+  for (int i = 0; i < st->n; ++i) omega_of(st, i, w + 3 * i);
+}
+
+/* Sweep order, colour boundaries, per-atom sector and colour, sector grid. */
+void orc_get_order(const orc_state* st, int* order, int* colour_start, int* sector, int* colour, int* nsec) {
+  if (order) memcpy(order, st->order, (size_t)st->n * sizeof(int));
+  if (colour_start) memcpy(colour_start, st->colour_start, 9 * sizeof(int));
+  if (sector) memcpy(sector, st->sector, (size_t)st->n * sizeof(int));
+  if (colour) memcpy(colour, st->colour, (size_t)st->n * sizeof(int));
+  if (nsec) { nsec[0] = st->nsec[0]; nsec[1] = st->nsec[1]; nsec[2] = st->nsec[2]; }
+}
+
+long orc_get_step(const orc_state* st) { return st->step; }
+int orc_get_rebuilds(const orc_state* st) { return st->rebuilds; }
+int orc_get_error(const orc_state* st) { return st->err; }
+int orc_count_pairs(const orc_state* st, int which) {
+  return which == 0 ? st->ex.off[st->n] : st->mo.off[st->n];
+}
+
+/* out[0..7] = E_kin, E_morse, E_exch, E_zeeman, E_total (eV), T_L, T_S (K), 0. */
+void orc_energy(const orc_state* st, double out[8]) {
+  int n = st->n;
+  double ek = 0.0, em = 0.0, ex = 0.0, ez = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double* v = st->v + 3 * i;
+    ek += 0.5 * st->p.mass * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / ORC_FTOA;
+  }
+  double vshift = st->p.morse_shift ? morse_V(&st->p, st->p.m_rc) : 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int k = st->mo.off[i]; k < st->mo.off[i + 1]; ++k) {
+      int j = st->mo.j[k];
+      if (j <= i) continue;
+      double d[3];
+      min_image(st, i, j, d);
+      double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      em += morse_V(&st->p, r) - vshift;
+    }
+  for (int i = 0; i < n; ++i)
+    for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
+      int j = st->ex.j[k];
+      if (j <= i) continue;
+      const double* si = st->s + 3 * i;
+      const double* sj = st->s + 3 * j;
+      ex -= st->exJ[k] * (si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2]);
+    }
+  double zf = st->p.mu_s * ORC_MUB;
+  for (int i = 0; i < n; ++i) {
+    const double* si = st->s + 3 * i;
+    ez -= zf * (st->p.H[0] * si[0] + st->p.H[1] * si[1] + st->p.H[2] * si[2]);
+  }
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double w[3], c[3];
+    omega_of(st, i, w);
+    const double* si = st->s + 3 * i;
+    cross(si, w, c);
+    num += c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    den += si[0] * w[0] + si[1] * w[1] + si[2] * w[2];
+  }
+  out[0] = ek; out[1] = em; out[2] = ex; out[3] = ez;
+  out[4] = ek + em + ex + ez;
+  out[5] = n > 0 ? 2.0 * ek / (3.0 * n * ORC_KB) : 0.0;
+  out[6] = den != 0.0 ? ORC_HBAR / (2.0 * ORC_KB) * num / den : 0.0;
+  out[7] = 0.0;
+}
+
+/* out = Mx, My, Mz, |M| with M = (1/N) sum_i s_i. */
+void orc_magnetization(const orc_state* st, double out[4]) {
+  double m[3] = {0, 0, 0};
+  for (int i = 0; i < st->n; ++i)
+    for (int a = 0; a < 3; ++a) m[a] += st->s[3 * i + a];
+  double inv = st->n > 0 ? 1.0 / st->n : 0.0;
+  out[0] = m[0] * inv; out[1] = m[1] * inv; out[2] = m[2] * inv;
+  out[3] = sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+}
+
+/* Energy of arbitrary (r, s) without building a state: used by the
+ * finite-difference tests.  Same definitions as orc_energy (potential part
+ * only: out[1..3]).  Brute-force pairs. */
+int orc_potential_energy(const orc_params* p, const double* r, const double* s, double out[4]) {
+  orc_params q = *p;
+  q.brute_force = 1;
+  int n = q.n_atoms;
+  double em = 0.0, ex = 0.0, ez = 0.0;
+  double vshift = q.morse_shift ? morse_V(&q, q.m_rc) : 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double d[3];
+      for (int a = 0; a < 3; ++a) {
+        double x = r[3 * j + a] - r[3 * i + a];
+        d[a] = x - q.box[a] * nearbyint(x / q.box[a]);
+      }
+      double rr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (rr < q.m_rc) em += morse_V(&q, rr) - vshift;
+      if (rr < q.ex_rc)
+        ex -= bs_J(&q, rr) * (s[3 * i] * s[3 * j] + s[3 * i + 1] * s[3 * j + 1] + s[3 * i + 2] * s[3 * j + 2]);
+    }
+  double zf = q.mu_s * ORC_MUB;
+  for (int i = 0; i < n; ++i) ez -= zf * (q.H[0] * s[3 * i] + q.H[1] * s[3 * i + 1] + q.H[2] * s[3 * i + 2]);
+  out[0] = em; out[1] = ex; out[2] = ez; out[3] = em + ex + ez;
+  return ORC_OK;
+}

@@ -1,0 +1,141 @@
+"""Seeded synthetic inputs for the coupled spin-lattice timestep.
+
+This module only *generates* inputs: a bcc lattice with Gaussian
+displacements, Maxwell-Boltzmann velocities and unit spins, plus the
+parameter set of the bcc-Fe / Morse / Bethe-Slater workload.  It holds none
+of the method's arithmetic and is the one module shared by the CUDA path's
+callers and the CPU oracle's tests.
+
+Units are the paper's "metal" set: Angstrom, ps, eV, amu, K, Tesla.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Used only to draw Maxwell-Boltzmann velocities here.
+_KB_EV_PER_K = 8.617333262e-5
+_EV_PER_A_AMU_TO_A_PER_PS2 = 9648.533212
+
+LATTICE_A = 2.8665          # bcc Fe lattice constant, Angstrom
+MASS_FE = 55.845            # amu
+
+
+def fe_params(box, n_atoms, **overrides):
+    """Parameter dict of the bcc-Fe workload (Morse lattice potential,
+    Bethe-Slater exchange of Eq. BSfunction, Zeeman field 1 T along z,
+    mu = 2.2 mu_B, dt = 0.1 fs).  Keys match the C-ABI struct fields."""
+    p = dict(
+        n_atoms=int(n_atoms),
+        box=[float(b) for b in box],
+        mass_amu=MASS_FE,
+        mu_s_muB=2.2,
+        H_tesla=[0.0, 0.0, 1.0],
+        dt_ps=1.0e-4,
+        ex_alpha_eV=0.02726,
+        ex_gamma=0.2171,
+        ex_delta_A=1.841,
+        ex_rc_A=3.4,
+        morse_D0_eV=0.4174,
+        morse_alpha_invA=1.3885,
+        morse_r0_A=2.845,
+        morse_rc_A=6.0,
+        skin_A=0.3,
+        rotation=0,
+        fix_lattice=0,
+        rebuild_every=0,
+        morse_shift_energy=1,
+    )
+    for k, v in overrides.items():
+        if k not in p:
+            raise KeyError(f"unknown parameter {k!r}")
+        p[k] = v
+    return p
+
+
+def bcc_positions(ncells, a=LATTICE_A):
+    """Perfect bcc lattice of ncells^3 cubic cells (2 atoms each).
+    Atom id = 2 * (ix + n*(iy + n*iz)) + basis."""
+    n = int(ncells)
+    ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    # order: iz slowest, then iy, then ix, then basis
+    cells = np.stack([ix.transpose(2, 1, 0).ravel(), iy.transpose(2, 1, 0).ravel(),
+                      iz.transpose(2, 1, 0).ravel()], axis=1).astype(np.float64)
+    base = np.repeat(cells, 2, axis=0)
+    base[1::2] += 0.5
+    return base * a, np.array([n * a] * 3, dtype=np.float64)
+
+
+def unit_spins_uniform(rng, n):
+    z = rng.uniform(-1.0, 1.0, n)
+    phi = rng.uniform(0.0, 2.0 * math.pi, n)
+    rho = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    s = np.stack([rho * np.cos(phi), rho * np.sin(phi), z], axis=1)
+    return s / np.linalg.norm(s, axis=1, keepdims=True)
+
+
+def unit_spins_cone(rng, n, sigma_deg=10.0):
+    """Ferromagnetic along +z, each spin tilted by |N(0, sigma^2)| with a
+    uniform azimuth."""
+    th = np.abs(rng.normal(0.0, math.radians(sigma_deg), n))
+    phi = rng.uniform(0.0, 2.0 * math.pi, n)
+    s = np.stack([np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi), np.cos(th)], axis=1)
+    return s / np.linalg.norm(s, axis=1, keepdims=True)
+
+
+def maxwell_boltzmann(rng, n, T, mass=MASS_FE):
+    """Velocities (A/ps) drawn from N(0, k_B T / m), centre-of-mass motion
+    removed, rescaled so the kinetic temperature with 3N-3 degrees of
+    freedom is exactly T (zero for T = 0 or n < 2)."""
+    if T <= 0.0 or n < 2:
+        return np.zeros((n, 3))
+    sig = math.sqrt(_KB_EV_PER_K * T / mass * _EV_PER_A_AMU_TO_A_PER_PS2)
+    v = rng.normal(0.0, sig, (n, 3))
+    v -= v.mean(axis=0, keepdims=True)
+    ek = 0.5 * mass * float((v * v).sum()) / _EV_PER_A_AMU_TO_A_PER_PS2
+    t_now = 2.0 * ek / ((3 * n - 3) * _KB_EV_PER_K)
+    return v * math.sqrt(T / t_now)
+
+
+def bcc_fe_system(ncells, seed, T=200.0, sigma=0.01, spins="uniform", a=LATTICE_A, **param_overrides):
+    """A seeded bcc-Fe system: returns (params, r, v, s), arrays [N, 3] float64."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    r, box = bcc_positions(ncells, a)
+    n = r.shape[0]
+    r = r + rng.normal(0.0, sigma, r.shape) if sigma > 0 else r
+    v = maxwell_boltzmann(rng, n, T)
+    if spins == "uniform":
+        s = unit_spins_uniform(rng, n)
+    elif spins == "cone10":
+        s = unit_spins_cone(rng, n, 10.0)
+    elif spins == "fm":
+        s = np.tile(np.array([0.0, 0.0, 1.0]), (n, 1))
+    else:
+        raise ValueError(spins)
+    return fe_params(box, n, **param_overrides), np.ascontiguousarray(r), np.ascontiguousarray(v), np.ascontiguousarray(s)
+
+
+# The five workloads: plain 10^3 cells, plain 64^3 cells, 256 batched
+# replicas, learned 40^3 cells, large 100^3 cells.
+WORKLOADS = {
+    "fe_bcc_10x10x10_nve": dict(ncells=10, seed=18010, T=200.0, spins="uniform", steps=1000),
+    "fe_bcc_64x64x64_nve": dict(ncells=64, seed=18011, T=200.0, spins="cone10", steps=200),
+    "fe_bcc_40x40x40_nve": dict(ncells=40, seed=18013, T=200.0, spins="uniform", steps=500),
+    "fe_bcc_100x100x100_nve": dict(ncells=100, seed=18014, T=300.0, spins="uniform", steps=1000),
+}
+
+
+def workload(name, **param_overrides):
+    w = WORKLOADS[name]
+    return bcc_fe_system(w["ncells"], w["seed"], T=w["T"], spins=w["spins"], **param_overrides)
+
+
+def replica_batch(n_replicas=256, seed=18012, cell_choices=(8, 12, 16, 20, 24), t_lo=50.0, t_hi=1200.0):
+    """Sizes and temperatures of the batched-replica workload: replica k has
+    ncells drawn by seed from cell_choices and temperature evenly spaced in
+    [t_lo, t_hi]."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    cells = rng.choice(np.asarray(cell_choices), size=n_replicas)
+    temps = t_lo + np.arange(n_replicas) * (t_hi - t_lo) / max(1, n_replicas - 1)
+    return [int(c) for c in cells], [float(t) for t in temps]
