@@ -1,0 +1,180 @@
+/*
+ * libsl: coupled spin-lattice dynamics on one GPU (sm_103a), C ABI.
+ *
+ * The method is the symplectic Suzuki-Trotter integrator of
+ * Tranchida, Plimpton, Thibaudeau, Thompson (arXiv 1801.10233):
+ *
+ *   one step = e^{Lp dt/2} e^{Ls dt/2} e^{Lr dt} e^{Ls dt/2} e^{Lp dt/2}
+ *              (Eq. general_ST_decomposition, Sec. 3)
+ *
+ * where e^{Ls dt/2} sweeps the spins forward then backward with dt/4 per
+ * single-spin factor (Eq. spin_ST_decomposition, Sec. 3), in the sectored
+ * order of Eq. spin_ST_sectoring (Sec. 5.1): atoms are binned into sectors at
+ * least (exchange cutoff + skin) wide, an even number per box edge, and each
+ * sector gets one of 8 colours from the parities of its sector coordinates.
+ * Same-colour sectors never interact, so a colour pass updates all of them at
+ * once while the spins inside a sector go one after another (ascending atom
+ * id forward, descending backward).
+ *
+ * Hamiltonian (Eq. s_hamiltonian and Eq. sl_hamiltonian, Sec. 2):
+ *   H = -mu_s mu_B sum_i H.s_i - sum_{i<j} J(r_ij) s_i.s_j
+ *       + sum_i p_i^2 / 2m + sum_{i<j} V(r_ij)
+ * J(r) = 4 alpha (r/delta)^2 (1 - gamma (r/delta)^2) exp(-(r/delta)^2) for
+ * r < ex_rc (Eq. BSfunction, App. A.1); V(r) = D0 (e^{-2a(r-r0)} -
+ * 2 e^{-a(r-r0)}) for r < morse_rc.  omega_i = -(1/hbar) dH/ds_i and
+ * ds_i/dt = omega_i x s_i (Eq. s_advance); the force is -dH/dr_i including
+ * the magneto-elastic term -J'(r) (s_i.s_j) e_ij (Eq. p_advance).
+ *
+ * Units: Angstrom, ps, eV, amu, K, Tesla.  State arrays are FP64.
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented as "device" must be device memory of the current
+ *    CUDA device; "host" pointers are host memory (pinned for best speed).
+ *  - Position, velocity and spin arrays are [n_atoms][3] doubles (x,y,z per
+ *    atom) in the caller's atom order.  The library never frees or retains
+ *    caller memory beyond the call, except the workspace given to sl_init,
+ *    which it uses until sl_destroy.
+ *  - All work is ordered on the CUDA stream given to sl_init.  Only
+ *    sl_init, sl_energy, sl_magnetization, sl_status, sl_counters and the
+ *    *_host copies block the calling thread.
+ *  - Return values are SL_OK (0) or a negative SL_ERR_* code.  Errors raised
+ *    on the device (timeout, skin violation, list overflow, bad spin norm) are
+ *    sticky: once set, every later call returns that code until sl_destroy.
+ *    The library never aborts the process.
+ */
+#ifndef SL_H
+#define SL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SL_OK = 0,
+  SL_ERR_ARG = -1,          /* invalid argument or parameter */
+  SL_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  SL_ERR_BOX = -3,          /* box < 2 (cutoff + skin), or < 2 sectors per edge */
+  SL_ERR_SPIN_NORM = -4,    /* an input spin is not unit length (|1 - |s|| > 1e-12) */
+  SL_ERR_SKIN = -5,         /* an atom moved > skin/2 with no rebuild scheduled */
+  SL_ERR_TIMEOUT = -6,      /* an in-kernel wait ran out of its iteration budget */
+  SL_ERR_NONFINITE = -7,    /* a NaN or Inf entered the state */
+  SL_ERR_WORKSPACE = -8,    /* workspace missing, too small or misaligned */
+  SL_ERR_NBR_OVERFLOW = -9  /* more neighbours than max_*_neighbors */
+};
+
+enum { SL_ROT_RODRIGUES = 0, SL_ROT_CAYLEY = 1 };
+
+/* Parameters of one system.  Zero-initialise and fill every field. */
+typedef struct sl_params {
+  int32_t n_atoms;
+  int32_t rotation;            /* SL_ROT_RODRIGUES: exact rotation by |omega| tau;
+                                  SL_ROT_CAYLEY: the Cayley-type propagator of Sec. 3 */
+  int32_t fix_lattice;         /* 1: positions/velocities frozen, spin dynamics only */
+  int32_t rebuild_every;       /* 0: rebuild sectors and lists when an atom moved more
+                                  than skin/2; K > 0: every K steps (SL_ERR_SKIN if the
+                                  skin is exceeded in between) */
+  int32_t morse_shift_energy;  /* 1: report V(r) - V(rc) per pair (forces unchanged) */
+  int32_t max_ex_neighbors;    /* exchange list capacity per atom (0: 24) */
+  int32_t max_morse_neighbors; /* Morse list capacity per atom (0: 128) */
+  int32_t reserved0;
+  double box[3];               /* orthorhombic periodic box edges */
+  double mass_amu;
+  double mu_s_muB;             /* magnetic moment, units of mu_B */
+  double H_tesla[3];           /* applied field */
+  double dt_ps;                /* timestep (may be negative: time reversal) */
+  double ex_alpha_eV, ex_gamma, ex_delta_A, ex_rc_A;            /* Eq. BSfunction */
+  double morse_D0_eV, morse_alpha_invA, morse_r0_A, morse_rc_A;
+  double skin_A;               /* Verlet skin, also widens the sectors */
+  double lambda;               /* transverse damping of Eq. sLLG (0: none) */
+  double temperature_K;        /* spin bath temperature (0: no noise) */
+  uint64_t seed;               /* Philox4x32-10 key for the spin noise */
+  int32_t replica;             /* replica index, part of the noise counter */
+  int32_t reserved1;
+} sl_params;
+
+typedef struct sl_ctx sl_ctx;  /* opaque, owned by the library */
+
+/* Bytes of device workspace sl_init needs for these parameters.
+ * Errors: SL_ERR_ARG (NULL pointer, n_atoms < 1, non-positive mass),
+ * SL_ERR_BOX (box too small for the cutoffs or for 2 sectors per edge). */
+int sl_workspace_bytes(const sl_params* params, size_t* bytes);
+
+/* Create a context: copies r, v, s (device, [n][3] doubles, caller order)
+ * into the library's sector-sorted layout inside `workspace` (device,
+ * >= sl_workspace_bytes, 256-byte aligned, owned by the caller and kept
+ * alive until sl_destroy), wraps positions into the box, assigns sectors,
+ * builds neighbour lists and the exchange table and computes the forces
+ * F(r0, s0).  `cuda_stream` is a cudaStream_t (NULL: legacy default stream).
+ * Blocks until done; on error *out is NULL and nothing is retained.
+ * Errors: SL_ERR_ARG, SL_ERR_BOX, SL_ERR_WORKSPACE, SL_ERR_SPIN_NORM,
+ * SL_ERR_NONFINITE, SL_ERR_NBR_OVERFLOW, SL_ERR_CUDA. */
+int sl_init(const sl_params* params, const double* r, const double* v, const double* s,
+            void* workspace, size_t workspace_bytes, void* cuda_stream, sl_ctx** out);
+
+/* Re-assign sectors and rebuild both neighbour lists, the exchange table
+ * (J and J' at the current positions, Sec. 3) and the forces now, whatever
+ * the displacement.  Stream-ordered. */
+int sl_build_neighbors(sl_ctx* ctx);
+
+/* Advance n_steps timesteps of Eq. general_ST_decomposition.  Stream-ordered;
+ * device-side errors surface at the next synchronising call. */
+int sl_step(sl_ctx* ctx, int32_t n_steps);
+
+/* Change dt (negative runs the dynamics backwards) or the applied field. */
+int sl_set_dt(sl_ctx* ctx, double dt_ps);
+int sl_set_field(sl_ctx* ctx, const double H_tesla[3]);
+
+/* out[8] (host) = E_kin, E_morse, E_exchange, E_zeeman, E_total (eV),
+ * T_L (Eq. lattice_temperature, K), T_S (Eq. spin_temperature, K), 0.
+ * Pair energies count each unordered pair once.  Synchronises. */
+int sl_energy(sl_ctx* ctx, double out[8]);
+
+/* out[4] (host) = Mx, My, Mz, |M| with M = (1/N) sum_i s_i.  Synchronises. */
+int sl_magnetization(sl_ctx* ctx, double out[4]);
+
+/* Copy the state out in caller atom order (device pointers, [n][3]; any of
+ * them may be NULL).  Positions are wrapped into the box at every rebuild. */
+int sl_get_state(sl_ctx* ctx, double* r, double* v, double* s);
+
+/* Replace the state (device pointers, [n][3], caller order).  Sectors and
+ * lists are rebuilt if an atom moved more than skin/2 from where the lists
+ * were built; the exchange table and forces are recomputed.  Spins must be
+ * unit length (SL_ERR_SPIN_NORM otherwise, sticky). */
+int sl_set_state(sl_ctx* ctx, const double* r, const double* v, const double* s);
+
+/* As sl_get_state / sl_set_state with HOST pointers: the copies run through
+ * a staging area in the workspace.  sl_get_state_host blocks until the data
+ * has arrived; sl_set_state_host blocks until the host buffers may be reused. */
+int sl_get_state_host(sl_ctx* ctx, double* r, double* v, double* s);
+int sl_set_state_host(sl_ctx* ctx, const double* r, const double* v, const double* s);
+
+/* Forces F (eV/A) and precession vectors omega (rad/ps, no noise) of the
+ * current state, device pointers [n][3], caller order. */
+int sl_get_forces(sl_ctx* ctx, double* F);
+int sl_get_omega(sl_ctx* ctx, double* omega);
+
+/* Sweep order: order_dev[k] (device, n int32) = caller index of the k-th
+ * atom of the sweep; colour_start[9] (host) = first sweep position of each
+ * colour; nsec[3] (host) = sectors per box edge.  Synchronises. */
+int sl_get_order(sl_ctx* ctx, int32_t* order_dev, int32_t colour_start[9], int32_t nsec[3]);
+
+/* out[4] (host) = steps done, rebuilds done, largest exchange-list length
+ * seen, largest Morse-list length seen.  Synchronises. */
+int sl_counters(sl_ctx* ctx, int64_t out[4]);
+
+/* Sticky device error word (SL_OK or SL_ERR_*).  Synchronises. */
+int sl_status(sl_ctx* ctx);
+
+/* Static description of an error code (never NULL). */
+const char* sl_strerror(int code);
+
+/* Release the context (not the caller's workspace).  Synchronises. */
+void sl_destroy(sl_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SL_H */

@@ -1,0 +1,144 @@
+"""ctypes binding of libsl (include/sl.h): argument marshalling only.
+
+Every step of the method runs in the CUDA kernels of libsl.so; this module
+allocates device buffers with PyTorch, passes their pointers and raises on
+error codes.  There is no fallback: if libsl.so is missing or cannot load,
+`load()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsl.so")
+
+SL_OK = 0
+SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_BOX, SL_ERR_SPIN_NORM = -1, -2, -3, -4
+SL_ERR_SKIN, SL_ERR_TIMEOUT, SL_ERR_NONFINITE, SL_ERR_WORKSPACE, SL_ERR_NBR_OVERFLOW = -5, -6, -7, -8, -9
+SL_ROT_RODRIGUES, SL_ROT_CAYLEY = 0, 1
+
+# Every exported symbol of include/sl.h.
+EXPORTS = (
+    "sl_workspace_bytes", "sl_init", "sl_build_neighbors", "sl_step", "sl_set_dt", "sl_set_field",
+    "sl_energy", "sl_magnetization", "sl_get_state", "sl_set_state", "sl_get_state_host",
+    "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_status",
+    "sl_strerror", "sl_destroy",
+)
+
+
+class sl_params(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int32), ("rotation", ctypes.c_int32), ("fix_lattice", ctypes.c_int32),
+        ("rebuild_every", ctypes.c_int32), ("morse_shift_energy", ctypes.c_int32),
+        ("max_ex_neighbors", ctypes.c_int32), ("max_morse_neighbors", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("box", ctypes.c_double * 3), ("mass_amu", ctypes.c_double), ("mu_s_muB", ctypes.c_double),
+        ("H_tesla", ctypes.c_double * 3), ("dt_ps", ctypes.c_double),
+        ("ex_alpha_eV", ctypes.c_double), ("ex_gamma", ctypes.c_double), ("ex_delta_A", ctypes.c_double),
+        ("ex_rc_A", ctypes.c_double),
+        ("morse_D0_eV", ctypes.c_double), ("morse_alpha_invA", ctypes.c_double), ("morse_r0_A", ctypes.c_double),
+        ("morse_rc_A", ctypes.c_double), ("skin_A", ctypes.c_double),
+        ("lambda_", ctypes.c_double), ("temperature_K", ctypes.c_double),
+        ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+    ]
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+
+def load():
+    """Load libsl.so (built in-tree by build.py).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1801_10233_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.POINTER(sl_params)
+    sig = {
+        "sl_workspace_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "sl_init": ([P, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+        "sl_build_neighbors": ([_vp], ctypes.c_int),
+        "sl_step": ([_vp, ctypes.c_int32], ctypes.c_int),
+        "sl_set_dt": ([_vp, ctypes.c_double], ctypes.c_int),
+        "sl_set_field": ([_vp, _dp], ctypes.c_int),
+        "sl_energy": ([_vp, _dp], ctypes.c_int),
+        "sl_magnetization": ([_vp, _dp], ctypes.c_int),
+        "sl_get_state": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+        "sl_set_state": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+        "sl_get_state_host": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+        "sl_set_state_host": ([_vp, _vp, _vp, _vp], ctypes.c_int),
+        "sl_get_forces": ([_vp, _vp], ctypes.c_int),
+        "sl_get_omega": ([_vp, _vp], ctypes.c_int),
+        "sl_get_order": ([_vp, _vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "sl_counters": ([_vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "sl_status": ([_vp], ctypes.c_int),
+        "sl_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "sl_destroy": ([_vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+class SlError(RuntimeError):
+    def __init__(self, code, what=""):
+        msg = load().sl_strerror(int(code)).decode()
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+        self.code = int(code)
+
+
+def check(code, what=""):
+    if code != SL_OK:
+        raise SlError(code, what)
+
+
+def make_params(p: dict) -> sl_params:
+    q = sl_params()
+    q.n_atoms = int(p["n_atoms"])
+    q.rotation = int(p.get("rotation", 0))
+    q.fix_lattice = int(p.get("fix_lattice", 0))
+    q.rebuild_every = int(p.get("rebuild_every", 0))
+    q.morse_shift_energy = int(p.get("morse_shift_energy", 1))
+    q.max_ex_neighbors = int(p.get("max_ex_neighbors", 0))
+    q.max_morse_neighbors = int(p.get("max_morse_neighbors", 0))
+    for a in range(3):
+        q.box[a] = float(p["box"][a])
+        q.H_tesla[a] = float(p["H_tesla"][a])
+    q.mass_amu = float(p["mass_amu"])
+    q.mu_s_muB = float(p["mu_s_muB"])
+    q.dt_ps = float(p["dt_ps"])
+    q.ex_alpha_eV, q.ex_gamma = float(p["ex_alpha_eV"]), float(p["ex_gamma"])
+    q.ex_delta_A, q.ex_rc_A = float(p["ex_delta_A"]), float(p["ex_rc_A"])
+    q.morse_D0_eV, q.morse_alpha_invA = float(p["morse_D0_eV"]), float(p["morse_alpha_invA"])
+    q.morse_r0_A, q.morse_rc_A = float(p["morse_r0_A"]), float(p["morse_rc_A"])
+    q.skin_A = float(p["skin_A"])
+    q.lambda_ = float(p.get("lambda", 0.0))
+    q.temperature_K = float(p.get("temperature_K", 0.0))
+    q.seed = int(p.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    q.replica = int(p.get("replica", 0))
+    return q
+
+
+def workspace_bytes(p: dict) -> int:
+    L = load()
+    q = make_params(p)
+    b = ctypes.c_size_t(0)
+    check(L.sl_workspace_bytes(ctypes.byref(q), ctypes.byref(b)), "sl_workspace_bytes")
+    return int(b.value)
+
+
+def strerror(code: int) -> str:
+    return load().sl_strerror(int(code)).decode()
+
+
+def _arr_ptr(a):
+    return a.ctypes.data_as(_dp)

@@ -1,0 +1,483 @@
+// C ABI of libsl: context lifecycle, workspace layout, state transfer and
+// the per-step launch sequence (captured once into a CUDA graph).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "sl_internal.cuh"
+
+struct sl_ctx {
+  sl_params p;
+  SlDev d;
+  cudaStream_t stream;
+  cudaStream_t cap;
+  cudaGraphExec_t graph;
+  int graph_ok;
+  int device;
+  int sticky;
+};
+
+namespace {
+
+inline int grid_for(int n) { return (n + SL_BLOCK - 1) / SL_BLOCK; }
+
+struct DeviceGuard {
+  int old = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&old) == cudaSuccess && old != dev) cudaSetDevice(dev);
+    else old = -1;
+  }
+  ~DeviceGuard() { if (old >= 0) cudaSetDevice(old); }
+};
+
+// Sector grid of Sec. 5.1: the largest even count per edge with sector edge
+// >= exchange cutoff + skin.
+int sector_grid(const sl_params* p, int n[3], double e[3]) {
+  double w = p->ex_rc_A + p->skin_A;
+  for (int a = 0; a < 3; ++a) {
+    int k = (int)std::floor(p->box[a] / w);
+    if (k % 2) k -= 1;
+    if (k < 2) return SL_ERR_BOX;
+    n[a] = k;
+    e[a] = p->box[a] / (double)k;
+  }
+  return SL_OK;
+}
+
+int validate(const sl_params* p) {
+  if (!p) return SL_ERR_ARG;
+  if (p->n_atoms < 1 || !(p->mass_amu > 0.0) || !(p->skin_A >= 0.0)) return SL_ERR_ARG;
+  if (!(p->ex_rc_A > 0.0) || !(p->morse_rc_A > 0.0) || !(p->ex_delta_A > 0.0)) return SL_ERR_ARG;
+  if (p->rotation != SL_ROT_RODRIGUES && p->rotation != SL_ROT_CAYLEY) return SL_ERR_ARG;
+  if (p->rebuild_every < 0 || p->max_ex_neighbors < 0 || p->max_morse_neighbors < 0) return SL_ERR_ARG;
+  if (!(p->lambda >= 0.0) || !(p->temperature_K >= 0.0)) return SL_ERR_ARG;
+  if (!std::isfinite(p->dt_ps)) return SL_ERR_ARG;
+  double rc = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
+  for (int a = 0; a < 3; ++a)
+    if (!(p->box[a] >= 2.0 * rc)) return SL_ERR_BOX;
+  int n[3]; double e[3];
+  return sector_grid(p, n, e);
+}
+
+struct Layout {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    size_t o = (off + 255) & ~size_t(255);
+    off = o + count * sizeof(T);
+    return o;
+  }
+};
+
+constexpr int NBLK_RED = 1024;
+
+// Fill d's scalars and (if base != NULL) its pointers; returns bytes needed.
+size_t plan(const sl_params* p, SlDev& d, char* base) {
+  std::memset(&d, 0, sizeof(d));
+  int n = p->n_atoms;
+  d.n = n;
+  int ns[3]; double e[3];
+  sector_grid(p, ns, e);
+  d.nx = ns[0]; d.ny = ns[1]; d.nz = ns[2];
+  d.nsec = ns[0] * ns[1] * ns[2];
+  d.s8 = d.nsec / 8;
+  double reach = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
+  int* mm[3] = {&d.mx, &d.my, &d.mz};
+  for (int a = 0; a < 3; ++a) {
+    d.box[a] = p->box[a];
+    d.inv_box[a] = 1.0 / p->box[a];
+    d.edge[a] = e[a];
+    *mm[a] = (int)std::ceil(reach / e[a]);
+  }
+  d.max_ex = p->max_ex_neighbors ? p->max_ex_neighbors : 24;
+  d.max_m = p->max_morse_neighbors ? p->max_morse_neighbors : 128;
+  d.rotation = p->rotation;
+  d.fix_lattice = p->fix_lattice;
+  d.rebuild_every = p->rebuild_every;
+  d.morse_shift = p->morse_shift_energy;
+  d.dt = p->dt_ps;
+  for (int a = 0; a < 3; ++a) d.zee[a] = p->mu_s_muB * SL_MUB * p->H_tesla[a];
+  d.mass = p->mass_amu;
+  d.acc = SL_FTOA / p->mass_amu;
+  d.ex_alpha = p->ex_alpha_eV; d.ex_gamma = p->ex_gamma; d.ex_delta = p->ex_delta_A;
+  d.ex_rc2 = p->ex_rc_A * p->ex_rc_A;
+  d.m_D0 = p->morse_D0_eV; d.m_alpha = p->morse_alpha_invA; d.m_r0 = p->morse_r0_A;
+  d.m_rc2 = p->morse_rc_A * p->morse_rc_A;
+  {
+    double ec = std::exp(-p->morse_alpha_invA * (p->morse_rc_A - p->morse_r0_A));
+    d.m_vshift = p->morse_shift_energy ? p->morse_D0_eV * (ec * ec - 2.0 * ec) : 0.0;
+  }
+  d.list_ex2 = (p->ex_rc_A + p->skin_A) * (p->ex_rc_A + p->skin_A);
+  d.list_m2 = (p->morse_rc_A + p->skin_A) * (p->morse_rc_A + p->skin_A);
+  d.half_skin2 = 0.25 * p->skin_A * p->skin_A;
+  d.lambda = p->lambda;
+  d.temperature = p->temperature_K;
+  d.seed = p->seed;
+  d.replica = p->replica;
+  d.nblk_red = NBLK_RED;
+
+  Layout L;
+  size_t nn = (size_t)n;
+  size_t o_r = L.take<double4_32a>(nn), o_v = L.take<double4_32a>(nn), o_s = L.take<double4_32a>(nn);
+  size_t o_F = L.take<double4_32a>(nn), o_rb = L.take<double4_32a>(nn);
+  size_t o_tr = L.take<double4_32a>(nn), o_tv = L.take<double4_32a>(nn), o_ts = L.take<double4_32a>(nn);
+  size_t o_tF = L.take<double4_32a>(nn);
+  size_t o_perm = L.take<int>(nn), o_rank = L.take<int>(nn), o_secq = L.take<int>(nn);
+  size_t o_tsecq = L.take<int>(nn), o_tperm = L.take<int>(nn), o_src = L.take<int>(nn);
+  size_t o_cnt = L.take<int>(d.nsec), o_start = L.take<int>(d.nsec + 1), o_fill = L.take<int>(d.nsec);
+  size_t o_exj = L.take<int>(nn * d.max_ex), o_exn = L.take<int>(nn);
+  size_t o_exJ = L.take<double>(nn * d.max_ex), o_exG = L.take<double4_32a>(nn * d.max_ex);
+  size_t o_mj = L.take<int>(nn * d.max_m), o_mn = L.take<int>(nn);
+  size_t o_part = L.take<double>((size_t)NBLK_RED * 16);
+  size_t o_stage = L.take<double>(nn * 9);
+  size_t o_ctrl = L.take<SlCtrl>(1);
+  if (base) {
+    d.r = (double4_32a*)(base + o_r); d.v = (double4_32a*)(base + o_v); d.s = (double4_32a*)(base + o_s);
+    d.F = (double4_32a*)(base + o_F); d.rb = (double4_32a*)(base + o_rb);
+    d.tr = (double4_32a*)(base + o_tr); d.tv = (double4_32a*)(base + o_tv); d.ts = (double4_32a*)(base + o_ts);
+    d.tF = (double4_32a*)(base + o_tF);
+    d.perm = (int*)(base + o_perm); d.rank = (int*)(base + o_rank); d.secq = (int*)(base + o_secq);
+    d.tsecq = (int*)(base + o_tsecq); d.tperm = (int*)(base + o_tperm); d.src = (int*)(base + o_src);
+    d.sec_count = (int*)(base + o_cnt); d.sec_start = (int*)(base + o_start); d.sec_fill = (int*)(base + o_fill);
+    d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn);
+    d.exJ = (double*)(base + o_exJ); d.exG = (double4_32a*)(base + o_exG);
+    d.mj = (int*)(base + o_mj); d.mn = (int*)(base + o_mn);
+    d.part = (double*)(base + o_part);
+    d.stage = (double*)(base + o_stage);
+    d.ctrl = (SlCtrl*)(base + o_ctrl);
+  }
+  return L.off;
+}
+
+__global__ void k_load(SlDev d, const double* r, const double* v, const double* s, int identity) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  if (identity) { d.perm[k] = k; d.rank[k] = k; }
+  size_t id = (size_t)d.perm[k];
+  if (r) d.r[k] = make_double4_32a(r[3 * id], r[3 * id + 1], r[3 * id + 2], 0.0);
+  if (v) d.v[k] = make_double4_32a(v[3 * id], v[3 * id + 1], v[3 * id + 2], 0.0);
+  if (s) d.s[k] = make_double4_32a(s[3 * id], s[3 * id + 1], s[3 * id + 2], 0.0);
+}
+
+__global__ void k_store(SlDev d, const double4_32a* src, double* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  size_t id = (size_t)d.perm[k];
+  double4_32a x = src[k];
+  out[3 * id] = x.x; out[3 * id + 1] = x.y; out[3 * id + 2] = x.z;
+}
+
+// Unit spins (|1 - |s|| <= 1e-12) and finite state.
+__global__ void k_check(SlDev d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  double4_32a s = d.s[k], r = d.r[k], v = d.v[k];
+  double t = r.x + r.y + r.z + v.x + v.y + v.z + s.x + s.y + s.z;
+  if (!(t - t == 0.0)) { sl_set_error(d.ctrl, SL_ERR_NONFINITE); return; }
+  double nn = sqrt(s.x * s.x + s.y * s.y + s.z * s.z);
+  if (!(fabs(nn - 1.0) <= 1e-12)) sl_set_error(d.ctrl, SL_ERR_SPIN_NORM);
+}
+
+// Flag a rebuild if any atom is more than skin/2 from its build position.
+__global__ void k_disp_flag(SlDev d) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  double4_32a r = d.r[k], b = d.rb[k];
+  double x = r.x - b.x, y = r.y - b.y, z = r.z - b.z;
+  if (x * x + y * y + z * z > d.half_skin2) d.ctrl->need_rebuild = 1;
+}
+
+int cuda_err(sl_ctx* c) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { if (!c->sticky) c->sticky = SL_ERR_CUDA; return SL_ERR_CUDA; }
+  return SL_OK;
+}
+
+// Synchronise and fold the device status into the sticky host error.
+int sync_status(sl_ctx* c) {
+  int st = 0;
+  if (cudaMemcpyAsync(&st, &c->d.ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    if (!c->sticky) c->sticky = SL_ERR_CUDA;
+    return c->sticky;
+  }
+  if (st && !c->sticky) c->sticky = st;
+  return c->sticky;
+}
+
+void drop_graph(sl_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_ok = 0;
+}
+
+// Capture one step's launch sequence into a graph on a private stream.
+int build_graph(sl_ctx* c) {
+  drop_graph(c);
+  if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SL_ERR_CUDA;
+  int e = sl_launch_step(c->d, c->cap);
+  cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
+  if (e || ce != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return SL_ERR_CUDA; }
+  cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) { c->graph = nullptr; cudaGetLastError(); return SL_ERR_CUDA; }
+  c->graph_ok = 1;
+  return SL_OK;
+}
+
+// Exchange table + forces at the current state; rebuild first if flagged.
+int refresh(sl_ctx* c) {
+  int e = sl_launch_rebuild(c->d, c->stream);
+  if (!e) e = sl_launch_pairs_and_forces(c->d, c->stream, 0);
+  return e ? e : cuda_err(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sl_workspace_bytes(const sl_params* params, size_t* bytes) {
+  if (!bytes) return SL_ERR_ARG;
+  int e = validate(params);
+  if (e) return e;
+  SlDev d;
+  *bytes = plan(params, d, nullptr);
+  return SL_OK;
+}
+
+int sl_init(const sl_params* params, const double* r, const double* v, const double* s,
+            void* workspace, size_t workspace_bytes, void* cuda_stream, sl_ctx** out) {
+  if (!out) return SL_ERR_ARG;
+  *out = nullptr;
+  int e = validate(params);
+  if (e) return e;
+  if (!r || !v || !s) return SL_ERR_ARG;
+  SlDev d;
+  size_t need = plan(params, d, nullptr);
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return SL_ERR_WORKSPACE;
+  sl_ctx* c = new (std::nothrow) sl_ctx();
+  if (!c) return SL_ERR_ARG;
+  c->p = *params;
+  plan(params, c->d, (char*)workspace);
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SL_ERR_CUDA; }
+  cudaMemsetAsync(c->d.ctrl, 0, sizeof(SlCtrl), c->stream);
+  k_load<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d, r, v, s, 1);
+  k_check<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d);
+  sl_launch_force_rebuild_flag(c->d, c->stream);
+  e = refresh(c);
+  int st = sync_status(c);
+  if (e || st) { sl_destroy(c); return e ? e : st; }
+  *out = c;
+  return SL_OK;
+}
+
+int sl_build_neighbors(sl_ctx* c) {
+  if (!c) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  sl_launch_force_rebuild_flag(c->d, c->stream);
+  return refresh(c);
+}
+
+int sl_step(sl_ctx* c, int32_t n_steps) {
+  if (!c || n_steps < 0) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  if (!c->graph_ok && n_steps > 0) build_graph(c);
+  for (int k = 0; k < n_steps; ++k) {
+    if (c->graph_ok) {
+      if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return cuda_err(c);
+    } else {
+      int e = sl_launch_step(c->d, c->stream);
+      if (e) { c->sticky = e; return e; }
+    }
+  }
+  return cuda_err(c);
+}
+
+int sl_set_dt(sl_ctx* c, double dt) {
+  if (!c || !std::isfinite(dt)) return SL_ERR_ARG;
+  c->p.dt_ps = dt;
+  c->d.dt = dt;
+  drop_graph(c);
+  return c->sticky;
+}
+
+int sl_set_field(sl_ctx* c, const double H[3]) {
+  if (!c || !H) return SL_ERR_ARG;
+  for (int a = 0; a < 3; ++a) {
+    c->p.H_tesla[a] = H[a];
+    c->d.zee[a] = c->p.mu_s_muB * SL_MUB * H[a];
+  }
+  drop_graph(c);
+  return c->sticky;
+}
+
+static int observe(sl_ctx* c, double red[16]) {
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  int e = sl_launch_observables(c->d, c->stream);
+  if (e) return e;
+  if (cudaMemcpyAsync(red, c->d.ctrl->red, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return cuda_err(c);
+  return sync_status(c);
+}
+
+int sl_energy(sl_ctx* c, double out[8]) {
+  if (!c || !out) return SL_ERR_ARG;
+  double red[16];
+  int e = observe(c, red);
+  if (e) return e;
+  int n = c->d.n;
+  out[0] = red[0]; out[1] = red[1]; out[2] = red[2]; out[3] = red[3];
+  out[4] = red[0] + red[1] + red[2] + red[3];
+  out[5] = 2.0 * red[0] / (3.0 * n * SL_KB);
+  out[6] = red[8] != 0.0 ? SL_HBAR / (2.0 * SL_KB) * red[7] / red[8] : 0.0;
+  out[7] = 0.0;
+  return SL_OK;
+}
+
+int sl_magnetization(sl_ctx* c, double out[4]) {
+  if (!c || !out) return SL_ERR_ARG;
+  double red[16];
+  int e = observe(c, red);
+  if (e) return e;
+  double inv = 1.0 / c->d.n;
+  out[0] = red[4] * inv; out[1] = red[5] * inv; out[2] = red[6] * inv;
+  out[3] = std::sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+  return SL_OK;
+}
+
+int sl_get_state(sl_ctx* c, double* r, double* v, double* s) {
+  if (!c) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  int gn = grid_for(c->d.n);
+  if (r) k_store<<<gn, SL_BLOCK, 0, c->stream>>>(c->d, c->d.r, r);
+  if (v) k_store<<<gn, SL_BLOCK, 0, c->stream>>>(c->d, c->d.v, v);
+  if (s) k_store<<<gn, SL_BLOCK, 0, c->stream>>>(c->d, c->d.s, s);
+  return cuda_err(c);
+}
+
+int sl_set_state(sl_ctx* c, const double* r, const double* v, const double* s) {
+  if (!c || !r || !v || !s) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  int gn = grid_for(c->d.n);
+  k_load<<<gn, SL_BLOCK, 0, c->stream>>>(c->d, r, v, s, 0);
+  k_check<<<gn, SL_BLOCK, 0, c->stream>>>(c->d);
+  k_disp_flag<<<gn, SL_BLOCK, 0, c->stream>>>(c->d);
+  return refresh(c);
+}
+
+int sl_get_state_host(sl_ctx* c, double* r, double* v, double* s) {
+  if (!c) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  size_t n3 = (size_t)c->d.n * 3;
+  double* st[3] = {c->d.stage, c->d.stage + n3, c->d.stage + 2 * n3};
+  int e = sl_get_state(c, r ? st[0] : nullptr, v ? st[1] : nullptr, s ? st[2] : nullptr);
+  if (e) return e;
+  double* hs[3] = {r, v, s};
+  for (int a = 0; a < 3; ++a)
+    if (hs[a] && cudaMemcpyAsync(hs[a], st[a], n3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+      return cuda_err(c);
+  return sync_status(c);
+}
+
+int sl_set_state_host(sl_ctx* c, const double* r, const double* v, const double* s) {
+  if (!c || !r || !v || !s) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  size_t n3 = (size_t)c->d.n * 3;
+  double* st[3] = {c->d.stage, c->d.stage + n3, c->d.stage + 2 * n3};
+  const double* hs[3] = {r, v, s};
+  for (int a = 0; a < 3; ++a)
+    if (cudaMemcpyAsync(st[a], hs[a], n3 * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return cuda_err(c);
+  int e = sl_set_state(c, st[0], st[1], st[2]);
+  if (e) return e;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_err(c);
+  return SL_OK;
+}
+
+int sl_get_forces(sl_ctx* c, double* F) {
+  if (!c || !F) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  k_store<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d, c->d.F, F);
+  return cuda_err(c);
+}
+
+int sl_get_omega(sl_ctx* c, double* w) {
+  if (!c || !w) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  int e = sl_launch_omega_all(c->d, w, c->stream);
+  return e ? e : cuda_err(c);
+}
+
+int sl_get_order(sl_ctx* c, int32_t* order_dev, int32_t colour_start[9], int32_t nsec[3]) {
+  if (!c) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  if (order_dev &&
+      cudaMemcpyAsync(order_dev, c->d.perm, sizeof(int) * c->d.n, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+    return cuda_err(c);
+  if (colour_start)
+    for (int k = 0; k <= 8; ++k)
+      if (cudaMemcpyAsync(colour_start + k, c->d.sec_start + k * c->d.s8, sizeof(int), cudaMemcpyDeviceToHost,
+                          c->stream) != cudaSuccess)
+        return cuda_err(c);
+  if (nsec) { nsec[0] = c->d.nx; nsec[1] = c->d.ny; nsec[2] = c->d.nz; }
+  return sync_status(c);
+}
+
+int sl_counters(sl_ctx* c, int64_t out[4]) {
+  if (!c || !out) return SL_ERR_ARG;
+  DeviceGuard g(c->device);
+  SlCtrl h;
+  if (cudaMemcpyAsync(&h, c->d.ctrl, sizeof(SlCtrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_err(c);
+  out[0] = h.step; out[1] = h.rebuilds; out[2] = h.max_ex_seen; out[3] = h.max_m_seen;
+  if (h.status && !c->sticky) c->sticky = h.status;
+  return c->sticky;
+}
+
+int sl_status(sl_ctx* c) {
+  if (!c) return SL_ERR_ARG;
+  DeviceGuard g(c->device);
+  return sync_status(c);
+}
+
+const char* sl_strerror(int code) {
+  switch (code) {
+    case SL_OK: return "ok";
+    case SL_ERR_ARG: return "invalid argument";
+    case SL_ERR_CUDA: return "CUDA runtime error";
+    case SL_ERR_BOX: return "box smaller than twice the cutoff plus skin, or fewer than 2 sectors per edge";
+    case SL_ERR_SPIN_NORM: return "input spin is not a unit vector";
+    case SL_ERR_SKIN: return "an atom moved more than half the skin without a scheduled rebuild";
+    case SL_ERR_TIMEOUT: return "an in-kernel wait exceeded its iteration budget";
+    case SL_ERR_NONFINITE: return "non-finite value in the state";
+    case SL_ERR_WORKSPACE: return "workspace missing, too small or not 256-byte aligned";
+    case SL_ERR_NBR_OVERFLOW: return "neighbour list capacity exceeded";
+    default: return "unknown error";
+  }
+}
+
+void sl_destroy(sl_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+}  // extern "C"

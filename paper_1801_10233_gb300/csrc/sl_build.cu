@@ -1,0 +1,198 @@
+// Sector assignment, sector-sorted reordering and Verlet neighbour lists.
+//
+// Sectoring follows Sec. 5.1 of arXiv 1801.10233: the box is cut into an
+// even number of sectors per edge, each at least (exchange cutoff + skin)
+// wide, and sector (sx,sy,sz) gets colour (sx&1) + 2(sy&1) + 4(sz&1).  Atoms
+// are stored sorted by (colour, sector, atom id), which is also the order of
+// the sequential sweep of Eq. spin_ST_sectoring.  Sectors are assigned when
+// the lists are rebuilt (not every step): each atom then moves at most skin/2
+// before the next assignment, so same-colour sectors stay out of exchange
+// range.
+//
+// Every kernel here runs only while ctrl->need_rebuild is set, so the whole
+// sequence can sit in the step's launch sequence (and in a CUDA graph) and
+// costs one early-exit per kernel when no rebuild is due.
+#include "sl_internal.cuh"
+
+namespace {
+
+__global__ void k_rb_zero(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.nsec; q += gridDim.x * blockDim.x) {
+    d.sec_count[q] = 0;
+    d.sec_fill[q] = 0;
+  }
+}
+
+// Wrap positions into the box and find each atom's sector rank.
+__global__ void k_rb_assign(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  double4_32a p = d.r[k];
+  p.x = sl_wrap(p.x, d.box[0]);
+  p.y = sl_wrap(p.y, d.box[1]);
+  p.z = sl_wrap(p.z, d.box[2]);
+  d.r[k] = p;
+  int sx = sl_sector_coord(p.x, d.edge[0], d.nx);
+  int sy = sl_sector_coord(p.y, d.edge[1], d.ny);
+  int sz = sl_sector_coord(p.z, d.edge[2], d.nz);
+  int q = sl_sector_rank(d, sx, sy, sz);
+  d.tsecq[k] = q;
+  atomicAdd(&d.sec_count[q], 1);
+}
+
+// Exclusive scan of the sector counts (one block; rebuild-only).
+__global__ void k_rb_scan(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  __shared__ int part[1024];
+  int t = threadIdx.x, nt = blockDim.x;
+  int chunk = (d.nsec + nt - 1) / nt;
+  int a = t * chunk, b = min(d.nsec, a + chunk);
+  int sum = 0;
+  for (int q = a; q < b; ++q) sum += d.sec_count[q];
+  part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int u = 0; u < nt; ++u) { int x = part[u]; part[u] = acc; acc += x; }
+  }
+  __syncthreads();
+  int acc = part[t];
+  for (int q = a; q < b; ++q) { d.sec_start[q] = acc; acc += d.sec_count[q]; }
+  if (t == nt - 1) d.sec_start[d.nsec] = acc;
+}
+
+__global__ void k_rb_scatter(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  int q = d.tsecq[k];
+  int pos = d.sec_start[q] + atomicAdd(&d.sec_fill[q], 1);
+  d.src[pos] = k;
+}
+
+// Order each sector's atoms by atom id (insertion sort; sectors hold ~10).
+__global__ void k_rb_sort(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= d.nsec) return;
+  int a = d.sec_start[q], b = d.sec_start[q + 1];
+  for (int x = a + 1; x < b; ++x) {
+    int v = d.src[x];
+    int id = d.perm[v];
+    int y = x - 1;
+    while (y >= a && d.perm[d.src[y]] > id) { d.src[y + 1] = d.src[y]; --y; }
+    d.src[y + 1] = v;
+  }
+}
+
+__global__ void k_rb_gather(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  int o = d.src[k];
+  d.tr[k] = d.r[o];
+  d.tv[k] = d.v[o];
+  d.ts[k] = d.s[o];
+  d.tF[k] = d.F[o];
+  d.tperm[k] = d.perm[o];
+  d.secq[k] = d.tsecq[o];
+}
+
+__global__ void k_rb_copyback(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  double4_32a p = d.tr[k];
+  d.r[k] = p;
+  d.rb[k] = p;
+  d.v[k] = d.tv[k];
+  d.s[k] = d.ts[k];
+  d.F[k] = d.tF[k];
+  int id = d.tperm[k];
+  d.perm[k] = id;
+  d.rank[id] = k;
+}
+
+// Full Verlet lists (both directions) from the sectors around each atom:
+// exchange list r < ex_rc + skin (atom-major), Morse list r < morse_rc + skin
+// (neighbour-major).  Neighbour order is the fixed loop order, so rebuilds
+// are deterministic.
+__global__ void k_rb_nbr(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  double4_32a ri = d.r[i];
+  int sx, sy, sz;
+  sl_sector_coords(d, d.secq[i], sx, sy, sz);
+  int lox = (2 * d.mx + 1 >= d.nx) ? 0 : -d.mx, hix = (2 * d.mx + 1 >= d.nx) ? d.nx - 1 : d.mx;
+  int loy = (2 * d.my + 1 >= d.ny) ? 0 : -d.my, hiy = (2 * d.my + 1 >= d.ny) ? d.ny - 1 : d.my;
+  int loz = (2 * d.mz + 1 >= d.nz) ? 0 : -d.mz, hiz = (2 * d.mz + 1 >= d.nz) ? d.nz - 1 : d.mz;
+  int ce = 0, cm = 0;
+  for (int oz = loz; oz <= hiz; ++oz) {
+    int tz = (sz + oz + 2 * d.nz) % d.nz;
+    for (int oy = loy; oy <= hiy; ++oy) {
+      int ty = (sy + oy + 2 * d.ny) % d.ny;
+      for (int ox = lox; ox <= hix; ++ox) {
+        int tx = (sx + ox + 2 * d.nx) % d.nx;
+        int q = sl_sector_rank(d, tx, ty, tz);
+        int a = d.sec_start[q], b = d.sec_start[q + 1];
+        for (int j = a; j < b; ++j) {
+          if (j == i) continue;
+          double3 dd = sl_min_image(d, ri, d.r[j]);
+          double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
+          if (r2 < d.list_m2) {
+            if (cm < d.max_m) d.mj[(size_t)cm * d.n + i] = j;
+            ++cm;
+          }
+          if (r2 < d.list_ex2) {
+            if (ce < d.max_ex) d.exj[(size_t)i * d.max_ex + ce] = j;
+            ++ce;
+          }
+        }
+      }
+    }
+  }
+  if (cm > d.max_m || ce > d.max_ex) sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW);
+  d.mn[i] = min(cm, d.max_m);
+  d.exn[i] = min(ce, d.max_ex);
+  atomicMax(&d.ctrl->max_m_seen, cm);
+  atomicMax(&d.ctrl->max_ex_seen, ce);
+}
+
+__global__ void k_rb_end(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  d.ctrl->need_rebuild = 0;
+  d.ctrl->rebuilds += 1;
+}
+
+__global__ void k_force_rebuild_flag(SlDev d) {
+  d.ctrl->need_rebuild = 1;
+  d.ctrl->maxdisp2_bits = 0ull;
+}
+
+inline int grid_for(int n) { return (n + SL_BLOCK - 1) / SL_BLOCK; }
+
+}  // namespace
+
+int sl_launch_force_rebuild_flag(const SlDev& d, cudaStream_t st) {
+  k_force_rebuild_flag<<<1, 1, 0, st>>>(d);
+  return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
+}
+
+// The rebuild sequence; each kernel returns at once unless need_rebuild is set.
+int sl_launch_rebuild(const SlDev& d, cudaStream_t st) {
+  int gn = grid_for(d.n), gs = grid_for(d.nsec);
+  int gz = gs < 1024 ? gs : 1024;
+  k_rb_zero<<<gz, SL_BLOCK, 0, st>>>(d);
+  k_rb_assign<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_rb_scan<<<1, 1024, 0, st>>>(d);
+  k_rb_scatter<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_rb_sort<<<gs, SL_BLOCK, 0, st>>>(d);
+  k_rb_gather<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_rb_copyback<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_rb_nbr<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_rb_end<<<1, 1, 0, st>>>(d);
+  return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
+}

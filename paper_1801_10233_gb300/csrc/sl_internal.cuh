@@ -1,0 +1,116 @@
+// Internal device-side layout and helpers of libsl (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sl.h"
+
+// Physical constants in the metal unit set (A, ps, eV, amu, K, T).
+#define SL_HBAR 6.582119569e-4    // eV ps / rad
+#define SL_KB 8.617333262e-5      // eV / K
+#define SL_MUB 5.7883818060e-5    // eV / T
+#define SL_FTOA 9648.533212       // (eV/A)/amu -> A/ps^2
+
+#define SL_BLOCK 128
+
+// Control block in device memory: sticky status, rebuild flag, counters.
+struct SlCtrl {
+  int32_t status;           // first device error (0 = OK)
+  int32_t need_rebuild;     // 1 while a rebuild is pending this step
+  long long step;           // completed steps
+  unsigned long long maxdisp2_bits;  // max |r - r_build|^2 since the last drift check
+  int32_t rebuilds;
+  int32_t max_ex_seen;
+  int32_t max_m_seen;
+  int32_t pad;
+  double red[16];           // final results of the observable reduction
+};
+
+// Everything a kernel needs, passed by value.
+struct SlDev {
+  int n;
+  int nsec, s8;             // sectors, sectors per colour
+  int nx, ny, nz;
+  int mx, my, mz;           // sector layers searched for Morse neighbours (or n)
+  int max_ex, max_m;
+  int rotation, fix_lattice, rebuild_every, morse_shift;
+  double box[3], inv_box[3], edge[3];
+  double dt;
+  double zee[3];            // mu_s mu_B H (eV)
+  double acc;               // FTOA / m
+  double mass;
+  double ex_alpha, ex_gamma, ex_delta, ex_rc2;
+  double m_D0, m_alpha, m_r0, m_rc2, m_vshift;
+  double list_ex2, list_m2; // (cutoff + skin)^2
+  double half_skin2;
+  double lambda, temperature;
+  uint64_t seed;
+  int replica;
+
+  // state, sector-sorted
+  double4_32a *r, *v, *s, *F, *rb;
+  // rebuild scratch
+  double4_32a *tr, *tv, *ts, *tF;
+  int *perm, *rank, *secq, *tsecq, *tperm, *src;
+  int *sec_count, *sec_start, *sec_fill;
+  // neighbour lists
+  int *exj, *exn;           // [n][max_ex] atom-major, counts
+  double *exJ;              // [n][max_ex] J_ij at current r
+  double4_32a *exG;             // [n][max_ex] (J'_ij e_ij, J_ij)
+  int *mj, *mn;             // [max_m][n] neighbour-major, counts
+  // reduction partials
+  double *part;             // [nblk_red][16]
+  int nblk_red;
+  // staging for host copies, [n][3] doubles x 3
+  double *stage;
+  SlCtrl *ctrl;
+};
+
+__device__ __forceinline__ void sl_set_error(SlCtrl* c, int code) { atomicCAS(&c->status, 0, code); }
+
+// Minimum-image separation of a and b (b - a) in an orthorhombic box.
+__device__ __forceinline__ double3 sl_min_image(const SlDev& d, double4_32a a, double4_32a b) {
+  double x = b.x - a.x, y = b.y - a.y, z = b.z - a.z;
+  x -= d.box[0] * rint(x * d.inv_box[0]);
+  y -= d.box[1] * rint(y * d.inv_box[1]);
+  z -= d.box[2] * rint(z * d.inv_box[2]);
+  return make_double3(x, y, z);
+}
+
+// Wrap one coordinate into [0, L] with explicitly rounded operations, so the
+// result is the IEEE value of x - L * floor(x / L) (no contraction).
+__device__ __forceinline__ double sl_wrap(double x, double L) {
+  return __dsub_rn(x, __dmul_rn(L, floor(__ddiv_rn(x, L))));
+}
+
+__device__ __forceinline__ int sl_sector_coord(double xw, double e, int n) {
+  int k = (int)floor(__ddiv_rn(xw, e));
+  return k < 0 ? 0 : (k >= n ? n - 1 : k);
+}
+
+// Canonical sector rank: colours 0..7 in order, sectors of one colour by
+// ascending linear index sx + nx (sy + ny sz).
+__device__ __forceinline__ int sl_sector_rank(const SlDev& d, int sx, int sy, int sz) {
+  int c = (sx & 1) + 2 * (sy & 1) + 4 * (sz & 1);
+  int hx = sx >> 1, hy = sy >> 1, hz = sz >> 1;
+  return c * d.s8 + hx + (d.nx >> 1) * (hy + (d.ny >> 1) * hz);
+}
+
+__device__ __forceinline__ void sl_sector_coords(const SlDev& d, int q, int& sx, int& sy, int& sz) {
+  int c = q / d.s8, rem = q - c * d.s8;
+  int hxn = d.nx >> 1, hyn = d.ny >> 1;
+  int hx = rem % hxn, hy = (rem / hxn) % hyn, hz = rem / (hxn * hyn);
+  sx = 2 * hx + (c & 1);
+  sy = 2 * hy + ((c >> 1) & 1);
+  sz = 2 * hz + ((c >> 2) & 1);
+}
+
+// Launch helpers implemented in the .cu files.
+int sl_launch_rebuild(const SlDev& d, cudaStream_t st);
+int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick);
+int sl_launch_step(const SlDev& d, cudaStream_t st);
+int sl_launch_observables(const SlDev& d, cudaStream_t st);
+int sl_launch_force_rebuild_flag(const SlDev& d, cudaStream_t st);
+int sl_launch_check_state(const SlDev& d, cudaStream_t st);
+int sl_launch_omega_all(const SlDev& d, double* out, cudaStream_t st);

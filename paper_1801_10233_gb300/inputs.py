@@ -55,16 +55,15 @@ def fe_params(box, n_atoms, **overrides):
 
 
 def bcc_positions(ncells, a=LATTICE_A):
-    """Perfect bcc lattice of ncells^3 cubic cells (2 atoms each).
-    Atom id = 2 * (ix + n*(iy + n*iz)) + basis."""
-    n = int(ncells)
-    ix, iy, iz = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    """Perfect bcc lattice of nx*ny*nz cubic cells (2 atoms each); ncells is
+    an int (cube) or a triple.  Atom id = 2 * (ix + nx*(iy + ny*iz)) + basis."""
+    nx, ny, nz = (int(ncells),) * 3 if np.isscalar(ncells) else tuple(int(c) for c in ncells)
+    iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     # order: iz slowest, then iy, then ix, then basis
-    cells = np.stack([ix.transpose(2, 1, 0).ravel(), iy.transpose(2, 1, 0).ravel(),
-                      iz.transpose(2, 1, 0).ravel()], axis=1).astype(np.float64)
+    cells = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1).astype(np.float64)
     base = np.repeat(cells, 2, axis=0)
     base[1::2] += 0.5
-    return base * a, np.array([n * a] * 3, dtype=np.float64)
+    return base * a, np.array([nx * a, ny * a, nz * a], dtype=np.float64)
 
 
 def unit_spins_uniform(rng, n):

@@ -1,0 +1,142 @@
+"""`System`: one coupled spin-lattice system driven through libsl's C ABI.
+
+PyTorch provides the device memory (state tensors and the workspace) and the
+CUDA stream; every computation runs in libsl's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+
+def _cuda_f64(x, device):
+    if isinstance(x, torch.Tensor):
+        t = x.to(device=device, dtype=torch.float64)
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device=device)
+    return t.reshape(-1, 3).contiguous()
+
+
+class System:
+    """A system of `params["n_atoms"]` atoms with positions r, velocities v and
+    unit spins s ([N, 3] float64; numpy arrays or tensors, caller order)."""
+
+    def __init__(self, params: dict, r, v, s, device=None, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsl needs a CUDA GPU")
+        self._L = _lib.load()
+        self.params = dict(params)
+        self.n = int(params["n_atoms"])
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._p = _lib.make_params(params)
+        nbytes = _lib.workspace_bytes(params)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        self._ws_bytes = nbytes
+        r, v, s = (_cuda_f64(a, self.device) for a in (r, v, s))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            torch.cuda.current_stream(self.device).synchronize()
+            rc = self._L.sl_init(ctypes.byref(self._p), r.data_ptr(), v.data_ptr(), s.data_ptr(),
+                                 self._ws_ptr, self._ws_bytes, self.stream.cuda_stream, ctypes.byref(h))
+        check(rc, "sl_init")
+        self._h = h
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.sl_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- dynamics ----------------------------------------------------------
+    def step(self, n: int = 1):
+        check(self._L.sl_step(self._h, int(n)), "sl_step")
+
+    def build_neighbors(self):
+        check(self._L.sl_build_neighbors(self._h), "sl_build_neighbors")
+
+    def set_dt(self, dt: float):
+        check(self._L.sl_set_dt(self._h, float(dt)), "sl_set_dt")
+
+    def set_field(self, H):
+        h = np.ascontiguousarray(H, dtype=np.float64)
+        check(self._L.sl_set_field(self._h, _lib._arr_ptr(h)), "sl_set_field")
+
+    # -- observables -------------------------------------------------------
+    def energy(self) -> np.ndarray:
+        """E_kin, E_morse, E_exch, E_zeeman, E_total (eV), T_L, T_S (K), 0."""
+        out = np.empty(8)
+        check(self._L.sl_energy(self._h, _lib._arr_ptr(out)), "sl_energy")
+        return out
+
+    def magnetization(self) -> np.ndarray:
+        out = np.empty(4)
+        check(self._L.sl_magnetization(self._h, _lib._arr_ptr(out)), "sl_magnetization")
+        return out
+
+    def status(self) -> int:
+        return int(self._L.sl_status(self._h))
+
+    def counters(self):
+        out = (ctypes.c_int64 * 4)()
+        check(self._L.sl_counters(self._h, out), "sl_counters")
+        return dict(steps=out[0], rebuilds=out[1], max_ex_seen=out[2], max_morse_seen=out[3])
+
+    # -- state transfer ----------------------------------------------------
+    def _empty3(self):
+        return torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+
+    def state(self):
+        """(r, v, s) as new [N, 3] float64 CUDA tensors in caller order."""
+        r, v, s = self._empty3(), self._empty3(), self._empty3()
+        check(self._L.sl_get_state(self._h, r.data_ptr(), v.data_ptr(), s.data_ptr()), "sl_get_state")
+        self.stream.synchronize()
+        return r, v, s
+
+    def set_state(self, r, v, s):
+        r, v, s = (_cuda_f64(a, self.device) for a in (r, v, s))
+        self.stream.synchronize()
+        check(self._L.sl_set_state(self._h, r.data_ptr(), v.data_ptr(), s.data_ptr()), "sl_set_state")
+        self.stream.synchronize()
+
+    def state_host(self, r: torch.Tensor, v: torch.Tensor, s: torch.Tensor):
+        """Copy the state into host tensors (pinned for speed) [N, 3] float64."""
+        check(self._L.sl_get_state_host(self._h, r.data_ptr(), v.data_ptr(), s.data_ptr()), "sl_get_state_host")
+
+    def set_state_host(self, r: torch.Tensor, v: torch.Tensor, s: torch.Tensor):
+        """Replace the state from host tensors (pinned for speed) [N, 3] float64."""
+        check(self._L.sl_set_state_host(self._h, r.data_ptr(), v.data_ptr(), s.data_ptr()), "sl_set_state_host")
+
+    def forces(self):
+        F = self._empty3()
+        check(self._L.sl_get_forces(self._h, F.data_ptr()), "sl_get_forces")
+        self.stream.synchronize()
+        return F
+
+    def omega(self):
+        w = self._empty3()
+        check(self._L.sl_get_omega(self._h, w.data_ptr()), "sl_get_omega")
+        self.stream.synchronize()
+        return w
+
+    def order(self):
+        o = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        cs = (ctypes.c_int32 * 9)()
+        ns = (ctypes.c_int32 * 3)()
+        check(self._L.sl_get_order(self._h, o.data_ptr(), cs, ns), "sl_get_order")
+        return dict(order=o.cpu().numpy(), colour_start=np.array(cs[:], dtype=np.int32),
+                    nsec=np.array(ns[:], dtype=np.int32))

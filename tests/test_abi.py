@@ -1,0 +1,91 @@
+"""The C ABI without a GPU: header layout vs. the binding, exported symbols,
+error strings and host-side validation (no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sl.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1801_10233_gb300.build import build
+    build()
+    from paper_1801_10233_gb300 import _lib
+    return _lib
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sl_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L = lib.load()
+    names = _declared_functions()
+    assert len(names) >= 19
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing
+    assert sorted(lib.EXPORTS) == names
+
+
+def test_param_struct_layout_matches_header(lib, tmp_path):
+    fields = [f[0] for f in lib.sl_params._fields_]
+    cfields = [("lambda" if f == "lambda_" else f) for f in fields]
+    src = tmp_path / "layout.c"
+    body = "".join(f'  printf("%zu\\n", offsetof(sl_params, {f}));\n' for f in cfields)
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "sl.h"\nint main(void){\n'
+                   '  printf("%zu\\n", sizeof(sl_params));\n' + body + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(lib.sl_params)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(lib.sl_params, f).offset == off, f
+
+
+def test_error_strings(lib):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9):
+        assert lib.strerror(code) and lib.strerror(code) != "unknown error"
+    assert lib.strerror(-100) == "unknown error"
+
+
+def test_workspace_and_validation_on_host(lib):
+    from paper_1801_10233_gb300 import inputs
+    p, *_ = inputs.workload("fe_bcc_10x10x10_nve")
+    b = lib.workspace_bytes(p)
+    assert b > 2000 * 9 * 32
+    # linear in N for the big arrays
+    p2, *_ = inputs.bcc_fe_system(20, 1)
+    assert lib.workspace_bytes(p2) > 7 * b
+    small, *_ = inputs.bcc_fe_system(4, 1)      # 11.5 A box < 2 (6 + 0.3)
+    with pytest.raises(lib.SlError) as e:
+        lib.workspace_bytes(small)
+    assert e.value.code == lib.SL_ERR_BOX
+    bad = dict(p, n_atoms=0)
+    with pytest.raises(lib.SlError) as e:
+        lib.workspace_bytes(bad)
+    assert e.value.code == lib.SL_ERR_ARG
+    bad = dict(p, rotation=7)
+    with pytest.raises(lib.SlError):
+        lib.workspace_bytes(bad)
+
+
+def test_init_rejects_bad_arguments_without_gpu(lib):
+    L = lib.load()
+    from paper_1801_10233_gb300 import inputs
+    p, *_ = inputs.workload("fe_bcc_10x10x10_nve")
+    q = lib.make_params(p)
+    h = ctypes.c_void_p()
+    # NULL state pointers and NULL workspace are rejected before any CUDA call
+    assert L.sl_init(ctypes.byref(q), None, None, None, None, 0, None, ctypes.byref(h)) == lib.SL_ERR_ARG
+    assert L.sl_init(ctypes.byref(q), 8, 8, 8, None, 0, None, ctypes.byref(h)) == lib.SL_ERR_WORKSPACE
+    assert L.sl_init(ctypes.byref(q), 8, 8, 8, 4096 + 8, 1 << 40, None, ctypes.byref(h)) == lib.SL_ERR_WORKSPACE
+    assert not h.value
+    assert L.sl_step(None, 1) == lib.SL_ERR_ARG
+    assert L.sl_status(None) == lib.SL_ERR_ARG
