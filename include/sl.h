@@ -161,9 +161,21 @@ int sl_get_omega(sl_ctx* ctx, double* omega);
  * colour; nsec[3] (host) = sectors per box edge.  Synchronises. */
 int sl_get_order(sl_ctx* ctx, int32_t* order_dev, int32_t colour_start[9], int32_t nsec[3]);
 
-/* out[4] (host) = steps done, rebuilds done, largest exchange-list length
- * seen, largest Morse-list length seen.  Synchronises. */
-int sl_counters(sl_ctx* ctx, int64_t out[4]);
+/* out[8] (host) = steps done, rebuilds done, largest exchange-list length
+ * seen, largest Morse-list length seen, kernel launches per step, 1 if steps
+ * run as a captured CUDA graph, 0, 0.  Synchronises. */
+int sl_counters(sl_ctx* ctx, int64_t out[8]);
+
+/* Per-phase timing.  With enable = 1, sl_step launches each step's kernels
+ * directly (no graph) and records a CUDA event pair on the context's stream
+ * around each phase: 0 half-kick, 1 first spin half-op (16 colour passes),
+ * 2 drift + rebuild check (+ rebuild), 3 exchange table, 4 second spin
+ * half-op, 5 forces + closing half-kick.  sl_get_timing synchronises and
+ * returns ms[k] = total milliseconds and count[k] = timed launches of phase
+ * k since timing was enabled (entries 6, 7 are 0).  sl_set_timing resets
+ * the totals. */
+int sl_set_timing(sl_ctx* ctx, int32_t enable);
+int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
 
 /* Sticky device error word (SL_OK or SL_ERR_*).  Synchronises. */
 int sl_status(sl_ctx* ctx);

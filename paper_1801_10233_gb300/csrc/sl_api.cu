@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "sl_internal.cuh"
 
@@ -16,6 +17,14 @@ struct sl_ctx {
   int graph_ok;
   int device;
   int sticky;
+  int kernels_per_step;
+  // optional per-phase event timing
+  int timing;
+  std::vector<cudaEvent_t> ev_pool;      // events owned by the context
+  std::vector<int> ev_phase;             // phase of each recorded (begin, end) pair
+  size_t ev_used;
+  double phase_ms[SL_NPHASE];
+  long long phase_n[SL_NPHASE];
 };
 
 namespace {
@@ -218,13 +227,42 @@ int build_graph(sl_ctx* c) {
   if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SL_ERR_CUDA;
-  int e = sl_launch_step(c->d, c->cap);
+  int e = sl_launch_step(c->d, c->cap, nullptr, nullptr, &c->kernels_per_step);
   cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
   if (e || ce != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return SL_ERR_CUDA; }
   cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
   cudaGraphDestroy(g);
   if (ie != cudaSuccess) { c->graph = nullptr; cudaGetLastError(); return SL_ERR_CUDA; }
   c->graph_ok = 1;
+  return SL_OK;
+}
+
+// Record a timing event at a phase boundary (pool grows as needed).
+void mark_phase(void* user, int phase, int end) {
+  sl_ctx* c = (sl_ctx*)user;
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return;
+    c->ev_pool.push_back(ev);
+  }
+  cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+  if (!end) c->ev_phase.push_back(phase);
+  c->ev_used += 1;
+}
+
+// Fold recorded event pairs into the per-phase totals (synchronises).
+int fold_timing(sl_ctx* c) {
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SL_ERR_CUDA;
+  for (size_t k = 0; k + 1 < c->ev_used && k / 2 < c->ev_phase.size(); k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[k], c->ev_pool[k + 1]) == cudaSuccess) {
+      int ph = c->ev_phase[k / 2];
+      c->phase_ms[ph] += ms;
+      c->phase_n[ph] += 1;
+    }
+  }
+  c->ev_used = 0;
+  c->ev_phase.clear();
   return SL_OK;
 }
 
@@ -287,16 +325,45 @@ int sl_step(sl_ctx* c, int32_t n_steps) {
   if (!c || n_steps < 0) return SL_ERR_ARG;
   if (c->sticky) return c->sticky;
   DeviceGuard g(c->device);
+  if (c->timing) {
+    // direct launches with an event pair around each phase
+    for (int k = 0; k < n_steps; ++k) {
+      int e = sl_launch_step(c->d, c->stream, mark_phase, c, &c->kernels_per_step);
+      if (e) { c->sticky = e; return e; }
+      if (c->ev_used > 4096 && fold_timing(c)) return cuda_err(c);
+    }
+    return cuda_err(c);
+  }
   if (!c->graph_ok && n_steps > 0) build_graph(c);
   for (int k = 0; k < n_steps; ++k) {
     if (c->graph_ok) {
       if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return cuda_err(c);
     } else {
-      int e = sl_launch_step(c->d, c->stream);
+      int e = sl_launch_step(c->d, c->stream, nullptr, nullptr, &c->kernels_per_step);
       if (e) { c->sticky = e; return e; }
     }
   }
   return cuda_err(c);
+}
+
+int sl_set_timing(sl_ctx* c, int32_t enable) {
+  if (!c) return SL_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (c->ev_used && fold_timing(c)) return cuda_err(c);
+  c->timing = enable ? 1 : 0;
+  for (int k = 0; k < SL_NPHASE; ++k) { c->phase_ms[k] = 0.0; c->phase_n[k] = 0; }
+  return c->sticky;
+}
+
+int sl_get_timing(sl_ctx* c, double ms[8], int64_t count[8]) {
+  if (!c || !ms || !count) return SL_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (c->ev_used && fold_timing(c)) return cuda_err(c);
+  for (int k = 0; k < 8; ++k) {
+    ms[k] = k < SL_NPHASE ? c->phase_ms[k] : 0.0;
+    count[k] = k < SL_NPHASE ? c->phase_n[k] : 0;
+  }
+  return c->sticky;
 }
 
 int sl_set_dt(sl_ctx* c, double dt) {
@@ -437,7 +504,7 @@ int sl_get_order(sl_ctx* c, int32_t* order_dev, int32_t colour_start[9], int32_t
   return sync_status(c);
 }
 
-int sl_counters(sl_ctx* c, int64_t out[4]) {
+int sl_counters(sl_ctx* c, int64_t out[8]) {
   if (!c || !out) return SL_ERR_ARG;
   DeviceGuard g(c->device);
   SlCtrl h;
@@ -445,6 +512,7 @@ int sl_counters(sl_ctx* c, int64_t out[4]) {
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return cuda_err(c);
   out[0] = h.step; out[1] = h.rebuilds; out[2] = h.max_ex_seen; out[3] = h.max_m_seen;
+  out[4] = c->kernels_per_step; out[5] = c->graph_ok; out[6] = 0; out[7] = 0;
   if (h.status && !c->sticky) c->sticky = h.status;
   return c->sticky;
 }
@@ -477,6 +545,7 @@ void sl_destroy(sl_ctx* c) {
   cudaStreamSynchronize(c->stream);
   drop_graph(c);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   delete c;
 }
 

@@ -109,8 +109,12 @@ __device__ __forceinline__ void sl_sector_coords(const SlDev& d, int q, int& sx,
 // Launch helpers implemented in the .cu files.
 int sl_launch_rebuild(const SlDev& d, cudaStream_t st);
 int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick);
-int sl_launch_step(const SlDev& d, cudaStream_t st);
+// Phases of one step, for optional event timing.
+enum { SL_PHASE_KICK = 0, SL_PHASE_SPIN1 = 1, SL_PHASE_DRIFT = 2, SL_PHASE_JTABLE = 3, SL_PHASE_SPIN2 = 4,
+       SL_PHASE_FORCE = 5, SL_NPHASE = 6 };
+#define SL_REBUILD_KERNELS 9
+typedef void (*SlPhaseMark)(void* user, int phase, int end);
+int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels);
 int sl_launch_observables(const SlDev& d, cudaStream_t st);
 int sl_launch_force_rebuild_flag(const SlDev& d, cudaStream_t st);
-int sl_launch_check_state(const SlDev& d, cudaStream_t st);
 int sl_launch_omega_all(const SlDev& d, double* out, cudaStream_t st);

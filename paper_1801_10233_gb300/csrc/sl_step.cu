@@ -284,21 +284,46 @@ int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick) {
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 
-int sl_launch_step(const SlDev& d, cudaStream_t st) {
+int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels) {
   int gn = grid_for(d.n);
   const int lat = !d.fix_lattice;
-  if (lat) k_kick<<<gn, SL_BLOCK, 0, st>>>(d, 0.5 * d.dt);
-  launch_half_op(d, st, 0.5 * d.dt, 0);
+  int nk = 0;
+  auto phase = [&](int ph, int end) { if (mark) mark(user, ph, end); };
   if (lat) {
+    phase(SL_PHASE_KICK, 0);
+    k_kick<<<gn, SL_BLOCK, 0, st>>>(d, 0.5 * d.dt);
+    phase(SL_PHASE_KICK, 1);
+    nk += 1;
+  }
+  phase(SL_PHASE_SPIN1, 0);
+  launch_half_op(d, st, 0.5 * d.dt, 0);
+  phase(SL_PHASE_SPIN1, 1);
+  nk += 16;
+  if (lat) {
+    phase(SL_PHASE_DRIFT, 0);
     k_drift<<<gn, SL_BLOCK, 0, st>>>(d);
     k_decide<<<1, 1, 0, st>>>(d);
     int e = sl_launch_rebuild(d, st);
     if (e) return e;
+    phase(SL_PHASE_DRIFT, 1);
+    phase(SL_PHASE_JTABLE, 0);
     k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
+    phase(SL_PHASE_JTABLE, 1);
+    nk += 2 + SL_REBUILD_KERNELS + 1;
   }
+  phase(SL_PHASE_SPIN2, 0);
   launch_half_op(d, st, 0.5 * d.dt, 2);
-  if (lat) k_force<<<gn, SL_BLOCK, 0, st>>>(d, 1);
+  phase(SL_PHASE_SPIN2, 1);
+  nk += 16;
+  if (lat) {
+    phase(SL_PHASE_FORCE, 0);
+    k_force<<<gn, SL_BLOCK, 0, st>>>(d, 1);
+    phase(SL_PHASE_FORCE, 1);
+    nk += 1;
+  }
   k_end_step<<<1, 1, 0, st>>>(d);
+  nk += 1;
+  if (kernels) *kernels = nk;
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 

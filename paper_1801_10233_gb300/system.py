@@ -92,9 +92,21 @@ class System:
         return int(self._L.sl_status(self._h))
 
     def counters(self):
-        out = (ctypes.c_int64 * 4)()
+        out = (ctypes.c_int64 * 8)()
         check(self._L.sl_counters(self._h, out), "sl_counters")
-        return dict(steps=out[0], rebuilds=out[1], max_ex_seen=out[2], max_morse_seen=out[3])
+        return dict(steps=out[0], rebuilds=out[1], max_ex_seen=out[2], max_morse_seen=out[3],
+                    kernels_per_step=out[4], graph=bool(out[5]))
+
+    def set_timing(self, enable: bool):
+        """Per-phase CUDA-event timing of each step (direct launches)."""
+        check(self._L.sl_set_timing(self._h, int(bool(enable))), "sl_set_timing")
+
+    def timing(self):
+        """{phase: (total ms, launches)} since timing was enabled."""
+        ms = np.zeros(8)
+        cnt = (ctypes.c_int64 * 8)()
+        check(self._L.sl_get_timing(self._h, _lib._arr_ptr(ms), cnt), "sl_get_timing")
+        return {name: (float(ms[k]), int(cnt[k])) for k, name in enumerate(_lib.PHASES)}
 
     # -- state transfer ----------------------------------------------------
     def _empty3(self):
