@@ -177,6 +177,25 @@ int sl_counters(sl_ctx* ctx, int64_t out[8]);
 int sl_set_timing(sl_ctx* ctx, int32_t enable);
 int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
 
+/* Magnetisation of a caller's spin array without a context and without any
+ * allocation, for callers that cannot call cudaMalloc (code running inside
+ * another allocator's hooks, plugins handed device pointers only, processes
+ * whose device footprint is fixed after start-up).  The paper has no
+ * counterpart: this is a service entry point of this library.
+ *   s        device, [n_atoms][3] doubles (caller order, not modified)
+ *   n_atoms  1 .. 2,097,152; larger counts return SL_ERR_ARG before any launch
+ *   out      device, 4 doubles: Mx, My, Mz, |M| with M = (1/N) sum_i s_i
+ * The block partial sums live in a 256 KB file-scope device array that every
+ * GPU loading libsl holds until the process exits; every block writes its own
+ * slot, so no part of it has to start at zero.  All calls on a device share
+ * that array: calls that overlap on the GPU (concurrent streams, or threads
+ * using different streams) race and may return wrong results.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress,
+ * done once per device, with that device current); make that first call
+ * before any stream capture.  Stream-ordered on cuda_stream; no host sync.
+ * Errors: SL_ERR_ARG, SL_ERR_CUDA. */
+int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void* cuda_stream);
+
 /* Sticky device error word (SL_OK or SL_ERR_*).  Synchronises. */
 int sl_status(sl_ctx* ctx);
 

@@ -25,7 +25,7 @@ EXPORTS = (
     "sl_workspace_bytes", "sl_init", "sl_build_neighbors", "sl_step", "sl_set_dt", "sl_set_field",
     "sl_energy", "sl_magnetization", "sl_get_state", "sl_set_state", "sl_get_state_host",
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
-    "sl_get_timing", "sl_status", "sl_strerror", "sl_destroy",
+    "sl_get_timing", "sl_magnetization_static", "sl_status", "sl_strerror", "sl_destroy",
 )
 PHASES = ("kick", "spin_half_op_1", "drift_rebuild", "exchange_table", "spin_half_op_2", "force_kick")
 
@@ -80,6 +80,7 @@ def load():
         "sl_counters": ([_vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "sl_set_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
         "sl_get_timing": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "sl_magnetization_static": ([_vp, ctypes.c_int32, _vp, _vp], ctypes.c_int),
         "sl_status": ([_vp], ctypes.c_int),
         "sl_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "sl_destroy": ([_vp], None),
