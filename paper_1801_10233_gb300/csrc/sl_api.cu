@@ -12,7 +12,9 @@ struct sl_ctx {
   sl_params p;
   SlDev d;
   cudaStream_t stream;
-  cudaStream_t cap;
+  cudaStream_t cap;         // private stream for graph capture
+  cudaStream_t side;        // private stream for work that overlaps the sweep
+  cudaEvent_t fork, join;
   cudaGraphExec_t graph;
   int graph_ok;
   int device;
@@ -60,6 +62,7 @@ int validate(const sl_params* p) {
   if (!(p->ex_rc_A > 0.0) || !(p->morse_rc_A > 0.0) || !(p->ex_delta_A > 0.0)) return SL_ERR_ARG;
   if (p->rotation != SL_ROT_RODRIGUES && p->rotation != SL_ROT_CAYLEY) return SL_ERR_ARG;
   if (p->rebuild_every < 0 || p->max_ex_neighbors < 0 || p->max_morse_neighbors < 0) return SL_ERR_ARG;
+  if (p->max_ex_neighbors > SL_MAX_EX_CAP) return SL_ERR_ARG;
   if (!(p->lambda >= 0.0) || !(p->temperature_K >= 0.0)) return SL_ERR_ARG;
   if (!std::isfinite(p->dt_ps)) return SL_ERR_ARG;
   double rc = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
@@ -80,6 +83,28 @@ struct Layout {
 };
 
 constexpr int NBLK_RED = 1024;
+
+// x = hi + lo with hi = float(x), lo = float(x - hi): the double-float form of
+// an FP64 scalar (host side).
+float2 split_f2(double x) {
+  float hi = (float)x;
+  float lo = (float)(x - (double)hi);
+  return make_float2(hi, lo);
+}
+
+// x = h + m + l exactly (three floats; the FP64 value has 53 bits).
+void split_f3(double x, float* h, float* m, float* l) {
+  *h = (float)x;
+  double r = x - (double)*h;
+  *m = (float)r;
+  *l = (float)(r - (double)*m);
+}
+
+// Double-float constants that depend on dt or H.
+void fill_df_constants(SlDev& d) {
+  for (int a = 0; a < 3; ++a) d.zee_f[a] = split_f2(d.zee[a]);
+  d.tau_f = split_f2(0.25 * d.dt);
+}
 
 // Fill d's scalars and (if base != NULL) its pointers; returns bytes needed.
 size_t plan(const sl_params* p, SlDev& d, char* base) {
@@ -102,6 +127,7 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
   d.max_ex = p->max_ex_neighbors ? p->max_ex_neighbors : 24;
   d.max_m = p->max_morse_neighbors ? p->max_morse_neighbors : 128;
   d.rotation = p->rotation;
+  d.overlap_morse = p->schedule & 1;
   d.fix_lattice = p->fix_lattice;
   d.rebuild_every = p->rebuild_every;
   d.morse_shift = p->morse_shift_energy;
@@ -125,6 +151,23 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
   d.seed = p->seed;
   d.replica = p->replica;
   d.nblk_red = NBLK_RED;
+  d.inv_hbar_f = split_f2(1.0 / SL_HBAR);
+  d.m_nalpha_f = split_f2(-p->morse_alpha_invA);
+  d.m_r0_f = split_f2(p->morse_r0_A);
+  d.m_c2_f = split_f2(2.0 * p->morse_alpha_invA * p->morse_D0_eV);
+  d.m_rc2_f = split_f2(d.m_rc2);
+  d.ex_ix_f = split_f2(1.0 / (p->ex_delta_A * p->ex_delta_A));
+  d.ex_4a_f = split_f2(4.0 * p->ex_alpha_eV);
+  d.ex_g_f = split_f2(p->ex_gamma);
+  d.ex_8ad2_f = split_f2(8.0 * p->ex_alpha_eV / (p->ex_delta_A * p->ex_delta_A));
+  d.ex_rc2_f = split_f2(d.ex_rc2);
+  d.lam_f = split_f2(p->lambda);
+  d.inv1pl2_f = split_f2(1.0 / (1.0 + p->lambda * p->lambda));
+  for (int a = 0; a < 3; ++a) {
+    split_f3(p->box[a], &d.box_h[a], &d.box_m[a], &d.box_l[a]);
+    d.inv_box_f[a] = (float)(1.0 / p->box[a]);
+  }
+  fill_df_constants(d);
 
   Layout L;
   size_t nn = (size_t)n;
@@ -135,8 +178,13 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
   size_t o_perm = L.take<int>(nn), o_rank = L.take<int>(nn), o_secq = L.take<int>(nn);
   size_t o_tsecq = L.take<int>(nn), o_tperm = L.take<int>(nn), o_src = L.take<int>(nn);
   size_t o_cnt = L.take<int>(d.nsec), o_start = L.take<int>(d.nsec + 1), o_fill = L.take<int>(d.nsec);
-  size_t o_exj = L.take<int>(nn * d.max_ex), o_exn = L.take<int>(nn);
-  size_t o_exJ = L.take<double>(nn * d.max_ex), o_exG = L.take<double4_32a>(nn * d.max_ex);
+  size_t o_exj = L.take<int>(nn * d.max_ex), o_exn = L.take<int>(nn), o_exin = L.take<int>(nn);
+  size_t o_exJ = L.take<float2>(nn * d.max_ex);
+  size_t o_exGh = L.take<float4>(nn * d.max_ex), o_exGl = L.take<float4>(nn * d.max_ex);
+  size_t o_rh = L.take<float4>(nn), o_rm = L.take<float4>(nn), o_rl = L.take<float4>(nn);
+  size_t o_sdf = L.take<float4>(2 * nn);
+  size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
+  size_t o_fmh = L.take<float4>(nn), o_fml = L.take<float4>(nn);
   size_t o_mj = L.take<int>(nn * d.max_m), o_mn = L.take<int>(nn);
   size_t o_part = L.take<double>((size_t)NBLK_RED * 16);
   size_t o_stage = L.take<double>(nn * 9);
@@ -149,8 +197,13 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
     d.perm = (int*)(base + o_perm); d.rank = (int*)(base + o_rank); d.secq = (int*)(base + o_secq);
     d.tsecq = (int*)(base + o_tsecq); d.tperm = (int*)(base + o_tperm); d.src = (int*)(base + o_src);
     d.sec_count = (int*)(base + o_cnt); d.sec_start = (int*)(base + o_start); d.sec_fill = (int*)(base + o_fill);
-    d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn);
-    d.exJ = (double*)(base + o_exJ); d.exG = (double4_32a*)(base + o_exG);
+    d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn); d.exin = (int*)(base + o_exin);
+    d.exJ = (float2*)(base + o_exJ);
+    d.exGh = (float4*)(base + o_exGh); d.exGl = (float4*)(base + o_exGl);
+    d.rh = (float4*)(base + o_rh); d.rm = (float4*)(base + o_rm); d.rl = (float4*)(base + o_rl);
+    d.sdf = (float4*)(base + o_sdf);
+    d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);
+    d.fmh = (float4*)(base + o_fmh); d.fml = (float4*)(base + o_fml);
     d.mj = (int*)(base + o_mj); d.mn = (int*)(base + o_mn);
     d.part = (double*)(base + o_part);
     d.stage = (double*)(base + o_stage);
@@ -221,13 +274,22 @@ void drop_graph(sl_ctx* c) {
   c->graph_ok = 0;
 }
 
+SlStreams streams(const sl_ctx* c, cudaStream_t main) {
+  SlStreams ss;
+  ss.main = main;
+  ss.side = c->side;
+  ss.fork = c->fork;
+  ss.join = c->join;
+  return ss;
+}
+
 // Capture one step's launch sequence into a graph on a private stream.
 int build_graph(sl_ctx* c) {
   drop_graph(c);
   if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SL_ERR_CUDA;
-  int e = sl_launch_step(c->d, c->cap, nullptr, nullptr, &c->kernels_per_step);
+  int e = sl_launch_step(c->d, streams(c, c->cap), nullptr, nullptr, &c->kernels_per_step);
   cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
   if (e || ce != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return SL_ERR_CUDA; }
   cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
@@ -237,15 +299,16 @@ int build_graph(sl_ctx* c) {
   return SL_OK;
 }
 
-// Record a timing event at a phase boundary (pool grows as needed).
-void mark_phase(void* user, int phase, int end) {
+// Record a timing event at a phase boundary on the phase's stream (the pool
+// grows as needed).
+void mark_phase(void* user, int phase, int end, cudaStream_t st) {
   sl_ctx* c = (sl_ctx*)user;
   if (c->ev_used == c->ev_pool.size()) {
     cudaEvent_t ev;
     if (cudaEventCreate(&ev) != cudaSuccess) return;
     c->ev_pool.push_back(ev);
   }
-  cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+  cudaEventRecord(c->ev_pool[c->ev_used], st);
   if (!end) c->ev_phase.push_back(phase);
   c->ev_used += 1;
 }
@@ -302,6 +365,13 @@ int sl_init(const sl_params* params, const double* r, const double* v, const dou
   plan(params, c->d, (char*)workspace);
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SL_ERR_CUDA; }
+  if (sl_prepare_kernels() != SL_OK ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+    sl_destroy(c);
+    return SL_ERR_CUDA;
+  }
   cudaMemsetAsync(c->d.ctrl, 0, sizeof(SlCtrl), c->stream);
   k_load<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d, r, v, s, 1);
   k_check<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d);
@@ -328,7 +398,7 @@ int sl_step(sl_ctx* c, int32_t n_steps) {
   if (c->timing) {
     // direct launches with an event pair around each phase
     for (int k = 0; k < n_steps; ++k) {
-      int e = sl_launch_step(c->d, c->stream, mark_phase, c, &c->kernels_per_step);
+      int e = sl_launch_step(c->d, streams(c, c->stream), mark_phase, c, &c->kernels_per_step);
       if (e) { c->sticky = e; return e; }
       if (c->ev_used > 4096 && fold_timing(c)) return cuda_err(c);
     }
@@ -339,7 +409,7 @@ int sl_step(sl_ctx* c, int32_t n_steps) {
     if (c->graph_ok) {
       if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return cuda_err(c);
     } else {
-      int e = sl_launch_step(c->d, c->stream, nullptr, nullptr, &c->kernels_per_step);
+      int e = sl_launch_step(c->d, streams(c, c->stream), nullptr, nullptr, &c->kernels_per_step);
       if (e) { c->sticky = e; return e; }
     }
   }
@@ -370,6 +440,7 @@ int sl_set_dt(sl_ctx* c, double dt) {
   if (!c || !std::isfinite(dt)) return SL_ERR_ARG;
   c->p.dt_ps = dt;
   c->d.dt = dt;
+  fill_df_constants(c->d);
   drop_graph(c);
   return c->sticky;
 }
@@ -380,6 +451,7 @@ int sl_set_field(sl_ctx* c, const double H[3]) {
     c->p.H_tesla[a] = H[a];
     c->d.zee[a] = c->p.mu_s_muB * SL_MUB * H[a];
   }
+  fill_df_constants(c->d);
   drop_graph(c);
   return c->sticky;
 }
@@ -437,6 +509,7 @@ int sl_set_state(sl_ctx* c, const double* r, const double* v, const double* s) {
   int gn = grid_for(c->d.n);
   k_load<<<gn, SL_BLOCK, 0, c->stream>>>(c->d, r, v, s, 0);
   k_check<<<gn, SL_BLOCK, 0, c->stream>>>(c->d);
+  sl_launch_split(c->d, c->stream, 0);
   k_disp_flag<<<gn, SL_BLOCK, 0, c->stream>>>(c->d);
   return refresh(c);
 }
@@ -544,7 +617,11 @@ void sl_destroy(sl_ctx* c) {
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   drop_graph(c);
+  if (c->side) cudaStreamSynchronize(c->side);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
   for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   delete c;
 }

@@ -118,7 +118,9 @@ __global__ void k_rb_copyback(SlDev d) {
 // Full Verlet lists (both directions) from the sectors around each atom:
 // exchange list r < ex_rc + skin (atom-major), Morse list r < morse_rc + skin
 // (neighbour-major).  Neighbour order is the fixed loop order, so rebuilds
-// are deterministic.
+// are deterministic.  Each exchange list is then reordered stably so that
+// neighbours in the atom's own sector come first (exin[i] of them): the
+// sweep sums the other sectors' field in parallel and only these in sequence.
 __global__ void k_rb_nbr(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,7 +149,7 @@ __global__ void k_rb_nbr(SlDev d) {
             ++cm;
           }
           if (r2 < d.list_ex2) {
-            if (ce < d.max_ex) d.exj[(size_t)i * d.max_ex + ce] = j;
+            if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;
             ++ce;
           }
         }
@@ -156,7 +158,22 @@ __global__ void k_rb_nbr(SlDev d) {
   }
   if (cm > d.max_m || ce > d.max_ex) sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW);
   d.mn[i] = min(cm, d.max_m);
-  d.exn[i] = min(ce, d.max_ex);
+  const int ne = min(ce, d.max_ex);
+  d.exn[i] = ne;
+  // stable partition: same-sector neighbours first
+  const int qi = d.secq[i];
+  const int sa = d.sec_start[qi], sb = d.sec_start[qi + 1];
+  int* col = d.exj + i;     // entry k at col[k * n]
+  const size_t n = (size_t)d.n;
+  int tmp[SL_MAX_EX_CAP];
+  int nin = 0, nout = 0;
+  for (int k = 0; k < ne; ++k) {
+    const int j = col[k * n];
+    if (j >= sa && j < sb) col[(nin++) * n] = j;
+    else tmp[nout++] = j;
+  }
+  for (int k = 0; k < nout; ++k) col[(nin + k) * n] = tmp[k];
+  d.exin[i] = nin;
   atomicMax(&d.ctrl->max_m_seen, cm);
   atomicMax(&d.ctrl->max_ex_seen, ce);
 }
@@ -192,6 +209,7 @@ int sl_launch_rebuild(const SlDev& d, cudaStream_t st) {
   k_rb_sort<<<gs, SL_BLOCK, 0, st>>>(d);
   k_rb_gather<<<gn, SL_BLOCK, 0, st>>>(d);
   k_rb_copyback<<<gn, SL_BLOCK, 0, st>>>(d);
+  sl_launch_split(d, st, 1);
   k_rb_nbr<<<gn, SL_BLOCK, 0, st>>>(d);
   k_rb_end<<<1, 1, 0, st>>>(d);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;

@@ -13,6 +13,7 @@
 #define SL_FTOA 9648.533212       // (eV/A)/amu -> A/ps^2
 
 #define SL_BLOCK 128
+#define SL_MAX_EX_CAP 64   // largest accepted max_ex_neighbors
 
 // Control block in device memory: sticky status, rebuild flag, counters.
 struct SlCtrl {
@@ -27,7 +28,8 @@ struct SlCtrl {
   double red[16];           // final results of the observable reduction
 };
 
-// Everything a kernel needs, passed by value.
+// Everything a kernel needs, passed by value.  Scalars used by the
+// double-float kernels are given as (hi, lo) float pairs split on the host.
 struct SlDev {
   int n;
   int nsec, s8;             // sectors, sectors per colour
@@ -35,6 +37,7 @@ struct SlDev {
   int mx, my, mz;           // sector layers searched for Morse neighbours (or n)
   int max_ex, max_m;
   int rotation, fix_lattice, rebuild_every, morse_shift;
+  int overlap_morse;
   double box[3], inv_box[3], edge[3];
   double dt;
   double zee[3];            // mu_s mu_B H (eV)
@@ -48,17 +51,30 @@ struct SlDev {
   uint64_t seed;
   int replica;
 
-  // state, sector-sorted
+  // double-float constants (hi, lo)
+  float2 zee_f[3], inv_hbar_f, tau_f;        // tau = dt/4
+  float2 m_nalpha_f, m_r0_f, m_c2_f, m_rc2_f; // -a, r0, 2 a D0, rc^2
+  float2 ex_ix_f, ex_4a_f, ex_g_f, ex_8ad2_f, ex_rc2_f;  // 1/delta^2, 4 alpha, gamma, 8 alpha/delta^2, rc^2
+  float2 lam_f, inv1pl2_f;                   // lambda, 1/(1 + lambda^2)
+  float box_h[3], box_m[3], box_l[3], inv_box_f[3];
+
+  // state, sector-sorted (FP64, authoritative)
   double4_32a *r, *v, *s, *F, *rb;
+  // split copies for the double-float kernels
+  float4 *rh, *rm, *rl;     // r = rh + rm + rl exactly
+  float4 *sdf;              // s = hi + lo to ~48 bits: sdf[2i] = hi, sdf[2i+1] = lo
   // rebuild scratch
   double4_32a *tr, *tv, *ts, *tF;
   int *perm, *rank, *secq, *tsecq, *tperm, *src;
   int *sec_count, *sec_start, *sec_fill;
   // neighbour lists
-  int *exj, *exn;           // [n][max_ex] atom-major, counts
-  double *exJ;              // [n][max_ex] J_ij at current r
-  double4_32a *exG;             // [n][max_ex] (J'_ij e_ij, J_ij)
+  int *exj, *exn, *exin;    // [max_ex][n] neighbour-major (same-sector entries first), counts
+  float2 *exJ;              // [max_ex][n] J_ij (hi, lo) at current r
+  float4 *exGh, *exGl;      // [max_ex][n] (J'_ij e_ij, J_ij) hi and lo parts
+  float4 *fmh, *fml;        // Morse force (hi, lo) per atom, from positions only
   int *mj, *mn;             // [max_m][n] neighbour-major, counts
+  // sweep scratch for blocks whose atoms exceed shared memory: [3 n] each
+  float2 *hbuf, *sbuf, *ebuf;
   // reduction partials
   double *part;             // [nblk_red][16]
   int nblk_red;
@@ -109,12 +125,20 @@ __device__ __forceinline__ void sl_sector_coords(const SlDev& d, int q, int& sx,
 // Launch helpers implemented in the .cu files.
 int sl_launch_rebuild(const SlDev& d, cudaStream_t st);
 int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick);
+int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild);
+int sl_prepare_kernels();
 // Phases of one step, for optional event timing.
 enum { SL_PHASE_KICK = 0, SL_PHASE_SPIN1 = 1, SL_PHASE_DRIFT = 2, SL_PHASE_JTABLE = 3, SL_PHASE_SPIN2 = 4,
-       SL_PHASE_FORCE = 5, SL_NPHASE = 6 };
-#define SL_REBUILD_KERNELS 9
-typedef void (*SlPhaseMark)(void* user, int phase, int end);
-int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels);
+       SL_PHASE_MORSE = 5, SL_PHASE_EXCH = 6, SL_NPHASE = 7 };
+#define SL_REBUILD_KERNELS 10
+typedef void (*SlPhaseMark)(void* user, int phase, int end, cudaStream_t st);
+// The step's two streams: the Morse forces (positions only) run on `side`
+// while the second spin half-op runs on `main`.
+struct SlStreams {
+  cudaStream_t main, side;
+  cudaEvent_t fork, join;
+};
+int sl_launch_step(const SlDev& d, const SlStreams& ss, SlPhaseMark mark, void* user, int* kernels);
 int sl_launch_observables(const SlDev& d, cudaStream_t st);
 int sl_launch_force_rebuild_flag(const SlDev& d, cudaStream_t st);
 int sl_launch_omega_all(const SlDev& d, double* out, cudaStream_t st);

@@ -5,6 +5,7 @@
 // Deterministic: per-block partials in a fixed tree order, then one thread
 // per quantity sums the block partials in block order.
 #include "sl_internal.cuh"
+#include "sl_df64.cuh"
 
 namespace {
 
@@ -33,10 +34,11 @@ __global__ void k_obs(SlDev d) {
     double hx = d.zee[0], hy = d.zee[1], hz = d.zee[2];
     double ex = 0.0;
     int ne = d.exn[i];
-    size_t base = (size_t)i * d.max_ex;
     for (int k = 0; k < ne; ++k) {
-      double J = d.exJ[base + k];
-      double4_32a sj = d.s[d.exj[base + k]];
+      const size_t e = (size_t)k * d.n + i;
+      const float2 J2 = d.exJ[e];
+      double J = double_from_float(J2.x) + double_from_float(J2.y);
+      double4_32a sj = d.s[d.exj[e]];
       ex += J * (si.x * sj.x + si.y * sj.y + si.z * sj.z);
       hx = fma(J, sj.x, hx); hy = fma(J, sj.y, hy); hz = fma(J, sj.z, hz);
     }

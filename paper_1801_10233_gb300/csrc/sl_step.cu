@@ -4,11 +4,84 @@
 // The spin half-op e^{Ls dt/2} is 8 colour passes forward then 8 backward
 // (Eq. spin_ST_sectoring, Sec. 5.1); each pass updates every sector of one
 // colour concurrently, the spins inside a sector one after another.
+//
+// The FP64 state (r, v, s, F) is authoritative.  Pair and rotation arithmetic
+// runs in double-float on the FP32 pipes (sl_df64.cuh) from split copies of r
+// (exact three-float pieces) and s (float pairs), and each result is added to
+// the FP64 state once per atom.
 #include "sl_internal.cuh"
+#include "sl_df64.cuh"
 
 namespace {
 
 inline int grid_for(int n) { return (n + SL_BLOCK - 1) / SL_BLOCK; }
+
+__device__ __forceinline__ df F2(float2 v) { return df_make(v.x, v.y); }
+__device__ __forceinline__ float2 D2(df a) { return make_float2(a.hi, a.lo); }
+
+struct df3 {
+  df x, y, z;
+};
+struct p3 {
+  f3 x, y, z;
+};
+
+__device__ __forceinline__ p3 load_pos(const SlDev& d, int j) {
+  float4 h = d.rh[j], m = d.rm[j], l = d.rl[j];
+  p3 p;
+  p.x.h = h.x; p.x.m = m.x; p.x.l = l.x;
+  p.y.h = h.y; p.y.m = m.y; p.y.l = l.y;
+  p.z.h = h.z; p.z.m = m.z; p.z.l = l.z;
+  return p;
+}
+
+__device__ __forceinline__ df3 load_spin(const SlDev& d, int j) {
+  float4 h = d.sdf[2 * (size_t)j], l = d.sdf[2 * (size_t)j + 1];
+  df3 s;
+  s.x = df_make(h.x, l.x); s.y = df_make(h.y, l.y); s.z = df_make(h.z, l.z);
+  return s;
+}
+
+__device__ __forceinline__ df3 pair_sep(const SlDev& d, const p3& a, const p3& b) {
+  df3 r;
+  f3 L0 = {d.box_h[0], d.box_m[0], d.box_l[0]};
+  f3 L1 = {d.box_h[1], d.box_m[1], d.box_l[1]};
+  f3 L2 = {d.box_h[2], d.box_m[2], d.box_l[2]};
+  r.x = f3_sep(b.x, a.x, L0, d.inv_box_f[0]);
+  r.y = f3_sep(b.y, a.y, L1, d.inv_box_f[1]);
+  r.z = f3_sep(b.z, a.z, L2, d.inv_box_f[2]);
+  return r;
+}
+
+__device__ __forceinline__ df dot3(const df3& a, const df3& b) {
+  float h = 0.0f, l = 0.0f;
+  acc_prod(h, l, a.x, b.x);
+  acc_prod(h, l, a.y, b.y);
+  acc_prod(h, l, a.z, b.z);
+  return acc_done(h, l);
+}
+
+__device__ __forceinline__ df3 cross3(const df3& a, const df3& b) {
+  df3 c;
+  float h, l;
+  h = l = 0.0f; acc_prod(h, l, a.y, b.z); acc_prod(h, l, df_neg(a.z), b.y); c.x = acc_done(h, l);
+  h = l = 0.0f; acc_prod(h, l, a.z, b.x); acc_prod(h, l, df_neg(a.x), b.z); c.y = acc_done(h, l);
+  h = l = 0.0f; acc_prod(h, l, a.x, b.y); acc_prod(h, l, df_neg(a.y), b.x); c.z = acc_done(h, l);
+  return c;
+}
+
+__device__ __forceinline__ void store_pos_split(const SlDev& d, int k, double4_32a r) {
+  f3 x = f3_from_double(r.x), y = f3_from_double(r.y), z = f3_from_double(r.z);
+  d.rh[k] = make_float4(x.h, y.h, z.h, 0.0f);
+  d.rm[k] = make_float4(x.m, y.m, z.m, 0.0f);
+  d.rl[k] = make_float4(x.l, y.l, z.l, 0.0f);
+}
+
+__device__ __forceinline__ void store_spin_split(const SlDev& d, int k, double4_32a s) {
+  df x = df_from_double(s.x), y = df_from_double(s.y), z = df_from_double(s.z);
+  d.sdf[2 * (size_t)k] = make_float4(x.hi, y.hi, z.hi, 0.0f);
+  d.sdf[2 * (size_t)k + 1] = make_float4(x.lo, y.lo, z.lo, 0.0f);
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals for the spin bath.
@@ -39,122 +112,275 @@ __device__ __forceinline__ double3 gauss3(uint64_t seed, int replica, long long 
 }
 
 // ---------------------------------------------------------------------------
-// Single-spin propagator e^{L_si tau}.
-//
-// Exact rotation of s about w by theta = |w| tau, written without |w| and as
-// an increment of s so that each component is rounded once:
-//   s' = s + [ -u B s + tau A (w x s) + tau^2 B (w.s) w ]
-// with u = theta^2, A = sin(theta)/theta and B = (1 - cos(theta))/theta^2
-// (so 1 - cos(theta) = u B).  A and B are even power series in theta; for
-// theta <= 0.25 the Taylor series truncated after the u^6 term are exact to
-// below 1e-17 relative.  Larger angles use sqrt and sincos.
+// Single-spin propagator e^{L_si tau} as an increment of s:
+//   s' - s = -u B s + tau A (w x s) + tau^2 B (w.s) w,      u = tau^2 |w|^2.
+// Exact rotation by theta = |w| tau: A = sin(theta)/theta,
+// B = (1 - cos theta)/theta^2 (even series in theta; for u <= 1e-3 the series
+// are summed in df, beyond that A and B come from FP64 sin).  Cayley map of
+// Sec. 3: A = 1/(1 + u/4), B = A/2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void rotate_exact(double3 w, double tau, double4_32a& s) {
-  double u = tau * tau * (w.x * w.x + w.y * w.y + w.z * w.z);
-  double A, B, uB;
-  if (u <= 0.0625) {
-    // 1/(2k+1)! and 1/(2k+2)! for k = 0..6
-    A = 1.0 / 6227020800.0;                 // 1/13!
-    A = fma(A, -u, 1.0 / 39916800.0);       // 1/11!
-    A = fma(A, -u, 1.0 / 362880.0);         // 1/9!
-    A = fma(A, -u, 1.0 / 5040.0);           // 1/7!
-    A = fma(A, -u, 1.0 / 120.0);            // 1/5!
-    A = fma(A, -u, 1.0 / 6.0);              // 1/3!
-    A = fma(A, -u, 1.0);
-    B = 1.0 / 87178291200.0;                // 1/14!
-    B = fma(B, -u, 1.0 / 479001600.0);      // 1/12!
-    B = fma(B, -u, 1.0 / 3628800.0);        // 1/10!
-    B = fma(B, -u, 1.0 / 40320.0);          // 1/8!
-    B = fma(B, -u, 1.0 / 720.0);            // 1/6!
-    B = fma(B, -u, 1.0 / 24.0);             // 1/4!
-    B = fma(B, -u, 0.5);                    // 1/2!
-    uB = u * B;
+__device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau, int cayley) {
+  float h = 0.0f, l = 0.0f;
+  acc_prod(h, l, w.x, w.x);
+  acc_prod(h, l, w.y, w.y);
+  acc_prod(h, l, w.z, w.z);
+  df w2 = acc_done(h, l);
+  df tau2 = df_sqr(tau);
+  df u = df_mul(w2, tau2);
+  df A, B;
+  if (cayley) {
+    df den = df_add_f(df_scale(u, 0.25f), 1.0f);
+    float y0 = __frcp_rn(den.hi);
+    df e = df_add_f(df_neg(df_mul_f(den, y0)), 1.0f);     // 1 - den y0
+    A = df_add_f(df_f(y0), y0 * e.hi);                     // 1 / den
+    B = df_scale(A, 0.5f);
+  } else if (u.hi <= 2e-4f) {
+    // theta <= 0.014: A = 1 - u (1/6 - u/120 + u^2/5040), B = 1/2 - u (1/24 - u/720 + u^2/40320);
+    // the u^2 terms and beyond are below 1e-17 of A and B
+    const df c6 = df_make(SL_INV_FACT3_HI, SL_INV_FACT3_LO);
+    const df c24 = df_make(SL_INV_FACT4_HI, SL_INV_FACT4_LO);
+    df a1 = df_add_f(c6, -u.hi * __fmaf_rn(-u.hi, 1.0f / 5040.0f, 1.0f / 120.0f));
+    df b1 = df_add_f(c24, -u.hi * __fmaf_rn(-u.hi, 1.0f / 40320.0f, 1.0f / 720.0f));
+    A = df_add_f(df_neg(df_mul(u, a1)), 1.0f);
+    B = df_add_f(df_neg(df_mul(u, b1)), 0.5f);
+  } else if (u.hi <= 1e-3f) {
+    const df c6 = df_make(SL_INV_FACT3_HI, SL_INV_FACT3_LO);       // 1/3!
+    const df c120 = df_make(SL_INV_FACT5_HI, SL_INV_FACT5_LO);     // 1/5!
+    const df c24 = df_make(SL_INV_FACT4_HI, SL_INV_FACT4_LO);      // 1/4!
+    const df c720 = df_make(SL_INV_FACT6_HI, SL_INV_FACT6_LO);     // 1/6!
+    float ta = __fmaf_rn(-u.hi, __fmaf_rn(-u.hi, 1.0f / 39916800.0f, 1.0f / 362880.0f), 1.0f / 5040.0f);
+    float tb = __fmaf_rn(-u.hi, __fmaf_rn(-u.hi, 1.0f / 479001600.0f, 1.0f / 3628800.0f), 1.0f / 40320.0f);
+    df a1 = df_sub(c6, df_mul(u, df_add_f(c120, -u.hi * ta)));     // 1/6 - u/120 + u^2/5040 - ...
+    df b1 = df_sub(c24, df_mul(u, df_add_f(c720, -u.hi * tb)));    // 1/24 - u/720 + u^2/40320 - ...
+    A = df_add_f(df_neg(df_mul(u, a1)), 1.0f);
+    B = df_add_f(df_neg(df_mul(u, b1)), 0.5f);
   } else {
-    double th = sqrt(u);
-    double h = sin(0.5 * th);
-    A = sin(th) / th;
-    uB = 2.0 * h * h;
-    B = uB / u;
+    double ud = df_to_double(u);
+    double th = sqrt(ud);
+    double hs = sin(0.5 * th);
+    A = df_from_double(sin(th) / th);
+    B = df_from_double(2.0 * hs * hs / ud);
   }
-  double tA = tau * A, tB = tau * tau * B * (w.x * s.x + w.y * s.y + w.z * s.z);
-  double cx = w.y * s.z - w.z * s.y;
-  double cy = w.z * s.x - w.x * s.z;
-  double cz = w.x * s.y - w.y * s.x;
-  double ix = fma(-uB, s.x, fma(tA, cx, tB * w.x));
-  double iy = fma(-uB, s.y, fma(tA, cy, tB * w.y));
-  double iz = fma(-uB, s.z, fma(tA, cz, tB * w.z));
-  s.x += ix; s.y += iy; s.z += iz;
+  df uB = df_mul(u, B);
+  df tA = df_mul(tau, A);
+  df tBws = df_mul(df_mul(tau2, B), dot3(w, s));
+  df3 c = cross3(w, s);
+  df3 inc;
+  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.x); acc_prod(h, l, tA, c.x); acc_prod(h, l, tBws, w.x);
+  inc.x = acc_done(h, l);
+  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.y); acc_prod(h, l, tA, c.y); acc_prod(h, l, tBws, w.y);
+  inc.y = acc_done(h, l);
+  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.z); acc_prod(h, l, tA, c.z); acc_prod(h, l, tBws, w.z);
+  inc.z = acc_done(h, l);
+  return inc;
 }
 
-// Cayley-type propagator printed in Sec. 3 (rotation by 2 atan(|w| tau/2)).
-__device__ __forceinline__ void rotate_cayley(double3 w, double tau, double4_32a& s) {
-  double w2 = w.x * w.x + w.y * w.y + w.z * w.z;
-  double ws = w.x * s.x + w.y * s.y + w.z * s.z;
-  double q = 0.25 * tau * tau;
-  double inv = 1.0 / (1.0 + q * w2);
-  double cx = w.y * s.z - w.z * s.y;
-  double cy = w.z * s.x - w.x * s.z;
-  double cz = w.x * s.y - w.y * s.x;
-  double x = s.x + tau * cx + q * (2.0 * w.x * ws - w2 * s.x);
-  double y = s.y + tau * cy + q * (2.0 * w.y * ws - w2 * s.y);
-  double z = s.z + tau * cz + q * (2.0 * w.z * ws - w2 * s.z);
-  s.x = x * inv; s.y = y * inv; s.z = z * inv;
+// ---------------------------------------------------------------------------
+// One colour pass.  A block takes SW_SPB consecutive sectors of the colour
+// (their atoms are contiguous in the sorted order):
+//   phase 1 (all threads, parallel over atoms): the exchange field from
+//           atoms outside the atom's own sector (fixed during this pass), the
+//           noise of the spin bath, and a copy of the atom's same-sector
+//           neighbour list (local index, J) into shared memory;
+//   phase 2 (one thread per sector, sequential): for each spin in order, add
+//           the field of the already-updated spins of its own sector, form
+//           omega and rotate -- shared memory only;
+//   phase 3 (parallel over atoms): add each increment to the FP64 spin once
+//           and refresh its float split.
+// Blocks with more than SW_MAXA atoms use workspace scratch and read their
+// lists from global memory.
+// ---------------------------------------------------------------------------
+constexpr int SW_SPB = 32;
+constexpr int SW_THREADS = 256;
+constexpr int SW_MAXA = 384;
+constexpr int SW_MAXIN = 12;   // same-sector neighbours staged per atom
+constexpr int SW_BATCH = 4;    // external neighbours gathered per batch
+
+// Dynamic shared memory of one block: H, S (and E with noise) as float2
+// [3 SW_MAXA], same-sector lists J [SW_MAXIN SW_MAXA] float2, local index
+// [SW_MAXIN SW_MAXA] short, counts [SW_MAXA] int.
+size_t sweep_smem_bytes(bool noise) {
+  return (size_t)(noise ? 3 : 2) * 3 * SW_MAXA * sizeof(float2) + (size_t)SW_MAXIN * SW_MAXA * sizeof(float2) +
+         (size_t)SW_MAXIN * SW_MAXA * sizeof(short) + (size_t)SW_MAXA * sizeof(int);
 }
 
-// omega_i = (mu_s mu_B H + sum_j J_ij s_j) / hbar.
-__device__ __forceinline__ double3 omega_of(const SlDev& d, int i) {
-  double hx = d.zee[0], hy = d.zee[1], hz = d.zee[2];
-  int ne = d.exn[i];
-  const int* jj = d.exj + (size_t)i * d.max_ex;
-  const double* JJ = d.exJ + (size_t)i * d.max_ex;
-  for (int k = 0; k < ne; ++k) {
-    double J = JJ[k];
-    double4_32a sj = d.s[jj[k]];
-    hx = fma(J, sj.x, hx);
-    hy = fma(J, sj.y, hy);
-    hz = fma(J, sj.z, hz);
-  }
-  const double ih = 1.0 / SL_HBAR;
-  return make_double3(hx * ih, hy * ih, hz * ih);
-}
+__global__ void __launch_bounds__(SW_THREADS, 3) k_sweep_pass(SlDev d, int colour, int backward, int subpass) {
+  extern __shared__ float2 smem[];
+  const bool noise = d.temperature > 0.0;
+  const bool bath = d.lambda != 0.0 || d.temperature != 0.0;
+  float2* sh_h = smem;
+  float2* sh_s = sh_h + 3 * SW_MAXA;
+  float2* sh_e = sh_s + 3 * SW_MAXA;
+  float2* sh_ij = sh_e + (noise ? 3 * SW_MAXA : 0);
+  short* sh_iu = (short*)(sh_ij + SW_MAXIN * SW_MAXA);
+  int* sh_in = (int*)(sh_iu + SW_MAXIN * SW_MAXA);
 
-__device__ __forceinline__ void update_spin(const SlDev& d, int i, double tau, int subpass, long long step) {
-  double3 w = omega_of(d, i);
-  double4_32a s = d.s[i];
-  if (d.lambda != 0.0 || d.temperature != 0.0) {
-    // Eq. sLLG as ds/dt = Om x s, Om = (w + eta + lambda s x w) / (1 + lambda^2),
-    // eta ~ N(0, 2 D_S / |tau|), D_S = lambda (1 + lambda^2) k_B T / hbar.
-    double lam = d.lambda;
-    double3 eta = make_double3(0.0, 0.0, 0.0);
-    if (d.temperature > 0.0) {
-      double3 g = gauss3(d.seed, d.replica, step, subpass, d.perm[i]);
-      double DS = lam * (1.0 + lam * lam) * SL_KB * d.temperature / SL_HBAR;
-      double sig = sqrt(2.0 * DS / fabs(tau));
-      eta = make_double3(sig * g.x, sig * g.y, sig * g.z);
+  const int qbeg = colour * d.s8, qend = qbeg + d.s8;
+  const int q0 = qbeg + blockIdx.x * SW_SPB;
+  const int q1 = min(q0 + SW_SPB, qend);
+  const int a0 = d.sec_start[q0], a1 = d.sec_start[q1];
+  const int na = a1 - a0;
+  const bool fits = na <= SW_MAXA;
+  float2* H = fits ? sh_h : d.hbuf + 3 * (size_t)a0;
+  float2* S = fits ? sh_s : d.sbuf + 3 * (size_t)a0;
+  float2* E = fits ? sh_e : d.ebuf + 3 * (size_t)a0;
+  const long long step = d.ctrl->step;
+  const df tau = F2(d.tau_f);
+  const size_t n = (size_t)d.n;
+  const int kin = min(SW_MAXIN, d.max_ex);
+
+  // phase 1
+  for (int t = threadIdx.x; t < na; t += blockDim.x) {
+    const int i = a0 + t;
+    const float4 s4h = d.sdf[2 * (size_t)i], s4l = d.sdf[2 * (size_t)i + 1];
+    const int ni = d.exin[i], ne = d.exn[i];
+    S[3 * t] = make_float2(s4h.x, s4l.x);
+    S[3 * t + 1] = make_float2(s4h.y, s4l.y);
+    S[3 * t + 2] = make_float2(s4h.z, s4l.z);
+    if (fits) {
+      sh_in[t] = ni;
+      const int m = min(ni, kin);
+#pragma unroll
+      for (int k = 0; k < SW_MAXIN; ++k) {
+        if (k < m) {
+          const size_t e = (size_t)k * n + i;
+          sh_iu[t * SW_MAXIN + k] = (short)(d.exj[e] - a0);
+          sh_ij[t * SW_MAXIN + k] = d.exJ[e];
+        }
+      }
     }
-    double sx = s.y * w.z - s.z * w.y;
-    double sy = s.z * w.x - s.x * w.z;
-    double sz = s.x * w.y - s.y * w.x;
-    double inv = 1.0 / (1.0 + lam * lam);
-    w = make_double3((w.x + eta.x + lam * sx) * inv, (w.y + eta.y + lam * sy) * inv,
-                     (w.z + eta.z + lam * sz) * inv);
+    float hx = d.zee_f[0].x, lx = d.zee_f[0].y;
+    float hy = d.zee_f[1].x, ly = d.zee_f[1].y;
+    float hz = d.zee_f[2].x, lz = d.zee_f[2].y;
+    for (int k0 = ni; k0 < ne; k0 += SW_BATCH) {
+      int jj[SW_BATCH];
+      float2 JJ[SW_BATCH];
+      float4 vh[SW_BATCH], vl[SW_BATCH];
+#pragma unroll
+      for (int q = 0; q < SW_BATCH; ++q) {
+        if (k0 + q < ne) {
+          const size_t e = (size_t)(k0 + q) * n + i;
+          jj[q] = d.exj[e];
+          JJ[q] = d.exJ[e];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < SW_BATCH; ++q) {
+        if (k0 + q < ne) {
+          vh[q] = d.sdf[2 * (size_t)jj[q]];
+          vl[q] = d.sdf[2 * (size_t)jj[q] + 1];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < SW_BATCH; ++q) {
+        if (k0 + q < ne) {
+          const df J = F2(JJ[q]);
+          acc_prod(hx, lx, J, df_make(vh[q].x, vl[q].x));
+          acc_prod(hy, ly, J, df_make(vh[q].y, vl[q].y));
+          acc_prod(hz, lz, J, df_make(vh[q].z, vl[q].z));
+        }
+      }
+    }
+    H[3 * t] = D2(acc_done(hx, lx));
+    H[3 * t + 1] = D2(acc_done(hy, ly));
+    H[3 * t + 2] = D2(acc_done(hz, lz));
+    if (noise) {
+      // eta ~ N(0, 2 D_S / |tau|), D_S = lambda (1 + lambda^2) k_B T / hbar
+      double3 g = gauss3(d.seed, d.replica, step, subpass, d.perm[i]);
+      double lam = d.lambda;
+      double DS = lam * (1.0 + lam * lam) * SL_KB * d.temperature / SL_HBAR;
+      double sig = sqrt(2.0 * DS / fabs(0.25 * d.dt));
+      E[3 * t] = D2(df_from_double(sig * g.x));
+      E[3 * t + 1] = D2(df_from_double(sig * g.y));
+      E[3 * t + 2] = D2(df_from_double(sig * g.z));
+    }
   }
-  if (d.rotation == SL_ROT_CAYLEY) rotate_cayley(w, tau, s);
-  else rotate_exact(w, tau, s);
-  d.s[i] = s;
-}
+  __syncthreads();
 
-// One colour pass: thread = sector of this colour, its spins in order.
-__global__ void k_sweep_pass(SlDev d, int colour, int backward, int subpass, double tau) {
-  int qi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (qi >= d.s8) return;
-  int q = colour * d.s8 + qi;
-  int a = d.sec_start[q], b = d.sec_start[q + 1];
-  long long step = d.ctrl->step;
-  if (!backward) {
-    for (int i = a; i < b; ++i) update_spin(d, i, tau, subpass, step);
-  } else {
-    for (int i = b - 1; i >= a; --i) update_spin(d, i, tau, subpass, step);
+  // phase 2
+  const int q = q0 + threadIdx.x;
+  if (q < q1) {
+    const int sa = d.sec_start[q], sb = d.sec_start[q + 1];
+    const int m = sb - sa;
+    const df ih = F2(d.inv_hbar_f);
+    for (int c = 0; c < m; ++c) {
+      const int i = backward ? sb - 1 - c : sa + c;
+      const int t = i - a0;
+      const float2 f0 = H[3 * t], f1 = H[3 * t + 1], f2 = H[3 * t + 2];
+      float hx = f0.x, lx = f0.y, hy = f1.x, ly = f1.y, hz = f2.x, lz = f2.y;
+      float gx = 0.0f, kx = 0.0f, gy = 0.0f, ky = 0.0f, gz = 0.0f, kz = 0.0f;
+      const int ni = fits ? sh_in[t] : d.exin[i];
+      const int nstage = fits ? min(ni, kin) : 0;
+      // all staged loads first, two interleaved accumulators
+      int uu[SW_MAXIN];
+      float2 JJ[SW_MAXIN];
+#pragma unroll
+      for (int k = 0; k < SW_MAXIN; ++k) {
+        if (k < nstage) {
+          uu[k] = sh_iu[t * SW_MAXIN + k];
+          JJ[k] = sh_ij[t * SW_MAXIN + k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < SW_MAXIN; ++k) {
+        if (k < nstage) {
+          const int u = uu[k];
+          const df J = F2(JJ[k]);
+          const float2 sx = S[3 * u], sy = S[3 * u + 1], sz = S[3 * u + 2];
+          if (k & 1) {
+            acc_prod(gx, kx, J, F2(sx)); acc_prod(gy, ky, J, F2(sy)); acc_prod(gz, kz, J, F2(sz));
+          } else {
+            acc_prod(hx, lx, J, F2(sx)); acc_prod(hy, ly, J, F2(sy)); acc_prod(hz, lz, J, F2(sz));
+          }
+        }
+      }
+      for (int k = nstage; k < ni; ++k) {   // lists not staged in shared memory
+        const size_t e = (size_t)k * n + i;
+        const int u = d.exj[e] - a0;
+        const df J = F2(d.exJ[e]);
+        acc_prod(hx, lx, J, F2(S[3 * u]));
+        acc_prod(hy, ly, J, F2(S[3 * u + 1]));
+        acc_prod(hz, lz, J, F2(S[3 * u + 2]));
+      }
+      df3 w;
+      w.x = df_mul(df_add(acc_done(hx, lx), acc_done(gx, kx)), ih);
+      w.y = df_mul(df_add(acc_done(hy, ly), acc_done(gy, ky)), ih);
+      w.z = df_mul(df_add(acc_done(hz, lz), acc_done(gz, kz)), ih);
+      df3 s;
+      s.x = F2(S[3 * t]); s.y = F2(S[3 * t + 1]); s.z = F2(S[3 * t + 2]);
+      if (bath) {
+        // Eq. sLLG as ds/dt = Om x s, Om = (w + eta + lambda s x w) / (1 + lambda^2)
+        df3 sxw = cross3(s, w);
+        const df lam = F2(d.lam_f), inv = F2(d.inv1pl2_f);
+        if (noise) {
+          w.x = df_add(w.x, F2(E[3 * t]));
+          w.y = df_add(w.y, F2(E[3 * t + 1]));
+          w.z = df_add(w.z, F2(E[3 * t + 2]));
+        }
+        w.x = df_mul(df_add(w.x, df_mul(lam, sxw.x)), inv);
+        w.y = df_mul(df_add(w.y, df_mul(lam, sxw.y)), inv);
+        w.z = df_mul(df_add(w.z, df_mul(lam, sxw.z)), inv);
+      }
+      const df3 inc = rot_increment(w, s, tau, d.rotation == SL_ROT_CAYLEY);
+      S[3 * t] = D2(df_add(s.x, inc.x));
+      S[3 * t + 1] = D2(df_add(s.y, inc.y));
+      S[3 * t + 2] = D2(df_add(s.z, inc.z));
+      H[3 * t] = D2(inc.x);
+      H[3 * t + 1] = D2(inc.y);
+      H[3 * t + 2] = D2(inc.z);
+    }
+  }
+  __syncthreads();
+
+  // phase 3
+  for (int t = threadIdx.x; t < na; t += blockDim.x) {
+    const int i = a0 + t;
+    double4_32a s = d.s[i];
+    s.x += df_to_double(F2(H[3 * t]));
+    s.y += df_to_double(F2(H[3 * t + 1]));
+    s.z += df_to_double(F2(H[3 * t + 2]));
+    d.s[i] = s;
+    store_spin_split(d, i, s);
   }
 }
 
@@ -167,7 +393,7 @@ __global__ void k_kick(SlDev d, double h) {
   d.v[k] = v;
 }
 
-// r += dt v and the largest displacement since the last rebuild.
+// r += dt v, the largest displacement since the last rebuild, split copy of r.
 __global__ void k_drift(SlDev d) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   double m = 0.0;
@@ -175,6 +401,7 @@ __global__ void k_drift(SlDev d) {
     double4_32a r = d.r[k], v = d.v[k], b = d.rb[k];
     r.x = fma(d.dt, v.x, r.x); r.y = fma(d.dt, v.y, r.y); r.z = fma(d.dt, v.z, r.z);
     d.r[k] = r;
+    store_pos_split(d, k, r);
     double x = r.x - b.x, y = r.y - b.y, z = r.z - b.z;
     m = x * x + y * y + z * z;
     if (!(m == m) || !(fabs(r.x) + fabs(r.y) + fabs(r.z) < 1e300)) sl_set_error(d.ctrl, SL_ERR_NONFINITE);
@@ -200,62 +427,97 @@ __global__ void k_decide(SlDev d) {
 }
 
 // Exchange table at the current positions (recomputed after every drift,
-// Sec. 3): J_ij and J'_ij e_ij (e_ij = (r_j - r_i)/r_ij), zero beyond ex_rc.
+// Sec. 3), Eq. BSfunction: J = 4 alpha x (1 - gamma x) e^{-x}, x = r^2/delta^2,
+// and J'(r)/r = 8 alpha/delta^2 e^{-x} (1 - 2 gamma x - x + gamma x^2); the
+// table holds J and J'(r) e_ij = (J'(r)/r) (r_j - r_i), zero beyond the cutoff.
 __global__ void k_jtable(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
-  double4_32a ri = d.r[i];
-  int ne = d.exn[i];
-  size_t base = (size_t)i * d.max_ex;
-  double id2 = 1.0 / (d.ex_delta * d.ex_delta);
+  const p3 pi = load_pos(d, i);
+  const int ne = d.exn[i];
+  const size_t n = (size_t)d.n;
+  const df ix = F2(d.ex_ix_f), a4 = F2(d.ex_4a_f), g = F2(d.ex_g_f), a8 = F2(d.ex_8ad2_f);
+  const df rc2 = F2(d.ex_rc2_f);
   for (int k = 0; k < ne; ++k) {
-    int j = d.exj[base + k];
-    double3 dd = sl_min_image(d, ri, d.r[j]);
-    double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
-    double J = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
-    if (r2 < d.ex_rc2) {
-      double x = r2 * id2;
-      double e = exp(-x);
-      J = 4.0 * d.ex_alpha * x * (1.0 - d.ex_gamma * x) * e;
-      // J'(r)/r = 8 alpha / delta^2 e^{-x} (1 - 2 g x - x + g x^2)
-      double dJr = 8.0 * d.ex_alpha * id2 * e * (1.0 - 2.0 * d.ex_gamma * x - x + d.ex_gamma * x * x);
-      gx = dJr * dd.x; gy = dJr * dd.y; gz = dJr * dd.z;
+    const size_t e = (size_t)k * n + i;
+    const int j = d.exj[e];
+    const df3 dd = pair_sep(d, pi, load_pos(d, j));
+    float h = 0.0f, l = 0.0f;
+    acc_prod(h, l, dd.x, dd.x);
+    acc_prod(h, l, dd.y, dd.y);
+    acc_prod(h, l, dd.z, dd.z);
+    const df r2 = acc_done(h, l);
+    df J = df_f(0.0f), gx = df_f(0.0f), gy = df_f(0.0f), gz = df_f(0.0f);
+    if (df_lt(r2, rc2)) {
+      const df x = df_mul(r2, ix);
+      const df ex = df_exp(df_neg(x));
+      const df gxm = df_mul(g, x);                                   // gamma x
+      J = df_mul(df_mul(a4, x), df_mul(df_add_f(df_neg(gxm), 1.0f), ex));
+      // 1 - 2 g x - x + g x^2 = 1 - x (1 + 2 g - g x)
+      const df poly = df_add_f(df_neg(df_mul(x, df_add_f(df_sub(df_scale(g, 2.0f), gxm), 1.0f))), 1.0f);
+      const df dJr = df_mul(df_mul(a8, ex), poly);
+      gx = df_mul(dJr, dd.x); gy = df_mul(dJr, dd.y); gz = df_mul(dJr, dd.z);
     }
-    d.exJ[base + k] = J;
-    d.exG[base + k] = make_double4_32a(gx, gy, gz, J);
+    d.exJ[e] = D2(J);
+    d.exGh[e] = make_float4(gx.hi, gy.hi, gz.hi, J.hi);
+    d.exGl[e] = make_float4(gx.lo, gy.lo, gz.lo, J.lo);
   }
 }
 
-// F_i = sum_j V'(r) e_ij - sum_j J'_ij (s_i.s_j) e_ij, then optionally
-// v += (dt/2) F / m (the closing half-kick).
-__global__ void k_force(SlDev d, int kick) {
+// Morse part of the force, from positions only: F_i = sum_j V'(r) e_ij with
+// V'(r)/r = 2 a D0 e (1 - e) / r, e = exp(-a (r - r0)) (Eq. p_advance as
+// -dH/dr_i).  Stored as (hi, lo) floats.
+__global__ void k_morse(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
-  double4_32a ri = d.r[i];
-  double fx = 0.0, fy = 0.0, fz = 0.0;
-  int nm = d.mn[i];
-  double c2 = 2.0 * d.m_alpha * d.m_D0;
+  const p3 pi = load_pos(d, i);
+  float fxh = 0.0f, fxl = 0.0f, fyh = 0.0f, fyl = 0.0f, fzh = 0.0f, fzl = 0.0f;
+  const int nm = d.mn[i];
+  const df na = F2(d.m_nalpha_f), r0 = F2(d.m_r0_f), c2 = F2(d.m_c2_f), rc2 = F2(d.m_rc2_f);
   for (int k = 0; k < nm; ++k) {
-    int j = d.mj[(size_t)k * d.n + i];
-    double3 dd = sl_min_image(d, ri, d.r[j]);
-    double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
-    if (r2 < d.m_rc2) {
-      double rinv = rsqrt(r2);
-      double r = r2 * rinv;
-      double e = exp(-d.m_alpha * (r - d.m_r0));
-      double c = c2 * e * (1.0 - e) * rinv;   // V'(r)/r
-      fx = fma(c, dd.x, fx); fy = fma(c, dd.y, fy); fz = fma(c, dd.z, fz);
-    }
+    const int j = d.mj[(size_t)k * d.n + i];
+    const df3 dd = pair_sep(d, pi, load_pos(d, j));
+    float h = 0.0f, l = 0.0f;
+    acc_prod(h, l, dd.x, dd.x);
+    acc_prod(h, l, dd.y, dd.y);
+    acc_prod(h, l, dd.z, dd.z);
+    const df r2 = acc_done(h, l);
+    if (!df_lt(r2, rc2)) continue;
+    const df rinv = df_rsqrt(r2);
+    const df r = df_mul(r2, rinv);
+    const df e = df_exp(df_mul(na, df_sub(r, r0)));
+    const df c = df_mul(df_mul(c2, rinv), df_mul(e, df_add_f(df_neg(e), 1.0f)));
+    acc_prod(fxh, fxl, c, dd.x);
+    acc_prod(fyh, fyl, c, dd.y);
+    acc_prod(fzh, fzl, c, dd.z);
   }
-  double4_32a si = d.s[i];
-  int ne = d.exn[i];
-  size_t base = (size_t)i * d.max_ex;
+  const df fx = acc_done(fxh, fxl), fy = acc_done(fyh, fyl), fz = acc_done(fzh, fzl);
+  d.fmh[i] = make_float4(fx.hi, fy.hi, fz.hi, 0.0f);
+  d.fml[i] = make_float4(fx.lo, fy.lo, fz.lo, 0.0f);
+}
+
+// F_i = F_morse,i - sum_j J'_ij (s_i.s_j) e_ij, stored in FP64; then
+// optionally v += (dt/2) F / m (the closing half-kick).
+__global__ void k_exch_kick(SlDev d, int kick) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const float4 mh = d.fmh[i], ml = d.fml[i];
+  float fxh = mh.x, fxl = ml.x, fyh = mh.y, fyl = ml.y, fzh = mh.z, fzl = ml.z;
+  const df3 si = load_spin(d, i);
+  const int ne = d.exn[i];
+  const size_t n = (size_t)d.n;
   for (int k = 0; k < ne; ++k) {
-    double4_32a g = d.exG[base + k];
-    double4_32a sj = d.s[d.exj[base + k]];
-    double sij = si.x * sj.x + si.y * sj.y + si.z * sj.z;
-    fx = fma(-sij, g.x, fx); fy = fma(-sij, g.y, fy); fz = fma(-sij, g.z, fz);
+    const size_t e = (size_t)k * n + i;
+    const float4 gh = d.exGh[e], gl = d.exGl[e];
+    const df3 sj = load_spin(d, d.exj[e]);
+    const df nsij = df_neg(dot3(si, sj));
+    acc_prod(fxh, fxl, nsij, df_make(gh.x, gl.x));
+    acc_prod(fyh, fyl, nsij, df_make(gh.y, gl.y));
+    acc_prod(fzh, fzl, nsij, df_make(gh.z, gl.z));
   }
+  const double fx = df_to_double(acc_done(fxh, fxl));
+  const double fy = df_to_double(acc_done(fyh, fyl));
+  const double fz = df_to_double(acc_done(fzh, fzl));
   d.F[i] = make_double4_32a(fx, fy, fz, 0.0);
   if (kick) {
     double c = 0.5 * d.dt * d.acc;
@@ -267,58 +529,111 @@ __global__ void k_force(SlDev d, int kick) {
 
 __global__ void k_end_step(SlDev d) { d.ctrl->step += 1; }
 
-void launch_half_op(const SlDev& d, cudaStream_t st, double h, int subpass0) {
-  int g = grid_for(d.s8);
-  double tau = 0.5 * h;
-  for (int c = 0; c < 8; ++c) k_sweep_pass<<<g, SL_BLOCK, 0, st>>>(d, c, 0, subpass0, tau);
-  for (int c = 7; c >= 0; --c) k_sweep_pass<<<g, SL_BLOCK, 0, st>>>(d, c, 1, subpass0 + 1, tau);
+void launch_half_op(const SlDev& d, cudaStream_t st, int subpass0) {
+  int g = (d.s8 + SW_SPB - 1) / SW_SPB;
+  size_t sm = sweep_smem_bytes(d.temperature > 0.0);
+  for (int c = 0; c < 8; ++c) k_sweep_pass<<<g, SW_THREADS, sm, st>>>(d, c, 0, subpass0);
+  for (int c = 7; c >= 0; --c) k_sweep_pass<<<g, SW_THREADS, sm, st>>>(d, c, 1, subpass0 + 1);
+}
+
+// omega of every atom in caller order (device out [n][3]), FP64.
+__global__ void k_omega_all(SlDev d, double* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  double hx = d.zee[0], hy = d.zee[1], hz = d.zee[2];
+  for (int q = 0; q < d.exn[k]; ++q) {
+    const size_t e = (size_t)q * d.n + k;
+    float2 J2 = d.exJ[e];
+    double J = double_from_float(J2.x) + double_from_float(J2.y);
+    double4_32a sj = d.s[d.exj[e]];
+    hx = fma(J, sj.x, hx); hy = fma(J, sj.y, hy); hz = fma(J, sj.z, hz);
+  }
+  const double ih = 1.0 / SL_HBAR;
+  size_t id = (size_t)d.perm[k];
+  out[3 * id] = hx * ih; out[3 * id + 1] = hy * ih; out[3 * id + 2] = hz * ih;
+}
+
+// Split copies of r and s for every atom (after init, set_state, or a
+// rebuild when `only_if_rebuild` is set).
+__global__ void k_split_all(SlDev d, int only_if_rebuild) {
+  if (only_if_rebuild && !d.ctrl->need_rebuild) return;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= d.n) return;
+  store_pos_split(d, k, d.r[k]);
+  store_spin_split(d, k, d.s[k]);
 }
 
 }  // namespace
+
+// Allow the sweep's dynamic shared memory (above the 48 KB default).
+int sl_prepare_kernels() {
+  return cudaFuncSetAttribute(k_sweep_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sweep_smem_bytes(true)) == cudaSuccess ? SL_OK : SL_ERR_CUDA;
+}
+
+int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild) {
+  k_split_all<<<grid_for(d.n), SL_BLOCK, 0, st>>>(d, only_if_rebuild);
+  return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
+}
 
 // Exchange table and forces at the current state (after init/rebuild/set_state).
 int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick) {
   int gn = grid_for(d.n);
   k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
-  k_force<<<gn, SL_BLOCK, 0, st>>>(d, kick);
+  k_morse<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_exch_kick<<<gn, SL_BLOCK, 0, st>>>(d, kick);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 
-int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels) {
+int sl_launch_step(const SlDev& d, const SlStreams& ss, SlPhaseMark mark, void* user, int* kernels) {
   int gn = grid_for(d.n);
+  cudaStream_t st = ss.main;
   const int lat = !d.fix_lattice;
   int nk = 0;
-  auto phase = [&](int ph, int end) { if (mark) mark(user, ph, end); };
+  auto phase = [&](int ph, int end, cudaStream_t s) { if (mark) mark(user, ph, end, s); };
   if (lat) {
-    phase(SL_PHASE_KICK, 0);
+    phase(SL_PHASE_KICK, 0, st);
     k_kick<<<gn, SL_BLOCK, 0, st>>>(d, 0.5 * d.dt);
-    phase(SL_PHASE_KICK, 1);
+    phase(SL_PHASE_KICK, 1, st);
     nk += 1;
   }
-  phase(SL_PHASE_SPIN1, 0);
-  launch_half_op(d, st, 0.5 * d.dt, 0);
-  phase(SL_PHASE_SPIN1, 1);
+  phase(SL_PHASE_SPIN1, 0, st);
+  launch_half_op(d, st, 0);
+  phase(SL_PHASE_SPIN1, 1, st);
   nk += 16;
   if (lat) {
-    phase(SL_PHASE_DRIFT, 0);
+    phase(SL_PHASE_DRIFT, 0, st);
     k_drift<<<gn, SL_BLOCK, 0, st>>>(d);
     k_decide<<<1, 1, 0, st>>>(d);
     int e = sl_launch_rebuild(d, st);
     if (e) return e;
-    phase(SL_PHASE_DRIFT, 1);
-    phase(SL_PHASE_JTABLE, 0);
+    phase(SL_PHASE_DRIFT, 1, st);
+    phase(SL_PHASE_JTABLE, 0, st);
     k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
-    phase(SL_PHASE_JTABLE, 1);
+    phase(SL_PHASE_JTABLE, 1, st);
     nk += 2 + SL_REBUILD_KERNELS + 1;
+    // Morse forces depend on positions only: optionally run them beside the
+    // second spin half-op
+    cudaStream_t ms = d.overlap_morse ? ss.side : st;
+    if (d.overlap_morse) {
+      cudaEventRecord(ss.fork, st);
+      cudaStreamWaitEvent(ss.side, ss.fork, 0);
+    }
+    phase(SL_PHASE_MORSE, 0, ms);
+    k_morse<<<gn, SL_BLOCK, 0, ms>>>(d);
+    phase(SL_PHASE_MORSE, 1, ms);
+    if (d.overlap_morse) cudaEventRecord(ss.join, ss.side);
+    nk += 1;
   }
-  phase(SL_PHASE_SPIN2, 0);
-  launch_half_op(d, st, 0.5 * d.dt, 2);
-  phase(SL_PHASE_SPIN2, 1);
+  phase(SL_PHASE_SPIN2, 0, st);
+  launch_half_op(d, st, 2);
+  phase(SL_PHASE_SPIN2, 1, st);
   nk += 16;
   if (lat) {
-    phase(SL_PHASE_FORCE, 0);
-    k_force<<<gn, SL_BLOCK, 0, st>>>(d, 1);
-    phase(SL_PHASE_FORCE, 1);
+    if (d.overlap_morse) cudaStreamWaitEvent(st, ss.join, 0);
+    phase(SL_PHASE_EXCH, 0, st);
+    k_exch_kick<<<gn, SL_BLOCK, 0, st>>>(d, 1);
+    phase(SL_PHASE_EXCH, 1, st);
     nk += 1;
   }
   k_end_step<<<1, 1, 0, st>>>(d);
@@ -326,17 +641,6 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
   if (kernels) *kernels = nk;
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
-
-// omega of every atom in caller order (device out [n][3]).
-namespace {
-__global__ void k_omega_all(SlDev d, double* out) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n) return;
-  double3 w = omega_of(d, k);
-  int id = d.perm[k];
-  out[3 * (size_t)id] = w.x; out[3 * (size_t)id + 1] = w.y; out[3 * (size_t)id + 2] = w.z;
-}
-}  // namespace
 
 int sl_launch_omega_all(const SlDev& d, double* out, cudaStream_t st) {
   k_omega_all<<<grid_for(d.n), SL_BLOCK, 0, st>>>(d, out);
