@@ -40,7 +40,8 @@ SAMPLE_CELLS = 16
 # sine or cosine as 20 (bcc at 6 A: 64 Morse pairs, 14 exchange pairs).
 MORSE_PAIR_FLOPS = 3 + 5 + 10 + 2 + 20 + 3 + 10 + 6      # dr, r^2, sqrt, arg, exp, V'/r, accumulate
 EXCH_FORCE_FLOPS = 5 + 6                                # s_i.s_j, accumulate
-JTABLE_PAIR_FLOPS = 3 + 5 + 10 + 2 + 20 + 12 + 10 + 3   # dr, r^2, sqrt, x, exp, J and J'/r, e_ij
+JTABLE_PAIR_FLOPS = 3 + 5 + 2 + 20 + 6                  # dr, r^2, x, exp, J
+EXCH_DJ_FLOPS = 10 + 5                                  # J'/r from the shared exponential
 ROTATION_FLOPS = 14 * 6 + 3 + 5 + 20 + 20 + 9 + 12 + 6  # field, u, |w|, sincos, A/B, cross, increment
 PHASE_FLOPS_PER_ATOM = {
     "kick": 6,
@@ -48,8 +49,7 @@ PHASE_FLOPS_PER_ATOM = {
     "drift_rebuild": 6 + 8,
     "exchange_table": 14 * JTABLE_PAIR_FLOPS,
     "spin_half_op_2": 2 * ROTATION_FLOPS,
-    "morse_force": 64 * MORSE_PAIR_FLOPS,
-    "exchange_force_kick": 14 * EXCH_FORCE_FLOPS + 6,
+    "force_kick": 64 * MORSE_PAIR_FLOPS + 14 * (20 + EXCH_DJ_FLOPS + EXCH_FORCE_FLOPS) + 6,
 }
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 pipe, nominal at 2070 MHz
 # The kernels run the FP64-accurate arithmetic as double-float on the FP32

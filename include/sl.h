@@ -34,9 +34,7 @@
  *    atom) in the caller's atom order.  The library never frees or retains
  *    caller memory beyond the call, except the workspace given to sl_init,
  *    which it uses until sl_destroy.
- *  - All work is ordered on the CUDA stream given to sl_init (inside a step
- *    the Morse forces run on a private stream forked from and joined back to
- *    it).  Only
+ *  - All work is ordered on the CUDA stream given to sl_init.  Only
  *    sl_init, sl_energy, sl_magnetization, sl_status, sl_counters and the
  *    *_host copies block the calling thread.
  *  - Return values are SL_OK (0) or a negative SL_ERR_* code.  Errors raised
@@ -80,9 +78,10 @@ typedef struct sl_params {
                                   skin is exceeded in between) */
   int32_t morse_shift_energy;  /* 1: report V(r) - V(rc) per pair (forces unchanged) */
   int32_t max_ex_neighbors;    /* exchange list capacity per atom (0: 24) */
-  int32_t max_morse_neighbors; /* Morse list capacity per atom (0: 128) */
-  int32_t schedule;            /* bit 0: run the Morse forces (positions only) on a
-                                  second stream beside the second spin half-op */
+  int32_t max_morse_neighbors; /* Morse list capacity per atom (0: 128); the list
+                                  holds the exchange neighbours first, so values not
+                                  above max_ex_neighbors are raised to it + 1 */
+  int32_t reserved0;           /* must be 0 */
   double box[3];               /* orthorhombic periodic box edges */
   double mass_amu;
   double mu_s_muB;             /* magnetic moment, units of mu_B */
@@ -101,7 +100,8 @@ typedef struct sl_params {
 typedef struct sl_ctx sl_ctx;  /* opaque, owned by the library */
 
 /* Bytes of device workspace sl_init needs for these parameters.
- * Errors: SL_ERR_ARG (NULL pointer, n_atoms < 1, non-positive mass),
+ * Errors: SL_ERR_ARG (NULL pointer, n_atoms < 1, non-positive mass,
+ * morse_rc_A < ex_rc_A, max_ex_neighbors above 64),
  * SL_ERR_BOX (box too small for the cutoffs or for 2 sectors per edge). */
 int sl_workspace_bytes(const sl_params* params, size_t* bytes);
 
@@ -170,14 +170,13 @@ int sl_get_order(sl_ctx* ctx, int32_t* order_dev, int32_t colour_start[9], int32
 int sl_counters(sl_ctx* ctx, int64_t out[8]);
 
 /* Per-phase timing.  With enable = 1, sl_step launches each step's kernels
- * directly (no graph) and records a CUDA event pair around each phase on the
- * stream the phase runs on: 0 half-kick, 1 first spin half-op (16 colour
- * passes), 2 drift + rebuild check (+ rebuild), 3 exchange table, 4 second
- * spin half-op, 5 Morse forces (on the library's side stream, concurrent with
- * phase 4), 6 magneto-elastic forces + closing half-kick.  sl_get_timing
- * synchronises and returns ms[k] = total milliseconds and count[k] = timed
- * launches of phase k since timing was enabled (entry 7 is 0).  sl_set_timing
- * resets the totals. */
+ * directly (no graph) and records a CUDA event pair on the context's stream
+ * around each phase: 0 half-kick, 1 first spin half-op (16 colour passes),
+ * 2 drift + rebuild check (+ rebuild), 3 exchange table, 4 second spin
+ * half-op, 5 forces (Morse + magneto-elastic) + closing half-kick.
+ * sl_get_timing synchronises and returns ms[k] = total milliseconds and
+ * count[k] = timed launches of phase k since timing was enabled (entries 6,
+ * 7 are 0).  sl_set_timing resets the totals. */
 int sl_set_timing(sl_ctx* ctx, int32_t enable);
 int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
 

@@ -27,8 +27,7 @@ EXPORTS = (
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
     "sl_get_timing", "sl_magnetization_static", "sl_status", "sl_strerror", "sl_destroy",
 )
-PHASES = ("kick", "spin_half_op_1", "drift_rebuild", "exchange_table", "spin_half_op_2", "morse_force",
-          "exchange_force_kick")
+PHASES = ("kick", "spin_half_op_1", "drift_rebuild", "exchange_table", "spin_half_op_2", "force_kick")
 
 
 class sl_params(ctypes.Structure):
@@ -36,7 +35,7 @@ class sl_params(ctypes.Structure):
         ("n_atoms", ctypes.c_int32), ("rotation", ctypes.c_int32), ("fix_lattice", ctypes.c_int32),
         ("rebuild_every", ctypes.c_int32), ("morse_shift_energy", ctypes.c_int32),
         ("max_ex_neighbors", ctypes.c_int32), ("max_morse_neighbors", ctypes.c_int32),
-        ("schedule", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
         ("box", ctypes.c_double * 3), ("mass_amu", ctypes.c_double), ("mu_s_muB", ctypes.c_double),
         ("H_tesla", ctypes.c_double * 3), ("dt_ps", ctypes.c_double),
         ("ex_alpha_eV", ctypes.c_double), ("ex_gamma", ctypes.c_double), ("ex_delta_A", ctypes.c_double),
@@ -115,7 +114,6 @@ def make_params(p: dict) -> sl_params:
     q.morse_shift_energy = int(p.get("morse_shift_energy", 1))
     q.max_ex_neighbors = int(p.get("max_ex_neighbors", 0))
     q.max_morse_neighbors = int(p.get("max_morse_neighbors", 0))
-    q.schedule = int(p.get("schedule", 0))
     for a in range(3):
         q.box[a] = float(p["box"][a])
         q.H_tesla[a] = float(p["H_tesla"][a])

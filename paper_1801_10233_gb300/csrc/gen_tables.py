@@ -34,8 +34,8 @@ def hexf(v):
 
 def main():
     out = ["// Generated by gen_tables.py: constants of the double-float exp.", "#pragma once", ""]
-    out.append("// 2^(j/64) = hi + lo, j = 0..63")
-    out.append("__device__ __constant__ float2 kSlExp2Table[64] = {")
+    out.append("// 2^(j/64) = hi + lo, j = 0..63 (global memory: lanes index it independently)")
+    out.append("__device__ const float2 kSlExp2Table[64] = {")
     for j in range(64):
         x = Decimal(2) ** (Decimal(j) / Decimal(64))
         hi, lo = split2(x)

@@ -13,8 +13,6 @@ struct sl_ctx {
   SlDev d;
   cudaStream_t stream;
   cudaStream_t cap;         // private stream for graph capture
-  cudaStream_t side;        // private stream for work that overlaps the sweep
-  cudaEvent_t fork, join;
   cudaGraphExec_t graph;
   int graph_ok;
   int device;
@@ -60,6 +58,7 @@ int validate(const sl_params* p) {
   if (!p) return SL_ERR_ARG;
   if (p->n_atoms < 1 || !(p->mass_amu > 0.0) || !(p->skin_A >= 0.0)) return SL_ERR_ARG;
   if (!(p->ex_rc_A > 0.0) || !(p->morse_rc_A > 0.0) || !(p->ex_delta_A > 0.0)) return SL_ERR_ARG;
+  if (!(p->morse_rc_A >= p->ex_rc_A)) return SL_ERR_ARG;   // Morse list holds the exchange list
   if (p->rotation != SL_ROT_RODRIGUES && p->rotation != SL_ROT_CAYLEY) return SL_ERR_ARG;
   if (p->rebuild_every < 0 || p->max_ex_neighbors < 0 || p->max_morse_neighbors < 0) return SL_ERR_ARG;
   if (p->max_ex_neighbors > SL_MAX_EX_CAP) return SL_ERR_ARG;
@@ -126,8 +125,8 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
   }
   d.max_ex = p->max_ex_neighbors ? p->max_ex_neighbors : 24;
   d.max_m = p->max_morse_neighbors ? p->max_morse_neighbors : 128;
+  if (d.max_m <= d.max_ex) d.max_m = d.max_ex + 1;
   d.rotation = p->rotation;
-  d.overlap_morse = p->schedule & 1;
   d.fix_lattice = p->fix_lattice;
   d.rebuild_every = p->rebuild_every;
   d.morse_shift = p->morse_shift_energy;
@@ -180,11 +179,10 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
   size_t o_cnt = L.take<int>(d.nsec), o_start = L.take<int>(d.nsec + 1), o_fill = L.take<int>(d.nsec);
   size_t o_exj = L.take<int>(nn * d.max_ex), o_exn = L.take<int>(nn), o_exin = L.take<int>(nn);
   size_t o_exJ = L.take<float2>(nn * d.max_ex);
-  size_t o_exGh = L.take<float4>(nn * d.max_ex), o_exGl = L.take<float4>(nn * d.max_ex);
+  size_t o_p0 = L.take<float2>(3 * nn), o_p1 = L.take<float2>(3 * nn);
   size_t o_rh = L.take<float4>(nn), o_rm = L.take<float4>(nn), o_rl = L.take<float4>(nn);
   size_t o_sdf = L.take<float4>(2 * nn);
   size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
-  size_t o_fmh = L.take<float4>(nn), o_fml = L.take<float4>(nn);
   size_t o_mj = L.take<int>(nn * d.max_m), o_mn = L.take<int>(nn);
   size_t o_part = L.take<double>((size_t)NBLK_RED * 16);
   size_t o_stage = L.take<double>(nn * 9);
@@ -199,11 +197,10 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
     d.sec_count = (int*)(base + o_cnt); d.sec_start = (int*)(base + o_start); d.sec_fill = (int*)(base + o_fill);
     d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn); d.exin = (int*)(base + o_exin);
     d.exJ = (float2*)(base + o_exJ);
-    d.exGh = (float4*)(base + o_exGh); d.exGl = (float4*)(base + o_exGl);
+    d.hpart[0] = (float2*)(base + o_p0); d.hpart[1] = (float2*)(base + o_p1);
     d.rh = (float4*)(base + o_rh); d.rm = (float4*)(base + o_rm); d.rl = (float4*)(base + o_rl);
     d.sdf = (float4*)(base + o_sdf);
     d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);
-    d.fmh = (float4*)(base + o_fmh); d.fml = (float4*)(base + o_fml);
     d.mj = (int*)(base + o_mj); d.mn = (int*)(base + o_mn);
     d.part = (double*)(base + o_part);
     d.stage = (double*)(base + o_stage);
@@ -274,22 +271,13 @@ void drop_graph(sl_ctx* c) {
   c->graph_ok = 0;
 }
 
-SlStreams streams(const sl_ctx* c, cudaStream_t main) {
-  SlStreams ss;
-  ss.main = main;
-  ss.side = c->side;
-  ss.fork = c->fork;
-  ss.join = c->join;
-  return ss;
-}
-
 // Capture one step's launch sequence into a graph on a private stream.
 int build_graph(sl_ctx* c) {
   drop_graph(c);
   if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SL_ERR_CUDA;
-  int e = sl_launch_step(c->d, streams(c, c->cap), nullptr, nullptr, &c->kernels_per_step);
+  int e = sl_launch_step(c->d, c->cap, nullptr, nullptr, &c->kernels_per_step);
   cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
   if (e || ce != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return SL_ERR_CUDA; }
   cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
@@ -365,10 +353,7 @@ int sl_init(const sl_params* params, const double* r, const double* v, const dou
   plan(params, c->d, (char*)workspace);
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SL_ERR_CUDA; }
-  if (sl_prepare_kernels() != SL_OK ||
-      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+  if (sl_prepare_kernels() != SL_OK) {
     sl_destroy(c);
     return SL_ERR_CUDA;
   }
@@ -398,7 +383,7 @@ int sl_step(sl_ctx* c, int32_t n_steps) {
   if (c->timing) {
     // direct launches with an event pair around each phase
     for (int k = 0; k < n_steps; ++k) {
-      int e = sl_launch_step(c->d, streams(c, c->stream), mark_phase, c, &c->kernels_per_step);
+      int e = sl_launch_step(c->d, c->stream, mark_phase, c, &c->kernels_per_step);
       if (e) { c->sticky = e; return e; }
       if (c->ev_used > 4096 && fold_timing(c)) return cuda_err(c);
     }
@@ -409,7 +394,7 @@ int sl_step(sl_ctx* c, int32_t n_steps) {
     if (c->graph_ok) {
       if (cudaGraphLaunch(c->graph, c->stream) != cudaSuccess) return cuda_err(c);
     } else {
-      int e = sl_launch_step(c->d, streams(c, c->stream), nullptr, nullptr, &c->kernels_per_step);
+      int e = sl_launch_step(c->d, c->stream, nullptr, nullptr, &c->kernels_per_step);
       if (e) { c->sticky = e; return e; }
     }
   }
@@ -617,11 +602,7 @@ void sl_destroy(sl_ctx* c) {
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   drop_graph(c);
-  if (c->side) cudaStreamSynchronize(c->side);
   if (c->cap) cudaStreamDestroy(c->cap);
-  if (c->side) cudaStreamDestroy(c->side);
-  if (c->fork) cudaEventDestroy(c->fork);
-  if (c->join) cudaEventDestroy(c->join);
   for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   delete c;
 }

@@ -116,11 +116,14 @@ __global__ void k_rb_copyback(SlDev d) {
 }
 
 // Full Verlet lists (both directions) from the sectors around each atom:
-// exchange list r < ex_rc + skin (atom-major), Morse list r < morse_rc + skin
-// (neighbour-major).  Neighbour order is the fixed loop order, so rebuilds
-// are deterministic.  Each exchange list is then reordered stably so that
-// neighbours in the atom's own sector come first (exin[i] of them): the
-// sweep sums the other sectors' field in parallel and only these in sequence.
+// exchange list r < ex_rc + skin, Morse list r < morse_rc + skin, both
+// neighbour-major.  Neighbour order is the fixed loop order, so rebuilds are
+// deterministic.  Each exchange list is reordered stably so that neighbours
+// in the atom's own sector come first (exin[i] of them): the sweep sums the
+// other sectors' field in parallel and only these in sequence.  The Morse
+// list starts with the exchange list (same order) followed by the
+// Morse-only neighbours, so the force loop takes the magneto-elastic branch
+// only for its first exn[i] entries.  Requires morse_rc >= ex_rc.
 __global__ void k_rb_nbr(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,21 +147,22 @@ __global__ void k_rb_nbr(SlDev d) {
           if (j == i) continue;
           double3 dd = sl_min_image(d, ri, d.r[j]);
           double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
-          if (r2 < d.list_m2) {
-            if (cm < d.max_m) d.mj[(size_t)cm * d.n + i] = j;
-            ++cm;
-          }
           if (r2 < d.list_ex2) {
             if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;
             ++ce;
+          } else if (r2 < d.list_m2) {
+            // Morse-only entries go after a gap of max_ex rows for now
+            if (d.max_ex + cm < d.max_m) d.mj[(size_t)(d.max_ex + cm) * d.n + i] = j;
+            ++cm;
           }
         }
       }
     }
   }
-  if (cm > d.max_m || ce > d.max_ex) sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW);
-  d.mn[i] = min(cm, d.max_m);
+  if (d.max_ex + cm > d.max_m || ce > d.max_ex) sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW);
   const int ne = min(ce, d.max_ex);
+  const int nmo = min(cm, d.max_m - d.max_ex);
+  d.mn[i] = ne + nmo;
   d.exn[i] = ne;
   // stable partition: same-sector neighbours first
   const int qi = d.secq[i];
@@ -174,7 +178,11 @@ __global__ void k_rb_nbr(SlDev d) {
   }
   for (int k = 0; k < nout; ++k) col[(nin + k) * n] = tmp[k];
   d.exin[i] = nin;
-  atomicMax(&d.ctrl->max_m_seen, cm);
+  // Morse list: the exchange list, then the Morse-only entries moved down
+  int* mcol = d.mj + i;
+  for (int k = 0; k < nmo; ++k) mcol[(ne + k) * n] = mcol[(d.max_ex + k) * n];
+  for (int k = 0; k < ne; ++k) mcol[k * n] = col[k * n];
+  atomicMax(&d.ctrl->max_m_seen, ce + cm);
   atomicMax(&d.ctrl->max_ex_seen, ce);
 }
 

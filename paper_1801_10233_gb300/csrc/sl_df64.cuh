@@ -108,7 +108,7 @@ __device__ __forceinline__ df df_exp(df x) {
   df r3 = df_mul(r2, r);
   df p = df_add(df_add(r, df_scale(r2, 0.5f)), df_mul(r3, c));
   int j = n & 63, m = n >> 6;
-  float2 t = kSlExp2Table[j];
+  float2 t = __ldg(kSlExp2Table + j);
   df T = df_make(t.x, t.y);
   df e = df_add(T, df_mul(T, p));
   float s = __int_as_float((127 + m) << 23);  // 2^m, |m| < 126

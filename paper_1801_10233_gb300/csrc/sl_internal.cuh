@@ -37,7 +37,6 @@ struct SlDev {
   int mx, my, mz;           // sector layers searched for Morse neighbours (or n)
   int max_ex, max_m;
   int rotation, fix_lattice, rebuild_every, morse_shift;
-  int overlap_morse;
   double box[3], inv_box[3], edge[3];
   double dt;
   double zee[3];            // mu_s mu_B H (eV)
@@ -70,11 +69,11 @@ struct SlDev {
   // neighbour lists
   int *exj, *exn, *exin;    // [max_ex][n] neighbour-major (same-sector entries first), counts
   float2 *exJ;              // [max_ex][n] J_ij (hi, lo) at current r
-  float4 *exGh, *exGl;      // [max_ex][n] (J'_ij e_ij, J_ij) hi and lo parts
-  float4 *fmh, *fml;        // Morse force (hi, lo) per atom, from positions only
   int *mj, *mn;             // [max_m][n] neighbour-major, counts
   // sweep scratch for blocks whose atoms exceed shared memory: [3 n] each
   float2 *hbuf, *sbuf, *ebuf;
+  // partial external fields precomputed for the next colour pass (ping-pong)
+  float2 *hpart[2];         // [3 n] each
   // reduction partials
   double *part;             // [nblk_red][16]
   int nblk_red;
@@ -129,16 +128,10 @@ int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild);
 int sl_prepare_kernels();
 // Phases of one step, for optional event timing.
 enum { SL_PHASE_KICK = 0, SL_PHASE_SPIN1 = 1, SL_PHASE_DRIFT = 2, SL_PHASE_JTABLE = 3, SL_PHASE_SPIN2 = 4,
-       SL_PHASE_MORSE = 5, SL_PHASE_EXCH = 6, SL_NPHASE = 7 };
+       SL_PHASE_FORCE = 5, SL_NPHASE = 6 };
 #define SL_REBUILD_KERNELS 10
 typedef void (*SlPhaseMark)(void* user, int phase, int end, cudaStream_t st);
-// The step's two streams: the Morse forces (positions only) run on `side`
-// while the second spin half-op runs on `main`.
-struct SlStreams {
-  cudaStream_t main, side;
-  cudaEvent_t fork, join;
-};
-int sl_launch_step(const SlDev& d, const SlStreams& ss, SlPhaseMark mark, void* user, int* kernels);
+int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels);
 int sl_launch_observables(const SlDev& d, cudaStream_t st);
 int sl_launch_force_rebuild_flag(const SlDev& d, cudaStream_t st);
 int sl_launch_omega_all(const SlDev& d, double* out, cudaStream_t st);

@@ -26,8 +26,10 @@ struct p3 {
   f3 x, y, z;
 };
 
+// Positions, lists and tables are read-only in every kernel that gathers
+// them; their loads go through the read-only path and may be issued early.
 __device__ __forceinline__ p3 load_pos(const SlDev& d, int j) {
-  float4 h = d.rh[j], m = d.rm[j], l = d.rl[j];
+  float4 h = __ldg(d.rh + j), m = __ldg(d.rm + j), l = __ldg(d.rl + j);
   p3 p;
   p.x.h = h.x; p.x.m = m.x; p.x.l = l.x;
   p.y.h = h.y; p.y.m = m.y; p.y.l = l.y;
@@ -36,7 +38,7 @@ __device__ __forceinline__ p3 load_pos(const SlDev& d, int j) {
 }
 
 __device__ __forceinline__ df3 load_spin(const SlDev& d, int j) {
-  float4 h = d.sdf[2 * (size_t)j], l = d.sdf[2 * (size_t)j + 1];
+  float4 h = __ldg(d.sdf + 2 * (size_t)j), l = __ldg(d.sdf + 2 * (size_t)j + 1);
   df3 s;
   s.x = df_make(h.x, l.x); s.y = df_make(h.y, l.y); s.z = df_make(h.z, l.z);
   return s;
@@ -176,22 +178,28 @@ __device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau,
 }
 
 // ---------------------------------------------------------------------------
-// One colour pass.  A block takes SW_SPB consecutive sectors of the colour
+// One colour pass.  Block b takes SW_SPB consecutive sectors of the colour
 // (their atoms are contiguous in the sorted order):
-//   phase 1 (all threads, parallel over atoms): the exchange field from
-//           atoms outside the atom's own sector (fixed during this pass), the
-//           noise of the spin bath, and a copy of the atom's same-sector
-//           neighbour list (local index, J) into shared memory;
-//   phase 2 (one thread per sector, sequential): for each spin in order, add
-//           the field of the already-updated spins of its own sector, form
-//           omega and rotate -- shared memory only;
-//   phase 3 (parallel over atoms): add each increment to the FP64 spin once
-//           and refresh its float split.
+//   phase 1 (all warps, parallel over atoms): the exchange field from atoms
+//           outside the atom's own sector -- either in full, or as the
+//           partial field precomputed during the previous pass plus the
+//           contribution of the colour that pass updated -- the noise of the
+//           spin bath, and a copy of the atom's same-sector list (local
+//           index, J) into shared memory;
+//   phase 2 (warp 0, one lane per sector, sequential): for each spin in
+//           order, add the field of the already-updated spins of its own
+//           sector, form omega and rotate -- shared memory only.
+//           Meanwhile warps 1.. precompute, for block b's sectors of the
+//           next colour in the sweep, the external field of every
+//           neighbour not of this pass's colour (those spins are final for
+//           this pass);
+//   phase 3 (all warps, parallel over atoms): add each increment to the
+//           FP64 spin once and refresh its float split.
 // Blocks with more than SW_MAXA atoms use workspace scratch and read their
 // lists from global memory.
 // ---------------------------------------------------------------------------
 constexpr int SW_SPB = 32;
-constexpr int SW_THREADS = 256;
+constexpr int SW_THREADS = 192;
 constexpr int SW_MAXA = 384;
 constexpr int SW_MAXIN = 12;   // same-sector neighbours staged per atom
 constexpr int SW_BATCH = 4;    // external neighbours gathered per batch
@@ -204,7 +212,47 @@ size_t sweep_smem_bytes(bool noise) {
          (size_t)SW_MAXIN * SW_MAXA * sizeof(short) + (size_t)SW_MAXA * sizeof(int);
 }
 
-__global__ void __launch_bounds__(SW_THREADS, 3) k_sweep_pass(SlDev d, int colour, int backward, int subpass) {
+// (h, l) += sum of J_ij s_j over external entries [k0, k1) of atom i whose
+// neighbour index lies inside [lo, hi) (take = 1) or outside it (take = 0).
+__device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1, int lo, int hi, int take,
+                                          float& hx, float& lx, float& hy, float& ly, float& hz, float& lz) {
+  const size_t n = (size_t)d.n;
+  for (int kb = k0; kb < k1; kb += SW_BATCH) {
+    int jj[SW_BATCH];
+    float2 JJ[SW_BATCH];
+    float4 vh[SW_BATCH], vl[SW_BATCH];
+    bool use[SW_BATCH];
+#pragma unroll
+    for (int q = 0; q < SW_BATCH; ++q) {
+      use[q] = false;
+      if (kb + q < k1) {
+        const size_t e = (size_t)(kb + q) * n + i;
+        jj[q] = __ldg(d.exj + e);
+        JJ[q] = __ldg(d.exJ + e);
+        use[q] = ((jj[q] >= lo && jj[q] < hi) == (take != 0));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < SW_BATCH; ++q) {
+      if (use[q]) {
+        vh[q] = __ldg(d.sdf + 2 * (size_t)jj[q]);
+        vl[q] = __ldg(d.sdf + 2 * (size_t)jj[q] + 1);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < SW_BATCH; ++q) {
+      if (use[q]) {
+        const df J = F2(JJ[q]);
+        acc_prod(hx, lx, J, df_make(vh[q].x, vl[q].x));
+        acc_prod(hy, ly, J, df_make(vh[q].y, vl[q].y));
+        acc_prod(hz, lz, J, df_make(vh[q].z, vl[q].z));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SW_THREADS, 3)
+k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, int next_colour, int pin, int pout) {
   extern __shared__ float2 smem[];
   const bool noise = d.temperature > 0.0;
   const bool bath = d.lambda != 0.0 || d.temperature != 0.0;
@@ -215,9 +263,9 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sweep_pass(SlDev d, int colou
   short* sh_iu = (short*)(sh_ij + SW_MAXIN * SW_MAXA);
   int* sh_in = (int*)(sh_iu + SW_MAXIN * SW_MAXA);
 
-  const int qbeg = colour * d.s8, qend = qbeg + d.s8;
-  const int q0 = qbeg + blockIdx.x * SW_SPB;
-  const int q1 = min(q0 + SW_SPB, qend);
+  const int s8 = d.s8;
+  const int q0 = colour * s8 + blockIdx.x * SW_SPB;
+  const int q1 = min(q0 + SW_SPB, (colour + 1) * s8);
   const int a0 = d.sec_start[q0], a1 = d.sec_start[q1];
   const int na = a1 - a0;
   const bool fits = na <= SW_MAXA;
@@ -228,58 +276,40 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sweep_pass(SlDev d, int colou
   const df tau = F2(d.tau_f);
   const size_t n = (size_t)d.n;
   const int kin = min(SW_MAXIN, d.max_ex);
+  const float2* P = pin >= 0 ? d.hpart[pin] : nullptr;
+  int plo = 0, phi = 0;
+  if (P) { plo = d.sec_start[prev_colour * s8]; phi = d.sec_start[(prev_colour + 1) * s8]; }
 
   // phase 1
   for (int t = threadIdx.x; t < na; t += blockDim.x) {
     const int i = a0 + t;
-    const float4 s4h = d.sdf[2 * (size_t)i], s4l = d.sdf[2 * (size_t)i + 1];
-    const int ni = d.exin[i], ne = d.exn[i];
+    const float4 s4h = __ldg(d.sdf + 2 * (size_t)i), s4l = __ldg(d.sdf + 2 * (size_t)i + 1);
+    const int ni = __ldg(d.exin + i), ne = __ldg(d.exn + i);
+    float2 p0, p1, p2;
+    if (P) { p0 = __ldg(P + 3 * (size_t)i); p1 = __ldg(P + 3 * (size_t)i + 1); p2 = __ldg(P + 3 * (size_t)i + 2); }
+    if (fits) {
+      // read-only loads: free to run ahead of the shared-memory stores
+      const int m = min(ni, kin);
+#pragma unroll 4
+      for (int k = 0; k < m; ++k) {
+        const size_t e = (size_t)k * n + i;
+        sh_iu[t * SW_MAXIN + k] = (short)(__ldg(d.exj + e) - a0);
+        sh_ij[t * SW_MAXIN + k] = __ldg(d.exJ + e);
+      }
+      sh_in[t] = ni;
+    }
     S[3 * t] = make_float2(s4h.x, s4l.x);
     S[3 * t + 1] = make_float2(s4h.y, s4l.y);
     S[3 * t + 2] = make_float2(s4h.z, s4l.z);
-    if (fits) {
-      sh_in[t] = ni;
-      const int m = min(ni, kin);
-#pragma unroll
-      for (int k = 0; k < SW_MAXIN; ++k) {
-        if (k < m) {
-          const size_t e = (size_t)k * n + i;
-          sh_iu[t * SW_MAXIN + k] = (short)(d.exj[e] - a0);
-          sh_ij[t * SW_MAXIN + k] = d.exJ[e];
-        }
-      }
-    }
-    float hx = d.zee_f[0].x, lx = d.zee_f[0].y;
-    float hy = d.zee_f[1].x, ly = d.zee_f[1].y;
-    float hz = d.zee_f[2].x, lz = d.zee_f[2].y;
-    for (int k0 = ni; k0 < ne; k0 += SW_BATCH) {
-      int jj[SW_BATCH];
-      float2 JJ[SW_BATCH];
-      float4 vh[SW_BATCH], vl[SW_BATCH];
-#pragma unroll
-      for (int q = 0; q < SW_BATCH; ++q) {
-        if (k0 + q < ne) {
-          const size_t e = (size_t)(k0 + q) * n + i;
-          jj[q] = d.exj[e];
-          JJ[q] = d.exJ[e];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < SW_BATCH; ++q) {
-        if (k0 + q < ne) {
-          vh[q] = d.sdf[2 * (size_t)jj[q]];
-          vl[q] = d.sdf[2 * (size_t)jj[q] + 1];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < SW_BATCH; ++q) {
-        if (k0 + q < ne) {
-          const df J = F2(JJ[q]);
-          acc_prod(hx, lx, J, df_make(vh[q].x, vl[q].x));
-          acc_prod(hy, ly, J, df_make(vh[q].y, vl[q].y));
-          acc_prod(hz, lz, J, df_make(vh[q].z, vl[q].z));
-        }
-      }
+    float hx, lx, hy, ly, hz, lz;
+    if (P) {
+      hx = p0.x; lx = p0.y; hy = p1.x; ly = p1.y; hz = p2.x; lz = p2.y;
+      ext_field(d, i, ni, ne, plo, phi, 1, hx, lx, hy, ly, hz, lz);
+    } else {
+      hx = d.zee_f[0].x; lx = d.zee_f[0].y;
+      hy = d.zee_f[1].x; ly = d.zee_f[1].y;
+      hz = d.zee_f[2].x; lz = d.zee_f[2].y;
+      ext_field(d, i, ni, ne, 0, 0, 0, hx, lx, hy, ly, hz, lz);
     }
     H[3 * t] = D2(acc_done(hx, lx));
     H[3 * t + 1] = D2(acc_done(hy, ly));
@@ -297,77 +327,92 @@ __global__ void __launch_bounds__(SW_THREADS, 3) k_sweep_pass(SlDev d, int colou
   }
   __syncthreads();
 
-  // phase 2
-  const int q = q0 + threadIdx.x;
-  if (q < q1) {
-    const int sa = d.sec_start[q], sb = d.sec_start[q + 1];
-    const int m = sb - sa;
-    const df ih = F2(d.inv_hbar_f);
-    for (int c = 0; c < m; ++c) {
-      const int i = backward ? sb - 1 - c : sa + c;
-      const int t = i - a0;
-      const float2 f0 = H[3 * t], f1 = H[3 * t + 1], f2 = H[3 * t + 2];
-      float hx = f0.x, lx = f0.y, hy = f1.x, ly = f1.y, hz = f2.x, lz = f2.y;
-      float gx = 0.0f, kx = 0.0f, gy = 0.0f, ky = 0.0f, gz = 0.0f, kz = 0.0f;
-      const int ni = fits ? sh_in[t] : d.exin[i];
-      const int nstage = fits ? min(ni, kin) : 0;
-      // all staged loads first, two interleaved accumulators
-      int uu[SW_MAXIN];
-      float2 JJ[SW_MAXIN];
-#pragma unroll
-      for (int k = 0; k < SW_MAXIN; ++k) {
-        if (k < nstage) {
-          uu[k] = sh_iu[t * SW_MAXIN + k];
-          JJ[k] = sh_ij[t * SW_MAXIN + k];
+  if (threadIdx.x < 32) {
+    // phase 2
+    const int q = q0 + threadIdx.x;
+    if (q < q1) {
+      const int sa = d.sec_start[q], sb = d.sec_start[q + 1];
+      const int m = sb - sa;
+      const df ih = F2(d.inv_hbar_f);
+      for (int c = 0; c < m; ++c) {
+        const int i = backward ? sb - 1 - c : sa + c;
+        const int t = i - a0;
+        const float2 f0 = H[3 * t], f1 = H[3 * t + 1], f2 = H[3 * t + 2];
+        float hx = f0.x, lx = f0.y, hy = f1.x, ly = f1.y, hz = f2.x, lz = f2.y;
+        float gx = 0.0f, kx = 0.0f, gy = 0.0f, ky = 0.0f, gz = 0.0f, kz = 0.0f;
+        const int ni = fits ? sh_in[t] : d.exin[i];
+        const int nstage = fits ? min(ni, kin) : 0;
+        int k = 0;
+        for (; k + 1 < nstage; k += 2) {   // two interleaved accumulators
+          const int u0 = sh_iu[t * SW_MAXIN + k], u1 = sh_iu[t * SW_MAXIN + k + 1];
+          const df J0 = F2(sh_ij[t * SW_MAXIN + k]), J1 = F2(sh_ij[t * SW_MAXIN + k + 1]);
+          acc_prod(hx, lx, J0, F2(S[3 * u0]));
+          acc_prod(gx, kx, J1, F2(S[3 * u1]));
+          acc_prod(hy, ly, J0, F2(S[3 * u0 + 1]));
+          acc_prod(gy, ky, J1, F2(S[3 * u1 + 1]));
+          acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
+          acc_prod(gz, kz, J1, F2(S[3 * u1 + 2]));
         }
-      }
-#pragma unroll
-      for (int k = 0; k < SW_MAXIN; ++k) {
         if (k < nstage) {
-          const int u = uu[k];
-          const df J = F2(JJ[k]);
-          const float2 sx = S[3 * u], sy = S[3 * u + 1], sz = S[3 * u + 2];
-          if (k & 1) {
-            acc_prod(gx, kx, J, F2(sx)); acc_prod(gy, ky, J, F2(sy)); acc_prod(gz, kz, J, F2(sz));
-          } else {
-            acc_prod(hx, lx, J, F2(sx)); acc_prod(hy, ly, J, F2(sy)); acc_prod(hz, lz, J, F2(sz));
+          const int u0 = sh_iu[t * SW_MAXIN + k];
+          const df J0 = F2(sh_ij[t * SW_MAXIN + k]);
+          acc_prod(hx, lx, J0, F2(S[3 * u0]));
+          acc_prod(hy, ly, J0, F2(S[3 * u0 + 1]));
+          acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
+        }
+        for (k = nstage; k < ni; ++k) {   // lists not staged in shared memory
+          const size_t e = (size_t)k * n + i;
+          const int u = d.exj[e] - a0;
+          const df J = F2(d.exJ[e]);
+          acc_prod(hx, lx, J, F2(S[3 * u]));
+          acc_prod(hy, ly, J, F2(S[3 * u + 1]));
+          acc_prod(hz, lz, J, F2(S[3 * u + 2]));
+        }
+        df3 w;
+        w.x = df_mul(df_add(acc_done(hx, lx), acc_done(gx, kx)), ih);
+        w.y = df_mul(df_add(acc_done(hy, ly), acc_done(gy, ky)), ih);
+        w.z = df_mul(df_add(acc_done(hz, lz), acc_done(gz, kz)), ih);
+        df3 s;
+        s.x = F2(S[3 * t]); s.y = F2(S[3 * t + 1]); s.z = F2(S[3 * t + 2]);
+        if (bath) {
+          // Eq. sLLG as ds/dt = Om x s, Om = (w + eta + lambda s x w) / (1 + lambda^2)
+          df3 sxw = cross3(s, w);
+          const df lam = F2(d.lam_f), inv = F2(d.inv1pl2_f);
+          if (noise) {
+            w.x = df_add(w.x, F2(E[3 * t]));
+            w.y = df_add(w.y, F2(E[3 * t + 1]));
+            w.z = df_add(w.z, F2(E[3 * t + 2]));
           }
+          w.x = df_mul(df_add(w.x, df_mul(lam, sxw.x)), inv);
+          w.y = df_mul(df_add(w.y, df_mul(lam, sxw.y)), inv);
+          w.z = df_mul(df_add(w.z, df_mul(lam, sxw.z)), inv);
         }
+        const df3 inc = rot_increment(w, s, tau, d.rotation == SL_ROT_CAYLEY);
+        S[3 * t] = D2(df_add(s.x, inc.x));
+        S[3 * t + 1] = D2(df_add(s.y, inc.y));
+        S[3 * t + 2] = D2(df_add(s.z, inc.z));
+        H[3 * t] = D2(inc.x);
+        H[3 * t + 1] = D2(inc.y);
+        H[3 * t + 2] = D2(inc.z);
       }
-      for (int k = nstage; k < ni; ++k) {   // lists not staged in shared memory
-        const size_t e = (size_t)k * n + i;
-        const int u = d.exj[e] - a0;
-        const df J = F2(d.exJ[e]);
-        acc_prod(hx, lx, J, F2(S[3 * u]));
-        acc_prod(hy, ly, J, F2(S[3 * u + 1]));
-        acc_prod(hz, lz, J, F2(S[3 * u + 2]));
-      }
-      df3 w;
-      w.x = df_mul(df_add(acc_done(hx, lx), acc_done(gx, kx)), ih);
-      w.y = df_mul(df_add(acc_done(hy, ly), acc_done(gy, ky)), ih);
-      w.z = df_mul(df_add(acc_done(hz, lz), acc_done(gz, kz)), ih);
-      df3 s;
-      s.x = F2(S[3 * t]); s.y = F2(S[3 * t + 1]); s.z = F2(S[3 * t + 2]);
-      if (bath) {
-        // Eq. sLLG as ds/dt = Om x s, Om = (w + eta + lambda s x w) / (1 + lambda^2)
-        df3 sxw = cross3(s, w);
-        const df lam = F2(d.lam_f), inv = F2(d.inv1pl2_f);
-        if (noise) {
-          w.x = df_add(w.x, F2(E[3 * t]));
-          w.y = df_add(w.y, F2(E[3 * t + 1]));
-          w.z = df_add(w.z, F2(E[3 * t + 2]));
-        }
-        w.x = df_mul(df_add(w.x, df_mul(lam, sxw.x)), inv);
-        w.y = df_mul(df_add(w.y, df_mul(lam, sxw.y)), inv);
-        w.z = df_mul(df_add(w.z, df_mul(lam, sxw.z)), inv);
-      }
-      const df3 inc = rot_increment(w, s, tau, d.rotation == SL_ROT_CAYLEY);
-      S[3 * t] = D2(df_add(s.x, inc.x));
-      S[3 * t + 1] = D2(df_add(s.y, inc.y));
-      S[3 * t + 2] = D2(df_add(s.z, inc.z));
-      H[3 * t] = D2(inc.x);
-      H[3 * t + 1] = D2(inc.y);
-      H[3 * t + 2] = D2(inc.z);
+    }
+  } else if (pout >= 0) {
+    // precompute the next pass's partial external field (all neighbours not
+    // of this pass's colour) for block b's sectors of the next colour
+    const int clo = d.sec_start[colour * s8], chi = d.sec_start[(colour + 1) * s8];
+    const int nq0 = next_colour * s8 + blockIdx.x * SW_SPB;
+    const int nq1 = min(nq0 + SW_SPB, (next_colour + 1) * s8);
+    const int n0 = d.sec_start[nq0], n1 = d.sec_start[nq1];
+    float2* Q = d.hpart[pout];
+    for (int t = threadIdx.x - 32; t < n1 - n0; t += blockDim.x - 32) {
+      const int i = n0 + t;
+      float hx = d.zee_f[0].x, lx = d.zee_f[0].y;
+      float hy = d.zee_f[1].x, ly = d.zee_f[1].y;
+      float hz = d.zee_f[2].x, lz = d.zee_f[2].y;
+      ext_field(d, i, __ldg(d.exin + i), __ldg(d.exn + i), clo, chi, 0, hx, lx, hy, ly, hz, lz);
+      Q[3 * (size_t)i] = make_float2(hx, lx);
+      Q[3 * (size_t)i + 1] = make_float2(hy, ly);
+      Q[3 * (size_t)i + 2] = make_float2(hz, lz);
     }
   }
   __syncthreads();
@@ -426,94 +471,101 @@ __global__ void k_decide(SlDev d) {
   c->maxdisp2_bits = 0ull;
 }
 
-// Exchange table at the current positions (recomputed after every drift,
-// Sec. 3), Eq. BSfunction: J = 4 alpha x (1 - gamma x) e^{-x}, x = r^2/delta^2,
-// and J'(r)/r = 8 alpha/delta^2 e^{-x} (1 - 2 gamma x - x + gamma x^2); the
-// table holds J and J'(r) e_ij = (J'(r)/r) (r_j - r_i), zero beyond the cutoff.
+// Exchange coefficients at the current positions (recomputed after every
+// drift, Sec. 3): J_ij = 4 alpha x (1 - gamma x) e^{-x}, x = r_ij^2/delta^2
+// (Eq. BSfunction), zero beyond the cutoff.
 __global__ void k_jtable(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const p3 pi = load_pos(d, i);
   const int ne = d.exn[i];
   const size_t n = (size_t)d.n;
-  const df ix = F2(d.ex_ix_f), a4 = F2(d.ex_4a_f), g = F2(d.ex_g_f), a8 = F2(d.ex_8ad2_f);
+  const df ix = F2(d.ex_ix_f), a4 = F2(d.ex_4a_f), g = F2(d.ex_g_f);
   const df rc2 = F2(d.ex_rc2_f);
   for (int k = 0; k < ne; ++k) {
     const size_t e = (size_t)k * n + i;
-    const int j = d.exj[e];
+    const int j = __ldg(d.exj + e);
     const df3 dd = pair_sep(d, pi, load_pos(d, j));
     float h = 0.0f, l = 0.0f;
     acc_prod(h, l, dd.x, dd.x);
     acc_prod(h, l, dd.y, dd.y);
     acc_prod(h, l, dd.z, dd.z);
     const df r2 = acc_done(h, l);
-    df J = df_f(0.0f), gx = df_f(0.0f), gy = df_f(0.0f), gz = df_f(0.0f);
+    df J = df_f(0.0f);
     if (df_lt(r2, rc2)) {
       const df x = df_mul(r2, ix);
       const df ex = df_exp(df_neg(x));
-      const df gxm = df_mul(g, x);                                   // gamma x
-      J = df_mul(df_mul(a4, x), df_mul(df_add_f(df_neg(gxm), 1.0f), ex));
-      // 1 - 2 g x - x + g x^2 = 1 - x (1 + 2 g - g x)
-      const df poly = df_add_f(df_neg(df_mul(x, df_add_f(df_sub(df_scale(g, 2.0f), gxm), 1.0f))), 1.0f);
-      const df dJr = df_mul(df_mul(a8, ex), poly);
-      gx = df_mul(dJr, dd.x); gy = df_mul(dJr, dd.y); gz = df_mul(dJr, dd.z);
+      J = df_mul(df_mul(a4, x), df_mul(df_add_f(df_neg(df_mul(g, x)), 1.0f), ex));
     }
     d.exJ[e] = D2(J);
-    d.exGh[e] = make_float4(gx.hi, gy.hi, gz.hi, J.hi);
-    d.exGl[e] = make_float4(gx.lo, gy.lo, gz.lo, J.lo);
   }
 }
 
-// Morse part of the force, from positions only: F_i = sum_j V'(r) e_ij with
-// V'(r)/r = 2 a D0 e (1 - e) / r, e = exp(-a (r - r0)) (Eq. p_advance as
-// -dH/dr_i).  Stored as (hi, lo) floats.
-__global__ void k_morse(SlDev d) {
+// Forces at the current state, Eq. p_advance written as -dH/dr_i:
+//   F_i = sum_j [V'(r) - J'(r) (s_i.s_j)] (r_j - r_i)/r
+// with V'(r)/r = 2 a D0 e (1 - e)/r, e = exp(-a (r - r0)) (Morse, r < morse_rc)
+// and J'(r)/r = 8 alpha/delta^2 e^{-x} (1 - 2 gamma x - x + gamma x^2),
+// x = r^2/delta^2 (Eq. BSfunction, r < ex_rc).  One loop over the Morse list;
+// stored in FP64, then optionally v += (dt/2) F / m (the closing half-kick).
+__device__ __forceinline__ df morse_coeff(df r2, df na, df r0, df c2, df& rinv) {
+  rinv = df_rsqrt(r2);
+  const df r = df_mul(r2, rinv);
+  const df e = df_exp(df_mul(na, df_sub(r, r0)));
+  return df_mul(df_mul(c2, rinv), df_mul(e, df_add_f(df_neg(e), 1.0f)));   // V'(r)/r
+}
+
+__global__ void k_force(SlDev d, int kick) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const p3 pi = load_pos(d, i);
+  const df3 si = load_spin(d, i);
   float fxh = 0.0f, fxl = 0.0f, fyh = 0.0f, fyl = 0.0f, fzh = 0.0f, fzl = 0.0f;
-  const int nm = d.mn[i];
+  const int nm = d.mn[i], ne = d.exn[i];
   const df na = F2(d.m_nalpha_f), r0 = F2(d.m_r0_f), c2 = F2(d.m_c2_f), rc2 = F2(d.m_rc2_f);
-  for (int k = 0; k < nm; ++k) {
-    const int j = d.mj[(size_t)k * d.n + i];
+  const df ix = F2(d.ex_ix_f), g = F2(d.ex_g_f), a8 = F2(d.ex_8ad2_f), xrc2 = F2(d.ex_rc2_f);
+  const float rc2_hi = rc2.hi * 1.0001f;
+  // entries 0..ne-1: exchange neighbours (also inside the Morse cutoff)
+  for (int k = 0; k < ne; ++k) {
+    const int j = __ldg(d.mj + (size_t)k * d.n + i);
     const df3 dd = pair_sep(d, pi, load_pos(d, j));
+    float h = 0.0f, l = 0.0f;
+    acc_prod(h, l, dd.x, dd.x);
+    acc_prod(h, l, dd.y, dd.y);
+    acc_prod(h, l, dd.z, dd.z);
+    const df r2 = acc_done(h, l);
+    df rinv;
+    df c = df_lt(r2, rc2) ? morse_coeff(r2, na, r0, c2, rinv) : df_f(0.0f);
+    if (df_lt(r2, xrc2)) {
+      const df x = df_mul(r2, ix);
+      const df ex = df_exp(df_neg(x));
+      const df gxm = df_mul(g, x);
+      // 1 - 2 g x - x + g x^2 = 1 - x (1 + 2 g - g x)
+      const df poly = df_add_f(df_neg(df_mul(x, df_add_f(df_sub(df_scale(g, 2.0f), gxm), 1.0f))), 1.0f);
+      const df dJr = df_mul(df_mul(a8, ex), poly);
+      c = df_sub(c, df_mul(dJr, dot3(si, load_spin(d, j))));
+    }
+    acc_prod(fxh, fxl, c, dd.x);
+    acc_prod(fyh, fyl, c, dd.y);
+    acc_prod(fzh, fzl, c, dd.z);
+  }
+  // entries ne..nm-1: Morse only
+  for (int k = ne; k < nm; ++k) {
+    const int j = __ldg(d.mj + (size_t)k * d.n + i);
+    const df3 dd = pair_sep(d, pi, load_pos(d, j));
+    // float pre-check: pairs clearly outside the cutoff skip the df test
+    const float r2f = dd.x.hi * dd.x.hi + dd.y.hi * dd.y.hi + dd.z.hi * dd.z.hi;
+    if (r2f > rc2_hi) continue;
     float h = 0.0f, l = 0.0f;
     acc_prod(h, l, dd.x, dd.x);
     acc_prod(h, l, dd.y, dd.y);
     acc_prod(h, l, dd.z, dd.z);
     const df r2 = acc_done(h, l);
     if (!df_lt(r2, rc2)) continue;
-    const df rinv = df_rsqrt(r2);
-    const df r = df_mul(r2, rinv);
-    const df e = df_exp(df_mul(na, df_sub(r, r0)));
-    const df c = df_mul(df_mul(c2, rinv), df_mul(e, df_add_f(df_neg(e), 1.0f)));
+    df rinv;
+    const df c = morse_coeff(r2, na, r0, c2, rinv);
     acc_prod(fxh, fxl, c, dd.x);
     acc_prod(fyh, fyl, c, dd.y);
     acc_prod(fzh, fzl, c, dd.z);
-  }
-  const df fx = acc_done(fxh, fxl), fy = acc_done(fyh, fyl), fz = acc_done(fzh, fzl);
-  d.fmh[i] = make_float4(fx.hi, fy.hi, fz.hi, 0.0f);
-  d.fml[i] = make_float4(fx.lo, fy.lo, fz.lo, 0.0f);
-}
-
-// F_i = F_morse,i - sum_j J'_ij (s_i.s_j) e_ij, stored in FP64; then
-// optionally v += (dt/2) F / m (the closing half-kick).
-__global__ void k_exch_kick(SlDev d, int kick) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n) return;
-  const float4 mh = d.fmh[i], ml = d.fml[i];
-  float fxh = mh.x, fxl = ml.x, fyh = mh.y, fyl = ml.y, fzh = mh.z, fzl = ml.z;
-  const df3 si = load_spin(d, i);
-  const int ne = d.exn[i];
-  const size_t n = (size_t)d.n;
-  for (int k = 0; k < ne; ++k) {
-    const size_t e = (size_t)k * n + i;
-    const float4 gh = d.exGh[e], gl = d.exGl[e];
-    const df3 sj = load_spin(d, d.exj[e]);
-    const df nsij = df_neg(dot3(si, sj));
-    acc_prod(fxh, fxl, nsij, df_make(gh.x, gl.x));
-    acc_prod(fyh, fyl, nsij, df_make(gh.y, gl.y));
-    acc_prod(fzh, fzl, nsij, df_make(gh.z, gl.z));
   }
   const double fx = df_to_double(acc_done(fxh, fxl));
   const double fy = df_to_double(acc_done(fyh, fyl));
@@ -529,11 +581,20 @@ __global__ void k_exch_kick(SlDev d, int kick) {
 
 __global__ void k_end_step(SlDev d) { d.ctrl->step += 1; }
 
+// The 16 passes of a spin half-op: colours 0..7 forward, then 7..0 backward.
+// Pass p reads the partial field written by pass p - 1 (none for p = 0).
 void launch_half_op(const SlDev& d, cudaStream_t st, int subpass0) {
   int g = (d.s8 + SW_SPB - 1) / SW_SPB;
   size_t sm = sweep_smem_bytes(d.temperature > 0.0);
-  for (int c = 0; c < 8; ++c) k_sweep_pass<<<g, SW_THREADS, sm, st>>>(d, c, 0, subpass0);
-  for (int c = 7; c >= 0; --c) k_sweep_pass<<<g, SW_THREADS, sm, st>>>(d, c, 1, subpass0 + 1);
+  int col[16], bwd[16];
+  for (int p = 0; p < 8; ++p) { col[p] = p; bwd[p] = 0; col[15 - p] = p; bwd[15 - p] = 1; }
+  for (int p = 0; p < 16; ++p) {
+    const int prev = p > 0 ? col[p - 1] : -1;
+    const int next = p < 15 ? col[p + 1] : -1;
+    const int pin = p > 0 ? (p - 1) & 1 : -1;
+    const int pout = p < 15 ? p & 1 : -1;
+    k_sweep_pass<<<g, SW_THREADS, sm, st>>>(d, col[p], bwd[p], subpass0 + bwd[p], prev, next, pin, pout);
+  }
 }
 
 // omega of every atom in caller order (device out [n][3]), FP64.
@@ -580,60 +641,45 @@ int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild) {
 int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick) {
   int gn = grid_for(d.n);
   k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
-  k_morse<<<gn, SL_BLOCK, 0, st>>>(d);
-  k_exch_kick<<<gn, SL_BLOCK, 0, st>>>(d, kick);
+  k_force<<<gn, SL_BLOCK, 0, st>>>(d, kick);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 
-int sl_launch_step(const SlDev& d, const SlStreams& ss, SlPhaseMark mark, void* user, int* kernels) {
+int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels) {
   int gn = grid_for(d.n);
-  cudaStream_t st = ss.main;
   const int lat = !d.fix_lattice;
   int nk = 0;
-  auto phase = [&](int ph, int end, cudaStream_t s) { if (mark) mark(user, ph, end, s); };
+  auto phase = [&](int ph, int end) { if (mark) mark(user, ph, end, st); };
   if (lat) {
-    phase(SL_PHASE_KICK, 0, st);
+    phase(SL_PHASE_KICK, 0);
     k_kick<<<gn, SL_BLOCK, 0, st>>>(d, 0.5 * d.dt);
-    phase(SL_PHASE_KICK, 1, st);
+    phase(SL_PHASE_KICK, 1);
     nk += 1;
   }
-  phase(SL_PHASE_SPIN1, 0, st);
+  phase(SL_PHASE_SPIN1, 0);
   launch_half_op(d, st, 0);
-  phase(SL_PHASE_SPIN1, 1, st);
+  phase(SL_PHASE_SPIN1, 1);
   nk += 16;
   if (lat) {
-    phase(SL_PHASE_DRIFT, 0, st);
+    phase(SL_PHASE_DRIFT, 0);
     k_drift<<<gn, SL_BLOCK, 0, st>>>(d);
     k_decide<<<1, 1, 0, st>>>(d);
     int e = sl_launch_rebuild(d, st);
     if (e) return e;
-    phase(SL_PHASE_DRIFT, 1, st);
-    phase(SL_PHASE_JTABLE, 0, st);
+    phase(SL_PHASE_DRIFT, 1);
+    phase(SL_PHASE_JTABLE, 0);
     k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
-    phase(SL_PHASE_JTABLE, 1, st);
+    phase(SL_PHASE_JTABLE, 1);
     nk += 2 + SL_REBUILD_KERNELS + 1;
-    // Morse forces depend on positions only: optionally run them beside the
-    // second spin half-op
-    cudaStream_t ms = d.overlap_morse ? ss.side : st;
-    if (d.overlap_morse) {
-      cudaEventRecord(ss.fork, st);
-      cudaStreamWaitEvent(ss.side, ss.fork, 0);
-    }
-    phase(SL_PHASE_MORSE, 0, ms);
-    k_morse<<<gn, SL_BLOCK, 0, ms>>>(d);
-    phase(SL_PHASE_MORSE, 1, ms);
-    if (d.overlap_morse) cudaEventRecord(ss.join, ss.side);
-    nk += 1;
   }
-  phase(SL_PHASE_SPIN2, 0, st);
+  phase(SL_PHASE_SPIN2, 0);
   launch_half_op(d, st, 2);
-  phase(SL_PHASE_SPIN2, 1, st);
+  phase(SL_PHASE_SPIN2, 1);
   nk += 16;
   if (lat) {
-    if (d.overlap_morse) cudaStreamWaitEvent(st, ss.join, 0);
-    phase(SL_PHASE_EXCH, 0, st);
-    k_exch_kick<<<gn, SL_BLOCK, 0, st>>>(d, 1);
-    phase(SL_PHASE_EXCH, 1, st);
+    phase(SL_PHASE_FORCE, 0);
+    k_force<<<gn, SL_BLOCK, 0, st>>>(d, 1);
+    phase(SL_PHASE_FORCE, 1);
     nk += 1;
   }
   k_end_step<<<1, 1, 0, st>>>(d);
