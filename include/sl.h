@@ -117,6 +117,27 @@ int sl_workspace_bytes(const sl_params* params, size_t* bytes);
 int sl_init(const sl_params* params, const double* r, const double* v, const double* s,
             void* workspace, size_t workspace_bytes, void* cuda_stream, sl_ctx** out);
 
+/* Batches: n_replicas independent systems advanced together, for instance
+ * replicas of different sizes at different bath temperatures.  params[k]
+ * describes replica k; replicas may differ in n_atoms, box, temperature_K
+ * and replica (the noise counter word), and every other field must equal
+ * params[0]'s (SL_ERR_ARG otherwise).  r, v, s (device) hold all replicas'
+ * atoms back to back in replica order, [sum n_atoms][3] doubles.  Each colour
+ * pass of a step covers the sectors of every replica, so one step advances
+ * the whole batch.  sl_workspace_bytes and sl_init are the n_replicas = 1
+ * cases.  Replica k's trajectory is bitwise the one it has alone. */
+int sl_workspace_bytes_batch(const sl_params* params, int32_t n_replicas, size_t* bytes);
+int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, const double* v,
+                  const double* s, void* workspace, size_t workspace_bytes, void* cuda_stream, sl_ctx** out);
+
+/* Number of replicas in the context (SL_ERR_ARG for NULL). */
+int sl_batch_size(sl_ctx* ctx);
+
+/* Per-replica observables: out (host) [n_replicas][8] as sl_energy, and
+ * [n_replicas][4] as sl_magnetization.  Synchronise. */
+int sl_energy_batch(sl_ctx* ctx, double* out);
+int sl_magnetization_batch(sl_ctx* ctx, double* out);
+
 /* Re-assign sectors and rebuild both neighbour lists, the exchange table
  * (J and J' at the current positions, Sec. 3) and the forces now, whatever
  * the displacement.  Stream-ordered. */
@@ -132,10 +153,12 @@ int sl_set_field(sl_ctx* ctx, const double H_tesla[3]);
 
 /* out[8] (host) = E_kin, E_morse, E_exchange, E_zeeman, E_total (eV),
  * T_L (Eq. lattice_temperature, K), T_S (Eq. spin_temperature, K), 0.
- * Pair energies count each unordered pair once.  Synchronises. */
+ * Pair energies count each unordered pair once.  For a batch: energies summed
+ * over the replicas, temperatures over all atoms.  Synchronises. */
 int sl_energy(sl_ctx* ctx, double out[8]);
 
-/* out[4] (host) = Mx, My, Mz, |M| with M = (1/N) sum_i s_i.  Synchronises. */
+/* out[4] (host) = Mx, My, Mz, |M| with M = (1/N) sum_i s_i (all atoms of a
+ * batch).  Synchronises. */
 int sl_magnetization(sl_ctx* ctx, double out[4]);
 
 /* Copy the state out in caller atom order (device pointers, [n][3]; any of
@@ -161,7 +184,8 @@ int sl_get_omega(sl_ctx* ctx, double* omega);
 
 /* Sweep order: order_dev[k] (device, n int32) = caller index of the k-th
  * atom of the sweep; colour_start[9] (host) = first sweep position of each
- * colour; nsec[3] (host) = sectors per box edge.  Synchronises. */
+ * colour; nsec[3] (host) = sectors per box edge (of replica 0).  In a batch
+ * the order is colour-major across replicas.  Synchronises. */
 int sl_get_order(sl_ctx* ctx, int32_t* order_dev, int32_t colour_start[9], int32_t nsec[3]);
 
 /* out[8] (host) = steps done, rebuilds done, largest exchange-list length

@@ -26,6 +26,7 @@ EXPORTS = (
     "sl_energy", "sl_magnetization", "sl_get_state", "sl_set_state", "sl_get_state_host",
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
     "sl_get_timing", "sl_magnetization_static", "sl_status", "sl_strerror", "sl_destroy",
+    "sl_workspace_bytes_batch", "sl_init_batch", "sl_batch_size", "sl_energy_batch", "sl_magnetization_batch",
 )
 PHASES = ("kick", "spin_half_op_1", "drift_rebuild", "exchange_table", "spin_half_op_2", "force_kick")
 
@@ -82,6 +83,12 @@ def load():
         "sl_get_timing": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "sl_magnetization_static": ([_vp, ctypes.c_int32, _vp, _vp], ctypes.c_int),
         "sl_status": ([_vp], ctypes.c_int),
+        "sl_workspace_bytes_batch": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "sl_init_batch": ([P, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)],
+                          ctypes.c_int),
+        "sl_batch_size": ([_vp], ctypes.c_int),
+        "sl_energy_batch": ([_vp, _dp], ctypes.c_int),
+        "sl_magnetization_batch": ([_vp, _dp], ctypes.c_int),
         "sl_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "sl_destroy": ([_vp], None),
     }
@@ -132,11 +139,21 @@ def make_params(p: dict) -> sl_params:
     return q
 
 
-def workspace_bytes(p: dict) -> int:
+def params_array(ps) -> ctypes.Array:
+    """ctypes array of sl_params for one dict or a list of dicts (a batch)."""
+    ps = [ps] if isinstance(ps, dict) else list(ps)
+    arr = (sl_params * len(ps))()
+    for k, p in enumerate(ps):
+        arr[k] = make_params(p)
+    return arr
+
+
+def workspace_bytes(p) -> int:
+    """Workspace bytes for one system (dict) or a batch (list of dicts)."""
     L = load()
-    q = make_params(p)
+    arr = params_array(p)
     b = ctypes.c_size_t(0)
-    check(L.sl_workspace_bytes(ctypes.byref(q), ctypes.byref(b)), "sl_workspace_bytes")
+    check(L.sl_workspace_bytes_batch(arr, len(arr), ctypes.byref(b)), "sl_workspace_bytes_batch")
     return int(b.value)
 
 

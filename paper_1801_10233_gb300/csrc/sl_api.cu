@@ -9,7 +9,9 @@
 #include "sl_internal.cuh"
 
 struct sl_ctx {
-  sl_params p;
+  sl_params p;              // fields shared by every replica (replica 0's copy)
+  int nrep;
+  std::vector<SlRep> reps;  // host copy of the replica table
   SlDev d;
   cudaStream_t stream;
   cudaStream_t cap;         // private stream for graph capture
@@ -71,6 +73,32 @@ int validate(const sl_params* p) {
   return sector_grid(p, n, e);
 }
 
+// Replicas of a batch may differ in n_atoms, box, temperature_K and replica;
+// every other field must match replica 0.
+int validate_batch(const sl_params* p, int nrep) {
+  if (!p || nrep < 1) return SL_ERR_ARG;
+  long long total = 0;
+  for (int r = 0; r < nrep; ++r) {
+    int e = validate(p + r);
+    if (e) return e;
+    total += p[r].n_atoms;
+    const sl_params& a = p[0];
+    const sl_params& b = p[r];
+    bool same = a.rotation == b.rotation && a.fix_lattice == b.fix_lattice && a.rebuild_every == b.rebuild_every &&
+                a.morse_shift_energy == b.morse_shift_energy && a.max_ex_neighbors == b.max_ex_neighbors &&
+                a.max_morse_neighbors == b.max_morse_neighbors && a.mass_amu == b.mass_amu &&
+                a.mu_s_muB == b.mu_s_muB && a.dt_ps == b.dt_ps && a.ex_alpha_eV == b.ex_alpha_eV &&
+                a.ex_gamma == b.ex_gamma && a.ex_delta_A == b.ex_delta_A && a.ex_rc_A == b.ex_rc_A &&
+                a.morse_D0_eV == b.morse_D0_eV && a.morse_alpha_invA == b.morse_alpha_invA &&
+                a.morse_r0_A == b.morse_r0_A && a.morse_rc_A == b.morse_rc_A && a.skin_A == b.skin_A &&
+                a.lambda == b.lambda && a.seed == b.seed;
+    for (int c = 0; c < 3; ++c) same = same && a.H_tesla[c] == b.H_tesla[c];
+    if (!same) return SL_ERR_ARG;
+  }
+  if (total > 0x7fffffffLL) return SL_ERR_ARG;
+  return SL_OK;
+}
+
 struct Layout {
   size_t off = 0;
   template <class T>
@@ -80,8 +108,6 @@ struct Layout {
     return o;
   }
 };
-
-constexpr int NBLK_RED = 1024;
 
 // x = hi + lo with hi = float(x), lo = float(x - hi): the double-float form of
 // an FP64 scalar (host side).
@@ -105,24 +131,45 @@ void fill_df_constants(SlDev& d) {
   d.tau_f = split_f2(0.25 * d.dt);
 }
 
-// Fill d's scalars and (if base != NULL) its pointers; returns bytes needed.
-size_t plan(const sl_params* p, SlDev& d, char* base) {
+// Fill d's scalars, the replica table and (if base != NULL) d's pointers;
+// returns the workspace bytes needed.
+size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, char* base) {
   std::memset(&d, 0, sizeof(d));
-  int n = p->n_atoms;
-  d.n = n;
-  int ns[3]; double e[3];
-  sector_grid(p, ns, e);
-  d.nx = ns[0]; d.ny = ns[1]; d.nz = ns[2];
-  d.nsec = ns[0] * ns[1] * ns[2];
-  d.s8 = d.nsec / 8;
+  const sl_params* p = ps;
+  reps.assign(nrep, SlRep());
   double reach = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
-  int* mm[3] = {&d.mx, &d.my, &d.mz};
-  for (int a = 0; a < 3; ++a) {
-    d.box[a] = p->box[a];
-    d.inv_box[a] = 1.0 / p->box[a];
-    d.edge[a] = e[a];
-    *mm[a] = (int)std::ceil(reach / e[a]);
+  int atom0 = 0, sec8 = 0, noise = 0;
+  for (int r = 0; r < nrep; ++r) {
+    SlRep& R = reps[r];
+    std::memset(&R, 0, sizeof(R));
+    int ns[3]; double e[3];
+    sector_grid(ps + r, ns, e);
+    R.nx = ns[0]; R.ny = ns[1]; R.nz = ns[2];
+    R.s8 = ns[0] * ns[1] * ns[2] / 8;
+    int* mm[3] = {&R.mx, &R.my, &R.mz};
+    for (int a = 0; a < 3; ++a) {
+      R.box[a] = ps[r].box[a];
+      R.inv_box[a] = 1.0 / ps[r].box[a];
+      R.edge[a] = e[a];
+      *mm[a] = (int)std::ceil(reach / e[a]);
+      split_f3(ps[r].box[a], &R.box_h[a], &R.box_m[a], &R.box_l[a]);
+      R.inv_box_f[a] = (float)(1.0 / ps[r].box[a]);
+    }
+    R.sec8_off = sec8;
+    R.atom0 = atom0;
+    R.natoms = ps[r].n_atoms;
+    R.replica = ps[r].replica;
+    R.temperature = ps[r].temperature_K;
+    if (R.temperature > 0.0) noise = 1;
+    sec8 += R.s8;
+    atom0 += R.natoms;
   }
+  const int n = atom0;
+  d.n = n;
+  d.nrep = nrep;
+  d.s8 = sec8;
+  d.nsec = 8 * sec8;
+  d.any_noise = noise;
   d.max_ex = p->max_ex_neighbors ? p->max_ex_neighbors : 24;
   d.max_m = p->max_morse_neighbors ? p->max_morse_neighbors : 128;
   if (d.max_m <= d.max_ex) d.max_m = d.max_ex + 1;
@@ -146,10 +193,7 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
   d.list_m2 = (p->morse_rc_A + p->skin_A) * (p->morse_rc_A + p->skin_A);
   d.half_skin2 = 0.25 * p->skin_A * p->skin_A;
   d.lambda = p->lambda;
-  d.temperature = p->temperature_K;
   d.seed = p->seed;
-  d.replica = p->replica;
-  d.nblk_red = NBLK_RED;
   d.inv_hbar_f = split_f2(1.0 / SL_HBAR);
   d.m_nalpha_f = split_f2(-p->morse_alpha_invA);
   d.m_r0_f = split_f2(p->morse_r0_A);
@@ -162,10 +206,6 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
   d.ex_rc2_f = split_f2(d.ex_rc2);
   d.lam_f = split_f2(p->lambda);
   d.inv1pl2_f = split_f2(1.0 / (1.0 + p->lambda * p->lambda));
-  for (int a = 0; a < 3; ++a) {
-    split_f3(p->box[a], &d.box_h[a], &d.box_m[a], &d.box_l[a]);
-    d.inv_box_f[a] = (float)(1.0 / p->box[a]);
-  }
   fill_df_constants(d);
 
   Layout L;
@@ -176,15 +216,17 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
   size_t o_tF = L.take<double4_32a>(nn);
   size_t o_perm = L.take<int>(nn), o_rank = L.take<int>(nn), o_secq = L.take<int>(nn);
   size_t o_tsecq = L.take<int>(nn), o_tperm = L.take<int>(nn), o_src = L.take<int>(nn);
+  size_t o_arep = L.take<int>(nn), o_tarep = L.take<int>(nn);
   size_t o_cnt = L.take<int>(d.nsec), o_start = L.take<int>(d.nsec + 1), o_fill = L.take<int>(d.nsec);
   size_t o_exj = L.take<int>(nn * d.max_ex), o_exn = L.take<int>(nn), o_exin = L.take<int>(nn);
   size_t o_exJ = L.take<float2>(nn * d.max_ex);
-  size_t o_p0 = L.take<float2>(3 * nn), o_p1 = L.take<float2>(3 * nn);
   size_t o_rh = L.take<float4>(nn), o_rm = L.take<float4>(nn), o_rl = L.take<float4>(nn);
   size_t o_sdf = L.take<float4>(2 * nn);
   size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
+  size_t o_p0 = L.take<float2>(3 * nn), o_p1 = L.take<float2>(3 * nn);
   size_t o_mj = L.take<int>(nn * d.max_m), o_mn = L.take<int>(nn);
-  size_t o_part = L.take<double>((size_t)NBLK_RED * 16);
+  size_t o_oa = L.take<double>(nn * SL_NOBS), o_or = L.take<double>((size_t)nrep * SL_NOBS);
+  size_t o_reps = L.take<SlRep>((size_t)nrep);
   size_t o_stage = L.take<double>(nn * 9);
   size_t o_ctrl = L.take<SlCtrl>(1);
   if (base) {
@@ -194,15 +236,17 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
     d.tF = (double4_32a*)(base + o_tF);
     d.perm = (int*)(base + o_perm); d.rank = (int*)(base + o_rank); d.secq = (int*)(base + o_secq);
     d.tsecq = (int*)(base + o_tsecq); d.tperm = (int*)(base + o_tperm); d.src = (int*)(base + o_src);
+    d.arep = (int*)(base + o_arep); d.tarep = (int*)(base + o_tarep);
     d.sec_count = (int*)(base + o_cnt); d.sec_start = (int*)(base + o_start); d.sec_fill = (int*)(base + o_fill);
     d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn); d.exin = (int*)(base + o_exin);
     d.exJ = (float2*)(base + o_exJ);
-    d.hpart[0] = (float2*)(base + o_p0); d.hpart[1] = (float2*)(base + o_p1);
     d.rh = (float4*)(base + o_rh); d.rm = (float4*)(base + o_rm); d.rl = (float4*)(base + o_rl);
     d.sdf = (float4*)(base + o_sdf);
     d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);
+    d.hpart[0] = (float2*)(base + o_p0); d.hpart[1] = (float2*)(base + o_p1);
     d.mj = (int*)(base + o_mj); d.mn = (int*)(base + o_mn);
-    d.part = (double*)(base + o_part);
+    d.obs_atom = (double*)(base + o_oa); d.obs_rep = (double*)(base + o_or);
+    d.reps = (const SlRep*)(base + o_reps);
     d.stage = (double*)(base + o_stage);
     d.ctrl = (SlCtrl*)(base + o_ctrl);
   }
@@ -212,7 +256,16 @@ size_t plan(const sl_params* p, SlDev& d, char* base) {
 __global__ void k_load(SlDev d, const double* r, const double* v, const double* s, int identity) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.n) return;
-  if (identity) { d.perm[k] = k; d.rank[k] = k; }
+  if (identity) {
+    d.perm[k] = k;
+    d.rank[k] = k;
+    int lo = 0, hi = d.nrep - 1;   // replica whose caller range holds k
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (d.reps[mid].atom0 <= k) lo = mid; else hi = mid - 1;
+    }
+    d.arep[k] = lo;
+  }
   size_t id = (size_t)d.perm[k];
   if (r) d.r[k] = make_double4_32a(r[3 * id], r[3 * id + 1], r[3 * id + 2], 0.0);
   if (v) d.v[k] = make_double4_32a(v[3 * id], v[3 * id + 1], v[3 * id + 2], 0.0);
@@ -328,29 +381,36 @@ int refresh(sl_ctx* c) {
 
 extern "C" {
 
-int sl_workspace_bytes(const sl_params* params, size_t* bytes) {
+int sl_workspace_bytes_batch(const sl_params* params, int32_t n_replicas, size_t* bytes) {
   if (!bytes) return SL_ERR_ARG;
-  int e = validate(params);
+  int e = validate_batch(params, n_replicas);
   if (e) return e;
   SlDev d;
-  *bytes = plan(params, d, nullptr);
+  std::vector<SlRep> reps;
+  *bytes = plan(params, n_replicas, d, reps, nullptr);
   return SL_OK;
 }
 
-int sl_init(const sl_params* params, const double* r, const double* v, const double* s,
-            void* workspace, size_t workspace_bytes, void* cuda_stream, sl_ctx** out) {
+int sl_workspace_bytes(const sl_params* params, size_t* bytes) {
+  return sl_workspace_bytes_batch(params, 1, bytes);
+}
+
+int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, const double* v,
+                  const double* s, void* workspace, size_t workspace_bytes, void* cuda_stream, sl_ctx** out) {
   if (!out) return SL_ERR_ARG;
   *out = nullptr;
-  int e = validate(params);
+  int e = validate_batch(params, n_replicas);
   if (e) return e;
   if (!r || !v || !s) return SL_ERR_ARG;
   SlDev d;
-  size_t need = plan(params, d, nullptr);
+  std::vector<SlRep> reps;
+  size_t need = plan(params, n_replicas, d, reps, nullptr);
   if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return SL_ERR_WORKSPACE;
   sl_ctx* c = new (std::nothrow) sl_ctx();
   if (!c) return SL_ERR_ARG;
-  c->p = *params;
-  plan(params, c->d, (char*)workspace);
+  c->p = params[0];
+  c->nrep = n_replicas;
+  plan(params, n_replicas, c->d, c->reps, (char*)workspace);
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SL_ERR_CUDA; }
   if (sl_prepare_kernels() != SL_OK) {
@@ -358,6 +418,8 @@ int sl_init(const sl_params* params, const double* r, const double* v, const dou
     return SL_ERR_CUDA;
   }
   cudaMemsetAsync(c->d.ctrl, 0, sizeof(SlCtrl), c->stream);
+  cudaMemcpyAsync((void*)c->d.reps, c->reps.data(), sizeof(SlRep) * n_replicas, cudaMemcpyHostToDevice,
+                  c->stream);
   k_load<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d, r, v, s, 1);
   k_check<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d);
   sl_launch_force_rebuild_flag(c->d, c->stream);
@@ -367,6 +429,13 @@ int sl_init(const sl_params* params, const double* r, const double* v, const dou
   *out = c;
   return SL_OK;
 }
+
+int sl_init(const sl_params* params, const double* r, const double* v, const double* s,
+            void* workspace, size_t workspace_bytes, void* cuda_stream, sl_ctx** out) {
+  return sl_init_batch(params, 1, r, v, s, workspace, workspace_bytes, cuda_stream, out);
+}
+
+int sl_batch_size(sl_ctx* c) { return c ? c->nrep : SL_ERR_ARG; }
 
 int sl_build_neighbors(sl_ctx* c) {
   if (!c) return SL_ERR_ARG;
@@ -441,38 +510,72 @@ int sl_set_field(sl_ctx* c, const double H[3]) {
   return c->sticky;
 }
 
-static int observe(sl_ctx* c, double red[16]) {
+// Per-replica sums of the observable terms, host [nrep][SL_NOBS].
+static int observe(sl_ctx* c, std::vector<double>& red) {
   if (c->sticky) return c->sticky;
   DeviceGuard g(c->device);
   int e = sl_launch_observables(c->d, c->stream);
   if (e) return e;
-  if (cudaMemcpyAsync(red, c->d.ctrl->red, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+  red.assign((size_t)c->nrep * SL_NOBS, 0.0);
+  if (cudaMemcpyAsync(red.data(), c->d.obs_rep, red.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess)
     return cuda_err(c);
   return sync_status(c);
 }
 
-int sl_energy(sl_ctx* c, double out[8]) {
+static void energy_of(const double* q, long long n, double out[8]) {
+  out[0] = q[0]; out[1] = q[1]; out[2] = q[2]; out[3] = q[3];
+  out[4] = q[0] + q[1] + q[2] + q[3];
+  out[5] = n > 0 ? 2.0 * q[0] / (3.0 * (double)n * SL_KB) : 0.0;
+  out[6] = q[8] != 0.0 ? SL_HBAR / (2.0 * SL_KB) * q[7] / q[8] : 0.0;
+  out[7] = 0.0;
+}
+
+static void magnetization_of(const double* q, long long n, double out[4]) {
+  double inv = n > 0 ? 1.0 / (double)n : 0.0;
+  out[0] = q[4] * inv; out[1] = q[5] * inv; out[2] = q[6] * inv;
+  out[3] = std::sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+}
+
+int sl_energy_batch(sl_ctx* c, double* out) {
   if (!c || !out) return SL_ERR_ARG;
-  double red[16];
+  std::vector<double> red;
   int e = observe(c, red);
   if (e) return e;
-  int n = c->d.n;
-  out[0] = red[0]; out[1] = red[1]; out[2] = red[2]; out[3] = red[3];
-  out[4] = red[0] + red[1] + red[2] + red[3];
-  out[5] = 2.0 * red[0] / (3.0 * n * SL_KB);
-  out[6] = red[8] != 0.0 ? SL_HBAR / (2.0 * SL_KB) * red[7] / red[8] : 0.0;
-  out[7] = 0.0;
+  for (int r = 0; r < c->nrep; ++r) energy_of(&red[(size_t)r * SL_NOBS], c->reps[r].natoms, out + 8 * r);
+  return SL_OK;
+}
+
+int sl_magnetization_batch(sl_ctx* c, double* out) {
+  if (!c || !out) return SL_ERR_ARG;
+  std::vector<double> red;
+  int e = observe(c, red);
+  if (e) return e;
+  for (int r = 0; r < c->nrep; ++r) magnetization_of(&red[(size_t)r * SL_NOBS], c->reps[r].natoms, out + 4 * r);
+  return SL_OK;
+}
+
+int sl_energy(sl_ctx* c, double out[8]) {
+  if (!c || !out) return SL_ERR_ARG;
+  std::vector<double> red;
+  int e = observe(c, red);
+  if (e) return e;
+  double q[SL_NOBS] = {0};
+  for (int r = 0; r < c->nrep; ++r)
+    for (int k = 0; k < SL_NOBS; ++k) q[k] += red[(size_t)r * SL_NOBS + k];
+  energy_of(q, c->d.n, out);
   return SL_OK;
 }
 
 int sl_magnetization(sl_ctx* c, double out[4]) {
   if (!c || !out) return SL_ERR_ARG;
-  double red[16];
+  std::vector<double> red;
   int e = observe(c, red);
   if (e) return e;
-  double inv = 1.0 / c->d.n;
-  out[0] = red[4] * inv; out[1] = red[5] * inv; out[2] = red[6] * inv;
-  out[3] = std::sqrt(out[0] * out[0] + out[1] * out[1] + out[2] * out[2]);
+  double q[SL_NOBS] = {0};
+  for (int r = 0; r < c->nrep; ++r)
+    for (int k = 0; k < SL_NOBS; ++k) q[k] += red[(size_t)r * SL_NOBS + k];
+  magnetization_of(q, c->d.n, out);
   return SL_OK;
 }
 
@@ -558,7 +661,7 @@ int sl_get_order(sl_ctx* c, int32_t* order_dev, int32_t colour_start[9], int32_t
       if (cudaMemcpyAsync(colour_start + k, c->d.sec_start + k * c->d.s8, sizeof(int), cudaMemcpyDeviceToHost,
                           c->stream) != cudaSuccess)
         return cuda_err(c);
-  if (nsec) { nsec[0] = c->d.nx; nsec[1] = c->d.ny; nsec[2] = c->d.nz; }
+  if (nsec) { nsec[0] = c->reps[0].nx; nsec[1] = c->reps[0].ny; nsec[2] = c->reps[0].nz; }
   return sync_status(c);
 }
 

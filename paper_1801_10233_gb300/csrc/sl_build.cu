@@ -24,20 +24,21 @@ __global__ void k_rb_zero(SlDev d) {
   }
 }
 
-// Wrap positions into the box and find each atom's sector rank.
+// Wrap positions into their replica's box and find each atom's sector rank.
 __global__ void k_rb_assign(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.n) return;
+  const SlRep& R = d.reps[d.arep[k]];
   double4_32a p = d.r[k];
-  p.x = sl_wrap(p.x, d.box[0]);
-  p.y = sl_wrap(p.y, d.box[1]);
-  p.z = sl_wrap(p.z, d.box[2]);
+  p.x = sl_wrap(p.x, R.box[0]);
+  p.y = sl_wrap(p.y, R.box[1]);
+  p.z = sl_wrap(p.z, R.box[2]);
   d.r[k] = p;
-  int sx = sl_sector_coord(p.x, d.edge[0], d.nx);
-  int sy = sl_sector_coord(p.y, d.edge[1], d.ny);
-  int sz = sl_sector_coord(p.z, d.edge[2], d.nz);
-  int q = sl_sector_rank(d, sx, sy, sz);
+  int sx = sl_sector_coord(p.x, R.edge[0], R.nx);
+  int sy = sl_sector_coord(p.y, R.edge[1], R.ny);
+  int sz = sl_sector_coord(p.z, R.edge[2], R.nz);
+  int q = sl_sector_rank(d, R, sx, sy, sz);
   d.tsecq[k] = q;
   atomicAdd(&d.sec_count[q], 1);
 }
@@ -97,6 +98,7 @@ __global__ void k_rb_gather(SlDev d) {
   d.ts[k] = d.s[o];
   d.tF[k] = d.F[o];
   d.tperm[k] = d.perm[o];
+  d.tarep[k] = d.arep[o];
   d.secq[k] = d.tsecq[o];
 }
 
@@ -113,6 +115,7 @@ __global__ void k_rb_copyback(SlDev d) {
   int id = d.tperm[k];
   d.perm[k] = id;
   d.rank[id] = k;
+  d.arep[k] = d.tarep[k];
 }
 
 // Full Verlet lists (both directions) from the sectors around each atom:
@@ -129,23 +132,24 @@ __global__ void k_rb_nbr(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   double4_32a ri = d.r[i];
+  const SlRep& R = d.reps[d.arep[i]];
   int sx, sy, sz;
-  sl_sector_coords(d, d.secq[i], sx, sy, sz);
-  int lox = (2 * d.mx + 1 >= d.nx) ? 0 : -d.mx, hix = (2 * d.mx + 1 >= d.nx) ? d.nx - 1 : d.mx;
-  int loy = (2 * d.my + 1 >= d.ny) ? 0 : -d.my, hiy = (2 * d.my + 1 >= d.ny) ? d.ny - 1 : d.my;
-  int loz = (2 * d.mz + 1 >= d.nz) ? 0 : -d.mz, hiz = (2 * d.mz + 1 >= d.nz) ? d.nz - 1 : d.mz;
+  sl_sector_coords(d, R, d.secq[i], sx, sy, sz);
+  int lox = (2 * R.mx + 1 >= R.nx) ? 0 : -R.mx, hix = (2 * R.mx + 1 >= R.nx) ? R.nx - 1 : R.mx;
+  int loy = (2 * R.my + 1 >= R.ny) ? 0 : -R.my, hiy = (2 * R.my + 1 >= R.ny) ? R.ny - 1 : R.my;
+  int loz = (2 * R.mz + 1 >= R.nz) ? 0 : -R.mz, hiz = (2 * R.mz + 1 >= R.nz) ? R.nz - 1 : R.mz;
   int ce = 0, cm = 0;
   for (int oz = loz; oz <= hiz; ++oz) {
-    int tz = (sz + oz + 2 * d.nz) % d.nz;
+    int tz = (sz + oz + 2 * R.nz) % R.nz;
     for (int oy = loy; oy <= hiy; ++oy) {
-      int ty = (sy + oy + 2 * d.ny) % d.ny;
+      int ty = (sy + oy + 2 * R.ny) % R.ny;
       for (int ox = lox; ox <= hix; ++ox) {
-        int tx = (sx + ox + 2 * d.nx) % d.nx;
-        int q = sl_sector_rank(d, tx, ty, tz);
+        int tx = (sx + ox + 2 * R.nx) % R.nx;
+        int q = sl_sector_rank(d, R, tx, ty, tz);
         int a = d.sec_start[q], b = d.sec_start[q + 1];
         for (int j = a; j < b; ++j) {
           if (j == i) continue;
-          double3 dd = sl_min_image(d, ri, d.r[j]);
+          double3 dd = sl_min_image(R, ri, d.r[j]);
           double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
           if (r2 < d.list_ex2) {
             if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;

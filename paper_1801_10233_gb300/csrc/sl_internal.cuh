@@ -25,19 +25,32 @@ struct SlCtrl {
   int32_t max_ex_seen;
   int32_t max_m_seen;
   int32_t pad;
-  double red[16];           // final results of the observable reduction
+};
+
+// One system of a batch: its box, sector grid, atom range and spin bath.
+struct SlRep {
+  double box[3], inv_box[3], edge[3];
+  float box_h[3], box_m[3], box_l[3], inv_box_f[3];   // exact 3-float split of the box
+  int nx, ny, nz;           // sectors per edge (even, >= 2)
+  int s8;                   // sectors per colour
+  int mx, my, mz;           // sector layers searched for Morse neighbours
+  int sec8_off;             // this replica's first rank inside each colour block
+  int atom0, natoms;        // atom range in caller order
+  int replica;              // Philox counter word of the spin noise
+  double temperature;       // spin bath temperature (K)
 };
 
 // Everything a kernel needs, passed by value.  Scalars used by the
 // double-float kernels are given as (hi, lo) float pairs split on the host.
+// Sector ranks are global and colour-major: rank = colour * s8 + sec8_off of
+// the replica + rank of the sector within its colour, so one colour pass
+// covers the sectors of every replica.
 struct SlDev {
-  int n;
-  int nsec, s8;             // sectors, sectors per colour
-  int nx, ny, nz;
-  int mx, my, mz;           // sector layers searched for Morse neighbours (or n)
+  int n;                    // atoms of all replicas
+  int nrep;
+  int nsec, s8;             // sectors, sectors per colour (all replicas)
   int max_ex, max_m;
   int rotation, fix_lattice, rebuild_every, morse_shift;
-  double box[3], inv_box[3], edge[3];
   double dt;
   double zee[3];            // mu_s mu_B H (eV)
   double acc;               // FTOA / m
@@ -46,16 +59,19 @@ struct SlDev {
   double m_D0, m_alpha, m_r0, m_rc2, m_vshift;
   double list_ex2, list_m2; // (cutoff + skin)^2
   double half_skin2;
-  double lambda, temperature;
+  double lambda;
+  int any_noise;            // some replica has a bath temperature
   uint64_t seed;
-  int replica;
 
   // double-float constants (hi, lo)
   float2 zee_f[3], inv_hbar_f, tau_f;        // tau = dt/4
   float2 m_nalpha_f, m_r0_f, m_c2_f, m_rc2_f; // -a, r0, 2 a D0, rc^2
   float2 ex_ix_f, ex_4a_f, ex_g_f, ex_8ad2_f, ex_rc2_f;  // 1/delta^2, 4 alpha, gamma, 8 alpha/delta^2, rc^2
   float2 lam_f, inv1pl2_f;                   // lambda, 1/(1 + lambda^2)
-  float box_h[3], box_m[3], box_l[3], inv_box_f[3];
+
+  const SlRep* reps;        // [nrep]
+  int* arep;                // replica of each sorted atom
+  int* tarep;               // rebuild scratch
 
   // state, sector-sorted (FP64, authoritative)
   double4_32a *r, *v, *s, *F, *rb;
@@ -74,22 +90,23 @@ struct SlDev {
   float2 *hbuf, *sbuf, *ebuf;
   // partial external fields precomputed for the next colour pass (ping-pong)
   float2 *hpart[2];         // [3 n] each
-  // reduction partials
-  double *part;             // [nblk_red][16]
-  int nblk_red;
+  // per-atom observables in caller order [n][SL_NOBS], per-replica sums
+  double *obs_atom, *obs_rep;   // [nrep][SL_NOBS]
   // staging for host copies, [n][3] doubles x 3
   double *stage;
   SlCtrl *ctrl;
 };
 
+#define SL_NOBS 10  // Ek, Em, Ex, Ez, Mx, My, Mz, TS numerator, TS denominator, non-finite flag
+
 __device__ __forceinline__ void sl_set_error(SlCtrl* c, int code) { atomicCAS(&c->status, 0, code); }
 
-// Minimum-image separation of a and b (b - a) in an orthorhombic box.
-__device__ __forceinline__ double3 sl_min_image(const SlDev& d, double4_32a a, double4_32a b) {
+// Minimum-image separation of a and b (b - a) in the replica's box.
+__device__ __forceinline__ double3 sl_min_image(const SlRep& R, double4_32a a, double4_32a b) {
   double x = b.x - a.x, y = b.y - a.y, z = b.z - a.z;
-  x -= d.box[0] * rint(x * d.inv_box[0]);
-  y -= d.box[1] * rint(y * d.inv_box[1]);
-  z -= d.box[2] * rint(z * d.inv_box[2]);
+  x -= R.box[0] * rint(x * R.inv_box[0]);
+  y -= R.box[1] * rint(y * R.inv_box[1]);
+  z -= R.box[2] * rint(z * R.inv_box[2]);
   return make_double3(x, y, z);
 }
 
@@ -104,17 +121,17 @@ __device__ __forceinline__ int sl_sector_coord(double xw, double e, int n) {
   return k < 0 ? 0 : (k >= n ? n - 1 : k);
 }
 
-// Canonical sector rank: colours 0..7 in order, sectors of one colour by
-// ascending linear index sx + nx (sy + ny sz).
-__device__ __forceinline__ int sl_sector_rank(const SlDev& d, int sx, int sy, int sz) {
+// Global sector rank: colours 0..7 in order; inside a colour, replicas in
+// order; inside a replica, sectors by ascending linear index sx + nx (sy + ny sz).
+__device__ __forceinline__ int sl_sector_rank(const SlDev& d, const SlRep& R, int sx, int sy, int sz) {
   int c = (sx & 1) + 2 * (sy & 1) + 4 * (sz & 1);
   int hx = sx >> 1, hy = sy >> 1, hz = sz >> 1;
-  return c * d.s8 + hx + (d.nx >> 1) * (hy + (d.ny >> 1) * hz);
+  return c * d.s8 + R.sec8_off + hx + (R.nx >> 1) * (hy + (R.ny >> 1) * hz);
 }
 
-__device__ __forceinline__ void sl_sector_coords(const SlDev& d, int q, int& sx, int& sy, int& sz) {
-  int c = q / d.s8, rem = q - c * d.s8;
-  int hxn = d.nx >> 1, hyn = d.ny >> 1;
+__device__ __forceinline__ void sl_sector_coords(const SlDev& d, const SlRep& R, int q, int& sx, int& sy, int& sz) {
+  int c = q / d.s8, rem = q - c * d.s8 - R.sec8_off;
+  int hxn = R.nx >> 1, hyn = R.ny >> 1;
   int hx = rem % hxn, hy = (rem / hxn) % hyn, hz = rem / (hxn * hyn);
   sx = 2 * hx + (c & 1);
   sy = 2 * hy + ((c >> 1) & 1);

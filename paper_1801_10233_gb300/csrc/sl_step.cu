@@ -44,14 +44,26 @@ __device__ __forceinline__ df3 load_spin(const SlDev& d, int j) {
   return s;
 }
 
-__device__ __forceinline__ df3 pair_sep(const SlDev& d, const p3& a, const p3& b) {
+// The replica's box as exact three-float pieces.
+struct box3 {
+  f3 L[3];
+  float inv[3];
+};
+__device__ __forceinline__ box3 load_box(const SlRep& R) {
+  box3 b;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    b.L[a].h = R.box_h[a]; b.L[a].m = R.box_m[a]; b.L[a].l = R.box_l[a];
+    b.inv[a] = R.inv_box_f[a];
+  }
+  return b;
+}
+
+__device__ __forceinline__ df3 pair_sep(const box3& B, const p3& a, const p3& b) {
   df3 r;
-  f3 L0 = {d.box_h[0], d.box_m[0], d.box_l[0]};
-  f3 L1 = {d.box_h[1], d.box_m[1], d.box_l[1]};
-  f3 L2 = {d.box_h[2], d.box_m[2], d.box_l[2]};
-  r.x = f3_sep(b.x, a.x, L0, d.inv_box_f[0]);
-  r.y = f3_sep(b.y, a.y, L1, d.inv_box_f[1]);
-  r.z = f3_sep(b.z, a.z, L2, d.inv_box_f[2]);
+  r.x = f3_sep(b.x, a.x, B.L[0], B.inv[0]);
+  r.y = f3_sep(b.y, a.y, B.L[1], B.inv[1]);
+  r.z = f3_sep(b.z, a.z, B.L[2], B.inv[2]);
   return r;
 }
 
@@ -254,8 +266,8 @@ __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1,
 __global__ void __launch_bounds__(SW_THREADS, 3)
 k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, int next_colour, int pin, int pout) {
   extern __shared__ float2 smem[];
-  const bool noise = d.temperature > 0.0;
-  const bool bath = d.lambda != 0.0 || d.temperature != 0.0;
+  const bool noise = d.any_noise != 0;
+  const bool bath = d.lambda != 0.0 || noise;
   float2* sh_h = smem;
   float2* sh_s = sh_h + 3 * SW_MAXA;
   float2* sh_e = sh_s + 3 * SW_MAXA;
@@ -315,11 +327,17 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
     H[3 * t + 1] = D2(acc_done(hy, ly));
     H[3 * t + 2] = D2(acc_done(hz, lz));
     if (noise) {
-      // eta ~ N(0, 2 D_S / |tau|), D_S = lambda (1 + lambda^2) k_B T / hbar
-      double3 g = gauss3(d.seed, d.replica, step, subpass, d.perm[i]);
-      double lam = d.lambda;
-      double DS = lam * (1.0 + lam * lam) * SL_KB * d.temperature / SL_HBAR;
-      double sig = sqrt(2.0 * DS / fabs(0.25 * d.dt));
+      // eta ~ N(0, 2 D_S / |tau|), D_S = lambda (1 + lambda^2) k_B T / hbar;
+      // counter (atom id within its replica, step, sub-pass, replica)
+      const SlRep& R = d.reps[__ldg(d.arep + i)];
+      double3 g = make_double3(0.0, 0.0, 0.0);
+      double sig = 0.0;
+      if (R.temperature > 0.0) {
+        g = gauss3(d.seed, R.replica, step, subpass, d.perm[i] - R.atom0);
+        double lam = d.lambda;
+        double DS = lam * (1.0 + lam * lam) * SL_KB * R.temperature / SL_HBAR;
+        sig = sqrt(2.0 * DS / fabs(0.25 * d.dt));
+      }
       E[3 * t] = D2(df_from_double(sig * g.x));
       E[3 * t + 1] = D2(df_from_double(sig * g.y));
       E[3 * t + 2] = D2(df_from_double(sig * g.z));
@@ -478,6 +496,7 @@ __global__ void k_jtable(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const p3 pi = load_pos(d, i);
+  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
   const int ne = d.exn[i];
   const size_t n = (size_t)d.n;
   const df ix = F2(d.ex_ix_f), a4 = F2(d.ex_4a_f), g = F2(d.ex_g_f);
@@ -485,7 +504,7 @@ __global__ void k_jtable(SlDev d) {
   for (int k = 0; k < ne; ++k) {
     const size_t e = (size_t)k * n + i;
     const int j = __ldg(d.exj + e);
-    const df3 dd = pair_sep(d, pi, load_pos(d, j));
+    const df3 dd = pair_sep(B, pi, load_pos(d, j));
     float h = 0.0f, l = 0.0f;
     acc_prod(h, l, dd.x, dd.x);
     acc_prod(h, l, dd.y, dd.y);
@@ -518,6 +537,7 @@ __global__ void k_force(SlDev d, int kick) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const p3 pi = load_pos(d, i);
+  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
   const df3 si = load_spin(d, i);
   float fxh = 0.0f, fxl = 0.0f, fyh = 0.0f, fyl = 0.0f, fzh = 0.0f, fzl = 0.0f;
   const int nm = d.mn[i], ne = d.exn[i];
@@ -527,7 +547,7 @@ __global__ void k_force(SlDev d, int kick) {
   // entries 0..ne-1: exchange neighbours (also inside the Morse cutoff)
   for (int k = 0; k < ne; ++k) {
     const int j = __ldg(d.mj + (size_t)k * d.n + i);
-    const df3 dd = pair_sep(d, pi, load_pos(d, j));
+    const df3 dd = pair_sep(B, pi, load_pos(d, j));
     float h = 0.0f, l = 0.0f;
     acc_prod(h, l, dd.x, dd.x);
     acc_prod(h, l, dd.y, dd.y);
@@ -551,7 +571,7 @@ __global__ void k_force(SlDev d, int kick) {
   // entries ne..nm-1: Morse only
   for (int k = ne; k < nm; ++k) {
     const int j = __ldg(d.mj + (size_t)k * d.n + i);
-    const df3 dd = pair_sep(d, pi, load_pos(d, j));
+    const df3 dd = pair_sep(B, pi, load_pos(d, j));
     // float pre-check: pairs clearly outside the cutoff skip the df test
     const float r2f = dd.x.hi * dd.x.hi + dd.y.hi * dd.y.hi + dd.z.hi * dd.z.hi;
     if (r2f > rc2_hi) continue;
@@ -585,7 +605,7 @@ __global__ void k_end_step(SlDev d) { d.ctrl->step += 1; }
 // Pass p reads the partial field written by pass p - 1 (none for p = 0).
 void launch_half_op(const SlDev& d, cudaStream_t st, int subpass0) {
   int g = (d.s8 + SW_SPB - 1) / SW_SPB;
-  size_t sm = sweep_smem_bytes(d.temperature > 0.0);
+  size_t sm = sweep_smem_bytes(d.any_noise != 0);
   int col[16], bwd[16];
   for (int p = 0; p < 8; ++p) { col[p] = p; bwd[p] = 0; col[15 - p] = p; bwd[15 - p] = 1; }
   for (int p = 0; p < 16; ++p) {

@@ -138,3 +138,24 @@ def replica_batch(n_replicas=256, seed=18012, cell_choices=(8, 12, 16, 20, 24), 
     cells = rng.choice(np.asarray(cell_choices), size=n_replicas)
     temps = t_lo + np.arange(n_replicas) * (t_hi - t_lo) / max(1, n_replicas - 1)
     return [int(c) for c in cells], [float(t) for t in temps]
+
+
+def replica_systems(cells, temps, seed, lam=0.01, **param_overrides):
+    """A batch of bcc-Fe replicas: replica k has cells[k]^3 cells, Maxwell-
+    Boltzmann velocities and a spin bath at temps[k], uniform spins, noise
+    counter word k.  Returns (params list, r, v, s) with the atoms of all
+    replicas back to back."""
+    plist, rs, vs, ss = [], [], [], []
+    for k, (nc, T) in enumerate(zip(cells, temps)):
+        p, r, v, s = bcc_fe_system(nc, int(seed) * 1000 + k, T=T, spins="uniform", **param_overrides)
+        p.update({"lambda": float(lam), "temperature_K": float(T), "seed": int(seed), "replica": k})
+        plist.append(p)
+        rs.append(r); vs.append(v); ss.append(s)
+    return plist, np.concatenate(rs), np.concatenate(vs), np.concatenate(ss)
+
+
+def batch_workload(n_replicas=256, seed=18012, **param_overrides):
+    """The batched workload: n_replicas replicas with sizes drawn by seed from
+    {8, 12, 16, 20, 24}^3 cells and bath temperatures 50..1200 K, lambda 0.01."""
+    cells, temps = replica_batch(n_replicas, seed)
+    return replica_systems(cells, temps, seed, **param_overrides)

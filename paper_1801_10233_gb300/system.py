@@ -24,18 +24,24 @@ def _cuda_f64(x, device):
 
 class System:
     """A system of `params["n_atoms"]` atoms with positions r, velocities v and
-    unit spins s ([N, 3] float64; numpy arrays or tensors, caller order)."""
+    unit spins s ([N, 3] float64; numpy arrays or tensors, caller order).
 
-    def __init__(self, params: dict, r, v, s, device=None, stream: torch.cuda.Stream | None = None):
+    `params` may also be a list of parameter dicts: a batch of independent
+    replicas (sl_init_batch), whose atoms are given back to back in r, v, s."""
+
+    def __init__(self, params, r, v, s, device=None, stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("libsl needs a CUDA GPU")
         self._L = _lib.load()
-        self.params = dict(params)
-        self.n = int(params["n_atoms"])
+        plist = [params] if isinstance(params, dict) else list(params)
+        self.params = dict(plist[0])
+        self.replica_params = [dict(p) for p in plist]
+        self.nrep = len(plist)
+        self.n = int(sum(int(p["n_atoms"]) for p in plist))
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
-        self._p = _lib.make_params(params)
-        nbytes = _lib.workspace_bytes(params)
+        self._p = _lib.params_array(plist)
+        nbytes = _lib.workspace_bytes(plist)
         self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         base = self._ws.data_ptr()
         self._ws_ptr = (base + 255) & ~255
@@ -44,9 +50,9 @@ class System:
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             torch.cuda.current_stream(self.device).synchronize()
-            rc = self._L.sl_init(ctypes.byref(self._p), r.data_ptr(), v.data_ptr(), s.data_ptr(),
-                                 self._ws_ptr, self._ws_bytes, self.stream.cuda_stream, ctypes.byref(h))
-        check(rc, "sl_init")
+            rc = self._L.sl_init_batch(self._p, self.nrep, r.data_ptr(), v.data_ptr(), s.data_ptr(),
+                                       self._ws_ptr, self._ws_bytes, self.stream.cuda_stream, ctypes.byref(h))
+        check(rc, "sl_init_batch")
         self._h = h
 
     # -- lifecycle ---------------------------------------------------------
@@ -86,6 +92,17 @@ class System:
     def magnetization(self) -> np.ndarray:
         out = np.empty(4)
         check(self._L.sl_magnetization(self._h, _lib._arr_ptr(out)), "sl_magnetization")
+        return out
+
+    def energy_per_replica(self) -> np.ndarray:
+        """[n_replicas, 8] as energy() for each replica."""
+        out = np.empty((self.nrep, 8))
+        check(self._L.sl_energy_batch(self._h, _lib._arr_ptr(out)), "sl_energy_batch")
+        return out
+
+    def magnetization_per_replica(self) -> np.ndarray:
+        out = np.empty((self.nrep, 4))
+        check(self._L.sl_magnetization_batch(self._h, _lib._arr_ptr(out)), "sl_magnetization_batch")
         return out
 
     def status(self) -> int:

@@ -89,3 +89,19 @@ def test_init_rejects_bad_arguments_without_gpu(lib):
     assert not h.value
     assert L.sl_step(None, 1) == lib.SL_ERR_ARG
     assert L.sl_status(None) == lib.SL_ERR_ARG
+
+
+def test_batch_validation_on_host(lib):
+    from paper_1801_10233_gb300 import inputs
+    plist, *_ = inputs.replica_systems([5, 6], [100.0, 200.0], seed=3)
+    b2 = lib.workspace_bytes(plist)
+    assert b2 > lib.workspace_bytes(plist[0])
+    bad = [dict(plist[0]), dict(plist[1], dt_ps=2e-4)]       # shared field differs
+    with pytest.raises(lib.SlError) as e:
+        lib.workspace_bytes(bad)
+    assert e.value.code == lib.SL_ERR_ARG
+    L = lib.load()
+    arr = lib.params_array(plist)
+    import ctypes as C
+    size = C.c_size_t(0)
+    assert L.sl_workspace_bytes_batch(arr, 0, C.byref(size)) == lib.SL_ERR_ARG
