@@ -66,7 +66,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=["fe_bcc_64x64x64_nve", "fe_bcc_10x10x10_nve", "fe_bcc_100x100x100_nve",
+                             "fe_bcc_batch256"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the extra per-form measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -161,6 +164,20 @@ def cpu_desc():
     return "unknown"
 
 
+def build_workload(name, rank=0):
+    """(params or params list, r, v, s, description) of a named workload;
+    rank shifts the seeds so replicas on different GPUs differ."""
+    from paper_1801_10233_gb300 import inputs
+    if name == "fe_bcc_batch256":
+        p, r, v, s = inputs.batch_workload(256, seed=18012 + 1000 * rank)
+        return p, r, v, s, ("256 bcc-Fe replicas, sizes drawn from {8,12,16,20,24}^3 cells, Langevin spin "
+                            "bath 50..1200 K (lambda 0.01), lattice NVE, dt 0.1 fs, one batched context")
+    w = inputs.WORKLOADS[name]
+    p, r, v, s = inputs.bcc_fe_system(w["ncells"], w["seed"] + rank, T=w["T"], spins=w["spins"])
+    return p, r, v, s, (f"bcc Fe {w['ncells']}^3 cells ({p['n_atoms']} atoms), Morse + Bethe-Slater exchange + "
+                        f"1 T Zeeman, {w['T']:.0f} K, {w['spins']} spins, NVE, dt 0.1 fs")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -197,10 +214,10 @@ def run_ours(args):
     from paper_1801_10233_gb300 import System, inputs
 
     # every rank runs its own replica (different seed)
-    w = inputs.WORKLOADS[args.workload]
-    p, r, v, s = inputs.bcc_fe_system(w["ncells"], w["seed"] + rank, T=w["T"], spins=w["spins"])
-    n = p["n_atoms"]
+    p, r, v, s, wdesc = build_workload(args.workload, rank)
+    n = int(sum(q["n_atoms"] for q in p)) if isinstance(p, list) else p["n_atoms"]
     sysm = System(p, r, v, s, device=dev)
+    p0 = p[0] if isinstance(p, list) else p
     stream = sysm.stream
     sysm.step(args.warmup)
     torch.cuda.synchronize()
@@ -269,6 +286,25 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e["value"] = world * n * esteps / float(t.item())
 
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms and args.workload == DEFAULT_WORKLOAD:
+        forms = {}
+        for name, steps in (("fe_bcc_batch256", 10), ("fe_bcc_10x10x10_nve", 100)):
+            fp, fr, fv, fs, fdesc = build_workload(name, 0)
+            fn = int(sum(q["n_atoms"] for q in fp)) if isinstance(fp, list) else fp["n_atoms"]
+            fsys = System(fp, fr, fv, fs, device=dev)
+            fsys.step(3)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(fsys.stream)
+            fsys.step(steps)
+            f1.record(fsys.stream)
+            torch.cuda.synchronize()
+            fms = f0.elapsed_time(f1) / steps
+            forms[name] = {"value": fn / (fms * 1e-3), "unit": UNIT, "ms_per_step": fms, "steps": steps,
+                           "n_atoms": fn, "workload": fdesc}
+            fsys.close()
+            del fsys
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ost = 40
@@ -281,11 +317,11 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n_atoms": n, "cells": w["ncells"], "dt_ps": p["dt_ps"],
+            "config": {"workload": args.workload, "description": wdesc, "n_atoms": n, "dt_ps": p0["dt_ps"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set > 129 MB L2 (no flush needed)", "graph": counters["graph"]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches,
+            "gpu_launches": launches, "forms": forms,
         }
         print(json.dumps(line))
     sysm.close()

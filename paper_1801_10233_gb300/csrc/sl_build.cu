@@ -127,12 +127,19 @@ __global__ void k_rb_copyback(SlDev d) {
 // list starts with the exchange list (same order) followed by the
 // Morse-only neighbours, so the force loop takes the magneto-elastic branch
 // only for its first exn[i] entries.  Requires morse_rc >= ex_rc.
+// Membership uses float distances from the split positions with a relative
+// margin of 1e-4 on r^2 (far above their rounding): a list may hold a pair
+// marginally outside its radius, which is harmless because every kernel
+// applies the exact cutoff to the pairs it reads.
 __global__ void k_rb_nbr(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
-  double4_32a ri = d.r[i];
+  const float4 rih = d.rh[i], rim = d.rm[i];
   const SlRep& R = d.reps[d.arep[i]];
+  const float Lx = (float)R.box[0], Ly = (float)R.box[1], Lz = (float)R.box[2];
+  const float iLx = R.inv_box_f[0], iLy = R.inv_box_f[1], iLz = R.inv_box_f[2];
+  const float lm2 = (float)d.list_m2 * 1.0001f, le2 = (float)d.list_ex2 * 1.0001f;
   int sx, sy, sz;
   sl_sector_coords(d, R, d.secq[i], sx, sy, sz);
   int lox = (2 * R.mx + 1 >= R.nx) ? 0 : -R.mx, hix = (2 * R.mx + 1 >= R.nx) ? R.nx - 1 : R.mx;
@@ -149,12 +156,18 @@ __global__ void k_rb_nbr(SlDev d) {
         int a = d.sec_start[q], b = d.sec_start[q + 1];
         for (int j = a; j < b; ++j) {
           if (j == i) continue;
-          double3 dd = sl_min_image(R, ri, d.r[j]);
-          double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
-          if (r2 < d.list_ex2) {
+          const float4 jh = __ldg(d.rh + j), jm = __ldg(d.rm + j);
+          float dx = (jh.x - rih.x) + (jm.x - rim.x);
+          float dy = (jh.y - rih.y) + (jm.y - rim.y);
+          float dz = (jh.z - rih.z) + (jm.z - rim.z);
+          dx -= Lx * rintf(dx * iLx);
+          dy -= Ly * rintf(dy * iLy);
+          dz -= Lz * rintf(dz * iLz);
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < le2) {
             if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;
             ++ce;
-          } else if (r2 < d.list_m2) {
+          } else if (r2 < lm2) {
             // Morse-only entries go after a gap of max_ex rows for now
             if (d.max_ex + cm < d.max_m) d.mj[(size_t)(d.max_ex + cm) * d.n + i] = j;
             ++cm;
