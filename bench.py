@@ -58,6 +58,10 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 pipe, nominal at 2070 MHz
 # corrections, two_sum, renormalisation), so FP64-accurate arithmetic peaks at
 # 40.3e12 / 20 x 2 flop = 4.03 TFLOP/s on this chip.
 DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 20 * 2 / 1e12
+# DRAM bytes (read + write) of one launch of each phase's kernel from an ncu
+# capture of the current kernels on the 64^3-cell workload
+# (profiles/force_fe_bcc_64x64x64_nve.md, profiles/jtable_fe_bcc_64x64x64_nve.md).
+NCU_TRAFFIC_64CUBED = {"force_kick": 305.9e6, "exchange_table": 86.1e6}
 
 
 def parse():
@@ -255,8 +259,9 @@ def run_ours(args):
     dom_ms = phases[dom][0] / max(1, phases[dom][1])
     flops = PHASE_FLOPS_PER_ATOM[dom] * n
     achieved = flops / (dom_ms * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC_64CUBED.get(dom) if args.workload == DEFAULT_WORKLOAD else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / DF_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                "frac": achieved / DF_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
                 "peak_kind": "FP64-accurate (double-float on FP32 pipes) peak derived from unit counts and clock",
                 "fp64_pipe_nominal_tflops": FP64_NOMINAL_TFLOPS,
                 "phase_ms_per_step": {k: v_[0] / max(1, v_[1]) for k, v_ in phases.items()}}
