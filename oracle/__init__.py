@@ -20,6 +20,19 @@ _c_int_p = ctypes.POINTER(ctypes.c_int)
 
 ORC_OK, ORC_ERR_ARG, ORC_ERR_BOX, ORC_ERR_SPIN_NORM, ORC_ERR_SKIN, ORC_ERR_OOM = 0, -1, -3, -4, -5, -8
 
+# Learned model layout (sl_learned.c): float params W1[64][48], b1[64],
+# W2[64][64], b2[64], w3[64], b3; float norm mean[48], inv_std[48], lo[48], hi[48].
+ML_NF, ML_NH, ML_RC = 48, 64, 6.0
+ML_OFF_W1 = 0
+ML_OFF_B1 = ML_OFF_W1 + ML_NH * ML_NF
+ML_OFF_W2 = ML_OFF_B1 + ML_NH
+ML_OFF_B2 = ML_OFF_W2 + ML_NH * ML_NH
+ML_OFF_W3 = ML_OFF_B2 + ML_NH
+ML_OFF_B3 = ML_OFF_W3 + ML_NH
+ML_NPARAM = ML_OFF_B3 + 1
+ML_NNORM = 4 * ML_NF
+HBAR = 6.582119569e-4
+
 
 class _Params(ctypes.Structure):
     _fields_ = [
@@ -32,7 +45,7 @@ class _Params(ctypes.Structure):
         ("m_D0", ctypes.c_double), ("m_alpha", ctypes.c_double), ("m_r0", ctypes.c_double),
         ("m_rc", ctypes.c_double), ("skin", ctypes.c_double),
         ("lam", ctypes.c_double), ("temperature", ctypes.c_double),
-        ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32), ("pad", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32), ("hamiltonian", ctypes.c_int32),
     ]
 
 
@@ -70,6 +83,24 @@ def lib():
                                         ctypes.POINTER(ctypes.c_uint32 * 4)]
         L.orc_gauss3.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_long, ctypes.c_int, ctypes.c_int,
                                  _c_double_p]
+        _f_p = ctypes.POINTER(ctypes.c_float)
+        L.orc_ml_set_model.restype = ctypes.c_int
+        L.orc_ml_set_model.argtypes = [ctypes.c_void_p, _f_p, _f_p]
+        L.orc_ml_gate.argtypes = [ctypes.c_void_p, _c_int_p]
+        L.orc_ml_eval.restype = ctypes.c_int
+        L.orc_ml_eval.argtypes = [ctypes.c_int, _c_double_p, _c_double_p, _c_double_p, _f_p, _f_p,
+                                  _c_double_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p]
+        L.orc_ml_vjp.restype = ctypes.c_int
+        L.orc_ml_vjp.argtypes = [ctypes.c_int, _c_double_p, _c_double_p, _c_double_p, _f_p, _f_p,
+                                 ctypes.c_double, _c_double_p, _c_double_p, _c_double_p]
+        L.orc_ml_loss.restype = ctypes.c_int
+        L.orc_ml_loss.argtypes = [ctypes.c_int, _c_int_p, _c_double_p, _c_double_p, _c_double_p, _c_double_p,
+                                  _c_double_p, _c_double_p, _c_double_p, ctypes.c_double, _f_p, _f_p,
+                                  _c_double_p, _c_double_p]
+        L.orc_ml_adam.argtypes = [ctypes.c_int, _f_p, _c_double_p, _c_double_p, _c_double_p, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_bf16_value.restype = ctypes.c_double
+        L.orc_bf16_value.argtypes = [ctypes.c_float]
         L.orc_params_size.restype = ctypes.c_int
         if L.orc_params_size() != ctypes.sizeof(_Params):
             raise RuntimeError("oracle parameter struct layout mismatch")
@@ -83,6 +114,21 @@ def _dp(a):
 
 def _ip(a):
     return a.ctypes.data_as(_c_int_p)
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _f32(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"expected {n} floats, got {a.size}")
+    return a
+
+
+def _opt(a):
+    return None if a is None else _dp(a)
 
 
 def make_params(p: dict, brute_force=False, lam=0.0, temperature=0.0, seed=0, replica=0) -> _Params:
@@ -108,6 +154,7 @@ def make_params(p: dict, brute_force=False, lam=0.0, temperature=0.0, seed=0, re
     q.temperature = float(temperature)
     q.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     q.replica = int(replica)
+    q.hamiltonian = int(p.get("hamiltonian", 0))
     return q
 
 
@@ -195,6 +242,19 @@ class Oracle:
         self._L.orc_magnetization(self._h, _dp(out))
         return out
 
+    def set_model(self, params, norm):
+        """Install the learned model (hamiltonian = 1 only) and recompute forces."""
+        self._ml = (_f32(params, ML_NPARAM), _f32(norm, ML_NNORM))
+        e = int(self._L.orc_ml_set_model(self._h, _fp(self._ml[0]), _fp(self._ml[1])))
+        if e:
+            raise OracleError(e)
+
+    def gate(self):
+        """(out-of-range atoms at the last learned evaluation point, points handed to the analytic H)."""
+        out = np.zeros(2, dtype=np.int32)
+        self._L.orc_ml_gate(self._h, _ip(out))
+        return int(out[0]), int(out[1])
+
 
 def potential_energy(params: dict, r, s):
     """(E_morse, E_exch, E_zeeman, sum) of arbitrary positions and spin
@@ -222,3 +282,76 @@ def gauss3(seed, replica, step, subpass, atom):
     g = np.empty(3)
     L.orc_gauss3(int(seed) & 0xFFFFFFFFFFFFFFFF, int(replica), int(step), int(subpass), int(atom), _dp(g))
     return g
+
+
+# ---------------------------------------------------------------------------
+# Learned model (sl_learned.c)
+# ---------------------------------------------------------------------------
+def bf16_value(x: float) -> float:
+    """x rounded to bfloat16 (nearest, ties to even), as the model uses its weights."""
+    return float(lib().orc_bf16_value(float(x)))
+
+
+def ml_eval(r, s, box, params, norm):
+    """Learned energy and gradients of one periodic frame (brute-force pairs).
+    Returns dict(e_atom, D, G, F, B, out_of_range)."""
+    L = lib()
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    s = np.ascontiguousarray(s, dtype=np.float64).reshape(-1, 3)
+    n = r.shape[0]
+    box = np.ascontiguousarray(box, dtype=np.float64).reshape(3)
+    pa, no = _f32(params, ML_NPARAM), _f32(norm, ML_NNORM)
+    e = np.empty(n); D = np.empty((n, ML_NF)); G = np.empty((n, ML_NF))
+    F = np.empty((n, 3)); B = np.empty((n, 3))
+    bad = L.orc_ml_eval(n, _dp(r), _dp(s), _dp(box), _fp(pa), _fp(no), _dp(e), _dp(D), _dp(G), _dp(F), _dp(B))
+    if bad < 0:
+        raise OracleError(bad)
+    return dict(e_atom=e, D=D, G=G, F=F, B=B, out_of_range=int(bad))
+
+
+def ml_vjp(r, s, box, params, norm, gE=0.0, gF=None, gB=None):
+    """d/dparams of gE E + sum gF.F + sum gB.B (F = -dE/dr, B = -dE/ds)."""
+    L = lib()
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    s = np.ascontiguousarray(s, dtype=np.float64).reshape(-1, 3)
+    n = r.shape[0]
+    box = np.ascontiguousarray(box, dtype=np.float64).reshape(3)
+    pa, no = _f32(params, ML_NPARAM), _f32(norm, ML_NNORM)
+    gF = None if gF is None else np.ascontiguousarray(gF, dtype=np.float64).reshape(n, 3)
+    gB = None if gB is None else np.ascontiguousarray(gB, dtype=np.float64).reshape(n, 3)
+    grad = np.empty(ML_NPARAM)
+    e = L.orc_ml_vjp(n, _dp(r), _dp(s), _dp(box), _fp(pa), _fp(no), float(gE), _opt(gF), _opt(gB), _dp(grad))
+    if e:
+        raise OracleError(e)
+    return grad
+
+
+def ml_loss(frames, E_ref, F_ref, B_ref, w, params, norm, want_grad=True):
+    """Training loss over frames [(r, s, box), ...] and its parameter gradient.
+    Returns (out[4] = L, L_E, L_F, L_omega; grad or None)."""
+    L = lib()
+    n_of = np.array([np.asarray(f[0]).reshape(-1, 3).shape[0] for f in frames], dtype=np.int32)
+    r = np.ascontiguousarray(np.concatenate([np.asarray(f[0], dtype=np.float64).reshape(-1, 3) for f in frames]))
+    s = np.ascontiguousarray(np.concatenate([np.asarray(f[1], dtype=np.float64).reshape(-1, 3) for f in frames]))
+    boxes = np.ascontiguousarray(np.array([f[2] for f in frames], dtype=np.float64).reshape(-1))
+    E_ref = np.ascontiguousarray(E_ref, dtype=np.float64)
+    F_ref = np.ascontiguousarray(F_ref, dtype=np.float64).reshape(-1, 3)
+    B_ref = np.ascontiguousarray(B_ref, dtype=np.float64).reshape(-1, 3)
+    wv = np.ascontiguousarray(w, dtype=np.float64)
+    pa, no = _f32(params, ML_NPARAM), _f32(norm, ML_NNORM)
+    out = np.empty(4)
+    grad = np.empty(ML_NPARAM) if want_grad else None
+    e = L.orc_ml_loss(len(frames), _ip(n_of), _dp(r), _dp(s), _dp(boxes), _dp(E_ref), _dp(F_ref), _dp(B_ref),
+                      _dp(wv), HBAR, _fp(pa), _fp(no), _dp(out), _opt(grad))
+    if e:
+        raise OracleError(e)
+    return out, grad
+
+
+def ml_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step on float32 params (in place); m, v float64 moments (in place)."""
+    L = lib()
+    assert params.dtype == np.float32 and params.flags.c_contiguous
+    g = np.ascontiguousarray(grad, dtype=np.float64)
+    L.orc_ml_adam(params.size, _fp(params), _dp(g), _dp(m), _dp(v), int(t), float(lr), float(beta1),
+                  float(beta2), float(eps))

@@ -31,6 +31,19 @@
  *                 (Eq. lattice_temperature), T_S (Eq. spin_temperature),
  *                 magnetisation M = (1/N) sum_i s_i.
  *
+ * Learned Hamiltonian mode (hamiltonian = 1; no counterpart in the paper):
+ * the Morse + exchange energy is replaced by the per-atom network of
+ * sl_learned.c.  Each evaluation point (the start of each spin half-op, the
+ * force computation) evaluates the network at the current state; if any
+ * atom's descriptor lies outside the model's trained range, that point uses
+ * the analytic Hamiltonian instead.  A learned spin half-op freezes the
+ * network's per-atom gradients G at the half-op's start: each single-spin
+ * factor then rotates s_i about omega_i = (mu_s mu_B H - sum_j (P_ij +
+ * 2 Q_ij s_i.s_j) s_j)/hbar with P, Q from the frozen G and the current
+ * spins (omega_i itself held fixed during the rotation).  Sectors are at
+ * least the model's 6 A cutoff + skin wide so that same-colour spins still
+ * do not interact.
+ *
  * Pair lists are rebuilt from scratch at the exact cutoffs whenever the
  * positions change (brute force, or a plain cell list that the tests check
  * against brute force); there is no Verlet skin here.  The skin only enters
@@ -44,6 +57,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include "orc_learned.h"
 
 /* Physical constants in the paper's "metal" unit set (A, ps, eV, amu, K, T). */
 #define ORC_HBAR 6.582119569e-4   /* eV ps / rad (Sec. 2.1 prints 1e3 too small) */
@@ -73,7 +88,7 @@ typedef struct {
   double temperature;    /* spin bath temperature, K (0: no noise) */
   uint64_t seed;
   int32_t replica;
-  int32_t pad;
+  int32_t hamiltonian;   /* 0 analytic (Morse + Bethe-Slater), 1 learned */
 } orc_params;
 
 typedef struct {
@@ -99,6 +114,13 @@ typedef struct {
   long step;               /* completed steps */
   int err;
   int rebuilds;
+  /* learned Hamiltonian */
+  orc_ml_model* ml;        /* NULL until orc_ml_set_model */
+  orc_list mll;            /* pairs with r < ML_RC */
+  double *mlP, *mlQ;       /* field coefficients per mll entry (frozen per half-op) */
+  int use_ml;              /* the current evaluation point uses the network */
+  int gate_bad;            /* out-of-range atoms at the last evaluation point */
+  int gate_trips;          /* evaluation points handed to the analytic Hamiltonian */
 } orc_state;
 
 /* ------------------------------------------------------------------ */
@@ -276,6 +298,10 @@ static int refresh_pairs(orc_state* st) {
   if (e) return e;
   e = build_list(st, st->p.m_rc, &st->mo);
   if (e) return e;
+  if (st->p.hamiltonian == 1) {
+    e = build_list(st, ML_RC, &st->mll);
+    if (e) return e;
+  }
   int np = st->ex.off[st->n];
   free(st->exJ); free(st->exdJ);
   st->exJ = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
@@ -296,7 +322,9 @@ static int refresh_pairs(orc_state* st) {
 /* Sector assignment (Sec. 5.1) and the sweep order                   */
 /* ------------------------------------------------------------------ */
 static int sector_grid(const orc_params* p, int nsec[3], double edge[3]) {
-  double w = p->ex_rc + p->skin;
+  double reach = p->ex_rc;
+  if (p->hamiltonian == 1 && ML_RC > reach) reach = ML_RC;
+  double w = reach + p->skin;
   for (int a = 0; a < 3; ++a) {
     int n = (int)floor(p->box[a] / w);
     if (n % 2) n -= 1;
@@ -368,6 +396,23 @@ static void omega_of(const orc_state* st, int i, double w[3]) {
   w[0] = h[0] / ORC_HBAR; w[1] = h[1] / ORC_HBAR; w[2] = h[2] / ORC_HBAR;
 }
 
+/* Learned-mode precession vector from the frozen pair coefficients:
+ * omega_i = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij s_i.s_j) s_j) / hbar. */
+static void omega_ml(const orc_state* st, int i, double w[3]) {
+  double zf = st->p.mu_s * ORC_MUB;
+  double h[3] = {zf * st->p.H[0], zf * st->p.H[1], zf * st->p.H[2]};
+  const double* si = st->s + 3 * i;
+  for (int k = st->mll.off[i]; k < st->mll.off[i + 1]; ++k) {
+    const double* sj = st->s + 3 * st->mll.j[k];
+    double c = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
+    double psi = st->mlP[k] + 2.0 * st->mlQ[k] * c;
+    h[0] -= psi * sj[0];
+    h[1] -= psi * sj[1];
+    h[2] -= psi * sj[2];
+  }
+  w[0] = h[0] / ORC_HBAR; w[1] = h[1] / ORC_HBAR; w[2] = h[2] / ORC_HBAR;
+}
+
 static void cross(const double a[3], const double b[3], double c[3]) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];
@@ -377,7 +422,8 @@ static void cross(const double a[3], const double b[3], double c[3]) {
 /* Update spin i over time tau (one factor e^{L_si tau} of Eq. spin_ST_decomposition). */
 static void rotate(orc_state* st, int i, double tau, int subpass) {
   double w[3];
-  omega_of(st, i, w);
+  if (st->use_ml) omega_ml(st, i, w);
+  else omega_of(st, i, w);
   double* s = st->s + 3 * i;
   if (st->p.lambda != 0.0 || st->p.temperature != 0.0) {
     /* Eq. sLLG written as ds/dt = Om x s with
@@ -425,9 +471,34 @@ static void rotate(orc_state* st, int i, double tau, int subpass) {
   }
 }
 
+/* One evaluation point of the learned Hamiltonian at the current state:
+ * sets use_ml (gate), the frozen field coefficients and, if F is given, the
+ * learned forces.  Returns an error code. */
+static int ml_point(orc_state* st, double* F) {
+  st->use_ml = 0;
+  if (st->p.hamiltonian != 1) return ORC_OK;
+  if (!st->ml) return ORC_ERR_ARG;
+  int np = st->mll.off[st->n];
+  free(st->mlP); free(st->mlQ);
+  st->mlP = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
+  st->mlQ = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
+  if (!st->mlP || !st->mlQ) return ORC_ERR_OOM;
+  int bad = orc_ml_frame(st->n, st->r, st->s, st->p.box, st->mll.off, st->mll.j, st->ml, NULL, NULL, NULL, F,
+                         NULL, st->mlP, st->mlQ);
+  if (bad < 0) return ORC_ERR_OOM;
+  st->gate_bad = bad;
+  st->use_ml = bad == 0;
+  if (bad) st->gate_trips += 1;
+  return ORC_OK;
+}
+
 /* e^{L_s h}: forward over the sweep order with h/2 per spin, then backward. */
 static void spin_half_op(orc_state* st, double h, int subpass0) {
   int n = st->n;
+  if (st->p.hamiltonian == 1) {
+    int e = ml_point(st, NULL);
+    if (e && st->err == ORC_OK) st->err = e;
+  }
   for (int k = 0; k < n; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
   for (int k = n - 1; k >= 0; --k) rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
 }
@@ -437,6 +508,18 @@ static void spin_half_op(orc_state* st, double h, int subpass0) {
 /* ------------------------------------------------------------------ */
 static void compute_forces(orc_state* st) {
   int n = st->n;
+  if (st->p.hamiltonian == 1 && st->ml) {
+    double* F = (double*)malloc((size_t)(n ? n : 1) * 3 * sizeof(double));
+    int e = F ? ml_point(st, F) : ORC_ERR_OOM;
+    if (e) {
+      if (st->err == ORC_OK) st->err = e;
+    } else if (st->use_ml) {
+      memcpy(st->F, F, (size_t)n * 3 * sizeof(double));
+      free(F);
+      return;
+    }
+    free(F);
+  }
   memset(st->F, 0, (size_t)n * 3 * sizeof(double));
   for (int i = 0; i < n; ++i) {
     double* f = st->F + 3 * i;
@@ -487,6 +570,7 @@ void orc_destroy(orc_state* st) {
   free(st->sector); free(st->colour); free(st->order);
   free(st->ex.off); free(st->ex.j); free(st->mo.off); free(st->mo.j);
   free(st->exJ); free(st->exdJ);
+  free(st->ml); free(st->mll.off); free(st->mll.j); free(st->mlP); free(st->mlQ);
   free(st);
 }
 
@@ -495,8 +579,13 @@ int orc_params_size(void) { return (int)sizeof(orc_params); }
 /* r, v, s: [n][3] in atom-id order.  Returns NULL and sets *err on failure. */
 orc_state* orc_create(const orc_params* p, const double* r, const double* v, const double* s, int* err) {
   *err = ORC_OK;
-  if (!p || p->n_atoms < 0 || p->mass <= 0.0) { *err = ORC_ERR_ARG; return NULL; }
-  double need = 2.0 * ((p->m_rc > p->ex_rc ? p->m_rc : p->ex_rc) + p->skin);
+  if (!p || p->n_atoms < 0 || p->mass <= 0.0 || p->hamiltonian < 0 || p->hamiltonian > 1) {
+    *err = ORC_ERR_ARG;
+    return NULL;
+  }
+  double reach = p->m_rc > p->ex_rc ? p->m_rc : p->ex_rc;
+  if (p->hamiltonian == 1 && ML_RC > reach) reach = ML_RC;
+  double need = 2.0 * (reach + p->skin);
   for (int a = 0; a < 3; ++a)
     if (!(p->box[a] >= need)) { *err = ORC_ERR_BOX; return NULL; }
   orc_state* st = (orc_state*)calloc(1, sizeof(orc_state));
@@ -529,8 +618,27 @@ orc_state* orc_create(const orc_params* p, const double* r, const double* v, con
   return st;
 }
 
+/* Install the learned model (float params[ML_NPARAM], norm[ML_NNORM]) and
+ * recompute the forces with it.  Only for hamiltonian = 1. */
+int orc_ml_set_model(orc_state* st, const float* params, const float* norm) {
+  if (st->p.hamiltonian != 1) return ORC_ERR_ARG;
+  if (!st->ml) st->ml = (orc_ml_model*)malloc(sizeof(orc_ml_model));
+  if (!st->ml) return ORC_ERR_OOM;
+  orc_ml_load(params, norm, st->ml);
+  compute_forces(st);
+  return st->err;
+}
+
+/* Out-of-range atoms at the last learned evaluation point, and the number
+ * of points handed to the analytic Hamiltonian so far. */
+void orc_ml_gate(const orc_state* st, int out[2]) {
+  out[0] = st->gate_bad;
+  out[1] = st->gate_trips;
+}
+
 /* One or more timesteps of Eq. general_ST_decomposition. */
 int orc_step(orc_state* st, int nsteps) {
+  if (st->p.hamiltonian == 1 && !st->ml) return ORC_ERR_ARG;
   for (int it = 0; it < nsteps; ++it) {
     double dt = st->p.dt;
     int lat = !st->p.fix_lattice;
@@ -577,9 +685,31 @@ void orc_get_forces(const orc_state* st, double* F) {
   memcpy(F, st->F, (size_t)st->n * 3 * sizeof(double));
 }
 
-/* omega_i of the current state, [n][3], rad/ps (no noise, no damping). */
+/* Learned energy per atom and field B = -dE/ds at the current state (exact
+ * gradient, nothing frozen).  Returns 1 if the network is in effect there
+ * (model set, every descriptor in range), 0 otherwise, -1 on failure. */
+static int ml_current(const orc_state* st, double* e_atom, double* B) {
+  if (st->p.hamiltonian != 1 || !st->ml) return 0;
+  int bad = orc_ml_frame(st->n, st->r, st->s, st->p.box, st->mll.off, st->mll.j, st->ml, e_atom, NULL, NULL, NULL,
+                         B, NULL, NULL);
+  if (bad < 0) return -1;
+  return bad == 0;
+}
+
+/* omega_i of the current state, [n][3], rad/ps (no noise, no damping):
+ * -(1/hbar) dH/ds_i of the Hamiltonian in effect. */
 void orc_get_omega(const orc_state* st, double* w) {
-  for (int i = 0; i < st->n; ++i) omega_of(st, i, w + 3 * i);
+  int n = st->n;
+  double* B = (double*)malloc((size_t)(n ? n : 1) * 3 * sizeof(double));
+  if (B && ml_current(st, NULL, B) == 1) {
+    double zf = st->p.mu_s * ORC_MUB;
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < 3; ++a) w[3 * i + a] = (B[3 * i + a] + zf * st->p.H[a]) / ORC_HBAR;
+    free(B);
+    return;
+  }
+  free(B);
+  for (int i = 0; i < n; ++i) omega_of(st, i, w + 3 * i);
 }
 
 /* Sweep order, colour boundaries, per-atom sector and colour, sector grid. */
@@ -598,15 +728,23 @@ int orc_count_pairs(const orc_state* st, int which) {
   return which == 0 ? st->ex.off[st->n] : st->mo.off[st->n];
 }
 
-/* out[0..7] = E_kin, E_morse, E_exch, E_zeeman, E_total (eV), T_L, T_S (K), 0. */
+/* out[0..7] = E_kin, E_morse, E_exch, E_zeeman, E_total (eV), T_L, T_S (K), 0.
+ * Where the learned Hamiltonian is in effect, out[1] is its energy sum_i E_i
+ * (lattice + exchange together) and out[2] = 0. */
 void orc_energy(const orc_state* st, double out[8]) {
   int n = st->n;
   double ek = 0.0, em = 0.0, ex = 0.0, ez = 0.0;
+  double* eat = (double*)malloc((size_t)(n ? n : 1) * sizeof(double));
+  double* B = (double*)malloc((size_t)(n ? n : 1) * 3 * sizeof(double));
+  int learned = (eat && B) ? ml_current(st, eat, B) == 1 : 0;
   for (int i = 0; i < n; ++i) {
     const double* v = st->v + 3 * i;
     ek += 0.5 * st->p.mass * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / ORC_FTOA;
   }
   double vshift = st->p.morse_shift ? morse_V(&st->p, st->p.m_rc) : 0.0;
+  if (learned) {
+    for (int i = 0; i < n; ++i) em += eat[i];
+  } else {
   for (int i = 0; i < n; ++i)
     for (int k = st->mo.off[i]; k < st->mo.off[i + 1]; ++k) {
       int j = st->mo.j[k];
@@ -624,6 +762,7 @@ void orc_energy(const orc_state* st, double out[8]) {
       const double* sj = st->s + 3 * j;
       ex -= st->exJ[k] * (si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2]);
     }
+  }
   double zf = st->p.mu_s * ORC_MUB;
   for (int i = 0; i < n; ++i) {
     const double* si = st->s + 3 * i;
@@ -632,7 +771,11 @@ void orc_energy(const orc_state* st, double out[8]) {
   double num = 0.0, den = 0.0;
   for (int i = 0; i < n; ++i) {
     double w[3], c[3];
-    omega_of(st, i, w);
+    if (learned) {
+      for (int a = 0; a < 3; ++a) w[a] = (B[3 * i + a] + zf * st->p.H[a]) / ORC_HBAR;
+    } else {
+      omega_of(st, i, w);
+    }
     const double* si = st->s + 3 * i;
     cross(si, w, c);
     num += c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
@@ -643,6 +786,7 @@ void orc_energy(const orc_state* st, double out[8]) {
   out[5] = n > 0 ? 2.0 * ek / (3.0 * n * ORC_KB) : 0.0;
   out[6] = den != 0.0 ? ORC_HBAR / (2.0 * ORC_KB) * num / den : 0.0;
   out[7] = 0.0;
+  free(eat); free(B);
 }
 
 /* out = Mx, My, Mz, |M| with M = (1/N) sum_i s_i. */

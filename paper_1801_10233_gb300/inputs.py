@@ -46,6 +46,7 @@ def fe_params(box, n_atoms, **overrides):
         fix_lattice=0,
         rebuild_every=0,
         morse_shift_energy=1,
+        hamiltonian=0,
     )
     for k, v in overrides.items():
         if k not in p:
@@ -159,3 +160,23 @@ def batch_workload(n_replicas=256, seed=18012, **param_overrides):
     {8, 12, 16, 20, 24}^3 cells and bath temperatures 50..1200 K, lambda 0.01."""
     cells, temps = replica_batch(n_replicas, seed)
     return replica_systems(cells, temps, seed, **param_overrides)
+
+
+# ---------------------------------------------------------------------------
+# Learned per-atom Hamiltonian: initial weights (random draws only)
+# ---------------------------------------------------------------------------
+def ml_init_params(seed, n_in=48, n_hidden=64, e0=0.0):
+    """Seeded initial parameters of the 48 -> 64 -> 64 -> 1 network as one
+    float32 vector in the order W1[n_hidden][n_in], b1, W2[n_hidden][n_hidden],
+    b2, w3[n_hidden], b3.  Weights uniform in +-sqrt(6/(fan_in+fan_out))
+    (Glorot and Bengio, 2010), the output layer scaled by 0.1, biases zero
+    except b3 = e0."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+
+    def glorot(fo, fi, scale=1.0):
+        b = scale * math.sqrt(6.0 / (fi + fo))
+        return rng.uniform(-b, b, size=(fo, fi))
+
+    parts = [glorot(n_hidden, n_in).ravel(), np.zeros(n_hidden), glorot(n_hidden, n_hidden).ravel(),
+             np.zeros(n_hidden), glorot(1, n_hidden, 0.1).ravel(), np.array([e0])]
+    return np.concatenate(parts).astype(np.float32)
