@@ -66,6 +66,7 @@ enum {
 };
 
 enum { SL_ROT_RODRIGUES = 0, SL_ROT_CAYLEY = 1 };
+enum { SL_HAM_ANALYTIC = 0, SL_HAM_LEARNED = 1 };
 
 /* Parameters of one system.  Zero-initialise and fill every field. */
 typedef struct sl_params {
@@ -81,7 +82,7 @@ typedef struct sl_params {
   int32_t max_morse_neighbors; /* Morse list capacity per atom (0: 128); the list
                                   holds the exchange neighbours first, so values not
                                   above max_ex_neighbors are raised to it + 1 */
-  int32_t reserved0;           /* must be 0 */
+  int32_t hamiltonian;         /* SL_HAM_ANALYTIC (0) or SL_HAM_LEARNED (1), see below */
   double box[3];               /* orthorhombic periodic box edges */
   double mass_amu;
   double mu_s_muB;             /* magnetic moment, units of mu_B */
@@ -222,6 +223,106 @@ int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
  * before any stream capture.  Stream-ordered on cuda_stream; no host sync.
  * Errors: SL_ERR_ARG, SL_ERR_CUDA. */
 int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned per-atom Hamiltonian.  The paper has no learned model: this is an
+ * extension of the library in which a small network stands in for the Morse
+ * + exchange energy, so that the same integrator runs on it.
+ *
+ * Descriptor of atom i over its neighbours j with r_ij < SL_ML_RC:
+ *   D_i[3k+m] = sum_j g_k(r_ij) (s_i.s_j)^m,  k = 0..15, m = 0, 1, 2,
+ *   g_k(r) = exp(-(r - 0.4k)^2 / (2 * 0.4^2)) (1 + cos(pi r/SL_ML_RC))/2.
+ * Network: x = (D - mean) * inv_std,
+ *   E_i = w3 . silu(W2 silu(W1 x + b1) + b2) + b3,   silu(z) = z/(1+e^-z);
+ * W1, W2, w3 are used rounded to bfloat16 (nearest even), biases as float.
+ * E = sum_i E_i replaces the Morse + exchange terms; the Zeeman and kinetic
+ * terms are unchanged.  Forces -dE/dr and fields -dE/ds come from the
+ * hand-written backward pass (chain rule through D_i and every D_j).
+ *
+ * The network's GEMMs run on the tensor cores with bfloat16 operands and
+ * float32 accumulation; activations are passed as three bfloat16 pieces
+ * (hi + mid + lo) so that the products carry float32 precision.
+ *
+ * Parameters (float32, device): one vector of SL_ML_NPARAM floats, W1[64][48]
+ * (row = hidden unit), b1[64], W2[64][64], b2[64], w3[64], b3, at the
+ * SL_ML_OFF_* offsets.  Normalisation (float32, device): SL_ML_NNORM floats,
+ * mean[48], inv_std[48], gate lo[48], gate hi[48].
+ *
+ * Dynamics with hamiltonian = SL_HAM_LEARNED: sectors are at least
+ * SL_ML_RC + skin wide (the network couples spins up to SL_ML_RC apart) and
+ * morse_rc_A must be >= SL_ML_RC (the Morse list is the descriptor list).
+ * Each evaluation point (after the drift; with the forces) evaluates the
+ * network at the current state.  If any atom's descriptor lies outside
+ * [gate lo, gate hi], that point hands over to the analytic Hamiltonian: the
+ * following spin half-op and/or forces use Morse + Bethe-Slater instead.
+ * A learned spin half-op freezes the per-atom gradients G_i = dE_i/dD_i of its
+ * evaluation point; each single-spin factor rotates s_i about
+ *   omega_i = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij s_i.s_j) s_j) / hbar,
+ *   P_ij = sum_k (G_i+G_j)[3k+1] g_k(r_ij),  Q_ij = sum_k (G_i+G_j)[3k+2] g_k(r_ij),
+ * with the current neighbour spins.  The spin bath (lambda, temperature_K)
+ * is not available in this mode.
+ * ------------------------------------------------------------------------ */
+#define SL_ML_NF 48
+#define SL_ML_NH 64
+#define SL_ML_RC 6.0
+#define SL_ML_OFF_W1 0
+#define SL_ML_OFF_B1 3072
+#define SL_ML_OFF_W2 3136
+#define SL_ML_OFF_B2 7232
+#define SL_ML_OFF_W3 7296
+#define SL_ML_OFF_B3 7360
+#define SL_ML_NPARAM 7361
+#define SL_ML_NNORM 192
+
+/* Install a model (device float32 vectors, copied into the workspace) and
+ * evaluate it at the current state (forces, fields, gate).  The context must
+ * have been created with hamiltonian = SL_HAM_LEARNED (SL_ERR_ARG otherwise).
+ * sl_step and the sl_ml_* calls below return SL_ERR_ARG until a model is set.
+ * The optimiser state of sl_ml_train_step is reset.  Stream-ordered. */
+int sl_ml_set_model(sl_ctx* ctx, const float* params, const float* norm);
+
+/* Copy the current float32 parameters (after training) to params (device,
+ * SL_ML_NPARAM floats).  Stream-ordered. */
+int sl_ml_get_model(sl_ctx* ctx, float* params);
+
+/* Evaluate the network at the current state, gate ignored.  Outputs, any may
+ * be NULL: e_rep (host, [n_replicas]) sum_i E_i per replica; F and B (device,
+ * [n][3] doubles, caller order) = -dE/dr (eV/A) and -dE/ds (eV); D (device,
+ * [n][48] doubles, caller order) the raw descriptors.  Synchronises when
+ * e_rep is given. */
+int sl_ml_eval(sl_ctx* ctx, double* e_rep, double* F, double* B, double* D);
+
+/* Statistics of the raw descriptors of the current state over all atoms:
+ * out (host, [4][48]) = mean, standard deviation, minimum, maximum per
+ * feature, summed in a fixed order.  Synchronises. */
+int sl_ml_descriptor_stats(sl_ctx* ctx, double* out);
+
+/* out[4] (host) = atoms outside the gate range at the last evaluation point,
+ * 1 if the network was in use there, evaluation points handed to the analytic
+ * Hamiltonian so far, 0.  Synchronises. */
+int sl_ml_gate(sl_ctx* ctx, int64_t out[4]);
+
+/* Parameter gradient of  sum_r gE[r] E_r + sum_i gF_i . F_i + sum_i gB_i . B_i
+ * at the current state (E_r = sum of E_i over replica r; F, B as in
+ * sl_ml_eval): the vector-Jacobian product behind both the energy and its
+ * derivatives (forward-over-reverse through the network).  gE (device,
+ * [n_replicas] doubles), gF, gB (device, [n][3] doubles, caller order) may be
+ * NULL (zero).  grad (device, SL_ML_NPARAM doubles) is overwritten.
+ * Stream-ordered; the sum over atoms is in a fixed order. */
+int sl_ml_vjp(sl_ctx* ctx, const double* gE, const double* gF, const double* gB, double* grad);
+
+/* One training step on the frames currently loaded (one replica per frame):
+ *   L = w[0] mean_r (dE_r/N_r)^2 + w[1] (1/N) sum_i |dF_i|^2
+ *       + w[2] (1/N) sum_i |(1 - s_i s_i^T) dB_i / hbar|^2,
+ * d = network - reference, then one Adam update (Kingma and Ba, 2015) of the
+ * float32 parameters with learning rate lr and moments beta1, beta2, eps
+ * (moments kept in the workspace in FP64).  E_ref (device, [n_replicas]),
+ * F_ref, B_ref (device, [n][3], caller order): reference potential energy
+ * (Morse + exchange), forces and field -dE/ds (no Zeeman term).  loss (host,
+ * 4 doubles: L and its three terms at the parameters before the update) may
+ * be NULL; when given the call synchronises.  The gate is ignored. */
+int sl_ml_train_step(sl_ctx* ctx, const double* E_ref, const double* F_ref, const double* B_ref,
+                     const double w[3], double lr, double beta1, double beta2, double eps, double* loss);
 
 /* Sticky device error word (SL_OK or SL_ERR_*).  Synchronises. */
 int sl_status(sl_ctx* ctx);

@@ -19,6 +19,12 @@ SL_OK = 0
 SL_ERR_ARG, SL_ERR_CUDA, SL_ERR_BOX, SL_ERR_SPIN_NORM = -1, -2, -3, -4
 SL_ERR_SKIN, SL_ERR_TIMEOUT, SL_ERR_NONFINITE, SL_ERR_WORKSPACE, SL_ERR_NBR_OVERFLOW = -5, -6, -7, -8, -9
 SL_ROT_RODRIGUES, SL_ROT_CAYLEY = 0, 1
+SL_HAM_ANALYTIC, SL_HAM_LEARNED = 0, 1
+
+# Learned model layout (include/sl.h)
+SL_ML_NF, SL_ML_NH, SL_ML_RC = 48, 64, 6.0
+SL_ML_OFF_W1, SL_ML_OFF_B1, SL_ML_OFF_W2, SL_ML_OFF_B2, SL_ML_OFF_W3, SL_ML_OFF_B3 = 0, 3072, 3136, 7232, 7296, 7360
+SL_ML_NPARAM, SL_ML_NNORM = 7361, 192
 
 # Every exported symbol of include/sl.h.
 EXPORTS = (
@@ -27,6 +33,8 @@ EXPORTS = (
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
     "sl_get_timing", "sl_magnetization_static", "sl_status", "sl_strerror", "sl_destroy",
     "sl_workspace_bytes_batch", "sl_init_batch", "sl_batch_size", "sl_energy_batch", "sl_magnetization_batch",
+    "sl_ml_set_model", "sl_ml_get_model", "sl_ml_eval", "sl_ml_descriptor_stats", "sl_ml_gate", "sl_ml_vjp",
+    "sl_ml_train_step",
 )
 PHASES = ("kick", "spin_half_op_1", "drift_rebuild", "exchange_table", "spin_half_op_2", "force_kick")
 
@@ -36,7 +44,7 @@ class sl_params(ctypes.Structure):
         ("n_atoms", ctypes.c_int32), ("rotation", ctypes.c_int32), ("fix_lattice", ctypes.c_int32),
         ("rebuild_every", ctypes.c_int32), ("morse_shift_energy", ctypes.c_int32),
         ("max_ex_neighbors", ctypes.c_int32), ("max_morse_neighbors", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("hamiltonian", ctypes.c_int32),
         ("box", ctypes.c_double * 3), ("mass_amu", ctypes.c_double), ("mu_s_muB", ctypes.c_double),
         ("H_tesla", ctypes.c_double * 3), ("dt_ps", ctypes.c_double),
         ("ex_alpha_eV", ctypes.c_double), ("ex_gamma", ctypes.c_double), ("ex_delta_A", ctypes.c_double),
@@ -89,6 +97,14 @@ def load():
         "sl_batch_size": ([_vp], ctypes.c_int),
         "sl_energy_batch": ([_vp, _dp], ctypes.c_int),
         "sl_magnetization_batch": ([_vp, _dp], ctypes.c_int),
+        "sl_ml_set_model": ([_vp, _vp, _vp], ctypes.c_int),
+        "sl_ml_get_model": ([_vp, _vp], ctypes.c_int),
+        "sl_ml_eval": ([_vp, _dp, _vp, _vp, _vp], ctypes.c_int),
+        "sl_ml_descriptor_stats": ([_vp, _dp], ctypes.c_int),
+        "sl_ml_gate": ([_vp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "sl_ml_vjp": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+        "sl_ml_train_step": ([_vp, _vp, _vp, _vp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_double, _dp], ctypes.c_int),
         "sl_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "sl_destroy": ([_vp], None),
     }
@@ -136,6 +152,7 @@ def make_params(p: dict) -> sl_params:
     q.temperature_K = float(p.get("temperature_K", 0.0))
     q.seed = int(p.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
     q.replica = int(p.get("replica", 0))
+    q.hamiltonian = int(p.get("hamiltonian", 0))
     return q
 
 

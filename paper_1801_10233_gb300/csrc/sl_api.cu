@@ -27,6 +27,10 @@ struct sl_ctx {
   size_t ev_used;
   double phase_ms[SL_NPHASE];
   long long phase_n[SL_NPHASE];
+  // learned Hamiltonian
+  int ml_ready;             // a model has been set
+  int ml_stale;             // parameters changed since the last evaluation point
+  long long ml_t;           // Adam steps taken
 };
 
 namespace {
@@ -43,9 +47,12 @@ struct DeviceGuard {
 };
 
 // Sector grid of Sec. 5.1: the largest even count per edge with sector edge
-// >= exchange cutoff + skin.
+// >= exchange cutoff + skin (the network's cutoff + skin for the learned
+// Hamiltonian, whose spins interact up to that distance).
 int sector_grid(const sl_params* p, int n[3], double e[3]) {
-  double w = p->ex_rc_A + p->skin_A;
+  double reach = p->ex_rc_A;
+  if (p->hamiltonian == SL_HAM_LEARNED && SL_ML_RC > reach) reach = SL_ML_RC;
+  double w = reach + p->skin_A;
   for (int a = 0; a < 3; ++a) {
     int k = (int)std::floor(p->box[a] / w);
     if (k % 2) k -= 1;
@@ -66,6 +73,10 @@ int validate(const sl_params* p) {
   if (p->max_ex_neighbors > SL_MAX_EX_CAP) return SL_ERR_ARG;
   if (!(p->lambda >= 0.0) || !(p->temperature_K >= 0.0)) return SL_ERR_ARG;
   if (!std::isfinite(p->dt_ps)) return SL_ERR_ARG;
+  if (p->hamiltonian != SL_HAM_ANALYTIC && p->hamiltonian != SL_HAM_LEARNED) return SL_ERR_ARG;
+  if (p->hamiltonian == SL_HAM_LEARNED &&
+      (!(p->morse_rc_A >= SL_ML_RC) || p->lambda != 0.0 || p->temperature_K != 0.0))
+    return SL_ERR_ARG;
   double rc = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
   for (int a = 0; a < 3; ++a)
     if (!(p->box[a] >= 2.0 * rc)) return SL_ERR_BOX;
@@ -91,7 +102,7 @@ int validate_batch(const sl_params* p, int nrep) {
                 a.ex_gamma == b.ex_gamma && a.ex_delta_A == b.ex_delta_A && a.ex_rc_A == b.ex_rc_A &&
                 a.morse_D0_eV == b.morse_D0_eV && a.morse_alpha_invA == b.morse_alpha_invA &&
                 a.morse_r0_A == b.morse_r0_A && a.morse_rc_A == b.morse_rc_A && a.skin_A == b.skin_A &&
-                a.lambda == b.lambda && a.seed == b.seed;
+                a.lambda == b.lambda && a.seed == b.seed && a.hamiltonian == b.hamiltonian;
     for (int c = 0; c < 3; ++c) same = same && a.H_tesla[c] == b.H_tesla[c];
     if (!same) return SL_ERR_ARG;
   }
@@ -194,6 +205,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   d.half_skin2 = 0.25 * p->skin_A * p->skin_A;
   d.lambda = p->lambda;
   d.seed = p->seed;
+  d.ham = p->hamiltonian;
   d.inv_hbar_f = split_f2(1.0 / SL_HBAR);
   d.m_nalpha_f = split_f2(-p->morse_alpha_invA);
   d.m_r0_f = split_f2(p->morse_r0_A);
@@ -229,6 +241,33 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_reps = L.take<SlRep>((size_t)nrep);
   size_t o_stage = L.take<double>(nn * 9);
   size_t o_ctrl = L.take<SlCtrl>(1);
+  const bool ml = p->hamiltonian == SL_HAM_LEARNED;
+  const size_t ntile = (nn + SL_ML_ATOMS_PER_TILE - 1) / SL_ML_ATOMS_PER_TILE;
+  size_t o_mpar = 0, o_mnorm = 0, o_mtiles = 0, o_mfc = 0, o_mx = 0, o_mG = 0, o_me = 0, o_mB = 0, o_mpq = 0;
+  size_t o_mu = 0, o_mgF = 0, o_mgB = 0, o_malpha = 0, o_mgpart = 0, o_mgrad = 0, o_mm1 = 0, o_mm2 = 0;
+  size_t o_merep = 0, o_mlossat = 0, o_mloss = 0;
+  if (ml) {
+    o_mpar = L.take<float>(SL_ML_NPARAM); o_mnorm = L.take<float>(SL_ML_NNORM);
+    o_mtiles = L.take<uint4>(SL_ML_TILE_BYTES / 16); o_mfc = L.take<float>(SL_MLC_SIZE);
+    o_mx = L.take<float>(nn * SL_ML_NF); o_mG = L.take<float>(nn * 64); o_me = L.take<float>(nn);
+    o_mB = L.take<float4>(nn); o_mpq = L.take<float2>(nn * d.max_m);
+    o_mu = L.take<float>(nn * SL_ML_NF); o_mgF = L.take<float4>(nn); o_mgB = L.take<float4>(nn);
+    o_malpha = L.take<double>(nn); o_mgpart = L.take<float>(ntile * SL_ML_NPARAM);
+    o_mgrad = L.take<double>(SL_ML_NPARAM); o_mm1 = L.take<double>(SL_ML_NPARAM);
+    o_mm2 = L.take<double>(SL_ML_NPARAM); o_merep = L.take<double>((size_t)nrep);
+    o_mlossat = L.take<double>(2 * nn); o_mloss = L.take<double>(4);
+  }
+  if (base && ml) {
+    d.ml_par = (float*)(base + o_mpar); d.ml_norm = (float*)(base + o_mnorm);
+    d.ml_tiles = (uint4*)(base + o_mtiles); d.ml_fc = (float*)(base + o_mfc);
+    d.ml_x = (float*)(base + o_mx); d.ml_G = (float*)(base + o_mG); d.ml_e = (float*)(base + o_me);
+    d.ml_B = (float4*)(base + o_mB); d.ml_pq = (float2*)(base + o_mpq);
+    d.ml_u = (float*)(base + o_mu); d.ml_gF = (float4*)(base + o_mgF); d.ml_gB = (float4*)(base + o_mgB);
+    d.ml_alpha = (double*)(base + o_malpha); d.ml_gpart = (float*)(base + o_mgpart);
+    d.ml_grad = (double*)(base + o_mgrad); d.ml_m1 = (double*)(base + o_mm1); d.ml_m2 = (double*)(base + o_mm2);
+    d.ml_erep = (double*)(base + o_merep); d.ml_lossat = (double*)(base + o_mlossat);
+    d.ml_loss = (double*)(base + o_mloss);
+  }
   if (base) {
     d.r = (double4_32a*)(base + o_r); d.v = (double4_32a*)(base + o_v); d.s = (double4_32a*)(base + o_s);
     d.F = (double4_32a*)(base + o_F); d.rb = (double4_32a*)(base + o_rb);
@@ -371,10 +410,20 @@ int fold_timing(sl_ctx* c) {
 }
 
 // Exchange table + forces at the current state; rebuild first if flagged.
+// With the learned Hamiltonian (once a model is set) this is an evaluation
+// point: the analytic kernels only run where the gate closes.
 int refresh(sl_ctx* c) {
   int e = sl_launch_rebuild(c->d, c->stream);
+  if (!e && c->d.ham == SL_HAM_LEARNED && c->ml_ready) e = sl_ml_launch_point(c->d, c->stream, 1);
   if (!e) e = sl_launch_pairs_and_forces(c->d, c->stream, 0);
+  if (!e) c->ml_stale = 0;
   return e ? e : cuda_err(c);
+}
+
+// Re-evaluate after the parameters changed (training) before state-dependent use.
+int ml_fresh(sl_ctx* c) {
+  if (c->d.ham != SL_HAM_LEARNED || !c->ml_stale) return SL_OK;
+  return refresh(c);
 }
 
 }  // namespace
@@ -413,7 +462,7 @@ int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, 
   plan(params, n_replicas, c->d, c->reps, (char*)workspace);
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SL_ERR_CUDA; }
-  if (sl_prepare_kernels() != SL_OK) {
+  if (sl_prepare_kernels() != SL_OK || (c->d.ham == SL_HAM_LEARNED && sl_ml_prepare_kernels() != SL_OK)) {
     sl_destroy(c);
     return SL_ERR_CUDA;
   }
@@ -448,7 +497,9 @@ int sl_build_neighbors(sl_ctx* c) {
 int sl_step(sl_ctx* c, int32_t n_steps) {
   if (!c || n_steps < 0) return SL_ERR_ARG;
   if (c->sticky) return c->sticky;
+  if (c->d.ham == SL_HAM_LEARNED && !c->ml_ready) return SL_ERR_ARG;
   DeviceGuard g(c->device);
+  if (int e = ml_fresh(c)) return e;
   if (c->timing) {
     // direct launches with an event pair around each phase
     for (int k = 0; k < n_steps; ++k) {
@@ -514,6 +565,7 @@ int sl_set_field(sl_ctx* c, const double H[3]) {
 static int observe(sl_ctx* c, std::vector<double>& red) {
   if (c->sticky) return c->sticky;
   DeviceGuard g(c->device);
+  if (int e = ml_fresh(c)) return e;
   int e = sl_launch_observables(c->d, c->stream);
   if (e) return e;
   red.assign((size_t)c->nrep * SL_NOBS, 0.0);
@@ -637,6 +689,7 @@ int sl_get_forces(sl_ctx* c, double* F) {
   if (!c || !F) return SL_ERR_ARG;
   if (c->sticky) return c->sticky;
   DeviceGuard g(c->device);
+  if (int e = ml_fresh(c)) return e;
   k_store<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d, c->d.F, F);
   return cuda_err(c);
 }
@@ -645,6 +698,7 @@ int sl_get_omega(sl_ctx* c, double* w) {
   if (!c || !w) return SL_ERR_ARG;
   if (c->sticky) return c->sticky;
   DeviceGuard g(c->device);
+  if (int e = ml_fresh(c)) return e;
   int e = sl_launch_omega_all(c->d, w, c->stream);
   return e ? e : cuda_err(c);
 }
@@ -676,6 +730,117 @@ int sl_counters(sl_ctx* c, int64_t out[8]) {
   out[4] = c->kernels_per_step; out[5] = c->graph_ok; out[6] = 0; out[7] = 0;
   if (h.status && !c->sticky) c->sticky = h.status;
   return c->sticky;
+}
+
+// ---------------------------------------------------------------------------
+// Learned Hamiltonian
+// ---------------------------------------------------------------------------
+static int ml_check(sl_ctx* c, bool need_model) {
+  if (!c) return SL_ERR_ARG;
+  if (c->d.ham != SL_HAM_LEARNED) return SL_ERR_ARG;
+  if (need_model && !c->ml_ready) return SL_ERR_ARG;
+  return c->sticky;
+}
+
+int sl_ml_set_model(sl_ctx* c, const float* params, const float* norm) {
+  if (!params || !norm) return SL_ERR_ARG;
+  if (int e = ml_check(c, false)) return e;
+  DeviceGuard g(c->device);
+  const SlDev& d = c->d;
+  if (cudaMemcpyAsync(d.ml_par, params, sizeof(float) * SL_ML_NPARAM, cudaMemcpyDefault, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d.ml_norm, norm, sizeof(float) * SL_ML_NNORM, cudaMemcpyDefault, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(d.ml_m1, 0, sizeof(double) * SL_ML_NPARAM, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(d.ml_m2, 0, sizeof(double) * SL_ML_NPARAM, c->stream) != cudaSuccess)
+    return cuda_err(c);
+  c->ml_t = 0;
+  int e = sl_ml_launch_prep(d, c->stream);
+  if (e) return e;
+  c->ml_ready = 1;
+  drop_graph(c);
+  return refresh(c);
+}
+
+int sl_ml_get_model(sl_ctx* c, float* params) {
+  if (!params) return SL_ERR_ARG;
+  if (int e = ml_check(c, true)) return e;
+  DeviceGuard g(c->device);
+  if (cudaMemcpyAsync(params, c->d.ml_par, sizeof(float) * SL_ML_NPARAM, cudaMemcpyDefault, c->stream) !=
+      cudaSuccess)
+    return cuda_err(c);
+  return c->sticky;
+}
+
+int sl_ml_eval(sl_ctx* c, double* e_rep, double* F, double* B, double* D) {
+  if (int e = ml_check(c, true)) return e;
+  DeviceGuard g(c->device);
+  int e = sl_ml_launch_eval(c->d, c->stream, F, B, D);
+  if (e) return e;
+  if (e_rep) {
+    if (cudaMemcpyAsync(e_rep, c->d.ml_erep, sizeof(double) * c->nrep, cudaMemcpyDeviceToHost, c->stream) !=
+        cudaSuccess)
+      return cuda_err(c);
+    return sync_status(c);
+  }
+  return cuda_err(c);
+}
+
+int sl_ml_descriptor_stats(sl_ctx* c, double* out) {
+  if (!out) return SL_ERR_ARG;
+  if (int e = ml_check(c, false)) return e;
+  DeviceGuard g(c->device);
+  // the gradient buffer (SL_ML_NPARAM doubles) serves as device scratch
+  int e = sl_ml_launch_dstats(c->d, c->stream, c->d.ml_grad);
+  if (e) return e;
+  if (cudaMemcpyAsync(out, c->d.ml_grad, sizeof(double) * 4 * SL_ML_NF, cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return cuda_err(c);
+  return sync_status(c);
+}
+
+int sl_ml_gate(sl_ctx* c, int64_t out[4]) {
+  if (!out) return SL_ERR_ARG;
+  if (int e = ml_check(c, false)) return e;
+  DeviceGuard g(c->device);
+  if (int e = ml_fresh(c)) return e;
+  SlCtrl h;
+  if (cudaMemcpyAsync(&h, c->d.ctrl, sizeof(SlCtrl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return cuda_err(c);
+  out[0] = h.ml_bad_last; out[1] = h.ml_use; out[2] = h.ml_trips; out[3] = 0;
+  if (h.status && !c->sticky) c->sticky = h.status;
+  return c->sticky;
+}
+
+int sl_ml_vjp(sl_ctx* c, const double* gE, const double* gF, const double* gB, double* grad) {
+  if (!grad) return SL_ERR_ARG;
+  if (int e = ml_check(c, true)) return e;
+  DeviceGuard g(c->device);
+  int e = sl_ml_launch_eval(c->d, c->stream, nullptr, nullptr, nullptr);
+  if (!e) e = sl_ml_launch_vjp(c->d, c->stream, gE, gF, gB);
+  if (e) return e;
+  if (cudaMemcpyAsync(grad, c->d.ml_grad, sizeof(double) * SL_ML_NPARAM, cudaMemcpyDeviceToDevice, c->stream) !=
+      cudaSuccess)
+    return cuda_err(c);
+  return cuda_err(c);
+}
+
+int sl_ml_train_step(sl_ctx* c, const double* E_ref, const double* F_ref, const double* B_ref, const double w[3],
+                     double lr, double beta1, double beta2, double eps, double* loss) {
+  if (!E_ref || !F_ref || !B_ref || !w) return SL_ERR_ARG;
+  if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+    return SL_ERR_ARG;
+  if (int e = ml_check(c, true)) return e;
+  DeviceGuard g(c->device);
+  c->ml_t += 1;
+  int e = sl_ml_launch_train(c->d, c->stream, E_ref, F_ref, B_ref, w, lr, beta1, beta2, eps, c->ml_t);
+  if (e) return e;
+  c->ml_stale = 1;
+  if (loss) {
+    if (cudaMemcpyAsync(loss, c->d.ml_loss, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+      return cuda_err(c);
+    return sync_status(c);
+  }
+  return cuda_err(c);
 }
 
 int sl_status(sl_ctx* c) {

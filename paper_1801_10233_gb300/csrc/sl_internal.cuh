@@ -25,6 +25,11 @@ struct SlCtrl {
   int32_t max_ex_seen;
   int32_t max_m_seen;
   int32_t pad;
+  // learned Hamiltonian: range gate of the current evaluation point
+  int32_t ml_bad;           // atoms counted out of range by the descriptor kernel
+  int32_t ml_use;           // 1: this evaluation point uses the network
+  int32_t ml_trips;         // evaluation points handed to the analytic Hamiltonian
+  int32_t ml_bad_last;      // ml_bad of the last evaluation point
 };
 
 // One system of a batch: its box, sector grid, atom range and spin bath.
@@ -62,6 +67,7 @@ struct SlDev {
   double lambda;
   int any_noise;            // some replica has a bath temperature
   uint64_t seed;
+  int ham;                  // SL_HAM_ANALYTIC or SL_HAM_LEARNED
 
   // double-float constants (hi, lo)
   float2 zee_f[3], inv_hbar_f, tau_f;        // tau = dt/4
@@ -95,7 +101,42 @@ struct SlDev {
   // staging for host copies, [n][3] doubles x 3
   double *stage;
   SlCtrl *ctrl;
+
+  // learned Hamiltonian (NULL unless ham == SL_HAM_LEARNED)
+  float *ml_par;            // [SL_ML_NPARAM] float32 master parameters
+  float *ml_norm;           // [SL_ML_NNORM] mean, inv_std, gate lo, gate hi
+  uint4 *ml_tiles;          // bfloat16 weight tiles in the MMA's shared-memory layout
+  float *ml_fc;             // epilogue constants (SL_MLC_* offsets)
+  float *ml_x;              // [n][48] normalised descriptors
+  float *ml_G;              // [n][48] dE_i/dD_i
+  float *ml_e;              // [n] E_i
+  float4 *ml_B;             // [n] -dE/ds_i
+  float2 *ml_pq;            // [max_m][n] frozen field coefficients (P, Q)
+  float *ml_u;              // [n][48] tangent direction / descriptor scratch
+  float4 *ml_gF, *ml_gB;    // [n] upstream gradients of F and B (sorted order)
+  double *ml_alpha;         // [n] upstream gradient of E_i (its replica's)
+  float *ml_gpart;          // [tiles][SL_ML_NPARAM] per-tile parameter gradients
+  double *ml_grad;          // [SL_ML_NPARAM]
+  double *ml_m1, *ml_m2;    // Adam moments
+  double *ml_erep;          // [nrep] sum of E_i per replica
+  double *ml_lossat;        // [n][2] per-atom loss terms
+  double *ml_loss;          // [4]
 };
+
+// Offsets into ml_fc (floats): b1[64], b2[64], w3[64] (bfloat16 values), b3,
+// then mean, inv_std, lo, hi [48] each.
+#define SL_MLC_B1 0
+#define SL_MLC_B2 64
+#define SL_MLC_W3 128
+#define SL_MLC_B3 192
+#define SL_MLC_MEAN 256
+#define SL_MLC_ISTD 304
+#define SL_MLC_LO 352
+#define SL_MLC_HI 400
+#define SL_MLC_SIZE 448
+// Bytes of the bfloat16 weight tiles: W1 [64 x 48], W2 [64 x 64], W2^T [64 x 64], W1^T [48 x 64].
+#define SL_ML_TILE_BYTES (2 * (64 * 48 + 64 * 64 + 64 * 64 + 48 * 64))
+#define SL_ML_ATOMS_PER_TILE 128
 
 #define SL_NOBS 10  // Ek, Em, Ex, Ez, Mx, My, Mz, TS numerator, TS denominator, non-finite flag
 
@@ -152,3 +193,17 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
 int sl_launch_observables(const SlDev& d, cudaStream_t st);
 int sl_launch_force_rebuild_flag(const SlDev& d, cudaStream_t st);
 int sl_launch_omega_all(const SlDev& d, double* out, cudaStream_t st);
+// Learned Hamiltonian (sl_ml.cu).
+// Evaluation point: descriptors + gate, network, pair terms; fmode 0: only
+// the field table, 1: also forces into F, 3: forces and the closing half-kick.
+// With force = 1 the gate is ignored and left unchanged.
+int sl_ml_launch_point(const SlDev& d, cudaStream_t st, int fmode);
+int sl_ml_launch_half_op(const SlDev& d, cudaStream_t st);
+int sl_ml_launch_prep(const SlDev& d, cudaStream_t st);
+int sl_ml_launch_eval(const SlDev& d, cudaStream_t st, double* F, double* B, double* D);
+int sl_ml_launch_dstats(const SlDev& d, cudaStream_t st, double* out_dev);
+int sl_ml_launch_vjp(const SlDev& d, cudaStream_t st, const double* gE, const double* gF, const double* gB);
+int sl_ml_launch_train(const SlDev& d, cudaStream_t st, const double* E_ref, const double* F_ref,
+                       const double* B_ref, const double w[3], double lr, double b1, double b2, double eps,
+                       long long t);
+int sl_ml_prepare_kernels();

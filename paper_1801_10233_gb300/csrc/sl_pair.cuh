@@ -1,0 +1,185 @@
+// Device helpers shared by the kernels that gather pairs and rotate spins:
+// split positions and spins, exact minimum-image separations in
+// double-float, the spin bath's counter-based normals, and the single-spin
+// propagator.
+#pragma once
+
+#include "sl_internal.cuh"
+#include "sl_df64.cuh"
+
+namespace {
+
+__device__ __forceinline__ df F2(float2 v) { return df_make(v.x, v.y); }
+__device__ __forceinline__ float2 D2(df a) { return make_float2(a.hi, a.lo); }
+
+struct df3 {
+  df x, y, z;
+};
+struct p3 {
+  f3 x, y, z;
+};
+
+// Positions, lists and tables are read-only in every kernel that gathers
+// them; their loads go through the read-only path and may be issued early.
+__device__ __forceinline__ p3 load_pos(const SlDev& d, int j) {
+  float4 h = __ldg(d.rh + j), m = __ldg(d.rm + j), l = __ldg(d.rl + j);
+  p3 p;
+  p.x.h = h.x; p.x.m = m.x; p.x.l = l.x;
+  p.y.h = h.y; p.y.m = m.y; p.y.l = l.y;
+  p.z.h = h.z; p.z.m = m.z; p.z.l = l.z;
+  return p;
+}
+
+__device__ __forceinline__ df3 load_spin(const SlDev& d, int j) {
+  float4 h = __ldg(d.sdf + 2 * (size_t)j), l = __ldg(d.sdf + 2 * (size_t)j + 1);
+  df3 s;
+  s.x = df_make(h.x, l.x); s.y = df_make(h.y, l.y); s.z = df_make(h.z, l.z);
+  return s;
+}
+
+// The replica's box as exact three-float pieces.
+struct box3 {
+  f3 L[3];
+  float inv[3];
+};
+__device__ __forceinline__ box3 load_box(const SlRep& R) {
+  box3 b;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    b.L[a].h = R.box_h[a]; b.L[a].m = R.box_m[a]; b.L[a].l = R.box_l[a];
+    b.inv[a] = R.inv_box_f[a];
+  }
+  return b;
+}
+
+__device__ __forceinline__ df3 pair_sep(const box3& B, const p3& a, const p3& b) {
+  df3 r;
+  r.x = f3_sep(b.x, a.x, B.L[0], B.inv[0]);
+  r.y = f3_sep(b.y, a.y, B.L[1], B.inv[1]);
+  r.z = f3_sep(b.z, a.z, B.L[2], B.inv[2]);
+  return r;
+}
+
+__device__ __forceinline__ df dot3(const df3& a, const df3& b) {
+  float h = 0.0f, l = 0.0f;
+  acc_prod(h, l, a.x, b.x);
+  acc_prod(h, l, a.y, b.y);
+  acc_prod(h, l, a.z, b.z);
+  return acc_done(h, l);
+}
+
+__device__ __forceinline__ df3 cross3(const df3& a, const df3& b) {
+  df3 c;
+  float h, l;
+  h = l = 0.0f; acc_prod(h, l, a.y, b.z); acc_prod(h, l, df_neg(a.z), b.y); c.x = acc_done(h, l);
+  h = l = 0.0f; acc_prod(h, l, a.z, b.x); acc_prod(h, l, df_neg(a.x), b.z); c.y = acc_done(h, l);
+  h = l = 0.0f; acc_prod(h, l, a.x, b.y); acc_prod(h, l, df_neg(a.y), b.x); c.z = acc_done(h, l);
+  return c;
+}
+
+__device__ __forceinline__ void store_pos_split(const SlDev& d, int k, double4_32a r) {
+  f3 x = f3_from_double(r.x), y = f3_from_double(r.y), z = f3_from_double(r.z);
+  d.rh[k] = make_float4(x.h, y.h, z.h, 0.0f);
+  d.rm[k] = make_float4(x.m, y.m, z.m, 0.0f);
+  d.rl[k] = make_float4(x.l, y.l, z.l, 0.0f);
+}
+
+__device__ __forceinline__ void store_spin_split(const SlDev& d, int k, double4_32a s) {
+  df x = df_from_double(s.x), y = df_from_double(s.y), z = df_from_double(s.z);
+  d.sdf[2 * (size_t)k] = make_float4(x.hi, y.hi, z.hi, 0.0f);
+  d.sdf[2 * (size_t)k + 1] = make_float4(x.lo, y.lo, z.lo, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and Box-Muller normals for the spin bath.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ double3 gauss3(uint64_t seed, int replica, long long step, int subpass, int atom) {
+  uint4 x = philox4x32_10(make_uint4((unsigned)atom, (unsigned)step, (unsigned)subpass, (unsigned)replica),
+                          make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+  const double inv32 = 2.3283064365386962890625e-10;  // 2^-32
+  const double twopi = 6.283185307179586476925286766559;
+  double u0 = ((double)x.x + 0.5) * inv32, u1 = ((double)x.y + 0.5) * inv32;
+  double u2 = ((double)x.z + 0.5) * inv32, u3 = ((double)x.w + 0.5) * inv32;
+  double ra = sqrt(-2.0 * log(u0)), rb = sqrt(-2.0 * log(u2));
+  double s1, c1, s3, c3;
+  sincos(twopi * u1, &s1, &c1);
+  sincos(twopi * u3, &s3, &c3);
+  return make_double3(ra * c1, ra * s1, rb * c3);
+}
+
+// ---------------------------------------------------------------------------
+// Single-spin propagator e^{L_si tau} as an increment of s:
+//   s' - s = -u B s + tau A (w x s) + tau^2 B (w.s) w,      u = tau^2 |w|^2.
+// Exact rotation by theta = |w| tau: A = sin(theta)/theta,
+// B = (1 - cos theta)/theta^2 (even series in theta; for u <= 1e-3 the series
+// are summed in df, beyond that A and B come from FP64 sin).  Cayley map of
+// Sec. 3: A = 1/(1 + u/4), B = A/2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau, int cayley) {
+  float h = 0.0f, l = 0.0f;
+  acc_prod(h, l, w.x, w.x);
+  acc_prod(h, l, w.y, w.y);
+  acc_prod(h, l, w.z, w.z);
+  df w2 = acc_done(h, l);
+  df tau2 = df_sqr(tau);
+  df u = df_mul(w2, tau2);
+  df A, B;
+  if (cayley) {
+    df den = df_add_f(df_scale(u, 0.25f), 1.0f);
+    float y0 = __frcp_rn(den.hi);
+    df e = df_add_f(df_neg(df_mul_f(den, y0)), 1.0f);     // 1 - den y0
+    A = df_add_f(df_f(y0), y0 * e.hi);                     // 1 / den
+    B = df_scale(A, 0.5f);
+  } else if (u.hi <= 2e-4f) {
+    // theta <= 0.014: A = 1 - u (1/6 - u/120 + u^2/5040), B = 1/2 - u (1/24 - u/720 + u^2/40320);
+    // the u^2 terms and beyond are below 1e-17 of A and B
+    const df c6 = df_make(SL_INV_FACT3_HI, SL_INV_FACT3_LO);
+    const df c24 = df_make(SL_INV_FACT4_HI, SL_INV_FACT4_LO);
+    df a1 = df_add_f(c6, -u.hi * __fmaf_rn(-u.hi, 1.0f / 5040.0f, 1.0f / 120.0f));
+    df b1 = df_add_f(c24, -u.hi * __fmaf_rn(-u.hi, 1.0f / 40320.0f, 1.0f / 720.0f));
+    A = df_add_f(df_neg(df_mul(u, a1)), 1.0f);
+    B = df_add_f(df_neg(df_mul(u, b1)), 0.5f);
+  } else if (u.hi <= 1e-3f) {
+    const df c6 = df_make(SL_INV_FACT3_HI, SL_INV_FACT3_LO);       // 1/3!
+    const df c120 = df_make(SL_INV_FACT5_HI, SL_INV_FACT5_LO);     // 1/5!
+    const df c24 = df_make(SL_INV_FACT4_HI, SL_INV_FACT4_LO);      // 1/4!
+    const df c720 = df_make(SL_INV_FACT6_HI, SL_INV_FACT6_LO);     // 1/6!
+    float ta = __fmaf_rn(-u.hi, __fmaf_rn(-u.hi, 1.0f / 39916800.0f, 1.0f / 362880.0f), 1.0f / 5040.0f);
+    float tb = __fmaf_rn(-u.hi, __fmaf_rn(-u.hi, 1.0f / 479001600.0f, 1.0f / 3628800.0f), 1.0f / 40320.0f);
+    df a1 = df_sub(c6, df_mul(u, df_add_f(c120, -u.hi * ta)));     // 1/6 - u/120 + u^2/5040 - ...
+    df b1 = df_sub(c24, df_mul(u, df_add_f(c720, -u.hi * tb)));    // 1/24 - u/720 + u^2/40320 - ...
+    A = df_add_f(df_neg(df_mul(u, a1)), 1.0f);
+    B = df_add_f(df_neg(df_mul(u, b1)), 0.5f);
+  } else {
+    double ud = df_to_double(u);
+    double th = sqrt(ud);
+    double hs = sin(0.5 * th);
+    A = df_from_double(sin(th) / th);
+    B = df_from_double(2.0 * hs * hs / ud);
+  }
+  df uB = df_mul(u, B);
+  df tA = df_mul(tau, A);
+  df tBws = df_mul(df_mul(tau2, B), dot3(w, s));
+  df3 c = cross3(w, s);
+  df3 inc;
+  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.x); acc_prod(h, l, tA, c.x); acc_prod(h, l, tBws, w.x);
+  inc.x = acc_done(h, l);
+  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.y); acc_prod(h, l, tA, c.y); acc_prod(h, l, tBws, w.y);
+  inc.y = acc_done(h, l);
+  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.z); acc_prod(h, l, tA, c.z); acc_prod(h, l, tBws, w.z);
+  inc.z = acc_done(h, l);
+  return inc;
+}
+
+}  // namespace

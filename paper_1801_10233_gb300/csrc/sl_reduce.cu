@@ -19,7 +19,7 @@ __global__ void k_obs_atoms(SlDev d) {
   double q[SL_NOBS];
   q[0] = 0.5 * d.mass * (v.x * v.x + v.y * v.y + v.z * v.z) / SL_FTOA;
   double em = 0.0;
-  const int nm = d.mn[i];
+  const int nm = (d.ham == SL_HAM_LEARNED && d.ctrl->ml_use) ? 0 : d.mn[i];
   for (int k = 0; k < nm; ++k) {
     const int j = d.mj[(size_t)k * d.n + i];
     const double3 dd = sl_min_image(R, ri, d.r[j]);
@@ -32,7 +32,14 @@ __global__ void k_obs_atoms(SlDev d) {
   q[1] = 0.5 * em;
   double hx = d.zee[0], hy = d.zee[1], hz = d.zee[2];
   double ex = 0.0;
-  const int ne = d.exn[i];
+  const bool learned = d.ham == SL_HAM_LEARNED && d.ctrl->ml_use;
+  if (learned) {
+    // the network's energy E_i (lattice + exchange together) and field -dE/ds_i
+    const float4 b = d.ml_B[i];
+    q[1] = (double)d.ml_e[i];
+    hx += b.x; hy += b.y; hz += b.z;
+  }
+  const int ne = learned ? 0 : d.exn[i];
   for (int k = 0; k < ne; ++k) {
     const size_t e = (size_t)k * d.n + i;
     const float2 J2 = d.exJ[e];

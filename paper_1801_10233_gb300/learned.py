@@ -1,0 +1,148 @@
+"""Learned per-atom Hamiltonian: PyTorch autograd front ends, training data
+and training loop around libsl's kernels (include/sl.h, "Learned per-atom
+Hamiltonian").
+
+Every number here comes from libsl: the descriptors, the network, its
+backward pass (forces -dE/dr and fields -dE/ds), the parameter gradients and
+the Adam update all run in CUDA kernels; this module only moves tensors.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from .system import System
+
+HBAR = 6.582119569e-4        # eV ps / rad
+MU_B = 5.7883818060e-5       # eV / T
+
+
+def zeeman_field(params) -> np.ndarray:
+    """mu_s mu_B H (eV): the Zeeman part of -dH/ds, which the network does not model."""
+    return float(params["mu_s_muB"]) * MU_B * np.asarray(params["H_tesla"], dtype=np.float64)
+
+
+class LearnedEnergy(torch.autograd.Function):
+    """E_r(r, s) = sum of the network's E_i over replica r.
+
+    forward(r, s, params, system) -> E [n_replicas]; backward gives
+    dE/dr = -F and dE/ds = -B from the hand-written backward kernel, and
+    dE/dparams from the parameter vector-Jacobian product kernel.  `system`
+    is a System created with hamiltonian = SL_HAM_LEARNED; its state is
+    replaced by (r, s) (velocities zero)."""
+
+    @staticmethod
+    def forward(ctx, r, s, params, system: System):
+        system.ml_set_model(params.detach(), system._ml_norm)
+        system.set_state(r.detach(), torch.zeros_like(r, dtype=torch.float64), s.detach())
+        e, F, B, _ = system.ml_eval()
+        ctx.system = system
+        ctx.save_for_backward(F, B)
+        return torch.as_tensor(e, dtype=torch.float64, device=r.device)
+
+    @staticmethod
+    def backward(ctx, gE):
+        F, B = ctx.saved_tensors
+        system = ctx.system
+        rep = system._atom_replica.to(gE.device)
+        g_atom = gE.to(torch.float64)[rep].unsqueeze(1)
+        grad_r = -g_atom * F if ctx.needs_input_grad[0] else None
+        grad_s = -g_atom * B if ctx.needs_input_grad[1] else None
+        grad_p = None
+        if ctx.needs_input_grad[2]:
+            grad_p = system.ml_vjp(gE=gE).to(torch.float32)
+        return grad_r, grad_s, grad_p, None
+
+
+class LearnedForces(torch.autograd.Function):
+    """(E [n_replicas], F [N,3], B [N,3]) of the network as functions of its
+    parameters; backward is the forward-over-reverse vector-Jacobian product
+    kernel, so a loss on forces and fields can be differentiated with respect
+    to the parameters."""
+
+    @staticmethod
+    def forward(ctx, params, system: System):
+        system.ml_set_model(params.detach(), system._ml_norm)
+        e, F, B, _ = system.ml_eval()
+        ctx.system = system
+        return torch.as_tensor(e, dtype=torch.float64, device=F.device), F, B
+
+    @staticmethod
+    def backward(ctx, gE, gF, gB):
+        g = ctx.system.ml_vjp(gE=gE, gF=gF, gB=gB)
+        return g.to(torch.float32), None
+
+
+def learned_system(params_list, r, v, s, norm, model, device=None) -> System:
+    """A System with the learned Hamiltonian and a model installed."""
+    plist = [params_list] if isinstance(params_list, dict) else list(params_list)
+    plist = [dict(p, hamiltonian=_lib.SL_HAM_LEARNED) for p in plist]
+    sysm = System(plist, r, v, s, device=device)
+    sysm._ml_norm = torch.as_tensor(norm, dtype=torch.float32)
+    counts = [int(p["n_atoms"]) for p in plist]
+    sysm._atom_replica = torch.repeat_interleave(torch.arange(len(counts)), torch.tensor(counts))
+    sysm.ml_set_model(model, norm)
+    return sysm
+
+
+def normalisation(stats: np.ndarray, gate_margin: float = 0.5) -> np.ndarray:
+    """Normalisation vector from descriptor statistics [4, 48] (mean, std,
+    min, max): inv_std = 1/(std + 1e-3); the gate accepts [min - m (max - min),
+    max + m (max - min)]."""
+    mean, std, lo, hi = stats
+    span = np.maximum(hi - lo, 1e-6)
+    out = np.concatenate([mean, 1.0 / (std + 1e-3), lo - gate_margin * span, hi + gate_margin * span])
+    return out.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Training data: snapshots of analytic trajectories
+# ---------------------------------------------------------------------------
+def snapshots(plist, r, v, s, n_snap, every, device=None, lam=None):
+    """Run the analytic Hamiltonian on the replicas of `plist` and take n_snap
+    snapshots, `every` steps apart.  Returns a dict of device tensors:
+    r, s [n_snap, N, 3], E [n_snap, n_replicas] (Morse + exchange energy),
+    F [n_snap, N, 3], B [n_snap, N, 3] (-dE/ds without the Zeeman part)."""
+    sysa = System(plist, r, v, s, device=device)
+    zee = torch.as_tensor(np.stack([zeeman_field(p) for p in plist]), device=sysa.device)
+    counts = [int(p["n_atoms"]) for p in plist]
+    rep = torch.repeat_interleave(torch.arange(len(counts)), torch.tensor(counts)).to(sysa.device)
+    out = {k: [] for k in ("r", "s", "E", "F", "B")}
+    for k in range(n_snap):
+        if k:
+            sysa.step(every)
+        rr, _, ss = sysa.state()
+        e = sysa.energy_per_replica()
+        out["r"].append(rr)
+        out["s"].append(ss)
+        out["E"].append(torch.as_tensor(e[:, 1] + e[:, 2], device=sysa.device))
+        out["F"].append(sysa.forces())
+        out["B"].append(sysa.omega() * HBAR - zee[rep])
+    sysa.close()
+    return {k: torch.stack(v) for k, v in out.items()}
+
+
+def train(sysm: System, data, epochs, lr, w=(1.0, 1.0, 1e-6), batch_frames=None, lr_min=None, log=None):
+    """Adam on the network of `sysm`, whose replicas are the frames of one
+    batch: data["r"], data["s"] [n_frames, N, 3] (N = sysm.n) with labels
+    data["E"] [n_frames, nrep], data["F"], data["B"].  Cosine learning-rate
+    decay to lr_min.  Returns the list of per-step losses."""
+    n_frames = data["r"].shape[0]
+    zeros = torch.zeros_like(data["r"][0])
+    losses = []
+    total = epochs * n_frames
+    lr_min = lr if lr_min is None else lr_min
+    step = 0
+    for ep in range(epochs):
+        for f in range(n_frames):
+            cur = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * step / max(1, total - 1)))
+            sysm.set_state(data["r"][f], zeros, data["s"][f])
+            loss = sysm.ml_train_step(data["E"][f], data["F"][f], data["B"][f], w, cur)
+            losses.append(loss.copy())
+            if log is not None and (step % log == 0):
+                print(f"train step {step} lr {cur:.2e} loss {loss}")
+            step += 1
+    return losses

@@ -169,3 +169,70 @@ class System:
         check(self._L.sl_get_order(self._h, o.data_ptr(), cs, ns), "sl_get_order")
         return dict(order=o.cpu().numpy(), colour_start=np.array(cs[:], dtype=np.int32),
                     nsec=np.array(ns[:], dtype=np.int32))
+
+    # -- learned Hamiltonian -----------------------------------------------
+    def ml_set_model(self, params, norm):
+        """Install the network (float32 params [SL_ML_NPARAM], norm [SL_ML_NNORM])."""
+        p = torch.as_tensor(params, dtype=torch.float32).to(self.device).contiguous()
+        q = torch.as_tensor(norm, dtype=torch.float32).to(self.device).contiguous()
+        self.stream.synchronize()
+        check(self._L.sl_ml_set_model(self._h, p.data_ptr(), q.data_ptr()), "sl_ml_set_model")
+        self.stream.synchronize()
+
+    def ml_get_model(self) -> torch.Tensor:
+        p = torch.empty(_lib.SL_ML_NPARAM, dtype=torch.float32, device=self.device)
+        check(self._L.sl_ml_get_model(self._h, p.data_ptr()), "sl_ml_get_model")
+        self.stream.synchronize()
+        return p
+
+    def ml_eval(self, want_D=False):
+        """Network at the current state (gate ignored): (E per replica [nrep]
+        numpy, F [N,3], B = -dE/ds [N,3], D [N,48] or None) in caller order."""
+        e = np.empty(self.nrep)
+        F, B = self._empty3(), self._empty3()
+        D = torch.empty((self.n, _lib.SL_ML_NF), dtype=torch.float64, device=self.device) if want_D else None
+        check(self._L.sl_ml_eval(self._h, _lib._arr_ptr(e), F.data_ptr(), B.data_ptr(),
+                                 D.data_ptr() if D is not None else None), "sl_ml_eval")
+        return e, F, B, D
+
+    def ml_descriptor_stats(self) -> np.ndarray:
+        """[4, 48]: mean, std, min, max of the raw descriptors over all atoms."""
+        out = np.empty((4, _lib.SL_ML_NF))
+        check(self._L.sl_ml_descriptor_stats(self._h, _lib._arr_ptr(out)), "sl_ml_descriptor_stats")
+        return out
+
+    def ml_gate(self):
+        """(atoms out of range at the last evaluation point, network in use there, points handed back)."""
+        out = (ctypes.c_int64 * 4)()
+        check(self._L.sl_ml_gate(self._h, out), "sl_ml_gate")
+        return int(out[0]), int(out[1]), int(out[2])
+
+    def ml_vjp(self, gE=None, gF=None, gB=None) -> torch.Tensor:
+        """d/dparams of sum gE.E_rep + sum gF.F + sum gB.B (float64 [SL_ML_NPARAM])."""
+        def dev(x, shape):
+            if x is None:
+                return None
+            return torch.as_tensor(x, dtype=torch.float64).to(self.device).reshape(shape).contiguous()
+        gE_, gF_, gB_ = dev(gE, (self.nrep,)), dev(gF, (self.n, 3)), dev(gB, (self.n, 3))
+        grad = torch.empty(_lib.SL_ML_NPARAM, dtype=torch.float64, device=self.device)
+        self.stream.synchronize()
+        check(self._L.sl_ml_vjp(self._h, gE_.data_ptr() if gE_ is not None else None,
+                                gF_.data_ptr() if gF_ is not None else None,
+                                gB_.data_ptr() if gB_ is not None else None, grad.data_ptr()), "sl_ml_vjp")
+        self.stream.synchronize()
+        return grad
+
+    def ml_train_step(self, E_ref, F_ref, B_ref, w, lr, beta1=0.9, beta2=0.999, eps=1e-8, want_loss=True):
+        """One Adam step on the frames currently loaded; returns the loss terms
+        (L, L_E, L_F, L_omega) before the update, or None."""
+        E_ref = torch.as_tensor(E_ref, dtype=torch.float64).to(self.device).contiguous()
+        F_ref = torch.as_tensor(F_ref, dtype=torch.float64).to(self.device).reshape(-1, 3).contiguous()
+        B_ref = torch.as_tensor(B_ref, dtype=torch.float64).to(self.device).reshape(-1, 3).contiguous()
+        wv = np.ascontiguousarray(w, dtype=np.float64)
+        loss = np.empty(4) if want_loss else None
+        check(self._L.sl_ml_train_step(self._h, E_ref.data_ptr(), F_ref.data_ptr(), B_ref.data_ptr(),
+                                       _lib._arr_ptr(wv), float(lr), float(beta1), float(beta2), float(eps),
+                                       _lib._arr_ptr(loss) if loss is not None else None), "sl_ml_train_step")
+        if loss is None:
+            self.stream.synchronize()
+        return loss

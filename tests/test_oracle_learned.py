@@ -18,38 +18,12 @@ from oracle import ML_NF, ML_NH, ML_NNORM, ML_NPARAM, ML_OFF_B1, ML_OFF_B2, ML_O
     ML_OFF_W3, HBAR
 from paper_1801_10233_gb300 import inputs
 
-BIG = np.float32(3e38)
-
-
-def open_norm():
-    n = np.zeros(ML_NNORM, np.float32)
-    n[ML_NF:2 * ML_NF] = 1.0
-    n[2 * ML_NF:3 * ML_NF] = -BIG
-    n[3 * ML_NF:] = BIG
-    return n
+from _ml_models import BIG, fitted_norm, model, open_norm, spin_free  # noqa: E402
 
 
 def frame(ncells=5, seed=7, sigma=0.05):
     p, r, v, s = inputs.bcc_fe_system(ncells, seed, T=300.0, sigma=sigma, spins="uniform")
     return p, r, v, s
-
-
-def fitted_norm(r, s, box):
-    """mean / inv_std of the frame's own descriptors, gate wide open."""
-    D = oracle.ml_eval(r, s, box, inputs.ml_init_params(1), open_norm())["D"]
-    n = open_norm()
-    n[:ML_NF] = D.mean(0)
-    n[ML_NF:2 * ML_NF] = 1.0 / (D.std(0) + 1e-3)
-    return n
-
-
-def model(seed=3):
-    p = inputs.ml_init_params(seed, e0=-4.0)
-    rng = np.random.default_rng(seed)
-    p[ML_OFF_B1:ML_OFF_B1 + ML_NH] = rng.normal(0, 0.3, ML_NH)
-    p[ML_OFF_B2:ML_OFF_B2 + ML_NH] = rng.normal(0, 0.3, ML_NH)
-    p[ML_OFF_W3:ML_OFF_W3 + ML_NH] *= 10.0
-    return p
 
 
 @pytest.fixture(scope="module")
@@ -294,15 +268,6 @@ def learned_oracle(par, norm, seed=31, ncells=5, **kw):
     o = oracle.Oracle(p, r, v, s)
     o.set_model(par, norm)
     return o, p, r, v, s
-
-
-def spin_free(par):
-    """Zero the weights of the s.s features: the energy no longer depends on the spins."""
-    q = par.copy()
-    W1 = q[ML_OFF_W1:ML_OFF_B1].reshape(ML_NH, ML_NF)
-    W1[:, 1::3] = 0.0
-    W1[:, 2::3] = 0.0
-    return q
 
 
 def test_learned_spin_free_model_gives_exact_larmor(sys5):
