@@ -36,13 +36,20 @@
  * sl_learned.c.  Each evaluation point (the start of each spin half-op, the
  * force computation) evaluates the network at the current state; if any
  * atom's descriptor lies outside the model's trained range, that point uses
- * the analytic Hamiltonian instead.  A learned spin half-op freezes the
- * network's per-atom gradients G at the half-op's start: each single-spin
- * factor then rotates s_i about omega_i = (mu_s mu_B H - sum_j (P_ij +
- * 2 Q_ij s_i.s_j) s_j)/hbar with P, Q from the frozen G and the current
- * spins (omega_i itself held fixed during the rotation).  Sectors are at
- * least the model's 6 A cutoff + skin wide so that same-colour spins still
- * do not interact.
+ * the analytic Hamiltonian instead.  A learned spin half-op is time
+ * symmetric:
+ *   1. P, Q from the per-atom gradients G at the half-op's start;
+ *   2. predictor: the palindromic sweep with those P, Q;
+ *   3. P, Q from G at the predicted end state; average them with step 1's;
+ *   4. corrector: the sweep again from the start spins with the averages.
+ * Each single-spin factor of a sweep rotates s_i exactly about omega_i taken
+ * at the rotation's midpoint, omega(s) = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij
+ * s.s_j) s_j)/hbar with the current neighbour spins: a trial rotation about
+ * omega(s_i) gives s*, then s_i rotates about omega(m), m = (s_i + s*)/|s_i + s*|.
+ * (Holding G, or omega during a rotation, fixed at the start of the step
+ * makes the energy error first order in dt; the symmetric forms make it
+ * second order.)  Sectors are at least the model's 6 A cutoff + skin wide
+ * so that same-colour spins still do not interact.
  *
  * Pair lists are rebuilt from scratch at the exact cutoffs whenever the
  * positions change (brute force, or a plain cell list that the tests check
@@ -398,10 +405,9 @@ static void omega_of(const orc_state* st, int i, double w[3]) {
 
 /* Learned-mode precession vector from the frozen pair coefficients:
  * omega_i = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij s_i.s_j) s_j) / hbar. */
-static void omega_ml(const orc_state* st, int i, double w[3]) {
+static void omega_ml_at(const orc_state* st, int i, const double* si, double w[3]) {
   double zf = st->p.mu_s * ORC_MUB;
   double h[3] = {zf * st->p.H[0], zf * st->p.H[1], zf * st->p.H[2]};
-  const double* si = st->s + 3 * i;
   for (int k = st->mll.off[i]; k < st->mll.off[i + 1]; ++k) {
     const double* sj = st->s + 3 * st->mll.j[k];
     double c = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
@@ -419,11 +425,40 @@ static void cross(const double a[3], const double b[3], double c[3]) {
   c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
+/* s rotated exactly about w by |w| tau (Rodrigues), into out. */
+static void rodrigues(const double w[3], const double* s, double tau, double out[3]) {
+  double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  double th = wn * tau;
+  if (wn == 0.0 || th == 0.0) { out[0] = s[0]; out[1] = s[1]; out[2] = s[2]; return; }
+  double nv[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
+  double c = cos(th), sn = sin(th), h = sin(0.5 * th);
+  double omc = 2.0 * h * h;
+  double nxs[3];
+  cross(nv, s, nxs);
+  double ns = nv[0] * s[0] + nv[1] * s[1] + nv[2] * s[2];
+  for (int a = 0; a < 3; ++a) out[a] = s[a] * c + nxs[a] * sn + nv[a] * ns * omc;
+}
+
+/* Learned single-spin factor: exact rotation about omega at the midpoint. */
+static void rotate_ml(orc_state* st, int i, double tau) {
+  double* s = st->s + 3 * i;
+  double w[3], trial[3], m[3];
+  omega_ml_at(st, i, s, w);
+  rodrigues(w, s, tau, trial);
+  for (int a = 0; a < 3; ++a) m[a] = s[a] + trial[a];
+  double mn = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+  for (int a = 0; a < 3; ++a) m[a] /= mn;
+  omega_ml_at(st, i, m, w);
+  double out[3];
+  rodrigues(w, s, tau, out);
+  s[0] = out[0]; s[1] = out[1]; s[2] = out[2];
+}
+
 /* Update spin i over time tau (one factor e^{L_si tau} of Eq. spin_ST_decomposition). */
 static void rotate(orc_state* st, int i, double tau, int subpass) {
+  if (st->use_ml) { rotate_ml(st, i, tau); return; }
   double w[3];
-  if (st->use_ml) omega_ml(st, i, w);
-  else omega_of(st, i, w);
+  omega_of(st, i, w);
   double* s = st->s + 3 * i;
   if (st->p.lambda != 0.0 || st->p.temperature != 0.0) {
     /* Eq. sLLG written as ds/dt = Om x s with
@@ -492,15 +527,45 @@ static int ml_point(orc_state* st, double* F) {
   return ORC_OK;
 }
 
-/* e^{L_s h}: forward over the sweep order with h/2 per spin, then backward. */
-static void spin_half_op(orc_state* st, double h, int subpass0) {
+/* The palindromic sweep: forward over the sweep order with h/2 per spin, then backward. */
+static void sweep(orc_state* st, double h, int subpass0) {
   int n = st->n;
-  if (st->p.hamiltonian == 1) {
-    int e = ml_point(st, NULL);
-    if (e && st->err == ORC_OK) st->err = e;
-  }
   for (int k = 0; k < n; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
   for (int k = n - 1; k >= 0; --k) rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
+}
+
+/* e^{L_s h}.  Learned Hamiltonian: predictor sweep, field coefficients at the
+ * predicted end averaged with the start's, corrector sweep from the start. */
+static void spin_half_op(orc_state* st, double h, int subpass0) {
+  if (st->p.hamiltonian != 1) { sweep(st, h, subpass0); return; }
+  int e = ml_point(st, NULL);
+  if (e) { if (st->err == ORC_OK) st->err = e; return; }
+  if (!st->use_ml) { sweep(st, h, subpass0); return; }
+  int n = st->n, np = st->mll.off[n];
+  double* P0 = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
+  double* Q0 = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
+  double* s0 = (double*)malloc((size_t)(n ? n : 1) * 3 * sizeof(double));
+  if (!P0 || !Q0 || !s0) { free(P0); free(Q0); free(s0); if (st->err == ORC_OK) st->err = ORC_ERR_OOM; return; }
+  memcpy(P0, st->mlP, (size_t)np * sizeof(double));
+  memcpy(Q0, st->mlQ, (size_t)np * sizeof(double));
+  memcpy(s0, st->s, (size_t)n * 3 * sizeof(double));
+  sweep(st, h, subpass0);                                   /* predictor */
+  double* P1 = st->mlP;
+  double* Q1 = st->mlQ;
+  st->mlP = NULL; st->mlQ = NULL;
+  free(P1); free(Q1);
+  int use = st->use_ml;
+  int gb = st->gate_bad, gt = st->gate_trips;
+  e = ml_point(st, NULL);                                   /* G at the predicted end (gate ignored) */
+  st->use_ml = use; st->gate_bad = gb; st->gate_trips = gt;
+  if (e) { if (st->err == ORC_OK) st->err = e; free(P0); free(Q0); free(s0); return; }
+  for (int k = 0; k < np; ++k) {
+    st->mlP[k] = 0.5 * (P0[k] + st->mlP[k]);
+    st->mlQ[k] = 0.5 * (Q0[k] + st->mlQ[k]);
+  }
+  memcpy(st->s, s0, (size_t)n * 3 * sizeof(double));
+  sweep(st, h, subpass0);                                   /* corrector */
+  free(P0); free(Q0); free(s0);
 }
 
 /* ------------------------------------------------------------------ */

@@ -342,3 +342,23 @@ def test_gate_hands_back_to_analytic_hamiltonian(sys5):
         assert np.array_equal(x, y)
     bad, trips = o.gate()
     assert bad == len(r) and trips == 1 + 3 * 7
+
+
+def test_learned_spin_energy_error_is_second_order_in_dt(sys5):
+    """The symmetric learned half-op (predictor-corrector G, midpoint omega)
+    has an energy error O(dt^2): halving dt quarters the energy excursion over
+    a fixed time (the frozen-G or frozen-omega forms are first order)."""
+    *_, norm = sys5
+    par = inputs.ml_init_params(21, e0=-4.0)
+    dev = []
+    for dt in (2e-4, 1e-4):
+        o, p, r, v, s = learned_oracle(par, norm, fix_lattice=1, dt_ps=dt)
+        n = len(r)
+        e0 = o.energy()[4]
+        steps = int(round(0.006 / dt))
+        ex = 0.0
+        for k in range(4):
+            o.step(steps // 4)
+            ex = max(ex, abs(o.energy()[4] - e0) / n)
+        dev.append(ex)
+    assert dev[0] / dev[1] > 3.0, dev
