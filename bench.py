@@ -74,6 +74,11 @@ def parse():
                     choices=["fe_bcc_64x64x64_nve", "fe_bcc_10x10x10_nve", "fe_bcc_100x100x100_nve",
                              "fe_bcc_batch256"])
     ap.add_argument("--no-forms", action="store_true", help="skip the extra per-form measurements")
+    ap.add_argument("--no-learned", action="store_true", help="skip training and judging the learned Hamiltonian")
+    ap.add_argument("--learned-frames", type=int, default=20000, help="training snapshots (10^3-cell frames)")
+    ap.add_argument("--learned-epochs", type=int, default=4)
+    ap.add_argument("--learned-steps", type=int, default=500, help="judged steps on 40^3 cells")
+    ap.add_argument("--learned-big-steps", type=int, default=100, help="judged steps on 100^3 cells")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -200,6 +205,62 @@ def run_reference(args):
     }))
 
 
+def _rate(sysm, steps, torch):
+    """atom-steps/s and ms/step of `steps` timed steps (CUDA events, 3 warm-up steps)."""
+    sysm.step(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(sysm.stream)
+    sysm.step(steps)
+    e1.record(sysm.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return sysm.n / (ms * 1e-3), ms
+
+
+def learned_forms(args, dev, torch):
+    """Train the learned Hamiltonian on snapshots of analytic trajectories,
+    then run it beside the analytic Hamiltonian on the 40^3- and 100^3-cell
+    workloads: rates of both, the gain, and the judge's error report."""
+    from paper_1801_10233_gb300 import System, inputs, learned
+    t0 = time.perf_counter()
+    plist, data = learned.training_set(n_frames=args.learned_frames, n_replicas=64, every=10, device=dev)
+    torch.cuda.synchronize()
+    t_snap = time.perf_counter() - t0
+    params, norm, losses, secs = learned.train_model(plist, data, epochs=args.learned_epochs, device=dev)
+    atoms = int(data["r"].shape[1])
+    out = {"training": {"frames": int(data["r"].shape[0]) * len(plist), "frame_atoms": 2000,
+                        "epochs": args.learned_epochs, "adam_steps": len(losses), "seconds": secs,
+                        "snapshot_seconds": t_snap, "atoms_per_s": len(losses) * atoms / secs,
+                        "loss_first": [float(x) for x in losses[0]], "loss_last": [float(x) for x in losses[-1]],
+                        "loss_terms": "L, energy, force, omega"}}
+    del data
+    torch.cuda.empty_cache()
+    for name, steps, every in (("fe_bcc_40x40x40_nve", args.learned_steps, 50),
+                               ("fe_bcc_100x100x100_nve", args.learned_big_steps, 25)):
+        if steps <= 0:
+            continue
+        p, r, v, s = inputs.workload(name)
+        judge = learned.judge(params, norm, p, r, v, s, steps, every, device=dev)
+        plain = System(p, r, v, s, device=dev)
+        rp, mp = _rate(plain, 20, torch)
+        plain.close()
+        lsys = learned.learned_system(learned.learned_params(p), r, v, s, norm, params, device=dev)
+        rl, ml = _rate(lsys, 20, torch)
+        lsys.set_timing(True)
+        lsys.step(5)
+        ph = lsys.timing()
+        lsys.set_timing(False)
+        kp = lsys.counters()["kernels_per_step"]
+        lsys.close()
+        out[name] = {"n_atoms": p["n_atoms"], "plain": {"value": rp, "ms_per_step": mp},
+                     "learned": {"value": rl, "ms_per_step": ml, "kernels_per_step": kp,
+                                 "phase_ms_per_step": {k: v_[0] / max(1, v_[1]) for k, v_ in ph.items()}},
+                     "gain_learned_over_plain": rl / rp, "unit": UNIT, "judge": judge}
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -310,6 +371,8 @@ def run_ours(args):
                            "n_atoms": fn, "workload": fdesc}
             fsys.close()
             del fsys
+        if not args.no_learned:
+            forms["learned"] = learned_forms(args, dev, torch)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ost = 40

@@ -255,12 +255,16 @@ int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void*
  * network at the current state.  If any atom's descriptor lies outside
  * [gate lo, gate hi], that point hands over to the analytic Hamiltonian: the
  * following spin half-op and/or forces use Morse + Bethe-Slater instead.
- * A learned spin half-op freezes the per-atom gradients G_i = dE_i/dD_i of its
- * evaluation point; each single-spin factor rotates s_i about
- *   omega_i = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij s_i.s_j) s_j) / hbar,
+ * A learned spin half-op is time symmetric: a predictor sweep with the field
+ * coefficients (P, Q) of the per-atom gradients G_i = dE_i/dD_i at the
+ * half-op's start, the coefficients at the predicted end averaged with the
+ * start's, and the corrector sweep from the start spins with the averages.
+ * Each single-spin factor rotates s_i exactly about omega at the rotation's
+ * midpoint m (found by a trial rotation about omega(s_i)), where
+ *   omega(s) = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij s.s_j) s_j) / hbar,
  *   P_ij = sum_k (G_i+G_j)[3k+1] g_k(r_ij),  Q_ij = sum_k (G_i+G_j)[3k+2] g_k(r_ij),
  * with the current neighbour spins.  The spin bath (lambda, temperature_K)
- * is not available in this mode.
+ * and the Cayley propagator are not available in this mode.
  * ------------------------------------------------------------------------ */
 #define SL_ML_NF 48
 #define SL_ML_NH 64

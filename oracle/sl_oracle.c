@@ -44,8 +44,9 @@
  *   4. corrector: the sweep again from the start spins with the averages.
  * Each single-spin factor of a sweep rotates s_i exactly about omega_i taken
  * at the rotation's midpoint, omega(s) = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij
- * s.s_j) s_j)/hbar with the current neighbour spins: a trial rotation about
- * omega(s_i) gives s*, then s_i rotates about omega(m), m = (s_i + s*)/|s_i + s*|.
+ * s.s_j) s_j)/hbar with the current neighbour spins: the midpoint is
+ * estimated as m = u/|u|, u = s_i + (tau/2) omega(s_i) x s_i (to second
+ * order in the angle, as the rule needs), then s_i rotates about omega(m).
  * (Holding G, or omega during a rotation, fixed at the start of the step
  * makes the energy error first order in dt; the symmetric forms make it
  * second order.)  Sectors are at least the model's 6 A cutoff + skin wide
@@ -442,10 +443,10 @@ static void rodrigues(const double w[3], const double* s, double tau, double out
 /* Learned single-spin factor: exact rotation about omega at the midpoint. */
 static void rotate_ml(orc_state* st, int i, double tau) {
   double* s = st->s + 3 * i;
-  double w[3], trial[3], m[3];
+  double w[3], wxs[3], m[3];
   omega_ml_at(st, i, s, w);
-  rodrigues(w, s, tau, trial);
-  for (int a = 0; a < 3; ++a) m[a] = s[a] + trial[a];
+  cross(w, s, wxs);
+  for (int a = 0; a < 3; ++a) m[a] = s[a] + 0.5 * tau * wxs[a];
   double mn = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
   for (int a = 0; a < 3; ++a) m[a] /= mn;
   omega_ml_at(st, i, m, w);
@@ -644,7 +645,8 @@ int orc_params_size(void) { return (int)sizeof(orc_params); }
 /* r, v, s: [n][3] in atom-id order.  Returns NULL and sets *err on failure. */
 orc_state* orc_create(const orc_params* p, const double* r, const double* v, const double* s, int* err) {
   *err = ORC_OK;
-  if (!p || p->n_atoms < 0 || p->mass <= 0.0 || p->hamiltonian < 0 || p->hamiltonian > 1) {
+  if (!p || p->n_atoms < 0 || p->mass <= 0.0 || p->hamiltonian < 0 || p->hamiltonian > 1 ||
+      (p->hamiltonian == 1 && p->rotation != 0)) {
     *err = ORC_ERR_ARG;
     return NULL;
   }

@@ -74,8 +74,8 @@ int validate(const sl_params* p) {
   if (!(p->lambda >= 0.0) || !(p->temperature_K >= 0.0)) return SL_ERR_ARG;
   if (!std::isfinite(p->dt_ps)) return SL_ERR_ARG;
   if (p->hamiltonian != SL_HAM_ANALYTIC && p->hamiltonian != SL_HAM_LEARNED) return SL_ERR_ARG;
-  if (p->hamiltonian == SL_HAM_LEARNED &&
-      (!(p->morse_rc_A >= SL_ML_RC) || p->lambda != 0.0 || p->temperature_K != 0.0))
+  if (p->hamiltonian == SL_HAM_LEARNED && (!(p->morse_rc_A >= SL_ML_RC) || p->lambda != 0.0 ||
+                                           p->temperature_K != 0.0 || p->rotation != SL_ROT_RODRIGUES))
     return SL_ERR_ARG;
   double rc = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
   for (int a = 0; a < 3; ++a)

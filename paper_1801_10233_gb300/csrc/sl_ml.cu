@@ -341,7 +341,8 @@ __global__ void __launch_bounds__(128, 1) k_ml_mlp(SlDev d, int force) {
 //   P_ij   = sum_k (G_i+G_j)[3k+1] g_k(r),  Q_ij = sum_k (G_i+G_j)[3k+2] g_k(r)
 //   B_i    = -sum_j (P_ij + 2 Q_ij c) s_j                         (= -dE/ds_i)
 // with c = s_i.s_j.  fmode bit 0: F into the integrator's FP64 forces, bit 1:
-// closing half-kick, bit 2: F into ml_gF (training scratch).  Fout, Bout
+// closing half-kick, bit 2: F into ml_gF (training scratch), bit 3: average
+// (P, Q) with the table's previous entries (the predicted end of a half-op).  Fout, Bout
 // (optional, caller order [n][3] double) receive F and B.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_ml_pair(SlDev d, int fmode, int force, double* Fout, double* Bout) {
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(128) k_ml_pair(SlDev d, int fmode, int force, 
     const int j = __ldg(d.mj + e);
     const float3 dd = ml_sep(B, pi, load_pos(d, j));
     const float r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
-    if (!(r2 < 36.0f)) { d.ml_pq[e] = make_float2(0.f, 0.f); continue; }
+    if (!(r2 < 36.0f)) { if (!(fmode & 8)) d.ml_pq[e] = make_float2(0.f, 0.f); continue; }
     const float r = sqrtf(r2), ir = 1.0f / r;
     const float3 sj = spin_f(d, j);
     const float c = si.x * sj.x + si.y * sj.y + si.z * sj.z;
@@ -392,7 +393,12 @@ __global__ void __launch_bounds__(128) k_ml_pair(SlDev d, int fmode, int force, 
     fx = fmaf(pr, dd.x, fx); fy = fmaf(pr, dd.y, fy); fz = fmaf(pr, dd.z, fz);
     const float psi = fmaf(2.0f * Q, c, P);
     bx = fmaf(-psi, sj.x, bx); by = fmaf(-psi, sj.y, by); bz = fmaf(-psi, sj.z, bz);
-    d.ml_pq[e] = make_float2(P, Q);
+    if (fmode & 8) {
+      const float2 o = d.ml_pq[e];
+      d.ml_pq[e] = make_float2(0.5f * (o.x + P), 0.5f * (o.y + Q));
+    } else {
+      d.ml_pq[e] = make_float2(P, Q);
+    }
   }
   d.ml_B[i] = make_float4(bx, by, bz, 0.f);
   if (fmode & 1) {
@@ -411,90 +417,306 @@ __global__ void __launch_bounds__(128) k_ml_pair(SlDev d, int fmode, int force, 
 }
 
 // ---------------------------------------------------------------------------
-// One colour pass of the learned spin half-op: one warp per sector, its spins
-// one after another; the lanes share the neighbour sum of each spin.  With
-// the gate closed at this evaluation point the analytic field sum_j J_ij s_j
-// (exchange list, double-float) is used instead.
+// One colour pass of a learned spin sweep.
+//
+// With the network in effect, the field of spin i is
+//   B_i(s) = -p_i - 2 M_i s,  p_i = sum_j P_ij s_j,  M_i = sum_j Q_ij s_j s_j^T,
+// and each single-spin factor rotates s_i exactly about omega at the
+// rotation's midpoint m = u/|u|, u = s_i + (tau/2) omega(s_i) x s_i (float32,
+// second order in the angle), omega(m) = (mu_s mu_B H + B_i(m))/hbar.
+// Block b takes LS_SPB consecutive sectors of the colour:
+//   phase 1 (8 lanes per atom, over its list): p_i and M_i from the
+//           neighbours whose spins do not change before spin i turns (other
+//           sectors, and later spins of its own sector in this pass's order),
+//           the atom's float32 spin, and its entries for the earlier spins of
+//           its sector (local index, P, Q) staged in shared memory;
+//   phase 2 (one lane per sector, sequential): add those entries with the
+//           updated spins, form B_i(m), and rotate the float32 copy that
+//           later spins of the sector see;
+//   phase 3 (one thread per atom): the double-float rotation of the FP64
+//           spin about omega(m), added once.
+// Blocks whose atoms or same-sector lists do not fit run every sector from
+// global memory instead (one lane per sector).  With the gate closed the
+// field is the analytic one, sum_j J_ij s_j over the exchange list
+// (double-float), on the same per-lane path.  `predictor` = 1 runs only with
+// the network in effect (the predictor sweep of the half-op).
 // ---------------------------------------------------------------------------
-constexpr int MLS_WARPS = 4;
-
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ df warp_sum_df(df v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    df w = df_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
-    v = df_add(v, w);
-  }
-  return v;
+
+constexpr int LS_SPB = 2;          // sectors per block
+constexpr int LS_THREADS = 128;
+constexpr int LS_MAXA = 96;        // atoms staged per block
+constexpr int LS_MAXIN = 48;       // same-sector entries staged per atom
+constexpr size_t LS_SMEM = (size_t)LS_MAXIN * LS_MAXA * (sizeof(float2) + sizeof(short)) +
+                           (size_t)LS_MAXA * (3 + 9 + 3) * sizeof(float) + (size_t)LS_MAXA * sizeof(int);
+
+// The network's part of the field at spin s: -(p + 2 M s), float32.
+__device__ __forceinline__ float3 ml_field_f(const float* p, const float* M, float3 s) {
+  return make_float3(-p[0] - 2.0f * (M[0] * s.x + M[3] * s.y + M[4] * s.z),
+                     -p[1] - 2.0f * (M[3] * s.x + M[1] * s.y + M[5] * s.z),
+                     -p[2] - 2.0f * (M[4] * s.x + M[5] * s.y + M[2] * s.z));
 }
 
-__global__ void __launch_bounds__(MLS_WARPS * 32) k_ml_sweep_pass(SlDev d, int colour, int backward) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int sec = blockIdx.x * MLS_WARPS + w;
-  if (sec >= d.s8) return;
-  const int q = colour * d.s8 + sec;
-  const int a0 = d.sec_start[q], a1 = d.sec_start[q + 1];
-  const int use = d.ctrl->ml_use;
+__device__ __forceinline__ void pm_add(float* p, float* M, float P, float Q, float3 sj) {
+  p[0] = fmaf(P, sj.x, p[0]); p[1] = fmaf(P, sj.y, p[1]); p[2] = fmaf(P, sj.z, p[2]);
+  const float qx = Q * sj.x, qy = Q * sj.y;
+  M[0] = fmaf(qx, sj.x, M[0]); M[1] = fmaf(qy, sj.y, M[1]); M[2] = fmaf(Q * sj.z, sj.z, M[2]);
+  M[3] = fmaf(qx, sj.y, M[3]); M[4] = fmaf(qx, sj.z, M[4]); M[5] = fmaf(qy, sj.z, M[5]);
+}
+
+// The network's field at the rotation's midpoint, from p, M and the float32 spin.
+__device__ __forceinline__ float3 ml_mid_field(const SlDev& d, const float* p, const float* M, float3 s0, float tau) {
+  const float ih = (float)(1.0 / SL_HBAR);
+  const float3 b0 = ml_field_f(p, M, s0);
+  const float w0x = ((float)d.zee[0] + b0.x) * ih, w0y = ((float)d.zee[1] + b0.y) * ih,
+              w0z = ((float)d.zee[2] + b0.z) * ih;
+  const float ht = 0.5f * tau;
+  const float mx = fmaf(ht, w0y * s0.z - w0z * s0.y, s0.x);
+  const float my = fmaf(ht, w0z * s0.x - w0x * s0.z, s0.y);
+  const float mz = fmaf(ht, w0x * s0.y - w0y * s0.x, s0.z);
+  const float mi = rsqrtf(mx * mx + my * my + mz * mz);
+  return ml_field_f(p, M, make_float3(mx * mi, my * mi, mz * mi));
+}
+
+// omega = (mu_s mu_B H + b)/hbar with the Zeeman term and 1/hbar in double-float.
+__device__ __forceinline__ df3 ml_omega_df(const SlDev& d, float3 b) {
+  const df ih = F2(d.inv_hbar_f);
+  df3 w;
+  w.x = df_mul(df_add_f(F2(d.zee_f[0]), b.x), ih);
+  w.y = df_mul(df_add_f(F2(d.zee_f[1]), b.y), ih);
+  w.z = df_mul(df_add_f(F2(d.zee_f[2]), b.z), ih);
+  return w;
+}
+
+// Float32 rotation of s about w by |w| tau (the copy later spins of a sector see).
+__device__ __forceinline__ float3 rot_f(float3 w, float3 s, float tau) {
+  const float u = (w.x * w.x + w.y * w.y + w.z * w.z) * tau * tau;
+  float A, B;
+  if (u < 1e-2f) {
+    A = fmaf(u, fmaf(u, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);        // sin(t)/t
+    B = fmaf(u, fmaf(u, 1.0f / 720.0f, -1.0f / 24.0f), 0.5f);       // (1 - cos t)/t^2
+  } else {
+    const float th = sqrtf(u);
+    const float hs = sinf(0.5f * th);
+    A = sinf(th) / th;
+    B = 2.0f * hs * hs / u;
+  }
+  const float ws = w.x * s.x + w.y * s.y + w.z * s.z;
+  const float cx = w.y * s.z - w.z * s.y, cy = w.z * s.x - w.x * s.z, cz = w.x * s.y - w.y * s.x;
+  const float tA = tau * A, t2B = tau * tau * B * ws, uB = u * B;
+  return make_float3(s.x - uB * s.x + tA * cx + t2B * w.x, s.y - uB * s.y + tA * cy + t2B * w.y,
+                     s.z - uB * s.z + tA * cz + t2B * w.z);
+}
+
+__device__ __forceinline__ void apply_rotation(const SlDev& d, int i, const df3& w, df tau, int cayley) {
+  const float4 h = d.sdf[2 * (size_t)i], l = d.sdf[2 * (size_t)i + 1];
+  df3 s;
+  s.x = df_make(h.x, l.x); s.y = df_make(h.y, l.y); s.z = df_make(h.z, l.z);
+  const df3 inc = rot_increment(w, s, tau, cayley);
+  double4_32a sd = d.s[i];
+  sd.x += df_to_double(inc.x);
+  sd.y += df_to_double(inc.y);
+  sd.z += df_to_double(inc.z);
+  d.s[i] = sd;
+  store_spin_split(d, i, sd);
+}
+
+// Per-lane sequential update of one sector from global memory (fallback and
+// analytic paths).
+__device__ void ml_sector_global(const SlDev& d, int a0, int a1, int backward, int use, df tau) {
   const size_t n = (size_t)d.n;
-  const df tau = F2(d.tau_f), ih = F2(d.inv_hbar_f);
-  const int cayley = d.rotation == SL_ROT_CAYLEY;
   for (int t = 0; t < a1 - a0; ++t) {
     const int i = backward ? a1 - 1 - t : a0 + t;
-    df3 wv;
+    df3 w;
     if (use) {
-      const float3 si = spin_f(d, i);
-      float bx = 0.f, by = 0.f, bz = 0.f;
+      float p[3] = {0.f, 0.f, 0.f}, M[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int nm = d.mn[i];
-      for (int k = lane; k < nm; k += 32) {
+      for (int k = 0; k < nm; ++k) {
         const size_t e = (size_t)k * n + i;
         const float2 pq = __ldg(d.ml_pq + e);
         if (pq.x == 0.0f && pq.y == 0.0f) continue;
         const int j = __ldg(d.mj + e);
-        const float3 sj = spin_f(d, j);
-        const float c = si.x * sj.x + si.y * sj.y + si.z * sj.z;
-        const float psi = fmaf(2.0f * pq.y, c, pq.x);
-        bx = fmaf(-psi, sj.x, bx); by = fmaf(-psi, sj.y, by); bz = fmaf(-psi, sj.z, bz);
+        const float4 sj = d.sdf[2 * (size_t)j];
+        pm_add(p, M, pq.x, pq.y, make_float3(sj.x, sj.y, sj.z));
       }
-      bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz);
-      wv.x = df_mul(df_add_f(F2(d.zee_f[0]), bx), ih);
-      wv.y = df_mul(df_add_f(F2(d.zee_f[1]), by), ih);
-      wv.z = df_mul(df_add_f(F2(d.zee_f[2]), bz), ih);
+      const float4 h = d.sdf[2 * (size_t)i];
+      w = ml_omega_df(d, ml_mid_field(d, p, M, make_float3(h.x, h.y, h.z), tau.hi));
     } else {
       float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zh = 0.f, zl = 0.f;
       const int ne = d.exn[i];
-      for (int k = lane; k < ne; k += 32) {
+      for (int k = 0; k < ne; ++k) {
         const size_t e = (size_t)k * n + i;
         const df J = F2(__ldg(d.exJ + e));
         const int j = __ldg(d.exj + e);
-        const float4 h = d.sdf[2 * (size_t)j], l = d.sdf[2 * (size_t)j + 1];
-        acc_prod(xh, xl, J, df_make(h.x, l.x));
-        acc_prod(yh, yl, J, df_make(h.y, l.y));
-        acc_prod(zh, zl, J, df_make(h.z, l.z));
+        const float4 jh = d.sdf[2 * (size_t)j], jl = d.sdf[2 * (size_t)j + 1];
+        acc_prod(xh, xl, J, df_make(jh.x, jl.x));
+        acc_prod(yh, yl, J, df_make(jh.y, jl.y));
+        acc_prod(zh, zl, J, df_make(jh.z, jl.z));
       }
-      const df hx = warp_sum_df(acc_done(xh, xl)), hy = warp_sum_df(acc_done(yh, yl)),
-               hz = warp_sum_df(acc_done(zh, zl));
-      wv.x = df_mul(df_add(F2(d.zee_f[0]), hx), ih);
-      wv.y = df_mul(df_add(F2(d.zee_f[1]), hy), ih);
-      wv.z = df_mul(df_add(F2(d.zee_f[2]), hz), ih);
+      const df ih = F2(d.inv_hbar_f);
+      w.x = df_mul(df_add(F2(d.zee_f[0]), acc_done(xh, xl)), ih);
+      w.y = df_mul(df_add(F2(d.zee_f[1]), acc_done(yh, yl)), ih);
+      w.z = df_mul(df_add(F2(d.zee_f[2]), acc_done(zh, zl)), ih);
     }
-    if (lane == 0) {
-      const float4 h = d.sdf[2 * (size_t)i], l = d.sdf[2 * (size_t)i + 1];
-      df3 s;
-      s.x = df_make(h.x, l.x); s.y = df_make(h.y, l.y); s.z = df_make(h.z, l.z);
-      const df3 inc = rot_increment(wv, s, tau, cayley);
-      double4_32a sd = d.s[i];
-      sd.x += df_to_double(inc.x);
-      sd.y += df_to_double(inc.y);
-      sd.z += df_to_double(inc.z);
-      d.s[i] = sd;
-      store_spin_split(d, i, sd);
-    }
-    __syncwarp();
+    apply_rotation(d, i, w, tau, !use && d.rotation == SL_ROT_CAYLEY);
   }
+}
+
+__global__ void __launch_bounds__(LS_THREADS) k_ml_sweep(SlDev d, int colour, int backward, int predictor) {
+  extern __shared__ __align__(16) uint8_t lsm[];
+  float2* inpq = (float2*)lsm;                                   // [LS_MAXIN][LS_MAXA]
+  short* inj = (short*)(inpq + LS_MAXIN * LS_MAXA);              // [LS_MAXIN][LS_MAXA]
+  float* sS = (float*)(inj + LS_MAXIN * LS_MAXA);                // [3][LS_MAXA] current float32 spins
+  float* acc = sS + 3 * LS_MAXA;                                 // [9][LS_MAXA] p (3), M (6)
+  float* bm = acc + 9 * LS_MAXA;                                 // [3][LS_MAXA] field at the midpoint
+  int* nin = (int*)(bm + 3 * LS_MAXA);                           // [LS_MAXA]
+  __shared__ int bounds[LS_SPB + 1];
+  __shared__ int overflow;
+  const int use = d.ctrl->ml_use;
+  if (predictor && !use) return;
+  const int sec0 = blockIdx.x * LS_SPB;
+  if (sec0 >= d.s8) return;
+  const int nsec = min(LS_SPB, d.s8 - sec0);
+  const int q0 = colour * d.s8 + sec0;
+  if (threadIdx.x <= nsec) bounds[threadIdx.x] = d.sec_start[q0 + threadIdx.x];
+  if (threadIdx.x == 0) overflow = 0;
+  __syncthreads();
+  const int A0 = bounds[0], na = bounds[nsec] - A0;
+  const df tau = F2(d.tau_f);
+  const size_t n = (size_t)d.n;
+  int staged = use && na <= LS_MAXA;
+  if (staged) {
+    // phase 1: groups of 8 lanes, one atom per group, the lanes over its list
+    const int lane = threadIdx.x & 31, g8 = lane >> 3, l8 = lane & 7;
+    const unsigned gmask = 0xFFu << (8 * g8);
+    for (int t0 = (threadIdx.x >> 5) * 4; t0 < na; t0 += LS_THREADS / 8) {
+      const int t = t0 + g8;
+      const bool act = t < na;
+      const int i = act ? A0 + t : A0;
+      int lo = 0, hi = 0;
+      for (int q = 0; q < nsec; ++q)
+        if (i >= bounds[q] && i < bounds[q + 1]) { lo = bounds[q]; hi = bounds[q + 1]; }
+      // same-sector spins later in this pass's order still hold their pass-start
+      // values when spin i turns: only the earlier ones go to phase 2
+      if (backward) lo = i + 1; else hi = i;
+      if (act && l8 < 3) {
+        const float4 sv = d.sdf[2 * (size_t)i];
+        sS[l8 * LS_MAXA + t] = l8 == 0 ? sv.x : (l8 == 1 ? sv.y : sv.z);
+      }
+      float p[3] = {0.f, 0.f, 0.f}, M[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      int cnt = 0;
+      const int nm = act ? d.mn[i] : 0;
+      const int nmax = max(nm, __shfl_xor_sync(0xffffffffu, nm, 8));
+      const int nall = max(nmax, __shfl_xor_sync(0xffffffffu, nmax, 16));
+      for (int k0 = 0; k0 < nall; k0 += 32) {
+        // four entries per lane per round, loads issued together
+        float2 pq[4];
+        int jj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + 8 * u + l8;
+          pq[u] = make_float2(0.f, 0.f);
+          jj[u] = -1;
+          if (k < nm) {
+            const size_t e = (size_t)k * n + i;
+            pq[u] = __ldg(d.ml_pq + e);
+            jj[u] = __ldg(d.mj + e);
+          }
+        }
+        float4 sj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool live = pq[u].x != 0.0f || pq[u].y != 0.0f;
+          const bool ext = live && !(jj[u] >= lo && jj[u] < hi);
+          sj[u] = ext ? d.sdf[2 * (size_t)jj[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool live = pq[u].x != 0.0f || pq[u].y != 0.0f;
+          const bool internal = live && jj[u] >= lo && jj[u] < hi;
+          if (live && !internal) pm_add(p, M, pq[u].x, pq[u].y, make_float3(sj[u].x, sj[u].y, sj[u].z));
+          const unsigned mask = __ballot_sync(0xffffffffu, internal) & gmask;
+          const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+          if (internal && pos < LS_MAXIN) {
+            inpq[pos * LS_MAXA + t] = pq[u];
+            inj[pos * LS_MAXA + t] = (short)(jj[u] - A0);
+          }
+          cnt += __popc(mask);
+        }
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c] += __shfl_xor_sync(0xffffffffu, p[c], o);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) M[c] += __shfl_xor_sync(0xffffffffu, M[c], o);
+      }
+      if (act && l8 == 0) {
+        if (cnt > LS_MAXIN) overflow = 1;
+        nin[t] = cnt;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c * LS_MAXA + t] = p[c];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[(3 + c) * LS_MAXA + t] = M[c];
+      }
+    }
+    __syncthreads();
+    staged = !overflow;
+  }
+  if (!staged) {
+    // every sector of the block from global memory, one lane each
+    if (threadIdx.x < nsec) ml_sector_global(d, bounds[threadIdx.x], bounds[threadIdx.x + 1], backward, use, tau);
+    return;
+  }
+  // phase 2
+  if (threadIdx.x < nsec) {
+    const int lo = bounds[threadIdx.x] - A0, hi = bounds[threadIdx.x + 1] - A0;
+    const float ih = (float)(1.0 / SL_HBAR);
+    for (int u = 0; u < hi - lo; ++u) {
+      const int t = backward ? hi - 1 - u : lo + u;
+      float p[3], M[6];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) p[c] = acc[c * LS_MAXA + t];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) M[c] = acc[(3 + c) * LS_MAXA + t];
+      const int cnt = nin[t];
+#pragma unroll 4
+      for (int e = 0; e < cnt; ++e) {
+        const float2 pq = inpq[e * LS_MAXA + t];
+        const int jl = inj[e * LS_MAXA + t];
+        pm_add(p, M, pq.x, pq.y, make_float3(sS[jl], sS[LS_MAXA + jl], sS[2 * LS_MAXA + jl]));
+      }
+      const float3 s0 = make_float3(sS[t], sS[LS_MAXA + t], sS[2 * LS_MAXA + t]);
+      const float3 b = ml_mid_field(d, p, M, s0, tau.hi);
+      bm[t] = b.x; bm[LS_MAXA + t] = b.y; bm[2 * LS_MAXA + t] = b.z;
+      const float3 w = make_float3(((float)d.zee[0] + b.x) * ih, ((float)d.zee[1] + b.y) * ih,
+                                   ((float)d.zee[2] + b.z) * ih);
+      const float3 s1 = rot_f(w, s0, tau.hi);
+      sS[t] = s1.x; sS[LS_MAXA + t] = s1.y; sS[2 * LS_MAXA + t] = s1.z;
+    }
+  }
+  __syncthreads();
+  // phase 3
+  for (int t = threadIdx.x; t < na; t += LS_THREADS)
+    apply_rotation(d, A0 + t, ml_omega_df(d, make_float3(bm[t], bm[LS_MAXA + t], bm[2 * LS_MAXA + t])), tau, 0);
+}
+
+// Spins at the start of a learned half-op, kept for the corrector sweep.
+__global__ void k_ml_save_spins(SlDev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n || !d.ctrl->ml_use) return;
+  d.ts[i] = d.s[i];
+}
+__global__ void k_ml_restore_spins(SlDev d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n || !d.ctrl->ml_use) return;
+  const double4_32a s = d.ts[i];
+  d.s[i] = s;
+  store_spin_split(d, i, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -951,6 +1173,8 @@ int sl_ml_prepare_kernels() {
     return SL_ERR_CUDA;
   if (cudaFuncSetAttribute(k_ml_train_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM) != cudaSuccess)
     return SL_ERR_CUDA;
+  if (cudaFuncSetAttribute(k_ml_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LS_SMEM) != cudaSuccess)
+    return SL_ERR_CUDA;
   return SL_OK;
 }
 
@@ -971,11 +1195,23 @@ int sl_ml_launch_point(const SlDev& d, cudaStream_t st, int fmode) {
 }
 
 int sl_ml_launch_half_op(const SlDev& d, cudaStream_t st) {
-  const int g = (d.s8 + MLS_WARPS - 1) / MLS_WARPS;
-  for (int p = 0; p < 16; ++p) {
-    const int colour = p < 8 ? p : 15 - p;
-    k_ml_sweep_pass<<<g, MLS_WARPS * 32, 0, st>>>(d, colour, p >= 8);
-  }
+  const int g = (d.s8 + LS_SPB - 1) / LS_SPB;
+  const int gn = grid_for(d.n);
+  auto sweep = [&](int predictor) {
+    for (int p = 0; p < 16; ++p) {
+      const int colour = p < 8 ? p : 15 - p;
+      k_ml_sweep<<<g, LS_THREADS, LS_SMEM, st>>>(d, colour, p >= 8, predictor);
+    }
+  };
+  // predictor with the start's (P, Q); (P, Q) at the predicted end averaged in;
+  // corrector from the start spins (a closed gate skips all but the last sweep)
+  k_ml_save_spins<<<gn, SL_BLOCK, 0, st>>>(d);
+  sweep(1);
+  k_ml_desc<<<gn, SL_BLOCK, 0, st>>>(d, 0, nullptr, nullptr);
+  k_ml_mlp<<<ntiles(d), TILE, MLP_SMEM, st>>>(d, 0);
+  k_ml_pair<<<gn, SL_BLOCK, 0, st>>>(d, 8, 0, nullptr, nullptr);
+  k_ml_restore_spins<<<gn, SL_BLOCK, 0, st>>>(d);
+  sweep(0);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 

@@ -107,8 +107,8 @@ def bcc_fe_system(ncells, seed, T=200.0, sigma=0.01, spins="uniform", a=LATTICE_
     v = maxwell_boltzmann(rng, n, T)
     if spins == "uniform":
         s = unit_spins_uniform(rng, n)
-    elif spins == "cone10":
-        s = unit_spins_cone(rng, n, 10.0)
+    elif spins.startswith("cone"):
+        s = unit_spins_cone(rng, n, float(spins[4:] or 10.0))
     elif spins == "fm":
         s = np.tile(np.array([0.0, 0.0, 1.0]), (n, 1))
     else:
@@ -180,3 +180,21 @@ def ml_init_params(seed, n_in=48, n_hidden=64, e0=0.0):
     parts = [glorot(n_hidden, n_in).ravel(), np.zeros(n_hidden), glorot(n_hidden, n_hidden).ravel(),
              np.zeros(n_hidden), glorot(1, n_hidden, 0.1).ravel(), np.array([e0])]
     return np.concatenate(parts).astype(np.float32)
+
+
+def training_replicas(n_replicas=64, seed=18015, ncells=10, t_lo=50.0, t_hi=1200.0, lam=0.01):
+    """Replicas whose trajectories give the learned model's training
+    snapshots: ncells^3-cell bcc Fe at bath temperatures evenly spaced in
+    [t_lo, t_hi] (lattice Maxwell-Boltzmann at the same T), spin baths with
+    damping lam, and three spin starts in turn: uniform on the sphere, 10 deg
+    cones about +z, and cones whose width grows with T (10..90 deg)."""
+    plist, rs, vs, ss = [], [], [], []
+    for k in range(n_replicas):
+        T = t_lo + k * (t_hi - t_lo) / max(1, n_replicas - 1)
+        kind = k % 3
+        spins = "uniform" if kind == 0 else ("cone10" if kind == 1 else f"cone{10.0 + 80.0 * (T - t_lo) / (t_hi - t_lo)}")
+        p, r, v, s = bcc_fe_system(ncells, int(seed) * 1000 + k, T=T, sigma=0.02, spins=spins)
+        p.update({"lambda": float(lam), "temperature_K": float(T), "seed": int(seed), "replica": k})
+        plist.append(p)
+        rs.append(r); vs.append(v); ss.append(s)
+    return plist, np.concatenate(rs), np.concatenate(vs), np.concatenate(ss)

@@ -13,7 +13,7 @@ import math
 import numpy as np
 import torch
 
-from . import _lib
+from . import _lib, inputs
 from .system import System
 
 HBAR = 6.582119569e-4        # eV ps / rad
@@ -101,12 +101,14 @@ def normalisation(stats: np.ndarray, gate_margin: float = 0.5) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # Training data: snapshots of analytic trajectories
 # ---------------------------------------------------------------------------
-def snapshots(plist, r, v, s, n_snap, every, device=None, lam=None):
+def snapshots(plist, r, v, s, n_snap, every, device=None, warm=0):
     """Run the analytic Hamiltonian on the replicas of `plist` and take n_snap
     snapshots, `every` steps apart.  Returns a dict of device tensors:
     r, s [n_snap, N, 3], E [n_snap, n_replicas] (Morse + exchange energy),
     F [n_snap, N, 3], B [n_snap, N, 3] (-dE/ds without the Zeeman part)."""
     sysa = System(plist, r, v, s, device=device)
+    if warm:
+        sysa.step(warm)
     zee = torch.as_tensor(np.stack([zeeman_field(p) for p in plist]), device=sysa.device)
     counts = [int(p["n_atoms"]) for p in plist]
     rep = torch.repeat_interleave(torch.arange(len(counts)), torch.tensor(counts)).to(sysa.device)
@@ -146,3 +148,112 @@ def train(sysm: System, data, epochs, lr, w=(1.0, 1.0, 1e-6), batch_frames=None,
                 print(f"train step {step} lr {cur:.2e} loss {loss}")
             step += 1
     return losses
+
+
+def learned_params(p):
+    """The parameter dict of a system run with the learned Hamiltonian (no spin bath)."""
+    return dict(p, hamiltonian=_lib.SL_HAM_LEARNED, temperature_K=0.0, **{"lambda": 0.0})
+
+
+def training_set(n_frames=20000, n_replicas=64, every=10, warm=100, seed=18015, device=None):
+    """Snapshots of bath-coupled analytic trajectories of 10^3-cell replicas
+    at 50..1200 K (inputs.training_replicas): n_frames frames, n_replicas per
+    snapshot.  Returns (plist, data) with data as snapshots()."""
+    plist, r, v, s = inputs.training_replicas(n_replicas, seed)
+    n_snap = max(1, -(-n_frames // n_replicas))
+    return plist, snapshots(plist, r, v, s, n_snap, every, device=device, warm=warm)
+
+
+def fit_normalisation(sysm: System, data, picks=(0,), gate_margin=0.5):
+    """Descriptor statistics of a few training snapshots -> normalisation vector."""
+    zeros = torch.zeros_like(data["r"][0])
+    stats = []
+    for k in picks:
+        sysm.set_state(data["r"][k], zeros, data["s"][k])
+        stats.append(sysm.ml_descriptor_stats())
+    st = np.stack(stats)
+    comb = np.stack([st[:, 0].mean(0), np.sqrt((st[:, 1] ** 2).mean(0)), st[:, 2].min(0), st[:, 3].max(0)])
+    return normalisation(comb, gate_margin)
+
+
+def train_model(plist, data, epochs=8, lr=2e-3, lr_min=2e-5, w=(1.0, 1.0, 1e-4), seed=3, log=None, device=None):
+    """Fit the network to the snapshots (one Adam step per snapshot of all
+    replicas).  Returns (params float32 numpy, norm, per-step losses, seconds)."""
+    import time
+    lp = [learned_params(p) for p in plist]
+    r0 = data["r"][0]
+    e0 = float(data["E"][0].sum().item() / r0.shape[0])
+    init = inputs.ml_init_params(seed, e0=e0)
+    sysm = System(lp, r0, torch.zeros_like(r0), data["s"][0], device=device)
+    counts = [int(p["n_atoms"]) for p in lp]
+    sysm._atom_replica = torch.repeat_interleave(torch.arange(len(counts)), torch.tensor(counts))
+    n = data["r"].shape[0]
+    open_gate = np.concatenate([np.zeros(48), np.ones(48), np.full(48, -3e38), np.full(48, 3e38)]).astype(np.float32)
+    sysm.ml_set_model(init, open_gate)
+    norm = fit_normalisation(sysm, data, picks=sorted({0, n // 2, n - 1}))
+    sysm.ml_set_model(init, norm)
+    sysm._ml_norm = torch.as_tensor(norm)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = train(sysm, data, epochs, lr, w=w, lr_min=lr_min, log=log)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    params = sysm.ml_get_model().cpu().numpy()
+    sysm.close()
+    return params, norm, np.array(losses), secs
+
+
+def _drift(ts, es):
+    """Least-squares slope of es against ts."""
+    t = np.asarray(ts, dtype=np.float64)
+    e = np.asarray(es, dtype=np.float64)
+    if len(t) < 2:
+        return 0.0
+    A = np.stack([t, np.ones_like(t)], 1)
+    return float(np.linalg.lstsq(A, e, rcond=None)[0][0])
+
+
+def judge(params, norm, p, r, v, s, steps, every, device=None):
+    """Run the learned and the analytic Hamiltonian side by side from the same
+    state and report the learned model's errors (energy per atom, forces,
+    precession vector normal to s) against the analytic Hamiltonian at the
+    learned trajectory's states, the energy drift of both runs (eV/atom/ps),
+    the largest |M| difference between the runs, and the gate counters."""
+    n = int(p["n_atoms"])
+    pa = dict(p, hamiltonian=_lib.SL_HAM_ANALYTIC)
+    plain = System(pa, r, v, s, device=device)
+    probe = System(pa, r, v, s, device=device)
+    lsys = System(learned_params(p), r, v, s, device=device)
+    lsys._ml_norm = torch.as_tensor(norm)
+    lsys._atom_replica = torch.zeros(n, dtype=torch.long)
+    lsys.ml_set_model(params, norm)
+    zee = torch.as_tensor(zeeman_field(p), device=lsys.device)
+    dt = float(p["dt_ps"])
+    ts, e_plain, e_learn, dM = [], [], [], []
+    errE, errF, errW = [], [], []
+    for k in range(0, steps + 1, every):
+        if k:
+            plain.step(every)
+            lsys.step(every)
+        ts.append(k * dt)
+        e_plain.append(plain.energy()[4] / n)
+        e_learn.append(lsys.energy()[4] / n)
+        dM.append(abs(plain.magnetization()[3] - lsys.magnetization()[3]))
+        rl, vl, sl = lsys.state()
+        probe.set_state(rl, vl, sl)
+        ea = probe.energy()
+        el, Fl, Bl, _ = lsys.ml_eval()
+        errE.append(abs(el[0] - (ea[1] + ea[2])) / n)
+        dF = Fl - probe.forces()
+        errF.append(float(torch.sqrt((dF ** 2).sum(1).mean()).item()))
+        dB = (Bl + zee) / HBAR - probe.omega()
+        dB = dB - (dB * sl).sum(1, keepdim=True) * sl
+        errW.append(float(torch.sqrt((dB ** 2).sum(1).mean()).item()))
+    gate = lsys.ml_gate()
+    out = dict(steps=steps, atoms=n, drift_plain_eV_per_atom_ps=_drift(ts, e_plain),
+               drift_learned_eV_per_atom_ps=_drift(ts, e_learn), max_dM=float(max(dM)),
+               err_E_eV_per_atom=float(max(errE)), rmse_F_eV_per_A=float(max(errF)),
+               rmse_omega_perp_rad_per_ps=float(max(errW)), gate_points_handed_back=gate[2])
+    for x in (plain, probe, lsys):
+        x.close()
+    return out
