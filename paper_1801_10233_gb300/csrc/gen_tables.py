@@ -64,6 +64,28 @@ def main():
         hi, lo = split2(Decimal(1) / Decimal(fac))
         out.append(f"#define SL_INV_FACT{k}_HI {hexf(hi)}")
         out.append(f"#define SL_INV_FACT{k}_LO {hexf(lo)}")
+    out.append("")
+    out.append("// ln2, 2 pi, 1/(2k+1) and 1/k! as hi + lo, for the double-float log, sincos")
+    out.append("// and the Box-Muller normals of the spin bath")
+    hi, lo = split2(ln2())
+    out.append(f"#define SL_LN2_HI {hexf(hi)}")
+    out.append(f"#define SL_LN2_LO {hexf(lo)}")
+    pi = Decimal("3.14159265358979323846264338327950288419716939937510582097494459")
+    hi, lo = split2(2 * pi)
+    out.append(f"#define SL_2PI_HI {hexf(hi)}")
+    out.append(f"#define SL_2PI_LO {hexf(lo)}")
+    hi, lo = split2(Decimal(2).sqrt())
+    out.append(f"#define SL_SQRT2_HI {hexf(hi)}")
+    for k in range(1, 13):
+        hi, lo = split2(Decimal(1) / Decimal(2 * k + 1))
+        out.append(f"#define SL_INV_ODD{2 * k + 1}_HI {hexf(hi)}")
+        out.append(f"#define SL_INV_ODD{2 * k + 1}_LO {hexf(lo)}")
+    fac = 1
+    for k in range(1, 19):
+        fac *= k
+        hi, lo = split2(Decimal(1) / Decimal(fac))
+        out.append(f"#define SL_INV_FAC{k}_HI {hexf(hi)}")
+        out.append(f"#define SL_INV_FAC{k}_LO {hexf(lo)}")
     assert float(f32(c1)) == float(c1)
     print("\n".join(out))
 

@@ -142,6 +142,17 @@ void fill_df_constants(SlDev& d) {
   d.tau_f = split_f2(0.25 * d.dt);
 }
 
+// Noise amplitude of each replica's spin bath for the current dt: each
+// single-spin factor over tau = dt/4 draws eta ~ N(0, 2 D_S / |tau|) per
+// component, D_S = lambda (1 + lambda^2) k_B T / hbar.
+void fill_noise(std::vector<SlRep>& reps, double lambda, double dt) {
+  for (SlRep& R : reps) {
+    double DS = lambda * (1.0 + lambda * lambda) * SL_KB * R.temperature / SL_HBAR;
+    R.noise_sig = R.temperature > 0.0 && dt != 0.0 ? split_f2(std::sqrt(2.0 * DS / std::fabs(0.25 * dt)))
+                                                   : make_float2(0.0f, 0.0f);
+  }
+}
+
 // Fill d's scalars, the replica table and (if base != NULL) d's pointers;
 // returns the workspace bytes needed.
 size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, char* base) {
@@ -219,6 +230,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   d.lam_f = split_f2(p->lambda);
   d.inv1pl2_f = split_f2(1.0 / (1.0 + p->lambda * p->lambda));
   fill_df_constants(d);
+  fill_noise(reps, p->lambda, p->dt_ps);
 
   Layout L;
   size_t nn = (size_t)n;
@@ -543,9 +555,17 @@ int sl_get_timing(sl_ctx* c, double ms[8], int64_t count[8]) {
 
 int sl_set_dt(sl_ctx* c, double dt) {
   if (!c || !std::isfinite(dt)) return SL_ERR_ARG;
+  DeviceGuard g(c->device);
   c->p.dt_ps = dt;
   c->d.dt = dt;
   fill_df_constants(c->d);
+  if (c->d.any_noise) {
+    fill_noise(c->reps, c->p.lambda, dt);
+    if (cudaMemcpyAsync((void*)c->d.reps, c->reps.data(), sizeof(SlRep) * c->nrep, cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return cuda_err(c);
+  }
   drop_graph(c);
   return c->sticky;
 }

@@ -227,3 +227,74 @@ __device__ __forceinline__ df acc_done(float h, float l) { return fast_two_sum(h
 
 // a < b for normalised df values.
 __device__ __forceinline__ bool df_lt(df a, df b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+// a / b: quotient, two corrections (~2^-46).
+__device__ __forceinline__ df df_div(df a, df b) {
+  const float q1 = a.hi / b.hi;
+  const df r = df_sub(a, df_mul_f(b, q1));
+  const float q2 = r.hi / b.hi;
+  const df r2 = df_sub(r, df_mul_f(b, q2));
+  const float q3 = r2.hi / b.hi;
+  return df_add_f(fast_two_sum(q1, q2), q3);
+}
+
+// sqrt(a), a > 0: correctly rounded float root, one Newton correction.
+__device__ __forceinline__ df df_sqrt(df a) {
+  const float y = sqrtf(a.hi);
+  const df e = df_sub(a, two_prod(y, y));
+  return fast_two_sum(y, e.hi / (2.0f * y));
+}
+
+// ln(u) for a normal positive u: u = m 2^e with m in [1/sqrt2, sqrt2),
+// ln m = 2 atanh(z), z = (m - 1)/(m + 1), |z| <= 0.172, as the odd series
+// 2 z sum_k z^(2k)/(2k+1) (terms beyond z^20 below 2^-48; the ones from
+// 1/13 on summed in float), ln u = e ln2 + ln m.  No cancellation for u
+// near 1 (e = 0, z small).
+__device__ __forceinline__ df df_log(df u) {
+  int e = ((__float_as_int(u.hi) >> 23) & 0xff) - 127;
+  const float sc = __int_as_float((127 - e) << 23);     // 2^-e, exact
+  df m = df_make(u.hi * sc, u.lo * sc);
+  if (m.hi > SL_SQRT2_HI) { m = df_scale(m, 0.5f); e += 1; }
+  const df z = df_div(df_add_f(m, -1.0f), df_add_f(m, 1.0f));
+  const df w = df_sqr(z);
+  const float wf = w.hi;
+  const float tail = 1.0f / 13.0f + wf * (1.0f / 15.0f + wf * (1.0f / 17.0f + wf * (1.0f / 19.0f + wf * (1.0f / 21.0f))));
+  df S = df_add_f(df_make(SL_INV_ODD11_HI, SL_INV_ODD11_LO), wf * tail);
+  S = df_add(df_mul(w, S), df_make(SL_INV_ODD9_HI, SL_INV_ODD9_LO));
+  S = df_add(df_mul(w, S), df_make(SL_INV_ODD7_HI, SL_INV_ODD7_LO));
+  S = df_add(df_mul(w, S), df_make(SL_INV_ODD5_HI, SL_INV_ODD5_LO));
+  S = df_add(df_mul(w, S), df_make(SL_INV_ODD3_HI, SL_INV_ODD3_LO));
+  S = df_add_f(df_mul(w, S), 1.0f);
+  const df lnm = df_scale(df_mul(z, S), 2.0f);
+  return df_add(df_mul_f(df_make(SL_LN2_HI, SL_LN2_LO), (float)e), lnm);
+}
+
+// sin(2 pi u), cos(2 pi u) for u in [0, 1]: quadrant k = rint(4u),
+// a = 2 pi (u - k/4) in [-pi/4, pi/4] (u - k/4 is exact), Taylor series of
+// sin a / a and cos a to a^18 (the terms from 1/11! and 1/10! on in float),
+// then the quadrant's swap and signs.
+__device__ __forceinline__ void df_sincos_2pi(df u, df& sn, df& cs) {
+  const float kf = rintf(u.hi * 4.0f);
+  const df fr = df_add_f(u, -0.25f * kf);
+  const df a = df_mul(fr, df_make(SL_2PI_HI, SL_2PI_LO));
+  const df a2 = df_sqr(a);
+  const float t = a2.hi;
+  float tail = SL_INV_FAC11_HI - t * (SL_INV_FAC13_HI - t * (SL_INV_FAC15_HI - t * SL_INV_FAC17_HI));
+  df S = df_add_f(df_make(SL_INV_FAC9_HI, SL_INV_FAC9_LO), -t * tail);
+  S = df_sub(df_make(SL_INV_FAC7_HI, SL_INV_FAC7_LO), df_mul(a2, S));
+  S = df_sub(df_make(SL_INV_FAC5_HI, SL_INV_FAC5_LO), df_mul(a2, S));
+  S = df_sub(df_make(SL_INV_FAC3_HI, SL_INV_FAC3_LO), df_mul(a2, S));
+  S = df_add_f(df_neg(df_mul(a2, S)), 1.0f);
+  const df s = df_mul(a, S);
+  tail = SL_INV_FAC10_HI - t * (SL_INV_FAC12_HI - t * (SL_INV_FAC14_HI - t * (SL_INV_FAC16_HI - t * SL_INV_FAC18_HI)));
+  df Cc = df_add_f(df_make(SL_INV_FAC8_HI, SL_INV_FAC8_LO), -t * tail);
+  Cc = df_sub(df_make(SL_INV_FAC6_HI, SL_INV_FAC6_LO), df_mul(a2, Cc));
+  Cc = df_sub(df_make(SL_INV_FAC4_HI, SL_INV_FAC4_LO), df_mul(a2, Cc));
+  Cc = df_sub(df_make(SL_INV_FAC2_HI, SL_INV_FAC2_LO), df_mul(a2, Cc));
+  const df c = df_add_f(df_neg(df_mul(a2, Cc)), 1.0f);
+  const int q = ((int)kf) & 3;
+  if (q == 0) { sn = s; cs = c; }
+  else if (q == 1) { sn = c; cs = df_neg(s); }
+  else if (q == 2) { sn = df_neg(s); cs = df_neg(c); }
+  else { sn = df_neg(c); cs = s; }
+}

@@ -43,6 +43,7 @@ struct SlRep {
   int atom0, natoms;        // atom range in caller order
   int replica;              // Philox counter word of the spin noise
   double temperature;       // spin bath temperature (K)
+  float2 noise_sig;         // sqrt(2 D_S / |dt/4|) as (hi, lo), D_S = lambda (1 + lambda^2) k_B T / hbar
 };
 
 // Everything a kernel needs, passed by value.  Scalars used by the

@@ -118,6 +118,29 @@ __device__ __forceinline__ double3 gauss3(uint64_t seed, int replica, long long 
   return make_double3(ra * c1, ra * s1, rb * c3);
 }
 
+// The same three normals in double-float on the FP32 pipes (Box-Muller with
+// the double-float log, sqrt and sincos of sl_df64.cuh), within ~1e-14 of the
+// FP64 values.
+__device__ __forceinline__ df unit_from_word(unsigned x) {
+  // (x + 1/2) 2^-32 exactly: 24 high bits and the rest as two floats
+  const df u = fast_two_sum(__uint2float_rn(x >> 8) * 256.0f, __uint2float_rn(x & 255u) + 0.5f);
+  return df_scale(u, 2.3283064365386962890625e-10f);
+}
+__device__ __forceinline__ df3 gauss3_df(uint64_t seed, int replica, long long step, int subpass, int atom) {
+  uint4 x = philox4x32_10(make_uint4((unsigned)atom, (unsigned)step, (unsigned)subpass, (unsigned)replica),
+                          make_uint2((unsigned)seed, (unsigned)(seed >> 32)));
+  const df ra = df_sqrt(df_scale(df_log(unit_from_word(x.x)), -2.0f));
+  const df rb = df_sqrt(df_scale(df_log(unit_from_word(x.z)), -2.0f));
+  df s1, c1, s3, c3;
+  df_sincos_2pi(unit_from_word(x.y), s1, c1);
+  df_sincos_2pi(unit_from_word(x.w), s3, c3);
+  df3 g;
+  g.x = df_mul(ra, c1);
+  g.y = df_mul(ra, s1);
+  g.z = df_mul(rb, c3);
+  return g;
+}
+
 // ---------------------------------------------------------------------------
 // Single-spin propagator e^{L_si tau} as an increment of s:
 //   s' - s = -u B s + tau A (w x s) + tau^2 B (w.s) w,      u = tau^2 |w|^2.

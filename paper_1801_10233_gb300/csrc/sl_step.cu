@@ -158,17 +158,16 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
       // eta ~ N(0, 2 D_S / |tau|), D_S = lambda (1 + lambda^2) k_B T / hbar;
       // counter (atom id within its replica, step, sub-pass, replica)
       const SlRep& R = d.reps[__ldg(d.arep + i)];
-      double3 g = make_double3(0.0, 0.0, 0.0);
-      double sig = 0.0;
+      df3 g;
+      g.x = g.y = g.z = df_f(0.0f);
+      df sig = df_f(0.0f);
       if (R.temperature > 0.0) {
-        g = gauss3(d.seed, R.replica, step, subpass, d.perm[i] - R.atom0);
-        double lam = d.lambda;
-        double DS = lam * (1.0 + lam * lam) * SL_KB * R.temperature / SL_HBAR;
-        sig = sqrt(2.0 * DS / fabs(0.25 * d.dt));
+        g = gauss3_df(d.seed, R.replica, step, subpass, d.perm[i] - R.atom0);
+        sig = F2(R.noise_sig);
       }
-      E[3 * t] = D2(df_from_double(sig * g.x));
-      E[3 * t + 1] = D2(df_from_double(sig * g.y));
-      E[3 * t + 2] = D2(df_from_double(sig * g.z));
+      E[3 * t] = D2(df_mul(sig, g.x));
+      E[3 * t + 1] = D2(df_mul(sig, g.y));
+      E[3 * t + 2] = D2(df_mul(sig, g.z));
     }
   }
   __syncthreads();

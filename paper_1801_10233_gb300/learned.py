@@ -257,3 +257,44 @@ def judge(params, norm, p, r, v, s, steps, every, device=None):
     for x in (plain, probe, lsys):
         x.close()
     return out
+
+
+def main(argv=None):
+    """Train the network on snapshots and run the learned Hamiltonian beside
+    the analytic one on a workload:
+        python -m paper_1801_10233_gb300.learned --frames 640 --epochs 1 \\
+            --workload fe_bcc_40x40x40_nve --steps 20
+    Prints one JSON line (training, rates, judge)."""
+    import argparse
+    import json
+    import time
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--frames", type=int, default=2560)
+    ap.add_argument("--epochs", type=int, default=2)
+    ap.add_argument("--workload", default="fe_bcc_40x40x40_nve", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--judge-steps", type=int, default=0)
+    args = ap.parse_args(argv)
+    from . import build
+    build.build()
+    plist, data = training_set(n_frames=args.frames)
+    params, norm, losses, secs = train_model(plist, data, epochs=args.epochs)
+    del data
+    p, r, v, s = inputs.workload(args.workload)
+    sysm = learned_system(learned_params(p), r, v, s, norm, params)
+    sysm.step(3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sysm.step(args.steps)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
+    out = {"workload": args.workload, "n_atoms": p["n_atoms"], "learned_ms_per_step": ms,
+           "train_seconds": secs, "loss_last": [float(x) for x in losses[-1]], "gate": sysm.ml_gate()}
+    sysm.close()
+    if args.judge_steps:
+        out["judge"] = judge(params, norm, p, r, v, s, args.judge_steps, max(1, args.judge_steps // 10))
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
