@@ -75,6 +75,7 @@ def parse():
                              "fe_bcc_batch256"])
     ap.add_argument("--no-forms", action="store_true", help="skip the extra per-form measurements")
     ap.add_argument("--no-learned", action="store_true", help="skip training and judging the learned Hamiltonian")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--learned-frames", type=int, default=20000, help="training snapshots (10^3-cell frames)")
     ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--learned-steps", type=int, default=500, help="judged steps on 40^3 cells")
@@ -284,6 +285,8 @@ def run_ours(args):
     sysm = System(p, r, v, s, device=dev)
     p0 = p[0] if isinstance(p, list) else p
     stream = sysm.stream
+    # launch shapes from the autotuner (state restored bitwise, outside the timed region)
+    tune = None if args.no_autotune else sysm.autotune(3)
     sysm.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -359,6 +362,7 @@ def run_ours(args):
             fp, fr, fv, fs, fdesc = build_workload(name, 0)
             fn = int(sum(q["n_atoms"] for q in fp)) if isinstance(fp, list) else fp["n_atoms"]
             fsys = System(fp, fr, fv, fs, device=dev)
+            ftune = None if args.no_autotune else fsys.autotune(2)
             fsys.step(3)
             torch.cuda.synchronize()
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -368,7 +372,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             fms = f0.elapsed_time(f1) / steps
             forms[name] = {"value": fn / (fms * 1e-3), "unit": UNIT, "ms_per_step": fms, "steps": steps,
-                           "n_atoms": fn, "workload": fdesc}
+                           "n_atoms": fn, "workload": fdesc, "launch_shape": ftune}
             fsys.close()
             del fsys
         if not args.no_learned:
@@ -387,7 +391,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": wdesc, "n_atoms": n, "dt_ps": p0["dt_ps"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "working set > 129 MB L2 (no flush needed)", "graph": counters["graph"]},
+                       "l2": "working set > 129 MB L2 (no flush needed)", "graph": counters["graph"],
+                       "launch_shape": tune},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "forms": forms,
         }

@@ -205,6 +205,27 @@ int sl_counters(sl_ctx* ctx, int64_t out[8]);
 int sl_set_timing(sl_ctx* ctx, int32_t enable);
 int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
 
+/* Launch-shape autotuner.  The colour-pass kernel comes in
+ * SL_SWEEP_VARIANTS tile shapes (sectors per block x threads per block:
+ * 32x192 (variant 0, the default), 32x256, 16x128, 16x192, 8x128) and the
+ * per-atom kernels (kick, drift, exchange table, forces) take 64, 128 (the
+ * default) or 256 threads per block.  The shape changes only how the work is
+ * grouped into blocks, never the arithmetic of a spin or an atom: results are
+ * bitwise the same for every shape.
+ * sl_autotune times `steps` timesteps (after one warm-up step) of every
+ * combination on the context's own state, restoring the whole workspace from
+ * `scratch` (device, >= the workspace's bytes, owned by the caller) before
+ * each candidate and at the end, so the state afterwards is bitwise the state
+ * before; then it keeps the fastest shape.  With the learned Hamiltonian only
+ * the block size is tuned.  out (host, 8): chosen variant, chosen block, its
+ * ns per step, the default shape's ns per step, candidates timed, sectors per
+ * block of the chosen variant, 0, 0.  Synchronises.
+ * Errors: SL_ERR_ARG, SL_ERR_WORKSPACE (scratch too small), SL_ERR_CUDA.
+ * sl_set_launch_shape sets a shape directly (SL_ERR_ARG for unknown ones). */
+#define SL_SWEEP_VARIANTS 5
+int sl_autotune(sl_ctx* ctx, void* scratch, size_t scratch_bytes, int32_t steps, int64_t out[8]);
+int sl_set_launch_shape(sl_ctx* ctx, int32_t sweep_variant, int32_t block);
+
 /* Magnetisation of a caller's spin array without a context and without any
  * allocation, for callers that cannot call cudaMalloc (code running inside
  * another allocator's hooks, plugins handed device pointers only, processes

@@ -34,7 +34,7 @@ EXPORTS = (
     "sl_get_timing", "sl_magnetization_static", "sl_status", "sl_strerror", "sl_destroy",
     "sl_workspace_bytes_batch", "sl_init_batch", "sl_batch_size", "sl_energy_batch", "sl_magnetization_batch",
     "sl_ml_set_model", "sl_ml_get_model", "sl_ml_eval", "sl_ml_descriptor_stats", "sl_ml_gate", "sl_ml_vjp",
-    "sl_ml_train_step",
+    "sl_ml_train_step", "sl_autotune", "sl_set_launch_shape",
 )
 PHASES = ("kick", "spin_half_op_1", "drift_rebuild", "exchange_table", "spin_half_op_2", "force_kick")
 
@@ -105,6 +105,8 @@ def load():
         "sl_ml_vjp": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
         "sl_ml_train_step": ([_vp, _vp, _vp, _vp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                               ctypes.c_double, _dp], ctypes.c_int),
+        "sl_autotune": ([_vp, _vp, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "sl_set_launch_shape": ([_vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "sl_strerror": ([ctypes.c_int], ctypes.c_char_p),
         "sl_destroy": ([_vp], None),
     }

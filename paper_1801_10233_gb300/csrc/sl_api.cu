@@ -28,6 +28,8 @@ struct sl_ctx {
   double phase_ms[SL_NPHASE];
   long long phase_n[SL_NPHASE];
   // learned Hamiltonian
+  void* ws_base;            // the caller's workspace (all device state of the context)
+  size_t ws_bytes;
   int ml_ready;             // a model has been set
   int ml_stale;             // parameters changed since the last evaluation point
   long long ml_t;           // Adam steps taken
@@ -471,6 +473,8 @@ int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, 
   if (!c) return SL_ERR_ARG;
   c->p = params[0];
   c->nrep = n_replicas;
+  c->ws_base = workspace;
+  c->ws_bytes = need;
   plan(params, n_replicas, c->d, c->reps, (char*)workspace);
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SL_ERR_CUDA; }
@@ -749,6 +753,83 @@ int sl_counters(sl_ctx* c, int64_t out[8]) {
   out[0] = h.step; out[1] = h.rebuilds; out[2] = h.max_ex_seen; out[3] = h.max_m_seen;
   out[4] = c->kernels_per_step; out[5] = c->graph_ok; out[6] = 0; out[7] = 0;
   if (h.status && !c->sticky) c->sticky = h.status;
+  return c->sticky;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the launch shapes
+// ---------------------------------------------------------------------------
+int sl_autotune(sl_ctx* c, void* scratch, size_t scratch_bytes, int32_t steps, int64_t out[8]) {
+  if (!c || !scratch || !out || steps < 1) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  if (scratch_bytes < c->ws_bytes) return SL_ERR_WORKSPACE;
+  if (c->d.ham == SL_HAM_LEARNED && !c->ml_ready) return SL_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (int e = ml_fresh(c)) return e;
+  cudaStream_t st = c->stream;
+  if (cudaMemcpyAsync(scratch, c->ws_base, c->ws_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return cuda_err(c);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_err(c);
+  }
+  const int blocks[3] = {64, 128, 256};
+  // the learned step has its own sweep kernel: only the block size applies
+  const int nvar = c->d.ham == SL_HAM_LEARNED ? 1 : SL_SWEEP_VARIANTS;
+  const int keep_sweep = c->d.tune_sweep, keep_block = c->d.tune_block;
+  double best = 1e300, base = 0.0;
+  int best_v = 0, best_b = SL_BLOCK, tried = 0, err = SL_OK;
+  for (int v = 0; v < nvar && !err; ++v)
+    for (int bi = 0; bi < 3 && !err; ++bi) {
+      c->d.tune_sweep = v;
+      c->d.tune_block = blocks[bi];
+      int kp = 0;
+      err = sl_launch_step(c->d, st, nullptr, nullptr, &kp);      // warm-up
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < steps && !err; ++k) err = sl_launch_step(c->d, st, nullptr, nullptr, &kp);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (!err && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        err = SL_ERR_CUDA;
+      // every candidate starts from the same state
+      if (cudaMemcpyAsync(c->ws_base, scratch, c->ws_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        err = SL_ERR_CUDA;
+      if (err) break;
+      const double per = (double)ms / steps;
+      if (v == 0 && blocks[bi] == SL_BLOCK) base = per;
+      if (per < best) { best = per; best_v = v; best_b = blocks[bi]; }
+      ++tried;
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaStreamSynchronize(st) != cudaSuccess) err = SL_ERR_CUDA;
+  if (err) {
+    c->d.tune_sweep = keep_sweep;
+    c->d.tune_block = keep_block;
+    if (!c->sticky) c->sticky = err;
+    return err;
+  }
+  c->d.tune_sweep = best_v;
+  c->d.tune_block = best_b;
+  drop_graph(c);
+  out[0] = best_v;
+  out[1] = best_b;
+  out[2] = (int64_t)(best * 1e6);
+  out[3] = (int64_t)(base * 1e6);
+  out[4] = tried;
+  out[5] = kSlSweepSPB[best_v];
+  out[6] = 0;
+  out[7] = 0;
+  return sync_status(c);
+}
+
+int sl_set_launch_shape(sl_ctx* c, int32_t sweep_variant, int32_t block) {
+  if (!c || sweep_variant < 0 || sweep_variant >= SL_SWEEP_VARIANTS) return SL_ERR_ARG;
+  if (block != 64 && block != 128 && block != 256) return SL_ERR_ARG;
+  c->d.tune_sweep = sweep_variant;
+  c->d.tune_block = block;
+  drop_graph(c);
   return c->sticky;
 }
 

@@ -13,6 +13,8 @@
 #define SL_FTOA 9648.533212       // (eV/A)/amu -> A/ps^2
 
 #define SL_BLOCK 128
+// Sectors per block of the colour-pass tile shapes (threads: 192, 256, 128, 192, 128).
+static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8};
 #define SL_MAX_EX_CAP 64   // largest accepted max_ex_neighbors
 
 // Control block in device memory: sticky status, rebuild flag, counters.
@@ -69,6 +71,8 @@ struct SlDev {
   int any_noise;            // some replica has a bath temperature
   uint64_t seed;
   int ham;                  // SL_HAM_ANALYTIC or SL_HAM_LEARNED
+  int tune_sweep;           // colour-pass tile shape variant (0 .. SL_SWEEP_VARIANTS-1)
+  int tune_block;           // threads per block of the per-atom kernels (0: SL_BLOCK)
 
   // double-float constants (hi, lo)
   float2 zee_f[3], inv_hbar_f, tau_f;        // tau = dt/4

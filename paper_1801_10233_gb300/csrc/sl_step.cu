@@ -38,18 +38,18 @@ inline int grid_for(int n) { return (n + SL_BLOCK - 1) / SL_BLOCK; }
 // Blocks with more than SW_MAXA atoms use workspace scratch and read their
 // lists from global memory.
 // ---------------------------------------------------------------------------
-constexpr int SW_SPB = 32;
-constexpr int SW_THREADS = 192;
-constexpr int SW_MAXA = 384;
+// Tile shapes (sectors per block SPB <= 32, threads per block): the
+// variants the autotuner chooses from (sl_autotune), variant 0 the default.
+// A block stages up to 12 atoms per sector in shared memory.
 constexpr int SW_MAXIN = 12;   // same-sector neighbours staged per atom
 constexpr int SW_BATCH = 4;    // external neighbours gathered per batch
 
-// Dynamic shared memory of one block: H, S (and E with noise) as float2
-// [3 SW_MAXA], same-sector lists J [SW_MAXIN SW_MAXA] float2, local index
-// [SW_MAXIN SW_MAXA] short, counts [SW_MAXA] int.
-size_t sweep_smem_bytes(bool noise) {
-  return (size_t)(noise ? 3 : 2) * 3 * SW_MAXA * sizeof(float2) + (size_t)SW_MAXIN * SW_MAXA * sizeof(float2) +
-         (size_t)SW_MAXIN * SW_MAXA * sizeof(short) + (size_t)SW_MAXA * sizeof(int);
+// Dynamic shared memory of one block with up to maxa atoms: H, S (and E
+// with noise) as float2 [3 maxa], same-sector lists J [SW_MAXIN maxa]
+// float2, local index [SW_MAXIN maxa] short, counts [maxa] int.
+size_t sweep_smem_bytes(bool noise, int maxa) {
+  return (size_t)(noise ? 3 : 2) * 3 * maxa * sizeof(float2) + (size_t)SW_MAXIN * maxa * sizeof(float2) +
+         (size_t)SW_MAXIN * maxa * sizeof(short) + (size_t)maxa * sizeof(int);
 }
 
 // (h, l) += sum of J_ij s_j over external entries [k0, k1) of atom i whose
@@ -91,8 +91,10 @@ __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1,
   }
 }
 
-__global__ void __launch_bounds__(SW_THREADS, 3)
+template <int SW_SPB, int SW_THREADS>
+__global__ void __launch_bounds__(SW_THREADS, 576 / SW_THREADS)
 k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, int next_colour, int pin, int pout) {
+  constexpr int SW_MAXA = 12 * SW_SPB;
   extern __shared__ float2 smem[];
   const bool noise = d.any_noise != 0;
   const bool bath = d.lambda != 0.0 || noise;
@@ -187,10 +189,25 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
         float gx = 0.0f, kx = 0.0f, gy = 0.0f, ky = 0.0f, gz = 0.0f, kz = 0.0f;
         const int ni = fits ? sh_in[t] : d.exin[i];
         const int nstage = fits ? min(ni, kin) : 0;
+        // the same-sector entries in pairs (two interleaved accumulators), from
+        // shared memory where staged; the order is the same whatever is staged,
+        // so every tile shape gives the same bits
+        auto entry = [&](int k, int& u, df& J) {
+          if (k < nstage) {
+            u = sh_iu[t * SW_MAXIN + k];
+            J = F2(sh_ij[t * SW_MAXIN + k]);
+          } else {
+            const size_t e = (size_t)k * n + i;
+            u = d.exj[e] - a0;
+            J = F2(d.exJ[e]);
+          }
+        };
         int k = 0;
-        for (; k + 1 < nstage; k += 2) {   // two interleaved accumulators
-          const int u0 = sh_iu[t * SW_MAXIN + k], u1 = sh_iu[t * SW_MAXIN + k + 1];
-          const df J0 = F2(sh_ij[t * SW_MAXIN + k]), J1 = F2(sh_ij[t * SW_MAXIN + k + 1]);
+        for (; k + 1 < ni; k += 2) {
+          int u0, u1;
+          df J0, J1;
+          entry(k, u0, J0);
+          entry(k + 1, u1, J1);
           acc_prod(hx, lx, J0, F2(S[3 * u0]));
           acc_prod(gx, kx, J1, F2(S[3 * u1]));
           acc_prod(hy, ly, J0, F2(S[3 * u0 + 1]));
@@ -198,20 +215,13 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
           acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
           acc_prod(gz, kz, J1, F2(S[3 * u1 + 2]));
         }
-        if (k < nstage) {
-          const int u0 = sh_iu[t * SW_MAXIN + k];
-          const df J0 = F2(sh_ij[t * SW_MAXIN + k]);
+        if (k < ni) {
+          int u0;
+          df J0;
+          entry(k, u0, J0);
           acc_prod(hx, lx, J0, F2(S[3 * u0]));
           acc_prod(hy, ly, J0, F2(S[3 * u0 + 1]));
           acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
-        }
-        for (k = nstage; k < ni; ++k) {   // lists not staged in shared memory
-          const size_t e = (size_t)k * n + i;
-          const int u = d.exj[e] - a0;
-          const df J = F2(d.exJ[e]);
-          acc_prod(hx, lx, J, F2(S[3 * u]));
-          acc_prod(hy, ly, J, F2(S[3 * u + 1]));
-          acc_prod(hz, lz, J, F2(S[3 * u + 2]));
         }
         df3 w;
         w.x = df_mul(df_add(acc_done(hx, lx), acc_done(gx, kx)), ih);
@@ -432,9 +442,10 @@ __global__ void k_end_step(SlDev d) { d.ctrl->step += 1; }
 
 // The 16 passes of a spin half-op: colours 0..7 forward, then 7..0 backward.
 // Pass p reads the partial field written by pass p - 1 (none for p = 0).
-void launch_half_op(const SlDev& d, cudaStream_t st, int subpass0) {
-  int g = (d.s8 + SW_SPB - 1) / SW_SPB;
-  size_t sm = sweep_smem_bytes(d.any_noise != 0);
+template <int SPB, int THREADS>
+void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
+  int g = (d.s8 + SPB - 1) / SPB;
+  size_t sm = sweep_smem_bytes(d.any_noise != 0, 12 * SPB);
   int col[16], bwd[16];
   for (int p = 0; p < 8; ++p) { col[p] = p; bwd[p] = 0; col[15 - p] = p; bwd[15 - p] = 1; }
   for (int p = 0; p < 16; ++p) {
@@ -442,9 +453,23 @@ void launch_half_op(const SlDev& d, cudaStream_t st, int subpass0) {
     const int next = p < 15 ? col[p + 1] : -1;
     const int pin = p > 0 ? (p - 1) & 1 : -1;
     const int pout = p < 15 ? p & 1 : -1;
-    k_sweep_pass<<<g, SW_THREADS, sm, st>>>(d, col[p], bwd[p], subpass0 + bwd[p], prev, next, pin, pout);
+    k_sweep_pass<SPB, THREADS><<<g, THREADS, sm, st>>>(d, col[p], bwd[p], subpass0 + bwd[p], prev, next, pin, pout);
   }
 }
+
+void launch_half_op(const SlDev& d, cudaStream_t st, int subpass0) {
+  switch (d.tune_sweep) {
+    case 1: launch_half_op_t<32, 256>(d, st, subpass0); break;
+    case 2: launch_half_op_t<16, 128>(d, st, subpass0); break;
+    case 3: launch_half_op_t<16, 192>(d, st, subpass0); break;
+    case 4: launch_half_op_t<8, 128>(d, st, subpass0); break;
+    default: launch_half_op_t<32, 192>(d, st, subpass0); break;
+  }
+}
+
+// threads per block of the per-atom kernels (autotuned)
+inline int tb(const SlDev& d) { return d.tune_block > 0 ? d.tune_block : SL_BLOCK; }
+inline int grid_tb(const SlDev& d) { return (d.n + tb(d) - 1) / tb(d); }
 
 // omega of every atom in caller order (device out [n][3]), FP64.
 __global__ void k_omega_all(SlDev d, double* out) {
@@ -485,8 +510,18 @@ __global__ void k_split_all(SlDev d, int only_if_rebuild) {
 
 // Allow the sweep's dynamic shared memory (above the 48 KB default).
 int sl_prepare_kernels() {
-  return cudaFuncSetAttribute(k_sweep_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sweep_smem_bytes(true)) == cudaSuccess ? SL_OK : SL_ERR_CUDA;
+  bool ok = true;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<32, 192>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 32)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<32, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 32)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 16)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<16, 192>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 16)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<8, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 8)) == cudaSuccess;
+  return ok ? SL_OK : SL_ERR_CUDA;
 }
 
 int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild) {
@@ -496,9 +531,8 @@ int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild) {
 
 // Exchange table and forces at the current state (after init/rebuild/set_state).
 int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick) {
-  int gn = grid_for(d.n);
-  k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
-  k_force<<<gn, SL_BLOCK, 0, st>>>(d, kick);
+  k_jtable<<<grid_tb(d), tb(d), 0, st>>>(d);
+  k_force<<<grid_tb(d), tb(d), 0, st>>>(d, kick);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 
@@ -555,13 +589,12 @@ static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark
 
 int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels) {
   if (d.ham == SL_HAM_LEARNED) return launch_step_learned(d, st, mark, user, kernels);
-  int gn = grid_for(d.n);
   const int lat = !d.fix_lattice;
   int nk = 0;
   auto phase = [&](int ph, int end) { if (mark) mark(user, ph, end, st); };
   if (lat) {
     phase(SL_PHASE_KICK, 0);
-    k_kick<<<gn, SL_BLOCK, 0, st>>>(d, 0.5 * d.dt);
+    k_kick<<<grid_tb(d), tb(d), 0, st>>>(d, 0.5 * d.dt);
     phase(SL_PHASE_KICK, 1);
     nk += 1;
   }
@@ -571,13 +604,13 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
   nk += 16;
   if (lat) {
     phase(SL_PHASE_DRIFT, 0);
-    k_drift<<<gn, SL_BLOCK, 0, st>>>(d);
+    k_drift<<<grid_tb(d), tb(d), 0, st>>>(d);
     k_decide<<<1, 1, 0, st>>>(d);
     int e = sl_launch_rebuild(d, st);
     if (e) return e;
     phase(SL_PHASE_DRIFT, 1);
     phase(SL_PHASE_JTABLE, 0);
-    k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
+    k_jtable<<<grid_tb(d), tb(d), 0, st>>>(d);
     phase(SL_PHASE_JTABLE, 1);
     nk += 2 + SL_REBUILD_KERNELS + 1;
   }
@@ -587,7 +620,7 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
   nk += 16;
   if (lat) {
     phase(SL_PHASE_FORCE, 0);
-    k_force<<<gn, SL_BLOCK, 0, st>>>(d, 1);
+    k_force<<<grid_tb(d), tb(d), 0, st>>>(d, 1);
     phase(SL_PHASE_FORCE, 1);
     nk += 1;
   }

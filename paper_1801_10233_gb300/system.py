@@ -170,6 +170,22 @@ class System:
         return dict(order=o.cpu().numpy(), colour_start=np.array(cs[:], dtype=np.int32),
                     nsec=np.array(ns[:], dtype=np.int32))
 
+    # -- launch shapes -------------------------------------------------------
+    def autotune(self, steps: int = 3):
+        """Time every launch shape on this system's own state (restored
+        afterwards) and keep the fastest.  Returns dict(variant, block,
+        ns_per_step, default_ns_per_step, candidates, sectors_per_block)."""
+        scratch = torch.empty(self._ws_bytes, dtype=torch.uint8, device=self.device)
+        out = (ctypes.c_int64 * 8)()
+        self.stream.synchronize()
+        check(self._L.sl_autotune(self._h, scratch.data_ptr(), self._ws_bytes, int(steps), out), "sl_autotune")
+        del scratch
+        return dict(variant=int(out[0]), block=int(out[1]), ns_per_step=int(out[2]),
+                    default_ns_per_step=int(out[3]), candidates=int(out[4]), sectors_per_block=int(out[5]))
+
+    def set_launch_shape(self, variant: int, block: int):
+        check(self._L.sl_set_launch_shape(self._h, int(variant), int(block)), "sl_set_launch_shape")
+
     # -- learned Hamiltonian -----------------------------------------------
     def ml_set_model(self, params, norm):
         """Install the network (float32 params [SL_ML_NPARAM], norm [SL_ML_NNORM])."""
