@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the extra per-form measurements")
     ap.add_argument("--no-learned", action="store_true", help="skip training and judging the learned Hamiltonian")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--launch-shape", default=None, help="VARIANT,BLOCK: set the headline's launch shape "
+                    "instead of autotuning it (to profile a known shape)")
     ap.add_argument("--learned-frames", type=int, default=20000, help="training snapshots (10^3-cell frames)")
     ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--learned-steps", type=int, default=500, help="judged steps on 40^3 cells")
@@ -286,7 +288,12 @@ def run_ours(args):
     p0 = p[0] if isinstance(p, list) else p
     stream = sysm.stream
     # launch shapes from the autotuner (state restored bitwise, outside the timed region)
-    tune = None if args.no_autotune else sysm.autotune(3)
+    if args.launch_shape:
+        sv, sb = (int(x) for x in args.launch_shape.split(","))
+        sysm.set_launch_shape(sv, sb)
+        tune = {"variant": sv, "block": sb, "set_by": "--launch-shape"}
+    else:
+        tune = None if args.no_autotune else sysm.autotune(3)
     sysm.step(args.warmup)
     torch.cuda.synchronize()
 
