@@ -274,12 +274,20 @@ def main(argv=None):
     ap.add_argument("--workload", default="fe_bcc_40x40x40_nve", choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--judge-steps", type=int, default=0)
+    ap.add_argument("--save-model", default=None, help="write params and norm to this .npz")
+    ap.add_argument("--load-model", default=None, help="skip training: params and norm from this .npz")
     args = ap.parse_args(argv)
     from . import build
     build.build()
-    plist, data = training_set(n_frames=args.frames)
-    params, norm, losses, secs = train_model(plist, data, epochs=args.epochs)
-    del data
+    if args.load_model:
+        m = np.load(args.load_model)
+        params, norm, secs, losses = m["params"], m["norm"], 0.0, [np.full(4, np.nan)]
+    else:
+        plist, data = training_set(n_frames=args.frames)
+        params, norm, losses, secs = train_model(plist, data, epochs=args.epochs)
+        del data
+        if args.save_model:
+            np.savez(args.save_model, params=params, norm=norm)
     p, r, v, s = inputs.workload(args.workload)
     sysm = learned_system(learned_params(p), r, v, s, norm, params)
     sysm.step(3)
