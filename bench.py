@@ -91,6 +91,23 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x, world, device):
+    """The largest of every rank's value x (float), all ranks receive it."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(atoms_per_rank, world, steps, seconds):
+    """Atom-steps per second of the whole job: every rank advanced
+    atoms_per_rank atoms by `steps` steps; `seconds` is the slowest rank's time."""
+    return world * atoms_per_rank * steps / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples during the timed region."""
 
@@ -311,12 +328,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = whole_job_rate(n, world, args.steps, ms * 1e-3)
     counters = sysm.counters()
     launches = counters["kernels_per_step"] * args.steps
 
@@ -355,12 +368,9 @@ def run_ours(args):
         sysm.state_host(hr, hv, hs)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * n * esteps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 3 * n * 3 * 8,
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e = {"value": whole_job_rate(n, world, esteps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 3 * n * 3 * 8,
            "d2h_bytes_per_step": 3 * n * 3 * 8, "steps": esteps}
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * n * esteps / float(t.item())
 
     forms = None
     if rank == 0 and world == 1 and not args.no_forms and args.workload == DEFAULT_WORKLOAD:
