@@ -99,6 +99,10 @@ def lib():
                                   _c_double_p, _c_double_p]
         L.orc_ml_adam.argtypes = [ctypes.c_int, _f_p, _c_double_p, _c_double_p, _c_double_p, ctypes.c_int,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.orc_ml_eval_sample.restype = ctypes.c_int
+        L.orc_ml_eval_sample.argtypes = [ctypes.c_int, _c_double_p, _c_double_p, _c_double_p, _f_p, _f_p,
+                                         ctypes.c_int, _c_int_p, _c_double_p, _c_double_p, _c_double_p,
+                                         _c_double_p]
         L.orc_bf16_value.restype = ctypes.c_double
         L.orc_bf16_value.argtypes = [ctypes.c_float]
         L.orc_params_size.restype = ctypes.c_int
@@ -355,3 +359,21 @@ def ml_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     g = np.ascontiguousarray(grad, dtype=np.float64)
     L.orc_ml_adam(params.size, _fp(params), _dp(g), _dp(m), _dp(v), int(t), float(lr), float(beta1),
                   float(beta2), float(eps))
+
+
+def ml_eval_sample(r, s, box, params, norm, idx):
+    """E_i, F_i, B_i, D_i of the sampled atoms idx of a (large) frame, each from
+    scratch by scans over all atoms.  Returns dict(e_atom, F, B, D)."""
+    L = lib()
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    s = np.ascontiguousarray(s, dtype=np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, dtype=np.float64).reshape(3)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    m = len(idx)
+    pa, no = _f32(params, ML_NPARAM), _f32(norm, ML_NNORM)
+    e = np.empty(m); F = np.empty((m, 3)); B = np.empty((m, 3)); D = np.empty((m, ML_NF))
+    rc = L.orc_ml_eval_sample(r.shape[0], _dp(r), _dp(s), _dp(box), _fp(pa), _fp(no), m, _ip(idx), _dp(e), _dp(F),
+                              _dp(B), _dp(D))
+    if rc:
+        raise OracleError(rc)
+    return dict(e_atom=e, F=F, B=B, D=D)

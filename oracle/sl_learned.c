@@ -463,3 +463,102 @@ void orc_ml_adam(int np, float* params, const double* grad, double* mom1, double
     params[i] = (float)((double)params[i] - lr * mh / (sqrt(vh) + eps));
   }
 }
+
+/* ------------------------------------------------------------------ */
+/* Sampled atoms of a large frame, one by one                          */
+/* ------------------------------------------------------------------ */
+/* Neighbours of atom a with r < ML_RC, by a scan over all n atoms. */
+static int scan_neighbours(int n, const double* r, const double box[3], int a, int* out, int cap) {
+  int cnt = 0;
+  for (int j = 0; j < n; ++j) {
+    if (j == a) continue;
+    double d[3];
+    sep(r, box, a, j, d);
+    if (dot3(d, d) < ML_RC * ML_RC) {
+      if (cnt < cap) out[cnt] = j;
+      ++cnt;
+    }
+  }
+  return cnt;
+}
+
+/* D and G of atom a from a scanned neighbour list. */
+static void atom_DG(int n, const double* r, const double* s, const double box[3], const orc_ml_model* m, int a,
+                    double D[ML_NF], double G[ML_NF], double* e) {
+  int nb[512];
+  int cnt = scan_neighbours(n, r, box, a, nb, 512);
+  int off[2] = {0, cnt < 512 ? cnt : 512};
+  /* descriptor() indexes off[i], off[i+1] with i = the atom: use a local list */
+  memset(D, 0, ML_NF * sizeof(double));
+  for (int k = 0; k < off[1]; ++k) {
+    int j = nb[k];
+    double d[3], g[ML_NK];
+    sep(r, box, a, j, d);
+    double rr = sqrt(dot3(d, d));
+    if (!(rr < ML_RC)) continue;
+    double c = dot3(s + 3 * a, s + 3 * j);
+    basis(rr, g, NULL);
+    for (int q = 0; q < ML_NK; ++q) {
+      D[3 * q] += g[q];
+      D[3 * q + 1] += g[q] * c;
+      D[3 * q + 2] += g[q] * c * c;
+    }
+  }
+  double x[ML_NF], gx[ML_NF];
+  act_t A;
+  normalise(m, D, x);
+  double ea = net_forward(m, x, &A);
+  if (e) *e = ea;
+  net_backward(m, &A, gx);
+  for (int f = 0; f < ML_NF; ++f) G[f] = gx[f] * m->istd[f];
+}
+
+/* For each sampled atom idx[q]: E_i, F_i (eV/A), B_i = -dE/ds_i (eV) and
+ * D_i, computed from scratch (every neighbourhood by a scan over all atoms).
+ * Returns -1 if an atom has more than 511 neighbours, else 0. */
+int orc_ml_eval_sample(int n, const double* r, const double* s, const double box[3], const float* params,
+                       const float* norm, int nsample, const int* idx, double* e_out, double* F_out,
+                       double* B_out, double* D_out) {
+  orc_ml_model* m = (orc_ml_model*)malloc(sizeof(orc_ml_model));
+  if (!m) return -1;
+  orc_ml_load(params, norm, m);
+  int rc = 0;
+  for (int q = 0; q < nsample && !rc; ++q) {
+    int i = idx[q];
+    int nb[512];
+    int cnt = scan_neighbours(n, r, box, i, nb, 512);
+    if (cnt > 511) { rc = -1; break; }
+    double Di[ML_NF], Gi[ML_NF], Dj[ML_NF], Gj[ML_NF], ei;
+    atom_DG(n, r, s, box, m, i, Di, Gi, &ei);
+    double f3[3] = {0, 0, 0}, b3[3] = {0, 0, 0};
+    const double* si = s + 3 * i;
+    for (int k = 0; k < cnt; ++k) {
+      int j = nb[k];
+      double d[3], g[ML_NK], dg[ML_NK];
+      sep(r, box, i, j, d);
+      double rr = sqrt(dot3(d, d));
+      atom_DG(n, r, s, box, m, j, Dj, Gj, NULL);
+      const double* sj = s + 3 * j;
+      double c = dot3(si, sj);
+      basis(rr, g, dg);
+      double phi = 0.0, pp = 0.0, qq = 0.0;
+      for (int t = 0; t < ML_NK; ++t) {
+        double s0 = Gi[3 * t] + Gj[3 * t], s1 = Gi[3 * t + 1] + Gj[3 * t + 1], s2 = Gi[3 * t + 2] + Gj[3 * t + 2];
+        phi += (s0 + s1 * c + s2 * c * c) * dg[t];
+        pp += s1 * g[t];
+        qq += s2 * g[t];
+      }
+      for (int a = 0; a < 3; ++a) f3[a] += phi * d[a] / rr;
+      double psi = pp + 2.0 * qq * c;
+      for (int a = 0; a < 3; ++a) b3[a] -= psi * sj[a];
+    }
+    if (e_out) e_out[q] = ei;
+    for (int a = 0; a < 3; ++a) {
+      if (F_out) F_out[3 * q + a] = f3[a];
+      if (B_out) B_out[3 * q + a] = b3[a];
+    }
+    if (D_out) memcpy(D_out + (size_t)q * ML_NF, Di, ML_NF * sizeof(double));
+  }
+  free(m);
+  return rc;
+}

@@ -309,3 +309,28 @@ def test_learned_spin_energy_error_is_second_order(lib):
         dev.append(ex)
         sysm.close()
     assert dev[0] / dev[1] > 3.0, dev
+
+
+@pytest.mark.parametrize("name", ["fe_bcc_40x40x40_nve", "fe_bcc_100x100x100_nve"])
+def test_full_size_sampled_atoms_match_oracle(lib, name):
+    """The learned workloads at full size, in the benchmark's configuration:
+    descriptors, forces and fields of sampled atoms against the oracle's
+    atom-by-atom evaluation."""
+    p, r, v, s = inputs.workload(name)
+    box = np.array(p["box"])
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(p["n_atoms"], 6, replace=False))
+    # normalisation from a cheap 6^3-cell frame of the same recipe
+    p6, r6, v6, s6 = inputs.bcc_fe_system(6, 9, T=300.0, spins="uniform")
+    norm = fitted_norm(r6, s6, np.array(p6["box"]))
+    par = inputs.ml_init_params(31, e0=-4.0)
+    sysm = lib.learned_system(lib.learned_params(p), r, v, s, norm, par)
+    e, F, B, D = sysm.ml_eval(want_D=True)
+    ref = oracle.ml_eval_sample(r, s, box, par, norm, idx)
+    Fg, Bg, Dg = F.cpu().numpy()[idx], B.cpu().numpy()[idx], D.cpu().numpy()[idx]
+    close(Dg, ref["D"], what="descriptors")
+    close(Fg, ref["F"], what="forces")
+    close(Bg, ref["B"], what="fields")
+    sysm.step(2)
+    assert sysm.ml_gate()[2] == 0
+    sysm.close()

@@ -362,3 +362,13 @@ def test_learned_spin_energy_error_is_second_order_in_dt(sys5):
             ex = max(ex, abs(o.energy()[4] - e0) / n)
         dev.append(ex)
     assert dev[0] / dev[1] > 3.0, dev
+
+
+def test_sampled_evaluation_equals_full_evaluation(sys5):
+    p, r, v, s, box, norm = sys5
+    par = model()
+    full = oracle.ml_eval(r, s, box, par, norm)
+    idx = [0, 17, 101, 249]
+    smp = oracle.ml_eval_sample(r, s, box, par, norm, idx)
+    for k in ("e_atom", "F", "B", "D"):
+        np.testing.assert_allclose(smp[k], full[k][idx], rtol=1e-13, atol=1e-13)
