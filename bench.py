@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--learned-frames", type=int, default=20000, help="training snapshots (10^3-cell frames)")
     ap.add_argument("--learned-epochs", type=int, default=4)
     ap.add_argument("--learned-steps", type=int, default=500, help="judged steps on 40^3 cells")
-    ap.add_argument("--learned-big-steps", type=int, default=100, help="judged steps on 100^3 cells")
+    ap.add_argument("--learned-big-steps", type=int, default=1000, help="judged steps on 100^3 cells")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -257,7 +257,7 @@ def learned_forms(args, dev, torch):
     del data
     torch.cuda.empty_cache()
     for name, steps, every in (("fe_bcc_40x40x40_nve", args.learned_steps, 50),
-                               ("fe_bcc_100x100x100_nve", args.learned_big_steps, 25)):
+                               ("fe_bcc_100x100x100_nve", args.learned_big_steps, 100)):
         if steps <= 0:
             continue
         p, r, v, s = inputs.workload(name)
