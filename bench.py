@@ -37,7 +37,10 @@ SAMPLE_CELLS = 16
 
 # Algorithmic FP64 work per atom and step of each phase, counting add, mul
 # and fma-halves as 1, a square root or division as 10 and an exponential,
-# sine or cosine as 20 (bcc at 6 A: 64 Morse pairs, 14 exchange pairs).
+# sine or cosine as 20.  Pair terms count each unordered pair once (bcc at
+# 6 A: 32 Morse pairs and 7 exchange pairs per atom), although the kernels
+# evaluate every pair from both atoms (deterministic per-atom sums without
+# atomics); the spin sweep needs all 14 exchange neighbours per update.
 MORSE_PAIR_FLOPS = 3 + 5 + 10 + 2 + 20 + 3 + 10 + 6      # dr, r^2, sqrt, arg, exp, V'/r, accumulate
 EXCH_FORCE_FLOPS = 5 + 6                                # s_i.s_j, accumulate
 JTABLE_PAIR_FLOPS = 3 + 5 + 2 + 20 + 6                  # dr, r^2, x, exp, J
@@ -47,9 +50,9 @@ PHASE_FLOPS_PER_ATOM = {
     "kick": 6,
     "spin_half_op_1": 2 * ROTATION_FLOPS,
     "drift_rebuild": 6 + 8,
-    "exchange_table": 14 * JTABLE_PAIR_FLOPS,
+    "exchange_table": 7 * JTABLE_PAIR_FLOPS,
     "spin_half_op_2": 2 * ROTATION_FLOPS,
-    "force_kick": 64 * MORSE_PAIR_FLOPS + 14 * (20 + EXCH_DJ_FLOPS + EXCH_FORCE_FLOPS) + 6,
+    "force_kick": 32 * MORSE_PAIR_FLOPS + 7 * (20 + EXCH_DJ_FLOPS + EXCH_FORCE_FLOPS) + 6,
 }
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 pipe, nominal at 2070 MHz
 # The kernels run the FP64-accurate arithmetic as double-float on the FP32
