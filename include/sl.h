@@ -93,9 +93,16 @@ typedef struct sl_params {
   double skin_A;               /* Verlet skin, also widens the sectors */
   double lambda;               /* transverse damping of Eq. sLLG (0: none) */
   double temperature_K;        /* spin bath temperature (0: no noise) */
-  uint64_t seed;               /* Philox4x32-10 key for the spin noise */
+  uint64_t seed;               /* Philox4x32-10 key for the spin and lattice noise */
   int32_t replica;             /* replica index, part of the noise counter */
   int32_t reserved1;
+  double lattice_gamma_ps;     /* lattice bath damping rate gamma_L/m of Eq. p_advance_T
+                                  (Sec. 4.2), 1/ps (0: NVE lattice) */
+  double lattice_temperature_K;/* lattice bath temperature (noise D_L = 2 m gamma_L/m k_B T,
+                                  the Einstein relation); the bath is the exact
+                                  Ornstein-Uhlenbeck flow of the velocities over dt/2 at
+                                  both ends of the step (before the first half-kick, after
+                                  the closing one), noise counter sub-passes 4 and 5 */
 } sl_params;
 
 typedef struct sl_ctx sl_ctx;  /* opaque, owned by the library */
@@ -120,9 +127,9 @@ int sl_init(const sl_params* params, const double* r, const double* v, const dou
 
 /* Batches: n_replicas independent systems advanced together, for instance
  * replicas of different sizes at different bath temperatures.  params[k]
- * describes replica k; replicas may differ in n_atoms, box, temperature_K
- * and replica (the noise counter word), and every other field must equal
- * params[0]'s (SL_ERR_ARG otherwise).  r, v, s (device) hold all replicas'
+ * describes replica k; replicas may differ in n_atoms, box, temperature_K,
+ * lattice_gamma_ps, lattice_temperature_K and replica (the noise counter
+ * word), and every other field must equal params[0]'s (SL_ERR_ARG otherwise).  r, v, s (device) hold all replicas'
  * atoms back to back in replica order, [sum n_atoms][3] doubles.  Each colour
  * pass of a step covers the sectors of every replica, so one step advances
  * the whole batch.  sl_workspace_bytes and sl_init are the n_replicas = 1

@@ -46,6 +46,7 @@ class _Params(ctypes.Structure):
         ("m_rc", ctypes.c_double), ("skin", ctypes.c_double),
         ("lam", ctypes.c_double), ("temperature", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32), ("hamiltonian", ctypes.c_int32),
+        ("lat_gamma", ctypes.c_double), ("lat_temperature", ctypes.c_double),
     ]
 
 
@@ -159,6 +160,8 @@ def make_params(p: dict, brute_force=False, lam=0.0, temperature=0.0, seed=0, re
     q.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     q.replica = int(replica)
     q.hamiltonian = int(p.get("hamiltonian", 0))
+    q.lat_gamma = float(p.get("lattice_gamma_ps", 0.0))
+    q.lat_temperature = float(p.get("lattice_temperature_K", 0.0))
     return q
 
 

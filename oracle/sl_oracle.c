@@ -26,7 +26,12 @@
  *   Single spin   exact rotation of s about omega by |omega| tau (default) or
  *                 the Cayley-type propagator printed in Sec. 3 (mode 1).
  *   Thermostat    stochastic precession vector of Eq. sLLG (Sec. 4.1) with
- *                 noise variance 2 D_S / tau per component.
+ *                 noise variance 2 D_S / tau per component; lattice bath of
+ *                 Eq. p_advance_T (Sec. 4.2): friction -(gamma_L/m) p and a
+ *                 white-noise force of strength D_L = 2 m (gamma_L/m) k_B T
+ *                 (Einstein relation), integrated as the exact
+ *                 Ornstein-Uhlenbeck flow over dt/2 at both ends of the step
+ *                 (O B S R S B O).
  *   Observables   kinetic, Morse, exchange, Zeeman energies; T_L
  *                 (Eq. lattice_temperature), T_S (Eq. spin_temperature),
  *                 magnetisation M = (1/N) sum_i s_i.
@@ -97,6 +102,8 @@ typedef struct {
   uint64_t seed;
   int32_t replica;
   int32_t hamiltonian;   /* 0 analytic (Morse + Bethe-Slater), 1 learned */
+  double lat_gamma;      /* lattice damping rate gamma_L/m of Eq. p_advance_T, 1/ps (0: none) */
+  double lat_temperature;/* lattice bath temperature, K */
 } orc_params;
 
 typedef struct {
@@ -615,6 +622,21 @@ static void kick(orc_state* st, double h) {
   for (int k = 0; k < 3 * st->n; ++k) st->v[k] += c * st->F[k];
 }
 
+/* Exact flow of the lattice bath over time |h| (Eq. p_advance_T without the
+ * conservative force): v <- v e^{-g|h|} + sqrt((1 - e^{-2g|h|}) k_B T/m) xi,
+ * xi ~ N(0, 1) per component from Philox (seed; atom, step, subpass, replica). */
+static void lattice_bath(orc_state* st, double h, int subpass) {
+  double g = st->p.lat_gamma;
+  if (!(g > 0.0)) return;
+  double c1 = exp(-g * fabs(h));
+  double sig = sqrt((1.0 - c1 * c1) * ORC_KB * st->p.lat_temperature * ORC_FTOA / st->p.mass);
+  for (int i = 0; i < st->n; ++i) {
+    double xi[3] = {0.0, 0.0, 0.0};
+    if (st->p.lat_temperature > 0.0) orc_gauss3(st->p.seed, st->p.replica, st->step, subpass, i, xi);
+    for (int a = 0; a < 3; ++a) st->v[3 * i + a] = c1 * st->v[3 * i + a] + sig * xi[a];
+  }
+}
+
 static double max_disp2(const orc_state* st) {
   double m = 0.0;
   for (int i = 0; i < st->n; ++i) {
@@ -646,7 +668,7 @@ int orc_params_size(void) { return (int)sizeof(orc_params); }
 orc_state* orc_create(const orc_params* p, const double* r, const double* v, const double* s, int* err) {
   *err = ORC_OK;
   if (!p || p->n_atoms < 0 || p->mass <= 0.0 || p->hamiltonian < 0 || p->hamiltonian > 1 ||
-      (p->hamiltonian == 1 && p->rotation != 0)) {
+      (p->hamiltonian == 1 && p->rotation != 0) || !(p->lat_gamma >= 0.0) || !(p->lat_temperature >= 0.0)) {
     *err = ORC_ERR_ARG;
     return NULL;
   }
@@ -709,7 +731,10 @@ int orc_step(orc_state* st, int nsteps) {
   for (int it = 0; it < nsteps; ++it) {
     double dt = st->p.dt;
     int lat = !st->p.fix_lattice;
-    if (lat) kick(st, 0.5 * dt);
+    if (lat) {
+      lattice_bath(st, 0.5 * dt, 4);
+      kick(st, 0.5 * dt);
+    }
     spin_half_op(st, 0.5 * dt, 0);
     if (lat) {
       for (int k = 0; k < 3 * st->n; ++k) st->r[k] += dt * st->v[k];
@@ -733,6 +758,7 @@ int orc_step(orc_state* st, int nsteps) {
     if (lat) {
       compute_forces(st);
       kick(st, 0.5 * dt);
+      lattice_bath(st, 0.5 * dt, 5);
     }
     st->step += 1;
   }

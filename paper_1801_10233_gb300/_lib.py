@@ -53,6 +53,7 @@ class sl_params(ctypes.Structure):
         ("morse_rc_A", ctypes.c_double), ("skin_A", ctypes.c_double),
         ("lambda_", ctypes.c_double), ("temperature_K", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("lattice_gamma_ps", ctypes.c_double), ("lattice_temperature_K", ctypes.c_double),
     ]
 
 
@@ -155,6 +156,8 @@ def make_params(p: dict) -> sl_params:
     q.seed = int(p.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
     q.replica = int(p.get("replica", 0))
     q.hamiltonian = int(p.get("hamiltonian", 0))
+    q.lattice_gamma_ps = float(p.get("lattice_gamma_ps", 0.0))
+    q.lattice_temperature_K = float(p.get("lattice_temperature_K", 0.0))
     return q
 
 

@@ -30,6 +30,7 @@ struct sl_ctx {
   // learned Hamiltonian
   void* ws_base;            // the caller's workspace (all device state of the context)
   size_t ws_bytes;
+  std::vector<double> lat_gamma, lat_temp;   // per-replica lattice bath (for sl_set_dt)
   int ml_ready;             // a model has been set
   int ml_stale;             // parameters changed since the last evaluation point
   long long ml_t;           // Adam steps taken
@@ -74,6 +75,7 @@ int validate(const sl_params* p) {
   if (p->rebuild_every < 0 || p->max_ex_neighbors < 0 || p->max_morse_neighbors < 0) return SL_ERR_ARG;
   if (p->max_ex_neighbors > SL_MAX_EX_CAP) return SL_ERR_ARG;
   if (!(p->lambda >= 0.0) || !(p->temperature_K >= 0.0)) return SL_ERR_ARG;
+  if (!(p->lattice_gamma_ps >= 0.0) || !(p->lattice_temperature_K >= 0.0)) return SL_ERR_ARG;
   if (!std::isfinite(p->dt_ps)) return SL_ERR_ARG;
   if (p->hamiltonian != SL_HAM_ANALYTIC && p->hamiltonian != SL_HAM_LEARNED) return SL_ERR_ARG;
   if (p->hamiltonian == SL_HAM_LEARNED && (!(p->morse_rc_A >= SL_ML_RC) || p->lambda != 0.0 ||
@@ -147,11 +149,18 @@ void fill_df_constants(SlDev& d) {
 // Noise amplitude of each replica's spin bath for the current dt: each
 // single-spin factor over tau = dt/4 draws eta ~ N(0, 2 D_S / |tau|) per
 // component, D_S = lambda (1 + lambda^2) k_B T / hbar.
-void fill_noise(std::vector<SlRep>& reps, double lambda, double dt) {
-  for (SlRep& R : reps) {
+void fill_noise(std::vector<SlRep>& reps, const sl_params* ps, double dt) {
+  for (size_t r = 0; r < reps.size(); ++r) {
+    SlRep& R = reps[r];
+    const double lambda = ps[0].lambda;
     double DS = lambda * (1.0 + lambda * lambda) * SL_KB * R.temperature / SL_HBAR;
     R.noise_sig = R.temperature > 0.0 && dt != 0.0 ? split_f2(std::sqrt(2.0 * DS / std::fabs(0.25 * dt)))
                                                    : make_float2(0.0f, 0.0f);
+    // lattice bath (Eq. p_advance_T) over |dt|/2: exact Ornstein-Uhlenbeck flow
+    const double g = ps[r].lattice_gamma_ps, T = ps[r].lattice_temperature_K;
+    R.lat_c1 = g > 0.0 ? std::exp(-g * 0.5 * std::fabs(dt)) : 1.0;
+    R.lat_sig = g > 0.0 && T > 0.0 ? std::sqrt((1.0 - R.lat_c1 * R.lat_c1) * SL_KB * T * SL_FTOA / ps[r].mass_amu)
+                                   : 0.0;
   }
 }
 
@@ -232,7 +241,9 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   d.lam_f = split_f2(p->lambda);
   d.inv1pl2_f = split_f2(1.0 / (1.0 + p->lambda * p->lambda));
   fill_df_constants(d);
-  fill_noise(reps, p->lambda, p->dt_ps);
+  fill_noise(reps, ps, p->dt_ps);
+  for (int r = 0; r < nrep; ++r)
+    if (ps[r].lattice_gamma_ps > 0.0) d.any_lattice_bath = 1;
 
   Layout L;
   size_t nn = (size_t)n;
@@ -475,6 +486,10 @@ int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, 
   c->nrep = n_replicas;
   c->ws_base = workspace;
   c->ws_bytes = need;
+  for (int r = 0; r < n_replicas; ++r) {
+    c->lat_gamma.push_back(params[r].lattice_gamma_ps);
+    c->lat_temp.push_back(params[r].lattice_temperature_K);
+  }
   plan(params, n_replicas, c->d, c->reps, (char*)workspace);
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SL_ERR_CUDA; }
@@ -563,8 +578,14 @@ int sl_set_dt(sl_ctx* c, double dt) {
   c->p.dt_ps = dt;
   c->d.dt = dt;
   fill_df_constants(c->d);
-  if (c->d.any_noise) {
-    fill_noise(c->reps, c->p.lambda, dt);
+  if (c->d.any_noise || c->d.any_lattice_bath) {
+    std::vector<sl_params> ps(c->nrep, c->p);
+    for (int r = 0; r < c->nrep; ++r) {
+      ps[r].lattice_gamma_ps = c->lat_gamma[r];
+      ps[r].lattice_temperature_K = c->lat_temp[r];
+      ps[r].mass_amu = c->p.mass_amu;
+    }
+    fill_noise(c->reps, ps.data(), dt);
     if (cudaMemcpyAsync((void*)c->d.reps, c->reps.data(), sizeof(SlRep) * c->nrep, cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)

@@ -46,6 +46,7 @@ struct SlRep {
   int replica;              // Philox counter word of the spin noise
   double temperature;       // spin bath temperature (K)
   float2 noise_sig;         // sqrt(2 D_S / |dt/4|) as (hi, lo), D_S = lambda (1 + lambda^2) k_B T / hbar
+  double lat_c1, lat_sig;   // lattice bath over dt/2: v <- c1 v + sig xi (c1 = 1, sig = 0: none)
 };
 
 // Everything a kernel needs, passed by value.  Scalars used by the
@@ -69,6 +70,7 @@ struct SlDev {
   double half_skin2;
   double lambda;
   int any_noise;            // some replica has a bath temperature
+  int any_lattice_bath;     // some replica has a lattice bath
   uint64_t seed;
   int ham;                  // SL_HAM_ANALYTIC or SL_HAM_LEARNED
   int tune_sweep;           // colour-pass tile shape variant (0 .. SL_SWEEP_VARIANTS-1)

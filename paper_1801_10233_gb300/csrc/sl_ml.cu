@@ -407,6 +407,7 @@ __global__ void __launch_bounds__(128) k_ml_pair(SlDev d, int fmode, int force, 
       const double cc = 0.5 * d.dt * d.acc;
       double4_32a v = d.v[i];
       v.x = fma(cc, (double)fx, v.x); v.y = fma(cc, (double)fy, v.y); v.z = fma(cc, (double)fz, v.z);
+      if (d.any_lattice_bath) v = lattice_bath(d, i, v, 5);
       d.v[i] = v;
     }
   }

@@ -141,6 +141,24 @@ __device__ __forceinline__ df3 gauss3_df(uint64_t seed, int replica, long long s
   return g;
 }
 
+// Lattice bath over |dt|/2 (Eq. p_advance_T without the conservative force),
+// the exact Ornstein-Uhlenbeck flow v <- c1 v + sig xi, xi ~ N(0, 1) per
+// component from Philox (seed; atom id within its replica, step, sub-pass,
+// replica); sub-pass 4 before the first half-kick, 5 after the closing one.
+__device__ __forceinline__ double4_32a lattice_bath(const SlDev& d, int i, double4_32a v, int subpass) {
+  const SlRep& R = d.reps[__ldg(d.arep + i)];
+  if (R.lat_c1 == 1.0 && R.lat_sig == 0.0) return v;
+  double xi[3] = {0.0, 0.0, 0.0};
+  if (R.lat_sig > 0.0) {
+    const df3 g = gauss3_df(d.seed, R.replica, d.ctrl->step, subpass, d.perm[i] - R.atom0);
+    xi[0] = df_to_double(g.x); xi[1] = df_to_double(g.y); xi[2] = df_to_double(g.z);
+  }
+  v.x = R.lat_c1 * v.x + R.lat_sig * xi[0];
+  v.y = R.lat_c1 * v.y + R.lat_sig * xi[1];
+  v.z = R.lat_c1 * v.z + R.lat_sig * xi[2];
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // Single-spin propagator e^{L_si tau} as an increment of s:
 //   s' - s = -u B s + tau A (w x s) + tau^2 B (w.s) w,      u = tau^2 |w|^2.

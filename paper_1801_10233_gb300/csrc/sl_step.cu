@@ -289,6 +289,7 @@ __global__ void k_kick(SlDev d, double h) {
   if (k >= d.n) return;
   double c = h * d.acc;
   double4_32a v = d.v[k], F = d.F[k];
+  if (d.any_lattice_bath) v = lattice_bath(d, k, v, 4);
   v.x = fma(c, F.x, v.x); v.y = fma(c, F.y, v.y); v.z = fma(c, F.z, v.z);
   d.v[k] = v;
 }
@@ -434,6 +435,7 @@ __global__ void k_force(SlDev d, int kick) {
     double c = 0.5 * d.dt * d.acc;
     double4_32a v = d.v[i];
     v.x = fma(c, fx, v.x); v.y = fma(c, fy, v.y); v.z = fma(c, fz, v.z);
+    if (d.any_lattice_bath) v = lattice_bath(d, i, v, 5);
     d.v[i] = v;
   }
 }

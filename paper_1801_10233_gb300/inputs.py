@@ -47,6 +47,8 @@ def fe_params(box, n_atoms, **overrides):
         rebuild_every=0,
         morse_shift_energy=1,
         hamiltonian=0,
+        lattice_gamma_ps=0.0,
+        lattice_temperature_K=0.0,
     )
     for k, v in overrides.items():
         if k not in p:

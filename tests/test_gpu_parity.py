@@ -113,6 +113,46 @@ def test_langevin_parity(System):
     assert_state_parity(gpu, ref, p)
 
 
+def test_lattice_and_spin_bath_parity(System):
+    """Both baths on (Eq. p_advance_T and Eq. s_advance_T): the lattice
+    noise draws sub-passes 4 and 5 of the same Philox counters."""
+    import oracle
+    p, r, v, s = inputs.bcc_fe_system(6, 13, T=300.0)
+    p = dict(p, **{"lambda": 0.05, "temperature_K": 400.0, "seed": 987654321, "replica": 2,
+                   "lattice_gamma_ps": 3.0, "lattice_temperature_K": 700.0})
+    gpu = System(p, r, v, s)
+    ref = oracle.Oracle(p, r, v, s, lam=0.05, temperature=400.0, seed=987654321, replica=2)
+    gpu.step(10)
+    ref.step(10)
+    assert_state_parity(gpu, ref, p)
+
+
+def test_lattice_bath_batch_parity(System):
+    """Replicas with different lattice-bath temperatures and damping."""
+    import oracle
+    plist, rs, vs, ss = [], [], [], []
+    for k, (cells, T, g) in enumerate([(6, 100.0, 1.0), (7, 900.0, 8.0)]):
+        p, r, v, s = inputs.bcc_fe_system(cells, 40 + k, T=300.0)
+        p = dict(p, **{"seed": 55, "replica": k, "lattice_gamma_ps": g, "lattice_temperature_K": T})
+        plist.append(p); rs.append(r); vs.append(v); ss.append(s)
+    gpu = System(plist, np.concatenate(rs), np.concatenate(vs), np.concatenate(ss))
+    gpu.step(8)
+    rg, vg, sg = (x.cpu().numpy() for x in gpu.state())
+    a0 = 0
+    for k, p in enumerate(plist):
+        n = p["n_atoms"]
+        ref = oracle.Oracle(p, rs[k], vs[k], ss[k], seed=55, replica=k)
+        ref.step(8)
+        ro, vo, so = ref.state()
+        L = np.array(p["box"])
+        dr = rg[a0:a0 + n] - ro
+        dr -= L * np.round(dr / L)
+        assert np.abs(dr).max() <= 1e-12 * L.max()
+        assert np.abs(vg[a0:a0 + n] - vo).max() <= 1e-12 * np.abs(vo).max()
+        assert np.abs(sg[a0:a0 + n] - so).max() <= 1e-12
+        a0 += n
+
+
 def test_displacement_trigger_parity(System):
     import oracle
     p, r, v, s = inputs.bcc_fe_system(6, 12, T=200.0)

@@ -455,3 +455,45 @@ def test_spin_temperature_closed_form(orc):
     ref = HBAR * w * math.sin(th) ** 2 / (2 * KB * math.cos(th))
     assert abs(e[6] - ref) < 1e-10 * ref
     assert abs(e[3] + n * 2.2 * MUB * 3.0 * math.cos(th)) < 1e-12 * n
+
+
+# ---------------------------------------------------------------------------
+# Lattice bath (Eq. p_advance_T, Sec. 4.2)
+# ---------------------------------------------------------------------------
+def _free_atoms(ncells, gen_seed, **kw):
+    """Atoms without forces (D0 = 0, J = 0): only the bath moves the velocities."""
+    p, r, v, s = inputs.bcc_fe_system(ncells, gen_seed, T=300.0, sigma=0.02, spins="uniform",
+                                      morse_D0_eV=0.0, ex_alpha_eV=0.0, **kw)
+    return p, r, v, s
+
+
+def test_lattice_bath_at_zero_temperature_is_exact_decay(orc):
+    g, n = 7.0, 40
+    p, r, v, s = _free_atoms(5, 3, lattice_gamma_ps=g, lattice_temperature_K=0.0, rebuild_every=10)
+    o = orc.Oracle(p, r, v, s)
+    o.step(n)
+    r1, v1, _ = o.state()
+    dt = p["dt_ps"]
+    np.testing.assert_allclose(v1, v * math.exp(-g * n * dt), rtol=1e-13, atol=1e-13)
+    # the drift sees v after the first O(dt/2) of each step: r_n = r_0 + dt v_0 sum_k e^{-g (k + 1/2) dt}
+    shift = dt * sum(math.exp(-g * (k + 0.5) * dt) for k in range(n))
+    L = np.array(p["box"])
+    dr = r1 - (r + shift * v)
+    dr -= L * np.round(dr / L)
+    assert np.abs(dr).max() < 1e-12
+
+
+def test_lattice_bath_reaches_equipartition(orc):
+    g, T = 40.0, 500.0
+    p, r, v, s = _free_atoms(5, 4, lattice_gamma_ps=g, lattice_temperature_K=T)
+    o = orc.Oracle(p, r, v * 0.0, s, seed=77)
+    kT_m = 8.617333262e-5 * T * 9648.533212 / p["mass_amu"]
+    samples = []
+    o.step(250)                                 # g t = 1: well past the start
+    for _ in range(6):
+        o.step(250)                             # 1/g apart: nearly independent
+        samples.append(o.state()[1].ravel())
+    x = np.concatenate(samples)
+    # exact OU flow: the stationary velocity distribution is N(0, k_B T/m)
+    assert abs(x.mean()) < 5 * math.sqrt(kT_m / x.size)
+    assert x.var() / kT_m == pytest.approx(1.0, abs=5 * math.sqrt(2.0 / x.size) * 2)
