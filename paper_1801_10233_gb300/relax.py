@@ -4,8 +4,11 @@ experiment of Sec. 4.2, on the bcc-Fe / Morse / Bethe-Slater Hamiltonian).
 Run A: the spin bath (Eq. s_advance_T, lambda = 0.01) at T, lattice at rest on
 perfect bcc sites (T_L = 0), spins drawn from a T magnetic equilibrium (a
 spin-only run with the bath on a frozen lattice).  Run B: the lattice bath
-(Eq. p_advance_T) at T, spins all along the field (T_S = 0), velocities from a
-Maxwell-Boltzmann distribution at T.  Each run records T_L and T_S
+(Eq. p_advance_T) at T, spins within 2-degree cones about the field (T_S of a
+few K), velocities from a Maxwell-Boltzmann distribution at T.  (Spins
+exactly along the field would never move: with isotropic exchange and the
+field along z the collinear state feels no torque however the lattice moves;
+the paper's cobalt model breaks that symmetry with spin-orbit terms.)  Each run records T_L and T_S
 (Eqs. lattice_temperature, spin_temperature): the unthermostatted part heats
 up through the spin-lattice coupling.
 
@@ -66,8 +69,8 @@ def run(cells=10, T=300.0, ps=20.0, dt=5e-4, every=None, gamma=10.0, lam=0.01, p
     a.close()
     out["spin_bath"] = {"t_ps": ts, "T_L": tl, "T_S": tsp, "tau_L_ps": _tau(ts, tl, T)}
 
-    # run B: lattice bath only; spins along the field (T_S = 0)
-    p, r, v, s = inputs.bcc_fe_system(cells, seed + 1, T=T, sigma=0.0, spins="fm", dt_ps=dt)
+    # run B: lattice bath only; spins within 2-degree cones about the field
+    p, r, v, s = inputs.bcc_fe_system(cells, seed + 1, T=T, sigma=0.0, spins="cone2", dt_ps=dt)
     pb = dict(p, lattice_gamma_ps=gamma, lattice_temperature_K=T, seed=seed + 1)
     b = System(pb, r, v, s, device=device)
     ts, tl, tsp = _series(b, steps, every, dt)
