@@ -47,6 +47,9 @@ class _Params(ctypes.Structure):
         ("lam", ctypes.c_double), ("temperature", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32), ("hamiltonian", ctypes.c_int32),
         ("lat_gamma", ctypes.c_double), ("lat_temperature", ctypes.c_double),
+        ("an_K", ctypes.c_double), ("an_axis", ctypes.c_double * 3),
+        ("neel_alpha", ctypes.c_double), ("neel_gamma", ctypes.c_double), ("neel_delta", ctypes.c_double),
+        ("dmi_alpha", ctypes.c_double), ("dmi_gamma", ctypes.c_double), ("dmi_delta", ctypes.c_double),
     ]
 
 
@@ -162,6 +165,13 @@ def make_params(p: dict, brute_force=False, lam=0.0, temperature=0.0, seed=0, re
     q.hamiltonian = int(p.get("hamiltonian", 0))
     q.lat_gamma = float(p.get("lattice_gamma_ps", 0.0))
     q.lat_temperature = float(p.get("lattice_temperature_K", 0.0))
+    q.an_K = float(p.get("aniso_K_eV", 0.0))
+    for a, x in enumerate(p.get("aniso_axis", (0.0, 0.0, 1.0))):
+        q.an_axis[a] = float(x)
+    q.neel_alpha, q.neel_gamma = float(p.get("neel_alpha_eV", 0.0)), float(p.get("neel_gamma", 0.0))
+    q.neel_delta = float(p.get("neel_delta_A", 1.0))
+    q.dmi_alpha, q.dmi_gamma = float(p.get("dmi_alpha_eV", 0.0)), float(p.get("dmi_gamma", 0.0))
+    q.dmi_delta = float(p.get("dmi_delta_A", 1.0))
     return q
 
 
@@ -264,13 +274,14 @@ class Oracle:
 
 
 def potential_energy(params: dict, r, s):
-    """(E_morse, E_exch, E_zeeman, sum) of arbitrary positions and spin
-    vectors (spins need not be unit length), brute-force pairs."""
+    """(E_morse, E_exch, E_zeeman, sum, E_spin_orbit) of arbitrary positions
+    and spin vectors (spins need not be unit length), brute-force pairs; the
+    sum includes the spin-orbit part."""
     L = lib()
     p = make_params(params)
     r = np.ascontiguousarray(r, dtype=np.float64)
     s = np.ascontiguousarray(s, dtype=np.float64)
-    out = np.empty(4)
+    out = np.empty(5)
     L.orc_potential_energy(ctypes.byref(p), _dp(r), _dp(s), _dp(out))
     return out
 

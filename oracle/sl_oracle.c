@@ -32,6 +32,12 @@
  *                 (Einstein relation), integrated as the exact
  *                 Ornstein-Uhlenbeck flow over dt/2 at both ends of the step
  *                 (O B S R S B O).
+ *   Spin-orbit    (App. A.2) uniaxial anisotropy -K (s.n)^2, Neel
+ *                 pseudo-dipolar -g1(r)((e.s_i)(e.s_j) - s_i.s_j/3) and DMI
+ *                 d(r) e_ij.(s_i x s_j) per unordered pair inside the exchange
+ *                 cutoff, g1 and d of the form of Eq. BSfunction; the
+ *                 anisotropy makes omega_i depend on s_i, so its factor
+ *                 rotates about omega at the midpoint s + (tau/2) omega x s.
  *   Observables   kinetic, Morse, exchange, Zeeman energies; T_L
  *                 (Eq. lattice_temperature), T_S (Eq. spin_temperature),
  *                 magnetisation M = (1/N) sum_i s_i.
@@ -104,6 +110,12 @@ typedef struct {
   int32_t hamiltonian;   /* 0 analytic (Morse + Bethe-Slater), 1 learned */
   double lat_gamma;      /* lattice damping rate gamma_L/m of Eq. p_advance_T, 1/ps (0: none) */
   double lat_temperature;/* lattice bath temperature, K */
+  /* spin-orbit terms of App. A.2 (all 0: none); g1 and d have the form of
+   * Eq. BSfunction and the exchange cutoff */
+  double an_K;           /* uniaxial anisotropy K, eV: H_an = -K sum_i (s_i.n)^2 */
+  double an_axis[3];     /* unit axis n */
+  double neel_alpha, neel_gamma, neel_delta;   /* g1(r): H = -sum_{i<j} g1 ((e.s_i)(e.s_j) - s_i.s_j/3) */
+  double dmi_alpha, dmi_gamma, dmi_delta;      /* d(r): H = sum_{i<j} d e_ij.(s_i x s_j), D_ij = d e_ij */
 } orc_params;
 
 typedef struct {
@@ -126,6 +138,8 @@ typedef struct {
   int colour_start[9];
   orc_list ex, mo;         /* exchange pairs (r < ex_rc), Morse pairs (r < m_rc) */
   double *exJ, *exdJ;      /* J(r_ij), J'(r_ij) per exchange list entry */
+  double *exG1, *exDm;     /* g1(r_ij), d(r_ij) per exchange list entry */
+  double *exE;             /* e_ij = (r_j - r_i)/r per exchange list entry, [3] */
   long step;               /* completed steps */
   int err;
   int rebuilds;
@@ -184,17 +198,21 @@ void orc_gauss3(uint64_t seed, int replica, long step, int subpass, int atom, do
 /* ------------------------------------------------------------------ */
 
 /* Bethe-Slater exchange, Eq. BSfunction (App. A.1), without the cutoff step. */
-static double bs_J(const orc_params* p, double r) {
-  double x = (r / p->ex_delta) * (r / p->ex_delta);
-  return 4.0 * p->ex_alpha * x * (1.0 - p->ex_gamma * x) * exp(-x);
+static double bs_f(double alpha, double gamma, double delta, double r) {
+  double x = (r / delta) * (r / delta);
+  return 4.0 * alpha * x * (1.0 - gamma * x) * exp(-x);
 }
-/* dJ/dr of the same expression. */
-static double bs_dJ(const orc_params* p, double r) {
-  double x = (r / p->ex_delta) * (r / p->ex_delta);
-  double dxdr = 2.0 * r / (p->ex_delta * p->ex_delta);
+/* d/dr of the same expression. */
+static double bs_df(double alpha, double gamma, double delta, double r) {
+  double x = (r / delta) * (r / delta);
+  double dxdr = 2.0 * r / (delta * delta);
   /* d/dx [x (1 - g x) e^{-x}] = e^{-x} (1 - 2 g x - x + g x^2) */
-  return 4.0 * p->ex_alpha * exp(-x) * (1.0 - 2.0 * p->ex_gamma * x - x + p->ex_gamma * x * x) * dxdr;
+  return 4.0 * alpha * exp(-x) * (1.0 - 2.0 * gamma * x - x + gamma * x * x) * dxdr;
 }
+static double bs_J(const orc_params* p, double r) { return bs_f(p->ex_alpha, p->ex_gamma, p->ex_delta, r); }
+static double bs_dJ(const orc_params* p, double r) { return bs_df(p->ex_alpha, p->ex_gamma, p->ex_delta, r); }
+static int has_neel(const orc_params* p) { return p->neel_alpha != 0.0; }
+static int has_dmi(const orc_params* p) { return p->dmi_alpha != 0.0; }
 /* Morse pair energy V(r) = D0 (e^{-2a(r-r0)} - 2 e^{-a(r-r0)}). */
 static double morse_V(const orc_params* p, double r) {
   double e = exp(-p->m_alpha * (r - p->m_r0));
@@ -318,10 +336,13 @@ static int refresh_pairs(orc_state* st) {
     if (e) return e;
   }
   int np = st->ex.off[st->n];
-  free(st->exJ); free(st->exdJ);
+  free(st->exJ); free(st->exdJ); free(st->exG1); free(st->exDm); free(st->exE);
   st->exJ = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
   st->exdJ = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
-  if (!st->exJ || !st->exdJ) return ORC_ERR_OOM;
+  st->exG1 = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
+  st->exDm = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
+  st->exE = (double*)malloc((size_t)(np ? np : 1) * 3 * sizeof(double));
+  if (!st->exJ || !st->exdJ || !st->exG1 || !st->exDm || !st->exE) return ORC_ERR_OOM;
   for (int i = 0; i < st->n; ++i)
     for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
       double d[3];
@@ -329,6 +350,9 @@ static int refresh_pairs(orc_state* st) {
       double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       st->exJ[k] = bs_J(&st->p, r);
       st->exdJ[k] = bs_dJ(&st->p, r);
+      st->exG1[k] = has_neel(&st->p) ? bs_f(st->p.neel_alpha, st->p.neel_gamma, st->p.neel_delta, r) : 0.0;
+      st->exDm[k] = has_dmi(&st->p) ? bs_f(st->p.dmi_alpha, st->p.dmi_gamma, st->p.dmi_delta, r) : 0.0;
+      for (int a = 0; a < 3; ++a) st->exE[3 * k + a] = d[a] / r;
     }
   return ORC_OK;
 }
@@ -398,8 +422,9 @@ static int assign_sectors(orc_state* st) {
 /* Precession vector and single-spin propagators                      */
 /* ------------------------------------------------------------------ */
 
-/* omega_i = (1/hbar) (mu_s mu_B H + sum_j J_ij s_j)  (= -(1/hbar) dH/ds_i). */
-static void omega_of(const orc_state* st, int i, double w[3]) {
+/* The part of omega_i that does not depend on s_i itself:
+ * (1/hbar) (mu_s mu_B H + sum_j [J_ij s_j + g1 ((e.s_j) e - s_j/3) + d e x s_j]). */
+static void omega_fixed(const orc_state* st, int i, double w[3]) {
   double zf = st->p.mu_s * ORC_MUB;
   double h[3] = {zf * st->p.H[0], zf * st->p.H[1], zf * st->p.H[2]};
   for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
@@ -407,8 +432,35 @@ static void omega_of(const orc_state* st, int i, double w[3]) {
     h[0] += st->exJ[k] * sj[0];
     h[1] += st->exJ[k] * sj[1];
     h[2] += st->exJ[k] * sj[2];
+    const double* e = st->exE + 3 * k;
+    if (has_neel(&st->p)) {
+      double g = st->exG1[k], es = e[0] * sj[0] + e[1] * sj[1] + e[2] * sj[2];
+      for (int a = 0; a < 3; ++a) h[a] += g * (es * e[a] - sj[a] / 3.0);
+    }
+    if (has_dmi(&st->p)) {
+      double dm = st->exDm[k];
+      h[0] += dm * (e[1] * sj[2] - e[2] * sj[1]);
+      h[1] += dm * (e[2] * sj[0] - e[0] * sj[2]);
+      h[2] += dm * (e[0] * sj[1] - e[1] * sj[0]);
+    }
   }
   w[0] = h[0] / ORC_HBAR; w[1] = h[1] / ORC_HBAR; w[2] = h[2] / ORC_HBAR;
+}
+
+/* Uniaxial anisotropy part of omega at spin s: (2K/hbar) (s.n) n. */
+static void omega_aniso(const orc_params* p, const double* s, double w[3]) {
+  double c = 2.0 * p->an_K / ORC_HBAR * (s[0] * p->an_axis[0] + s[1] * p->an_axis[1] + s[2] * p->an_axis[2]);
+  w[0] = c * p->an_axis[0]; w[1] = c * p->an_axis[1]; w[2] = c * p->an_axis[2];
+}
+
+/* omega_i = -(1/hbar) dH/ds_i at the current state. */
+static void omega_of(const orc_state* st, int i, double w[3]) {
+  omega_fixed(st, i, w);
+  if (st->p.an_K != 0.0) {
+    double a[3];
+    omega_aniso(&st->p, st->s + 3 * i, a);
+    w[0] += a[0]; w[1] += a[1]; w[2] += a[2];
+  }
 }
 
 /* Learned-mode precession vector from the frozen pair coefficients:
@@ -462,55 +514,71 @@ static void rotate_ml(orc_state* st, int i, double tau) {
   s[0] = out[0]; s[1] = out[1]; s[2] = out[2];
 }
 
-/* Update spin i over time tau (one factor e^{L_si tau} of Eq. spin_ST_decomposition). */
-static void rotate(orc_state* st, int i, double tau, int subpass) {
-  if (st->use_ml) { rotate_ml(st, i, tau); return; }
-  double w[3];
-  omega_of(st, i, w);
-  double* s = st->s + 3 * i;
-  if (st->p.lambda != 0.0 || st->p.temperature != 0.0) {
-    /* Eq. sLLG written as ds/dt = Om x s with
-     * Om = (omega + eta + lambda s x omega) / (1 + lambda^2);
-     * eta ~ N(0, 2 D_S / |tau|) per component, D_S = lambda (1+lambda^2) k_B T / hbar. */
-    double lam = st->p.lambda;
-    double eta[3] = {0, 0, 0};
-    if (st->p.temperature > 0.0) {
-      double g[3];
-      orc_gauss3(st->p.seed, st->p.replica, st->step, subpass, i, g);
-      double DS = lam * (1.0 + lam * lam) * ORC_KB * st->p.temperature / ORC_HBAR;
-      double sig = sqrt(2.0 * DS / fabs(tau));
-      eta[0] = sig * g[0]; eta[1] = sig * g[1]; eta[2] = sig * g[2];
-    }
-    double sxw[3];
-    cross(s, w, sxw);
-    double den = 1.0 + lam * lam;
-    for (int a = 0; a < 3; ++a) w[a] = (w[a] + eta[a] + lam * sxw[a]) / den;
-  }
-  double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-  if (st->p.rotation == 0) {
-    /* exact rotation about omega by theta = |omega| tau (Rodrigues) */
-    double wn = sqrt(w2);
-    double th = wn * tau;
-    if (wn == 0.0 || th == 0.0) return;
-    double nv[3] = {w[0] / wn, w[1] / wn, w[2] / wn};
-    double c = cos(th), sn = sin(th), h = sin(0.5 * th);
-    double omc = 2.0 * h * h;
-    double nxs[3];
-    cross(nv, s, nxs);
-    double ns = nv[0] * s[0] + nv[1] * s[1] + nv[2] * s[2];
-    double out[3];
-    for (int a = 0; a < 3; ++a) out[a] = s[a] * c + nxs[a] * sn + nv[a] * ns * omc;
-    s[0] = out[0]; s[1] = out[1]; s[2] = out[2];
+/* s turned about w over time tau with the configured propagator: the exact
+ * rotation by |w| tau (Rodrigues) or the Cayley-type form of Sec. 3. */
+static void turn(const orc_params* p, const double w[3], double* s, double tau) {
+  double out[3];
+  if (p->rotation == 0) {
+    rodrigues(w, s, tau, out);
   } else {
-    /* Cayley-type propagator of Sec. 3 over time tau */
     double wxs[3];
     cross(w, s, wxs);
+    double w2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     double ws = w[0] * s[0] + w[1] * s[1] + w[2] * s[2];
     double q = tau * tau / 4.0;
     double den = 1.0 + q * w2;
-    double out[3];
     for (int a = 0; a < 3; ++a) out[a] = (s[a] + tau * wxs[a] + q * (2.0 * w[a] * ws - w2 * s[a])) / den;
-    s[0] = out[0]; s[1] = out[1]; s[2] = out[2];
+  }
+  s[0] = out[0]; s[1] = out[1]; s[2] = out[2];
+}
+
+/* Update spin i over time tau (one factor e^{L_si tau} of Eq. spin_ST_decomposition).
+ * With uniaxial anisotropy the factor is itself split symmetrically: half a
+ * turn under the anisotropy alone, a full turn under the field of the
+ * neighbours and H, another anisotropy half turn.  The anisotropy precession
+ * vector (2K/hbar)(s.n) n keeps s.n fixed, so each half turn is the exact
+ * flow of that term and is undone exactly by the reversed step. */
+static void rotate(orc_state* st, int i, double tau, int subpass) {
+  if (st->use_ml) { rotate_ml(st, i, tau); return; }
+  const orc_params* p = &st->p;
+  double* s = st->s + 3 * i;
+  int langevin = p->lambda != 0.0 || p->temperature != 0.0;
+  double lam = p->lambda, den = 1.0 + lam * lam;
+  double a[3];
+  if (p->an_K != 0.0) {
+    omega_aniso(p, s, a);
+    if (langevin) for (int q = 0; q < 3; ++q) a[q] /= den;
+    turn(p, a, s, 0.5 * tau);
+  }
+  double w[3];
+  omega_fixed(st, i, w);
+  if (langevin) {
+    /* Eq. sLLG written as ds/dt = Om x s with
+     * Om = (omega + eta + lambda s x omega) / (1 + lambda^2);
+     * eta ~ N(0, 2 D_S / |tau|) per component, D_S = lambda (1+lambda^2) k_B T / hbar.
+     * The damping term takes the whole omega, anisotropy included. */
+    double eta[3] = {0, 0, 0};
+    if (p->temperature > 0.0) {
+      double g[3];
+      orc_gauss3(p->seed, p->replica, st->step, subpass, i, g);
+      double DS = lam * (1.0 + lam * lam) * ORC_KB * p->temperature / ORC_HBAR;
+      double sig = sqrt(2.0 * DS / fabs(tau));
+      eta[0] = sig * g[0]; eta[1] = sig * g[1]; eta[2] = sig * g[2];
+    }
+    double wt[3] = {w[0], w[1], w[2]};
+    if (p->an_K != 0.0) {
+      omega_aniso(p, s, a);
+      for (int q = 0; q < 3; ++q) wt[q] += a[q];
+    }
+    double sxw[3];
+    cross(s, wt, sxw);
+    for (int q = 0; q < 3; ++q) w[q] = (w[q] + eta[q] + lam * sxw[q]) / den;
+  }
+  turn(p, w, s, tau);
+  if (p->an_K != 0.0) {
+    omega_aniso(p, s, a);
+    if (langevin) for (int q = 0; q < 3; ++q) a[q] /= den;
+    turn(p, a, s, 0.5 * tau);
   }
 }
 
@@ -613,6 +681,27 @@ static void compute_forces(orc_state* st) {
       double sij = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
       double c = -st->exdJ[k] * sij / r;        /* F_i -= J'(r) s_i.s_j (r_j - r_i)/r */
       f[0] += c * d[0]; f[1] += c * d[1]; f[2] += c * d[2];
+      const double* e = st->exE + 3 * k;
+      if (has_neel(&st->p)) {
+        /* U = -g1(r) Q, Q = (e.s_i)(e.s_j) - s_i.s_j/3; de/dr_i = -(1 - e e^T)/r:
+         * F_i = -g1' Q e - (g1/r) (dQ/de - e (e.dQ/de)), dQ/de = (e.s_j) s_i + (e.s_i) s_j */
+        double g = st->exG1[k], gp = bs_df(st->p.neel_alpha, st->p.neel_gamma, st->p.neel_delta, r);
+        double a = e[0] * sj[0] + e[1] * sj[1] + e[2] * sj[2];
+        double b = e[0] * si[0] + e[1] * si[1] + e[2] * si[2];
+        double Q = a * b - sij / 3.0;
+        for (int q = 0; q < 3; ++q) {
+          double dq = a * si[q] + b * sj[q];
+          f[q] += -gp * Q * e[q] - g / r * (dq - e[q] * 2.0 * a * b);
+        }
+      }
+      if (has_dmi(&st->p)) {
+        /* W = d(r) e.X, X = s_i x s_j: F_i = d' (e.X) e + (d/r) (X - e (e.X)) */
+        double dm = st->exDm[k], dp = bs_df(st->p.dmi_alpha, st->p.dmi_gamma, st->p.dmi_delta, r);
+        double X[3];
+        cross(si, sj, X);
+        double eX = e[0] * X[0] + e[1] * X[1] + e[2] * X[2];
+        for (int q = 0; q < 3; ++q) f[q] += dp * eX * e[q] + dm / r * (X[q] - e[q] * eX);
+      }
     }
   }
 }
@@ -657,7 +746,7 @@ void orc_destroy(orc_state* st) {
   free(st->r); free(st->v); free(st->s); free(st->F); free(st->rb);
   free(st->sector); free(st->colour); free(st->order);
   free(st->ex.off); free(st->ex.j); free(st->mo.off); free(st->mo.j);
-  free(st->exJ); free(st->exdJ);
+  free(st->exJ); free(st->exdJ); free(st->exG1); free(st->exDm); free(st->exE);
   free(st->ml); free(st->mll.off); free(st->mll.j); free(st->mlP); free(st->mlQ);
   free(st);
 }
@@ -668,7 +757,9 @@ int orc_params_size(void) { return (int)sizeof(orc_params); }
 orc_state* orc_create(const orc_params* p, const double* r, const double* v, const double* s, int* err) {
   *err = ORC_OK;
   if (!p || p->n_atoms < 0 || p->mass <= 0.0 || p->hamiltonian < 0 || p->hamiltonian > 1 ||
-      (p->hamiltonian == 1 && p->rotation != 0) || !(p->lat_gamma >= 0.0) || !(p->lat_temperature >= 0.0)) {
+      (p->hamiltonian == 1 && p->rotation != 0) || !(p->lat_gamma >= 0.0) || !(p->lat_temperature >= 0.0) ||
+      (p->an_K != 0.0 && !(fabs(p->an_axis[0] * p->an_axis[0] + p->an_axis[1] * p->an_axis[1] +
+                                p->an_axis[2] * p->an_axis[2] - 1.0) <= 1e-12))) {
     *err = ORC_ERR_ARG;
     return NULL;
   }
@@ -821,7 +912,8 @@ int orc_count_pairs(const orc_state* st, int which) {
   return which == 0 ? st->ex.off[st->n] : st->mo.off[st->n];
 }
 
-/* out[0..7] = E_kin, E_morse, E_exch, E_zeeman, E_total (eV), T_L, T_S (K), 0.
+/* out[0..7] = E_kin, E_morse, E_exch, E_zeeman, E_total (eV), T_L, T_S (K),
+ * E_spin-orbit (anisotropy + Neel + DMI, eV; included in E_total).
  * Where the learned Hamiltonian is in effect, out[1] is its energy sum_i E_i
  * (lattice + exchange together) and out[2] = 0. */
 void orc_energy(const orc_state* st, double out[8]) {
@@ -861,6 +953,31 @@ void orc_energy(const orc_state* st, double out[8]) {
     const double* si = st->s + 3 * i;
     ez -= zf * (st->p.H[0] * si[0] + st->p.H[1] * si[1] + st->p.H[2] * si[2]);
   }
+  /* spin-orbit terms: anisotropy per site, Neel and DMI per unordered pair */
+  double eo = 0.0;
+  if (!learned) {
+    for (int i = 0; i < n; ++i) {
+      const double* si = st->s + 3 * i;
+      double sn = si[0] * st->p.an_axis[0] + si[1] * st->p.an_axis[1] + si[2] * st->p.an_axis[2];
+      eo -= st->p.an_K * sn * sn;
+      for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
+        int j = st->ex.j[k];
+        if (j <= i) continue;
+        const double* sj = st->s + 3 * j;
+        const double* e = st->exE + 3 * k;
+        double sij = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
+        if (has_neel(&st->p)) {
+          double a = e[0] * sj[0] + e[1] * sj[1] + e[2] * sj[2], b = e[0] * si[0] + e[1] * si[1] + e[2] * si[2];
+          eo -= st->exG1[k] * (a * b - sij / 3.0);
+        }
+        if (has_dmi(&st->p)) {
+          double X[3];
+          cross(si, sj, X);
+          eo += st->exDm[k] * (e[0] * X[0] + e[1] * X[1] + e[2] * X[2]);
+        }
+      }
+    }
+  }
   double num = 0.0, den = 0.0;
   for (int i = 0; i < n; ++i) {
     double w[3], c[3];
@@ -875,10 +992,10 @@ void orc_energy(const orc_state* st, double out[8]) {
     den += si[0] * w[0] + si[1] * w[1] + si[2] * w[2];
   }
   out[0] = ek; out[1] = em; out[2] = ex; out[3] = ez;
-  out[4] = ek + em + ex + ez;
+  out[4] = ek + em + ex + ez + eo;
   out[5] = n > 0 ? 2.0 * ek / (3.0 * n * ORC_KB) : 0.0;
   out[6] = den != 0.0 ? ORC_HBAR / (2.0 * ORC_KB) * num / den : 0.0;
-  out[7] = 0.0;
+  out[7] = eo;
   free(eat); free(B);
 }
 
@@ -895,11 +1012,11 @@ void orc_magnetization(const orc_state* st, double out[4]) {
 /* Energy of arbitrary (r, s) without building a state: used by the
  * finite-difference tests.  Same definitions as orc_energy (potential part
  * only: out[1..3]).  Brute-force pairs. */
-int orc_potential_energy(const orc_params* p, const double* r, const double* s, double out[4]) {
+int orc_potential_energy(const orc_params* p, const double* r, const double* s, double out[5]) {
   orc_params q = *p;
   q.brute_force = 1;
   int n = q.n_atoms;
-  double em = 0.0, ex = 0.0, ez = 0.0;
+  double em = 0.0, ex = 0.0, ez = 0.0, eo = 0.0;
   double vshift = q.morse_shift ? morse_V(&q, q.m_rc) : 0.0;
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j) {
@@ -910,11 +1027,28 @@ int orc_potential_energy(const orc_params* p, const double* r, const double* s, 
       }
       double rr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       if (rr < q.m_rc) em += morse_V(&q, rr) - vshift;
-      if (rr < q.ex_rc)
-        ex -= bs_J(&q, rr) * (s[3 * i] * s[3 * j] + s[3 * i + 1] * s[3 * j + 1] + s[3 * i + 2] * s[3 * j + 2]);
+      if (rr < q.ex_rc) {
+        const double* si = s + 3 * i;
+        const double* sj = s + 3 * j;
+        double sij = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
+        ex -= bs_J(&q, rr) * sij;
+        double e[3] = {d[0] / rr, d[1] / rr, d[2] / rr};
+        if (has_neel(&q)) {
+          double a = e[0] * sj[0] + e[1] * sj[1] + e[2] * sj[2], b = e[0] * si[0] + e[1] * si[1] + e[2] * si[2];
+          eo -= bs_f(q.neel_alpha, q.neel_gamma, q.neel_delta, rr) * (a * b - sij / 3.0);
+        }
+        if (has_dmi(&q)) {
+          double X[3] = {si[1] * sj[2] - si[2] * sj[1], si[2] * sj[0] - si[0] * sj[2], si[0] * sj[1] - si[1] * sj[0]};
+          eo += bs_f(q.dmi_alpha, q.dmi_gamma, q.dmi_delta, rr) * (e[0] * X[0] + e[1] * X[1] + e[2] * X[2]);
+        }
+      }
     }
   double zf = q.mu_s * ORC_MUB;
-  for (int i = 0; i < n; ++i) ez -= zf * (q.H[0] * s[3 * i] + q.H[1] * s[3 * i + 1] + q.H[2] * s[3 * i + 2]);
-  out[0] = em; out[1] = ex; out[2] = ez; out[3] = em + ex + ez;
+  for (int i = 0; i < n; ++i) {
+    ez -= zf * (q.H[0] * s[3 * i] + q.H[1] * s[3 * i + 1] + q.H[2] * s[3 * i + 2]);
+    double sn = s[3 * i] * q.an_axis[0] + s[3 * i + 1] * q.an_axis[1] + s[3 * i + 2] * q.an_axis[2];
+    eo -= q.an_K * sn * sn;
+  }
+  out[0] = em; out[1] = ex; out[2] = ez; out[3] = em + ex + ez + eo; out[4] = eo;
   return ORC_OK;
 }

@@ -49,6 +49,14 @@ def fe_params(box, n_atoms, **overrides):
         hamiltonian=0,
         lattice_gamma_ps=0.0,
         lattice_temperature_K=0.0,
+        aniso_K_eV=0.0,
+        aniso_axis=[0.0, 0.0, 1.0],
+        neel_alpha_eV=0.0,
+        neel_gamma=0.0,
+        neel_delta_A=1.841,
+        dmi_alpha_eV=0.0,
+        dmi_gamma=0.0,
+        dmi_delta_A=1.841,
     )
     for k, v in overrides.items():
         if k not in p:
