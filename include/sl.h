@@ -103,6 +103,20 @@ typedef struct sl_params {
                                   Ornstein-Uhlenbeck flow of the velocities over dt/2 at
                                   both ends of the step (before the first half-kick, after
                                   the closing one), noise counter sub-passes 4 and 5 */
+  /* Spin-orbit terms (App. A.2), analytic Hamiltonian only; zero turns each off.
+   * Uniaxial anisotropy H_an = -K sum_i (s_i.n)^2 with n a unit vector (|n| = 1
+   * within 1e-12, else SL_ERR_ARG).  Its precession vector (2K/hbar)(s_i.n) n
+   * keeps s_i.n fixed, so each single-spin factor turns s_i half its time about
+   * n alone, then the whole time about the rest of omega_i, then the other
+   * half about n: a symmetric split whose pieces are exact flows.
+   * Neel pseudo-dipolar pair term -g1(r) ((e.s_i)(e.s_j) - s_i.s_j/3) and
+   * Dzyaloshinskii-Moriya term d(r) e.(s_i x s_j), e = (r_j - r_i)/r, each
+   * unordered pair within ex_rc_A once; g1 and d take the form of
+   * Eq. BSfunction with their own (alpha, gamma, delta). */
+  double aniso_K_eV;
+  double aniso_axis[3];
+  double neel_alpha_eV, neel_gamma, neel_delta_A;
+  double dmi_alpha_eV, dmi_gamma, dmi_delta_A;
 } sl_params;
 
 typedef struct sl_ctx sl_ctx;  /* opaque, owned by the library */
@@ -160,7 +174,8 @@ int sl_set_dt(sl_ctx* ctx, double dt_ps);
 int sl_set_field(sl_ctx* ctx, const double H_tesla[3]);
 
 /* out[8] (host) = E_kin, E_morse, E_exchange, E_zeeman, E_total (eV),
- * T_L (Eq. lattice_temperature, K), T_S (Eq. spin_temperature, K), 0.
+ * T_L (Eq. lattice_temperature, K), T_S (Eq. spin_temperature, K), E_spin_orbit
+ * (anisotropy + Neel + DMI, eV; part of E_total).
  * Pair energies count each unordered pair once.  For a batch: energies summed
  * over the replicas, temperatures over all atoms.  Synchronises. */
 int sl_energy(sl_ctx* ctx, double out[8]);
@@ -291,8 +306,9 @@ int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void*
  * midpoint m (found by a trial rotation about omega(s_i)), where
  *   omega(s) = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij s.s_j) s_j) / hbar,
  *   P_ij = sum_k (G_i+G_j)[3k+1] g_k(r_ij),  Q_ij = sum_k (G_i+G_j)[3k+2] g_k(r_ij),
- * with the current neighbour spins.  The spin bath (lambda, temperature_K)
- * and the Cayley propagator are not available in this mode.
+ * with the current neighbour spins.  The spin bath (lambda, temperature_K),
+ * the Cayley propagator and the spin-orbit terms are not available in this
+ * mode (SL_ERR_ARG).
  * ------------------------------------------------------------------------ */
 #define SL_ML_NF 48
 #define SL_ML_NH 64

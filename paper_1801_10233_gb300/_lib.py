@@ -54,6 +54,9 @@ class sl_params(ctypes.Structure):
         ("lambda_", ctypes.c_double), ("temperature_K", ctypes.c_double),
         ("seed", ctypes.c_uint64), ("replica", ctypes.c_int32), ("reserved1", ctypes.c_int32),
         ("lattice_gamma_ps", ctypes.c_double), ("lattice_temperature_K", ctypes.c_double),
+        ("aniso_K_eV", ctypes.c_double), ("aniso_axis", ctypes.c_double * 3),
+        ("neel_alpha_eV", ctypes.c_double), ("neel_gamma", ctypes.c_double), ("neel_delta_A", ctypes.c_double),
+        ("dmi_alpha_eV", ctypes.c_double), ("dmi_gamma", ctypes.c_double), ("dmi_delta_A", ctypes.c_double),
     ]
 
 
@@ -158,6 +161,16 @@ def make_params(p: dict) -> sl_params:
     q.hamiltonian = int(p.get("hamiltonian", 0))
     q.lattice_gamma_ps = float(p.get("lattice_gamma_ps", 0.0))
     q.lattice_temperature_K = float(p.get("lattice_temperature_K", 0.0))
+    q.aniso_K_eV = float(p.get("aniso_K_eV", 0.0))
+    axis = p.get("aniso_axis", (0.0, 0.0, 1.0))
+    for a in range(3):
+        q.aniso_axis[a] = float(axis[a])
+    q.neel_alpha_eV = float(p.get("neel_alpha_eV", 0.0))
+    q.neel_gamma = float(p.get("neel_gamma", 0.0))
+    q.neel_delta_A = float(p.get("neel_delta_A", 1.0))
+    q.dmi_alpha_eV = float(p.get("dmi_alpha_eV", 0.0))
+    q.dmi_gamma = float(p.get("dmi_gamma", 0.0))
+    q.dmi_delta_A = float(p.get("dmi_delta_A", 1.0))
     return q
 
 

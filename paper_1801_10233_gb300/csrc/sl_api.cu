@@ -81,6 +81,18 @@ int validate(const sl_params* p) {
   if (p->hamiltonian == SL_HAM_LEARNED && (!(p->morse_rc_A >= SL_ML_RC) || p->lambda != 0.0 ||
                                            p->temperature_K != 0.0 || p->rotation != SL_ROT_RODRIGUES))
     return SL_ERR_ARG;
+  // spin-orbit terms: finite, a unit anisotropy axis, positive ranges; analytic Hamiltonian only
+  const bool so = p->aniso_K_eV != 0.0 || p->neel_alpha_eV != 0.0 || p->dmi_alpha_eV != 0.0;
+  if (!std::isfinite(p->aniso_K_eV) || !std::isfinite(p->neel_alpha_eV) || !std::isfinite(p->dmi_alpha_eV) ||
+      !std::isfinite(p->neel_gamma) || !std::isfinite(p->dmi_gamma))
+    return SL_ERR_ARG;
+  if (so && p->hamiltonian != SL_HAM_ANALYTIC) return SL_ERR_ARG;
+  if (p->aniso_K_eV != 0.0) {
+    const double* a = p->aniso_axis;
+    if (!(std::fabs(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] - 1.0) <= 1e-12)) return SL_ERR_ARG;
+  }
+  if (p->neel_alpha_eV != 0.0 && !(p->neel_delta_A > 0.0)) return SL_ERR_ARG;
+  if (p->dmi_alpha_eV != 0.0 && !(p->dmi_delta_A > 0.0)) return SL_ERR_ARG;
   double rc = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
   for (int a = 0; a < 3; ++a)
     if (!(p->box[a] >= 2.0 * rc)) return SL_ERR_BOX;
@@ -106,8 +118,11 @@ int validate_batch(const sl_params* p, int nrep) {
                 a.ex_gamma == b.ex_gamma && a.ex_delta_A == b.ex_delta_A && a.ex_rc_A == b.ex_rc_A &&
                 a.morse_D0_eV == b.morse_D0_eV && a.morse_alpha_invA == b.morse_alpha_invA &&
                 a.morse_r0_A == b.morse_r0_A && a.morse_rc_A == b.morse_rc_A && a.skin_A == b.skin_A &&
-                a.lambda == b.lambda && a.seed == b.seed && a.hamiltonian == b.hamiltonian;
-    for (int c = 0; c < 3; ++c) same = same && a.H_tesla[c] == b.H_tesla[c];
+                a.lambda == b.lambda && a.seed == b.seed && a.hamiltonian == b.hamiltonian &&
+                a.aniso_K_eV == b.aniso_K_eV && a.neel_alpha_eV == b.neel_alpha_eV &&
+                a.neel_gamma == b.neel_gamma && a.neel_delta_A == b.neel_delta_A &&
+                a.dmi_alpha_eV == b.dmi_alpha_eV && a.dmi_gamma == b.dmi_gamma && a.dmi_delta_A == b.dmi_delta_A;
+    for (int c = 0; c < 3; ++c) same = same && a.H_tesla[c] == b.H_tesla[c] && a.aniso_axis[c] == b.aniso_axis[c];
     if (!same) return SL_ERR_ARG;
   }
   if (total > 0x7fffffffLL) return SL_ERR_ARG;
@@ -240,6 +255,24 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   d.ex_rc2_f = split_f2(d.ex_rc2);
   d.lam_f = split_f2(p->lambda);
   d.inv1pl2_f = split_f2(1.0 / (1.0 + p->lambda * p->lambda));
+  // spin-orbit terms
+  d.so = (p->aniso_K_eV != 0.0 ? SL_SO_ANISO : 0) | (p->neel_alpha_eV != 0.0 ? SL_SO_NEEL : 0) |
+         (p->dmi_alpha_eV != 0.0 ? SL_SO_DMI : 0);
+  d.an_K = p->aniso_K_eV;
+  for (int a = 0; a < 3; ++a) {
+    d.an_n[a] = p->aniso_axis[a];
+    d.an_n_f[a] = split_f2(p->aniso_axis[a]);
+  }
+  d.an_c_f = split_f2(2.0 * p->aniso_K_eV / SL_HBAR);
+  d.an_cl_f = split_f2(2.0 * p->aniso_K_eV / SL_HBAR / (1.0 + p->lambda * p->lambda));
+  {
+    const double nd = p->neel_alpha_eV != 0.0 ? p->neel_delta_A : 1.0;
+    const double dd = p->dmi_alpha_eV != 0.0 ? p->dmi_delta_A : 1.0;
+    d.ne_bs = {split_f2(1.0 / (nd * nd)), split_f2(4.0 * p->neel_alpha_eV), split_f2(p->neel_gamma),
+               split_f2(8.0 * p->neel_alpha_eV / (nd * nd))};
+    d.dm_bs = {split_f2(1.0 / (dd * dd)), split_f2(4.0 * p->dmi_alpha_eV), split_f2(p->dmi_gamma),
+               split_f2(8.0 * p->dmi_alpha_eV / (dd * dd))};
+  }
   fill_df_constants(d);
   fill_noise(reps, ps, p->dt_ps);
   for (int r = 0; r < nrep; ++r)
@@ -257,6 +290,8 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_cnt = L.take<int>(d.nsec), o_start = L.take<int>(d.nsec + 1), o_fill = L.take<int>(d.nsec);
   size_t o_exj = L.take<int>(nn * d.max_ex), o_exn = L.take<int>(nn), o_exin = L.take<int>(nn);
   size_t o_exJ = L.take<float2>(nn * d.max_ex);
+  const bool so_pairs = d.so != 0;   // the spin-orbit sweep reads the tables whenever a term is on
+  size_t o_exso = so_pairs ? L.take<float2>(5 * nn * d.max_ex) : 0;
   size_t o_rh = L.take<float4>(nn), o_rm = L.take<float4>(nn), o_rl = L.take<float4>(nn);
   size_t o_sdf = L.take<float4>(2 * nn);
   size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
@@ -304,6 +339,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.sec_count = (int*)(base + o_cnt); d.sec_start = (int*)(base + o_start); d.sec_fill = (int*)(base + o_fill);
     d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn); d.exin = (int*)(base + o_exin);
     d.exJ = (float2*)(base + o_exJ);
+    d.exso = so_pairs ? (float2*)(base + o_exso) : nullptr;
     d.rh = (float4*)(base + o_rh); d.rm = (float4*)(base + o_rm); d.rl = (float4*)(base + o_rl);
     d.sdf = (float4*)(base + o_sdf);
     d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);
@@ -622,10 +658,10 @@ static int observe(sl_ctx* c, std::vector<double>& red) {
 
 static void energy_of(const double* q, long long n, double out[8]) {
   out[0] = q[0]; out[1] = q[1]; out[2] = q[2]; out[3] = q[3];
-  out[4] = q[0] + q[1] + q[2] + q[3];
+  out[4] = q[0] + q[1] + q[2] + q[3] + q[10];
   out[5] = n > 0 ? 2.0 * q[0] / (3.0 * (double)n * SL_KB) : 0.0;
   out[6] = q[8] != 0.0 ? SL_HBAR / (2.0 * SL_KB) * q[7] / q[8] : 0.0;
-  out[7] = 0.0;
+  out[7] = q[10];
 }
 
 static void magnetization_of(const double* q, long long n, double out[4]) {

@@ -49,6 +49,15 @@ struct SlRep {
   double lat_c1, lat_sig;   // lattice bath over dt/2: v <- c1 v + sig xi (c1 = 1, sig = 0: none)
 };
 
+// Spin-orbit term bits of SlDev::so.
+enum { SL_SO_ANISO = 1, SL_SO_NEEL = 2, SL_SO_DMI = 4 };
+
+// Double-float constants of one f(r) = 4 alpha x (1 - gamma x) e^{-x},
+// x = r^2/delta^2 (Eq. BSfunction): 1/delta^2, 4 alpha, gamma, 8 alpha/delta^2.
+struct SlBsF {
+  float2 ix, a4, g, a8d2;
+};
+
 // Everything a kernel needs, passed by value.  Scalars used by the
 // double-float kernels are given as (hi, lo) float pairs split on the host.
 // Sector ranks are global and colour-major: rank = colour * s8 + sec8_off of
@@ -82,6 +91,12 @@ struct SlDev {
   float2 ex_ix_f, ex_4a_f, ex_g_f, ex_8ad2_f, ex_rc2_f;  // 1/delta^2, 4 alpha, gamma, 8 alpha/delta^2, rc^2
   float2 lam_f, inv1pl2_f;                   // lambda, 1/(1 + lambda^2)
 
+  // spin-orbit terms (App. A.2): so = SL_SO_ANISO | SL_SO_NEEL | SL_SO_DMI bits
+  int so;
+  double an_K, an_n[3];                       // -K sum_i (s_i.n)^2
+  float2 an_c_f, an_cl_f, an_n_f[3];          // 2K/hbar, 2K/(hbar (1 + lambda^2)), n
+  SlBsF ne_bs, dm_bs;                         // double-float constants of g1 and d
+
   const SlRep* reps;        // [nrep]
   int* arep;                // replica of each sorted atom
   int* tarep;               // rebuild scratch
@@ -98,6 +113,9 @@ struct SlDev {
   // neighbour lists
   int *exj, *exn, *exin;    // [max_ex][n] neighbour-major (same-sector entries first), counts
   float2 *exJ;              // [max_ex][n] J_ij (hi, lo) at current r
+  // [5][max_ex][n] g1, d, e_x, e_y, e_z (hi, lo) at current r, e = (r_j - r_i)/r;
+  // zero beyond ex_rc (NULL when so == 0)
+  float2 *exso;
   int *mj, *mn;             // [max_m][n] neighbour-major, counts
   // sweep scratch for blocks whose atoms exceed shared memory: [3 n] each
   float2 *hbuf, *sbuf, *ebuf;
@@ -145,7 +163,7 @@ struct SlDev {
 #define SL_ML_TILE_BYTES (2 * (64 * 48 + 64 * 64 + 64 * 64 + 48 * 64))
 #define SL_ML_ATOMS_PER_TILE 128
 
-#define SL_NOBS 10  // Ek, Em, Ex, Ez, Mx, My, Mz, TS numerator, TS denominator, non-finite flag
+#define SL_NOBS 11  // Ek, Em, Ex, Ez, Mx, My, Mz, TS numerator, TS denominator, non-finite flag, E_spin_orbit
 
 __device__ __forceinline__ void sl_set_error(SlCtrl* c, int code) { atomicCAS(&c->status, 0, code); }
 

@@ -223,4 +223,85 @@ __device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau,
   return inc;
 }
 
+// ---------------------------------------------------------------------------
+// Spin-orbit terms (App. A.2)
+// ---------------------------------------------------------------------------
+// f(r) = 4 alpha x (1 - gamma x) e^{-x}, x = r^2/delta^2 (Eq. BSfunction), and
+// f'(r)/r = 8 alpha/delta^2 e^{-x} (1 - x (1 + 2 gamma - gamma x)), from r^2.
+__device__ __forceinline__ void bs_eval(const SlBsF& c, df r2, df& f, df& fpr) {
+  const df x = df_mul(r2, F2(c.ix));
+  const df ex = df_exp(df_neg(x));
+  const df g = F2(c.g);
+  f = df_mul(df_mul(F2(c.a4), x), df_mul(df_add_f(df_neg(df_mul(g, x)), 1.0f), ex));
+  const df poly = df_add_f(df_neg(df_mul(x, df_add_f(df_sub(df_scale(g, 2.0f), df_mul(g, x)), 1.0f))), 1.0f);
+  fpr = df_mul(df_mul(F2(c.a8d2), ex), poly);
+}
+
+// One exchange-list entry with its spin-orbit coefficients: J, g1, d and the
+// unit vector e from atom i to its neighbour.
+struct SoEntry {
+  df J, g, dm;
+  df3 e;
+};
+
+__device__ __forceinline__ SoEntry load_so(const SlDev& d, size_t e) {
+  const size_t P = (size_t)d.max_ex * (size_t)d.n;
+  SoEntry q;
+  q.J = F2(__ldg(d.exJ + e));
+  q.g = F2(__ldg(d.exso + e));
+  q.dm = F2(__ldg(d.exso + P + e));
+  q.e.x = F2(__ldg(d.exso + 2 * P + e));
+  q.e.y = F2(__ldg(d.exso + 3 * P + e));
+  q.e.z = F2(__ldg(d.exso + 4 * P + e));
+  return q;
+}
+
+// (h, l) += J s_j + g1 ((e.s_j) e - s_j/3) + d e x s_j: minus the derivative of
+// the exchange, Neel and DMI energies of the pair with respect to s_i.
+__device__ __forceinline__ void so_field_acc(const SoEntry& q, const df3& sj, float& hx, float& lx, float& hy,
+                                             float& ly, float& hz, float& lz) {
+  const df A = df_sub(q.J, df_mul(q.g, df_make(SL_INV_ODD3_HI, SL_INV_ODD3_LO)));
+  const df c = df_mul(q.g, dot3(q.e, sj));
+  const df3 X = cross3(q.e, sj);
+  acc_prod(hx, lx, A, sj.x); acc_prod(hx, lx, c, q.e.x); acc_prod(hx, lx, q.dm, X.x);
+  acc_prod(hy, ly, A, sj.y); acc_prod(hy, ly, c, q.e.y); acc_prod(hy, ly, q.dm, X.y);
+  acc_prod(hz, lz, A, sj.z); acc_prod(hz, lz, c, q.e.z); acc_prod(hz, lz, q.dm, X.z);
+}
+
+// Anisotropy precession vector c (s.n) n, c = 2K/hbar (or over 1 + lambda^2).
+__device__ __forceinline__ df3 aniso_vec(const SlDev& d, const df3& s, df c) {
+  df3 n;
+  n.x = F2(d.an_n_f[0]); n.y = F2(d.an_n_f[1]); n.z = F2(d.an_n_f[2]);
+  const df k = df_mul(c, dot3(s, n));
+  df3 a;
+  a.x = df_mul(k, n.x); a.y = df_mul(k, n.y); a.z = df_mul(k, n.z);
+  return a;
+}
+
+// FP64 versions for the observables: the spin-orbit field of one entry and
+// the pair's spin-orbit energy, from the tables.
+__device__ __forceinline__ double d_of(float2 v) { return double_from_float(v.x) + double_from_float(v.y); }
+
+__device__ __forceinline__ void so_field_d(const SlDev& d, size_t e, const double4_32a& sj, double& hx, double& hy,
+                                           double& hz) {
+  const size_t P = (size_t)d.max_ex * (size_t)d.n;
+  const double g = d_of(d.exso[e]), dm = d_of(d.exso[P + e]);
+  const double ex = d_of(d.exso[2 * P + e]), ey = d_of(d.exso[3 * P + e]), ez = d_of(d.exso[4 * P + e]);
+  const double es = ex * sj.x + ey * sj.y + ez * sj.z;
+  hx += g * (es * ex - sj.x / 3.0) + dm * (ey * sj.z - ez * sj.y);
+  hy += g * (es * ey - sj.y / 3.0) + dm * (ez * sj.x - ex * sj.z);
+  hz += g * (es * ez - sj.z / 3.0) + dm * (ex * sj.y - ey * sj.x);
+}
+
+__device__ __forceinline__ double so_pair_energy_d(const SlDev& d, size_t e, const double4_32a& si,
+                                                   const double4_32a& sj) {
+  const size_t P = (size_t)d.max_ex * (size_t)d.n;
+  const double g = d_of(d.exso[e]), dm = d_of(d.exso[P + e]);
+  const double ex = d_of(d.exso[2 * P + e]), ey = d_of(d.exso[3 * P + e]), ez = d_of(d.exso[4 * P + e]);
+  const double a = ex * sj.x + ey * sj.y + ez * sj.z, b = ex * si.x + ey * si.y + ez * si.z;
+  const double c = si.x * sj.x + si.y * sj.y + si.z * sj.z;
+  const double X = si.y * sj.z - si.z * sj.y, Y = si.z * sj.x - si.x * sj.z, Z = si.x * sj.y - si.y * sj.x;
+  return -g * (a * b - c / 3.0) + dm * (ex * X + ey * Y + ez * Z);
+}
+
 }  // namespace

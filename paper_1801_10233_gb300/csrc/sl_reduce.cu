@@ -6,6 +6,7 @@
 // block per replica then sums its contiguous range in a fixed order.
 #include "sl_internal.cuh"
 #include "sl_df64.cuh"
+#include "sl_pair.cuh"
 
 namespace {
 
@@ -40,6 +41,7 @@ __global__ void k_obs_atoms(SlDev d) {
     hx += b.x; hy += b.y; hz += b.z;
   }
   const int ne = learned ? 0 : d.exn[i];
+  double eso = 0.0;
   for (int k = 0; k < ne; ++k) {
     const size_t e = (size_t)k * d.n + i;
     const float2 J2 = d.exJ[e];
@@ -47,8 +49,18 @@ __global__ void k_obs_atoms(SlDev d) {
     const double4_32a sj = d.s[d.exj[e]];
     ex += J * (si.x * sj.x + si.y * sj.y + si.z * sj.z);
     hx = fma(J, sj.x, hx); hy = fma(J, sj.y, hy); hz = fma(J, sj.z, hz);
+    if (d.exso) {
+      so_field_d(d, e, sj, hx, hy, hz);
+      eso += so_pair_energy_d(d, e, si, sj);
+    }
   }
   q[2] = -0.5 * ex;
+  q[10] = 0.5 * eso;
+  if (d.so & SL_SO_ANISO) {
+    const double sn = si.x * d.an_n[0] + si.y * d.an_n[1] + si.z * d.an_n[2];
+    q[10] -= d.an_K * sn * sn;
+    hx += 2.0 * d.an_K * sn * d.an_n[0]; hy += 2.0 * d.an_K * sn * d.an_n[1]; hz += 2.0 * d.an_K * sn * d.an_n[2];
+  }
   q[3] = -(d.zee[0] * si.x + d.zee[1] * si.y + d.zee[2] * si.z);
   q[4] = si.x; q[5] = si.y; q[6] = si.z;
   const double ih = 1.0 / SL_HBAR;

@@ -52,8 +52,10 @@ size_t sweep_smem_bytes(bool noise, int maxa) {
          (size_t)SW_MAXIN * maxa * sizeof(short) + (size_t)maxa * sizeof(int);
 }
 
-// (h, l) += sum of J_ij s_j over external entries [k0, k1) of atom i whose
+// (h, l) += sum of J_ij s_j (with SO: the field of the exchange, Neel and DMI
+// terms of the pair) over external entries [k0, k1) of atom i whose
 // neighbour index lies inside [lo, hi) (take = 1) or outside it (take = 0).
+template <bool SO>
 __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1, int lo, int hi, int take,
                                           float& hx, float& lx, float& hy, float& ly, float& hz, float& lz) {
   const size_t n = (size_t)d.n;
@@ -79,19 +81,31 @@ __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1,
         vl[q] = __ldg(d.sdf + 2 * (size_t)jj[q] + 1);
       }
     }
+    if constexpr (SO) {
 #pragma unroll
-    for (int q = 0; q < SW_BATCH; ++q) {
-      if (use[q]) {
-        const df J = F2(JJ[q]);
-        acc_prod(hx, lx, J, df_make(vh[q].x, vl[q].x));
-        acc_prod(hy, ly, J, df_make(vh[q].y, vl[q].y));
-        acc_prod(hz, lz, J, df_make(vh[q].z, vl[q].z));
+      for (int q = 0; q < SW_BATCH; ++q) {
+        if (use[q]) {
+          const SoEntry so = load_so(d, (size_t)(kb + q) * n + i);
+          df3 sj;
+          sj.x = df_make(vh[q].x, vl[q].x); sj.y = df_make(vh[q].y, vl[q].y); sj.z = df_make(vh[q].z, vl[q].z);
+          so_field_acc(so, sj, hx, lx, hy, ly, hz, lz);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < SW_BATCH; ++q) {
+        if (use[q]) {
+          const df J = F2(JJ[q]);
+          acc_prod(hx, lx, J, df_make(vh[q].x, vl[q].x));
+          acc_prod(hy, ly, J, df_make(vh[q].y, vl[q].y));
+          acc_prod(hz, lz, J, df_make(vh[q].z, vl[q].z));
+        }
       }
     }
   }
 }
 
-template <int SW_SPB, int SW_THREADS>
+template <int SW_SPB, int SW_THREADS, bool SO>
 __global__ void __launch_bounds__(SW_THREADS, 576 / SW_THREADS)
 k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, int next_colour, int pin, int pout) {
   constexpr int SW_MAXA = 12 * SW_SPB;
@@ -117,7 +131,7 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
   const long long step = d.ctrl->step;
   const df tau = F2(d.tau_f);
   const size_t n = (size_t)d.n;
-  const int kin = min(SW_MAXIN, d.max_ex);
+  const int kin = SO ? 0 : min(SW_MAXIN, d.max_ex);   // SO: same-sector lists read from global memory
   const float2* P = pin >= 0 ? d.hpart[pin] : nullptr;
   int plo = 0, phi = 0;
   if (P) { plo = d.sec_start[prev_colour * s8]; phi = d.sec_start[(prev_colour + 1) * s8]; }
@@ -146,12 +160,12 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
     float hx, lx, hy, ly, hz, lz;
     if (P) {
       hx = p0.x; lx = p0.y; hy = p1.x; ly = p1.y; hz = p2.x; lz = p2.y;
-      ext_field(d, i, ni, ne, plo, phi, 1, hx, lx, hy, ly, hz, lz);
+      ext_field<SO>(d, i, ni, ne, plo, phi, 1, hx, lx, hy, ly, hz, lz);
     } else {
       hx = d.zee_f[0].x; lx = d.zee_f[0].y;
       hy = d.zee_f[1].x; ly = d.zee_f[1].y;
       hz = d.zee_f[2].x; lz = d.zee_f[2].y;
-      ext_field(d, i, ni, ne, 0, 0, 0, hx, lx, hy, ly, hz, lz);
+      ext_field<SO>(d, i, ni, ne, 0, 0, 0, hx, lx, hy, ly, hz, lz);
     }
     H[3 * t] = D2(acc_done(hx, lx));
     H[3 * t + 1] = D2(acc_done(hy, ly));
@@ -188,40 +202,52 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
         float hx = f0.x, lx = f0.y, hy = f1.x, ly = f1.y, hz = f2.x, lz = f2.y;
         float gx = 0.0f, kx = 0.0f, gy = 0.0f, ky = 0.0f, gz = 0.0f, kz = 0.0f;
         const int ni = fits ? sh_in[t] : d.exin[i];
-        const int nstage = fits ? min(ni, kin) : 0;
-        // the same-sector entries in pairs (two interleaved accumulators), from
-        // shared memory where staged; the order is the same whatever is staged,
-        // so every tile shape gives the same bits
-        auto entry = [&](int k, int& u, df& J) {
-          if (k < nstage) {
-            u = sh_iu[t * SW_MAXIN + k];
-            J = F2(sh_ij[t * SW_MAXIN + k]);
-          } else {
+        if constexpr (SO) {
+          // one accumulator, entries in list order (the same for every tile shape)
+          for (int k = 0; k < ni; ++k) {
             const size_t e = (size_t)k * n + i;
-            u = d.exj[e] - a0;
-            J = F2(d.exJ[e]);
+            const int u = __ldg(d.exj + e) - a0;
+            const SoEntry so = load_so(d, e);
+            df3 sj;
+            sj.x = F2(S[3 * u]); sj.y = F2(S[3 * u + 1]); sj.z = F2(S[3 * u + 2]);
+            so_field_acc(so, sj, hx, lx, hy, ly, hz, lz);
           }
-        };
-        int k = 0;
-        for (; k + 1 < ni; k += 2) {
-          int u0, u1;
-          df J0, J1;
-          entry(k, u0, J0);
-          entry(k + 1, u1, J1);
-          acc_prod(hx, lx, J0, F2(S[3 * u0]));
-          acc_prod(gx, kx, J1, F2(S[3 * u1]));
-          acc_prod(hy, ly, J0, F2(S[3 * u0 + 1]));
-          acc_prod(gy, ky, J1, F2(S[3 * u1 + 1]));
-          acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
-          acc_prod(gz, kz, J1, F2(S[3 * u1 + 2]));
-        }
-        if (k < ni) {
-          int u0;
-          df J0;
-          entry(k, u0, J0);
-          acc_prod(hx, lx, J0, F2(S[3 * u0]));
-          acc_prod(hy, ly, J0, F2(S[3 * u0 + 1]));
-          acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
+        } else {
+          const int nstage = fits ? min(ni, kin) : 0;
+          // the same-sector entries in pairs (two interleaved accumulators), from
+          // shared memory where staged; the order is the same whatever is staged,
+          // so every tile shape gives the same bits
+          auto entry = [&](int k, int& u, df& J) {
+            if (k < nstage) {
+              u = sh_iu[t * SW_MAXIN + k];
+              J = F2(sh_ij[t * SW_MAXIN + k]);
+            } else {
+              const size_t e = (size_t)k * n + i;
+              u = d.exj[e] - a0;
+              J = F2(d.exJ[e]);
+            }
+          };
+          int k = 0;
+          for (; k + 1 < ni; k += 2) {
+            int u0, u1;
+            df J0, J1;
+            entry(k, u0, J0);
+            entry(k + 1, u1, J1);
+            acc_prod(hx, lx, J0, F2(S[3 * u0]));
+            acc_prod(gx, kx, J1, F2(S[3 * u1]));
+            acc_prod(hy, ly, J0, F2(S[3 * u0 + 1]));
+            acc_prod(gy, ky, J1, F2(S[3 * u1 + 1]));
+            acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
+            acc_prod(gz, kz, J1, F2(S[3 * u1 + 2]));
+          }
+          if (k < ni) {
+            int u0;
+            df J0;
+            entry(k, u0, J0);
+            acc_prod(hx, lx, J0, F2(S[3 * u0]));
+            acc_prod(hy, ly, J0, F2(S[3 * u0 + 1]));
+            acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
+          }
         }
         df3 w;
         w.x = df_mul(df_add(acc_done(hx, lx), acc_done(gx, kx)), ih);
@@ -229,9 +255,25 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
         w.z = df_mul(df_add(acc_done(hz, lz), acc_done(gz, kz)), ih);
         df3 s;
         s.x = F2(S[3 * t]); s.y = F2(S[3 * t + 1]); s.z = F2(S[3 * t + 2]);
+        // uniaxial anisotropy: exact half turns about n before and after the
+        // turn under the rest of omega; inc_a collects the first one's increment
+        const bool aniso = SO && (d.so & SL_SO_ANISO);
+        const int cayley = d.rotation == SL_ROT_CAYLEY;
+        df3 inc_a;
+        inc_a.x = inc_a.y = inc_a.z = df_f(0.0f);
+        if (aniso) {
+          inc_a = rot_increment(aniso_vec(d, s, F2(bath ? d.an_cl_f : d.an_c_f)), s, df_scale(tau, 0.5f), cayley);
+          s.x = df_add(s.x, inc_a.x); s.y = df_add(s.y, inc_a.y); s.z = df_add(s.z, inc_a.z);
+        }
         if (bath) {
-          // Eq. sLLG as ds/dt = Om x s, Om = (w + eta + lambda s x w) / (1 + lambda^2)
-          df3 sxw = cross3(s, w);
+          // Eq. sLLG as ds/dt = Om x s, Om = (w + eta + lambda s x w) / (1 + lambda^2);
+          // the damping term takes the whole omega, anisotropy included
+          df3 wt = w;
+          if (aniso) {
+            const df3 a = aniso_vec(d, s, F2(d.an_c_f));
+            wt.x = df_add(wt.x, a.x); wt.y = df_add(wt.y, a.y); wt.z = df_add(wt.z, a.z);
+          }
+          df3 sxw = cross3(s, wt);
           const df lam = F2(d.lam_f), inv = F2(d.inv1pl2_f);
           if (noise) {
             w.x = df_add(w.x, F2(E[3 * t]));
@@ -242,10 +284,21 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
           w.y = df_mul(df_add(w.y, df_mul(lam, sxw.y)), inv);
           w.z = df_mul(df_add(w.z, df_mul(lam, sxw.z)), inv);
         }
-        const df3 inc = rot_increment(w, s, tau, d.rotation == SL_ROT_CAYLEY);
-        S[3 * t] = D2(df_add(s.x, inc.x));
-        S[3 * t + 1] = D2(df_add(s.y, inc.y));
-        S[3 * t + 2] = D2(df_add(s.z, inc.z));
+        df3 inc = rot_increment(w, s, tau, cayley);
+        if (aniso) {
+          s.x = df_add(s.x, inc.x); s.y = df_add(s.y, inc.y); s.z = df_add(s.z, inc.z);
+          const df3 i2 =
+              rot_increment(aniso_vec(d, s, F2(bath ? d.an_cl_f : d.an_c_f)), s, df_scale(tau, 0.5f), cayley);
+          s.x = df_add(s.x, i2.x); s.y = df_add(s.y, i2.y); s.z = df_add(s.z, i2.z);
+          inc.x = df_add(df_add(inc_a.x, inc.x), i2.x);
+          inc.y = df_add(df_add(inc_a.y, inc.y), i2.y);
+          inc.z = df_add(df_add(inc_a.z, inc.z), i2.z);
+          S[3 * t] = D2(s.x); S[3 * t + 1] = D2(s.y); S[3 * t + 2] = D2(s.z);
+        } else {
+          S[3 * t] = D2(df_add(s.x, inc.x));
+          S[3 * t + 1] = D2(df_add(s.y, inc.y));
+          S[3 * t + 2] = D2(df_add(s.z, inc.z));
+        }
         H[3 * t] = D2(inc.x);
         H[3 * t + 1] = D2(inc.y);
         H[3 * t + 2] = D2(inc.z);
@@ -264,7 +317,7 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
       float hx = d.zee_f[0].x, lx = d.zee_f[0].y;
       float hy = d.zee_f[1].x, ly = d.zee_f[1].y;
       float hz = d.zee_f[2].x, lz = d.zee_f[2].y;
-      ext_field(d, i, __ldg(d.exin + i), __ldg(d.exn + i), clo, chi, 0, hx, lx, hy, ly, hz, lz);
+      ext_field<SO>(d, i, __ldg(d.exin + i), __ldg(d.exn + i), clo, chi, 0, hx, lx, hy, ly, hz, lz);
       Q[3 * (size_t)i] = make_float2(hx, lx);
       Q[3 * (size_t)i + 1] = make_float2(hy, ly);
       Q[3 * (size_t)i + 2] = make_float2(hz, lz);
@@ -330,6 +383,9 @@ __global__ void k_decide(SlDev d) {
 // Exchange coefficients at the current positions (recomputed after every
 // drift, Sec. 3): J_ij = 4 alpha x (1 - gamma x) e^{-x}, x = r_ij^2/delta^2
 // (Eq. BSfunction), zero beyond the cutoff.
+// SO: also the spin-orbit tables (g1, d, e); the plain instance carries none
+// of that code.
+template <bool SO>
 __global__ void k_jtable(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
@@ -350,12 +406,31 @@ __global__ void k_jtable(SlDev d) {
     acc_prod(h, l, dd.z, dd.z);
     const df r2 = acc_done(h, l);
     df J = df_f(0.0f);
-    if (df_lt(r2, rc2)) {
+    const bool in = df_lt(r2, rc2);
+    if (in) {
       const df x = df_mul(r2, ix);
       const df ex = df_exp(df_neg(x));
       J = df_mul(df_mul(a4, x), df_mul(df_add_f(df_neg(df_mul(g, x)), 1.0f), ex));
     }
     d.exJ[e] = D2(J);
+    if (SO && d.exso) {
+      // g1(r), d(r) and e = (r_j - r_i)/r of the spin-orbit pair terms
+      const size_t P = (size_t)d.max_ex * n;
+      df g1 = df_f(0.0f), dm = df_f(0.0f), fpr;
+      df3 u;
+      u.x = u.y = u.z = df_f(0.0f);
+      if (in) {
+        const df rinv = df_rsqrt(r2);
+        u.x = df_mul(dd.x, rinv); u.y = df_mul(dd.y, rinv); u.z = df_mul(dd.z, rinv);
+        if (d.so & SL_SO_NEEL) bs_eval(d.ne_bs, r2, g1, fpr);
+        if (d.so & SL_SO_DMI) bs_eval(d.dm_bs, r2, dm, fpr);
+      }
+      d.exso[e] = D2(g1);
+      d.exso[P + e] = D2(dm);
+      d.exso[2 * P + e] = D2(u.x);
+      d.exso[3 * P + e] = D2(u.y);
+      d.exso[4 * P + e] = D2(u.z);
+    }
   }
 }
 
@@ -372,6 +447,7 @@ __device__ __forceinline__ df morse_coeff(df r2, df na, df r0, df c2, df& rinv) 
   return df_mul(df_mul(c2, rinv), df_mul(e, df_add_f(df_neg(e), 1.0f)));   // V'(r)/r
 }
 
+template <bool SO>
 __global__ void k_force(SlDev d, int kick) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
@@ -402,7 +478,44 @@ __global__ void k_force(SlDev d, int kick) {
       // 1 - 2 g x - x + g x^2 = 1 - x (1 + 2 g - g x)
       const df poly = df_add_f(df_neg(df_mul(x, df_add_f(df_sub(df_scale(g, 2.0f), gxm), 1.0f))), 1.0f);
       const df dJr = df_mul(df_mul(a8, ex), poly);
-      c = df_sub(c, df_mul(dJr, dot3(si, load_spin(d, j))));
+      const df3 sj = load_spin(d, j);
+      const df sij = dot3(si, sj);
+      c = df_sub(c, df_mul(dJr, sij));
+      if (SO && (d.so & (SL_SO_NEEL | SL_SO_DMI))) {
+        // Neel, U = -g1 Q, Q = (e.s_i)(e.s_j) - s_i.s_j/3 (A = e.s_j, B = e.s_i):
+        //   F_i = -g1' Q e - (g1/r) (A s_i + B s_j - 2 A B e);
+        // DMI, W = d e.X, X = s_i x s_j: F_i = d' (e.X) e + (d/r) (X - e (e.X)).
+        // With e = dd/r, the terms along e collect on dd (f' e = (f'/r) dd).
+        const df ri = df_rsqrt(r2);
+        df3 u;
+        u.x = df_mul(dd.x, ri); u.y = df_mul(dd.y, ri); u.z = df_mul(dd.z, ri);
+        df ci = df_f(0.0f), cj = df_f(0.0f), dr = df_f(0.0f);
+        df3 X;
+        X.x = X.y = X.z = df_f(0.0f);
+        if (d.so & SL_SO_NEEL) {
+          df g1, g1pr;
+          bs_eval(d.ne_bs, r2, g1, g1pr);
+          const df A = dot3(u, sj), Bv = dot3(u, si);
+          const df AB = df_mul(A, Bv);
+          const df Q = df_sub(AB, df_mul(sij, df_make(SL_INV_ODD3_HI, SL_INV_ODD3_LO)));
+          const df gr = df_mul(g1, ri);
+          c = df_sub(c, df_mul(g1pr, Q));
+          c = df_add(c, df_mul(df_scale(df_mul(gr, ri), 2.0f), AB));
+          ci = df_neg(df_mul(gr, A));
+          cj = df_neg(df_mul(gr, Bv));
+        }
+        if (d.so & SL_SO_DMI) {
+          df dm, dmpr;
+          bs_eval(d.dm_bs, r2, dm, dmpr);
+          X = cross3(si, sj);
+          const df eX = dot3(u, X);
+          dr = df_mul(dm, ri);
+          c = df_add(c, df_mul(eX, df_sub(dmpr, df_mul(dr, ri))));
+        }
+        acc_prod(fxh, fxl, ci, si.x); acc_prod(fxh, fxl, cj, sj.x); acc_prod(fxh, fxl, dr, X.x);
+        acc_prod(fyh, fyl, ci, si.y); acc_prod(fyh, fyl, cj, sj.y); acc_prod(fyh, fyl, dr, X.y);
+        acc_prod(fzh, fzl, ci, si.z); acc_prod(fzh, fzl, cj, sj.z); acc_prod(fzh, fzl, dr, X.z);
+      }
     }
     acc_prod(fxh, fxl, c, dd.x);
     acc_prod(fyh, fyl, c, dd.y);
@@ -442,9 +555,19 @@ __global__ void k_force(SlDev d, int kick) {
 
 __global__ void k_end_step(SlDev d) { d.ctrl->step += 1; }
 
+void launch_jtable(const SlDev& d, int grid, int block, cudaStream_t st) {
+  if (d.so) k_jtable<true><<<grid, block, 0, st>>>(d);
+  else k_jtable<false><<<grid, block, 0, st>>>(d);
+}
+
+void launch_force(const SlDev& d, int grid, int block, cudaStream_t st, int kick) {
+  if (d.so) k_force<true><<<grid, block, 0, st>>>(d, kick);
+  else k_force<false><<<grid, block, 0, st>>>(d, kick);
+}
+
 // The 16 passes of a spin half-op: colours 0..7 forward, then 7..0 backward.
 // Pass p reads the partial field written by pass p - 1 (none for p = 0).
-template <int SPB, int THREADS>
+template <int SPB, int THREADS, bool SO>
 void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
   int g = (d.s8 + SPB - 1) / SPB;
   size_t sm = sweep_smem_bytes(d.any_noise != 0, 12 * SPB);
@@ -455,18 +578,25 @@ void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
     const int next = p < 15 ? col[p + 1] : -1;
     const int pin = p > 0 ? (p - 1) & 1 : -1;
     const int pout = p < 15 ? p & 1 : -1;
-    k_sweep_pass<SPB, THREADS><<<g, THREADS, sm, st>>>(d, col[p], bwd[p], subpass0 + bwd[p], prev, next, pin, pout);
+    k_sweep_pass<SPB, THREADS, SO><<<g, THREADS, sm, st>>>(d, col[p], bwd[p], subpass0 + bwd[p], prev, next, pin,
+                                                           pout);
+  }
+}
+
+template <bool SO>
+void launch_half_op_so(const SlDev& d, cudaStream_t st, int subpass0) {
+  switch (d.tune_sweep) {
+    case 1: launch_half_op_t<32, 256, SO>(d, st, subpass0); break;
+    case 2: launch_half_op_t<16, 128, SO>(d, st, subpass0); break;
+    case 3: launch_half_op_t<16, 192, SO>(d, st, subpass0); break;
+    case 4: launch_half_op_t<8, 128, SO>(d, st, subpass0); break;
+    default: launch_half_op_t<32, 192, SO>(d, st, subpass0); break;
   }
 }
 
 void launch_half_op(const SlDev& d, cudaStream_t st, int subpass0) {
-  switch (d.tune_sweep) {
-    case 1: launch_half_op_t<32, 256>(d, st, subpass0); break;
-    case 2: launch_half_op_t<16, 128>(d, st, subpass0); break;
-    case 3: launch_half_op_t<16, 192>(d, st, subpass0); break;
-    case 4: launch_half_op_t<8, 128>(d, st, subpass0); break;
-    default: launch_half_op_t<32, 192>(d, st, subpass0); break;
-  }
+  if (d.so) launch_half_op_so<true>(d, st, subpass0);
+  else launch_half_op_so<false>(d, st, subpass0);
 }
 
 // threads per block of the per-atom kernels (autotuned)
@@ -492,6 +622,12 @@ __global__ void k_omega_all(SlDev d, double* out) {
     double J = double_from_float(J2.x) + double_from_float(J2.y);
     double4_32a sj = d.s[d.exj[e]];
     hx = fma(J, sj.x, hx); hy = fma(J, sj.y, hy); hz = fma(J, sj.z, hz);
+    if (d.exso) so_field_d(d, e, sj, hx, hy, hz);
+  }
+  if (d.so & SL_SO_ANISO) {
+    const double4_32a si = d.s[k];
+    const double c = 2.0 * d.an_K * (si.x * d.an_n[0] + si.y * d.an_n[1] + si.z * d.an_n[2]);
+    hx += c * d.an_n[0]; hy += c * d.an_n[1]; hz += c * d.an_n[2];
   }
   const double ih = 1.0 / SL_HBAR;
   size_t id = (size_t)d.perm[k];
@@ -508,21 +644,27 @@ __global__ void k_split_all(SlDev d, int only_if_rebuild) {
   store_spin_split(d, k, d.s[k]);
 }
 
+// Allow the sweep's dynamic shared memory (above the 48 KB default).
+template <bool SO>
+bool prepare_sweep() {
+  bool ok = true;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<32, 192, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 32)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<32, 256, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 32)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<16, 128, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 16)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<16, 192, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 16)) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_sweep_pass<8, 128, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sweep_smem_bytes(true, 12 * 8)) == cudaSuccess;
+  return ok;
+}
+
 }  // namespace
 
-// Allow the sweep's dynamic shared memory (above the 48 KB default).
 int sl_prepare_kernels() {
-  bool ok = true;
-  ok &= cudaFuncSetAttribute(k_sweep_pass<32, 192>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 32)) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_sweep_pass<32, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 32)) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_sweep_pass<16, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 16)) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_sweep_pass<16, 192>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 16)) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_sweep_pass<8, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 8)) == cudaSuccess;
+  const bool ok = prepare_sweep<false>() && prepare_sweep<true>();
   return ok ? SL_OK : SL_ERR_CUDA;
 }
 
@@ -533,8 +675,8 @@ int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild) {
 
 // Exchange table and forces at the current state (after init/rebuild/set_state).
 int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick) {
-  k_jtable<<<grid_tb(d), tb(d), 0, st>>>(d);
-  k_force<<<grid_tb(d), tb(d), 0, st>>>(d, kick);
+  launch_jtable(d, grid_tb(d), tb(d), st);
+  launch_force(d, grid_tb(d), tb(d), st, kick);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 
@@ -566,7 +708,7 @@ static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark
   }
   phase(SL_PHASE_JTABLE, 0);
   if (!e) e = sl_ml_launch_point(d, st, 0);
-  k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_jtable<false><<<gn, SL_BLOCK, 0, st>>>(d);
   phase(SL_PHASE_JTABLE, 1);
   nk += 5;
   phase(SL_PHASE_SPIN2, 0);
@@ -575,10 +717,10 @@ static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark
   nk += 16;
   phase(SL_PHASE_FORCE, 0);
   if (!e) e = sl_ml_launch_point(d, st, lat ? 3 : 0);
-  k_jtable<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_jtable<false><<<gn, SL_BLOCK, 0, st>>>(d);
   nk += 5;
   if (lat) {
-    k_force<<<gn, SL_BLOCK, 0, st>>>(d, 1);
+    k_force<false><<<gn, SL_BLOCK, 0, st>>>(d, 1);
     nk += 1;
   }
   phase(SL_PHASE_FORCE, 1);
@@ -612,7 +754,7 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
     if (e) return e;
     phase(SL_PHASE_DRIFT, 1);
     phase(SL_PHASE_JTABLE, 0);
-    k_jtable<<<grid_tb(d), tb(d), 0, st>>>(d);
+    launch_jtable(d, grid_tb(d), tb(d), st);
     phase(SL_PHASE_JTABLE, 1);
     nk += 2 + SL_REBUILD_KERNELS + 1;
   }
@@ -622,7 +764,7 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
   nk += 16;
   if (lat) {
     phase(SL_PHASE_FORCE, 0);
-    k_force<<<grid_tb(d), tb(d), 0, st>>>(d, 1);
+    launch_force(d, grid_tb(d), tb(d), st, 1);
     phase(SL_PHASE_FORCE, 1);
     nk += 1;
   }

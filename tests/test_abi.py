@@ -105,3 +105,25 @@ def test_batch_validation_on_host(lib):
     import ctypes as C
     size = C.c_size_t(0)
     assert L.sl_workspace_bytes_batch(arr, 0, C.byref(size)) == lib.SL_ERR_ARG
+
+
+def test_spin_orbit_validation_on_host(lib):
+    """Spin-orbit terms: a unit anisotropy axis, positive ranges, analytic
+    Hamiltonian only, the same terms in every replica; the pair tables add
+    workspace."""
+    from paper_1801_10233_gb300 import inputs
+    p, *_ = inputs.workload("fe_bcc_10x10x10_nve")
+    b0 = lib.workspace_bytes(p)
+    so = dict(p, aniso_K_eV=0.003, aniso_axis=[0.6, 0.0, 0.8], neel_alpha_eV=0.01, neel_delta_A=1.7,
+              dmi_alpha_eV=0.008, dmi_delta_A=1.9)
+    assert lib.workspace_bytes(so) > b0
+    for bad in (dict(so, aniso_axis=[0.6, 0.0, 0.81]), dict(so, neel_delta_A=0.0), dict(so, dmi_delta_A=-1.0),
+                dict(so, neel_gamma=float("nan")), dict(so, hamiltonian=1)):
+        with pytest.raises(lib.SlError) as e:
+            lib.workspace_bytes(bad)
+        assert e.value.code == lib.SL_ERR_ARG
+    # an axis that is not unit is fine while K = 0
+    assert lib.workspace_bytes(dict(p, aniso_axis=[1.0, 1.0, 1.0])) == b0
+    plist, *_ = inputs.replica_systems([5, 6], [100.0, 200.0], seed=3)
+    with pytest.raises(lib.SlError):
+        lib.workspace_bytes([dict(plist[0], dmi_alpha_eV=0.01), dict(plist[1])])

@@ -10,7 +10,9 @@ pytestmark = pytest.mark.gpu
 
 def test_one_bath_at_a_time():
     from paper_1801_10233_gb300 import relax
-    out = relax.run(cells=6, T=300.0, ps=1.0, dt=5e-4, every=200, prep_ps=0.5)
+    # lambda = 0.05 so that a 1 ps preparation brings the uniformly random
+    # spins down to the bath temperature (at 0.01 it takes ~2 ps)
+    out = relax.run(cells=6, T=300.0, ps=1.0, dt=5e-4, every=200, prep_ps=1.0, lam=0.05)
     a, b = out["spin_bath"], out["lattice_bath"]
     assert a["T_L"][0] == 0.0 and a["T_L"][-1] > 1.0          # lattice warmed by the spins
     assert 150.0 < sum(a["T_S"]) / len(a["T_S"]) < 450.0      # spins held near the bath
