@@ -50,6 +50,8 @@ class _Params(ctypes.Structure):
         ("an_K", ctypes.c_double), ("an_axis", ctypes.c_double * 3),
         ("neel_alpha", ctypes.c_double), ("neel_gamma", ctypes.c_double), ("neel_delta", ctypes.c_double),
         ("dmi_alpha", ctypes.c_double), ("dmi_gamma", ctypes.c_double), ("dmi_delta", ctypes.c_double),
+        ("eam_A", ctypes.c_double), ("eam_d", ctypes.c_double), ("eam_beta", ctypes.c_double),
+        ("ground_sub", ctypes.c_int32), ("pad2", ctypes.c_int32),
     ]
 
 
@@ -172,6 +174,9 @@ def make_params(p: dict, brute_force=False, lam=0.0, temperature=0.0, seed=0, re
     q.neel_delta = float(p.get("neel_delta_A", 1.0))
     q.dmi_alpha, q.dmi_gamma = float(p.get("dmi_alpha_eV", 0.0)), float(p.get("dmi_gamma", 0.0))
     q.dmi_delta = float(p.get("dmi_delta_A", 1.0))
+    q.eam_A, q.eam_d = float(p.get("eam_A_eV", 0.0)), float(p.get("eam_d_A", 1.0))
+    q.eam_beta = float(p.get("eam_beta", 0.0))
+    q.ground_sub = int(p.get("subtract_ground_exchange", 0))
     return q
 
 

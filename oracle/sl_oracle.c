@@ -116,6 +116,14 @@ typedef struct {
   double an_axis[3];     /* unit axis n */
   double neel_alpha, neel_gamma, neel_delta;   /* g1(r): H = -sum_{i<j} g1 ((e.s_i)(e.s_j) - s_i.s_j/3) */
   double dmi_alpha, dmi_gamma, dmi_delta;      /* d(r): H = sum_{i<j} d e_ij.(s_i x s_j), D_ij = d e_ij */
+  /* mechanical potential beyond the Morse pairs (App. B; 0: off): an
+   * embedding term sum_i F(rho_i), F(rho) = -A sqrt(rho), rho_i = sum_j f(r_ij),
+   * f(r) = (r - d)^2 + beta (r - d)^3 / d for r < d (Finnis-Sinclair form), and
+   * with ground_sub = 1 the collinear magnetic ground state taken out of the
+   * mechanical energy (Eq. app:mech1): + sum_{i<j} J(r_ij) */
+  double eam_A, eam_d, eam_beta;
+  int32_t ground_sub;
+  int32_t pad2;
 } orc_params;
 
 typedef struct {
@@ -223,6 +231,18 @@ static double morse_dV(const orc_params* p, double r) {
   double e = exp(-p->m_alpha * (r - p->m_r0));
   return p->m_D0 * (-2.0 * p->m_alpha * e * e + 2.0 * p->m_alpha * e);
 }
+/* Embedding term: density contribution f(r), f'(r) (r < d), F(rho), F'(rho). */
+static int has_eam(const orc_params* p) { return p->eam_A != 0.0; }
+static double eam_f(const orc_params* p, double r) {
+  double x = r - p->eam_d;
+  return r < p->eam_d ? x * x + p->eam_beta * x * x * x / p->eam_d : 0.0;
+}
+static double eam_df(const orc_params* p, double r) {
+  double x = r - p->eam_d;
+  return r < p->eam_d ? 2.0 * x + 3.0 * p->eam_beta * x * x / p->eam_d : 0.0;
+}
+static double eam_F(const orc_params* p, double rho) { return rho > 0.0 ? -p->eam_A * sqrt(rho) : 0.0; }
+static double eam_dF(const orc_params* p, double rho) { return rho > 0.0 ? -0.5 * p->eam_A / sqrt(rho) : 0.0; }
 
 /* Minimum-image separation d = r_j - r_i. */
 static void min_image(const orc_state* st, int i, int j, double d[3]) {
@@ -647,6 +667,17 @@ static void spin_half_op(orc_state* st, double h, int subpass0) {
 /* ------------------------------------------------------------------ */
 /* Forces (Eq. p_advance derived from the energy)                     */
 /* ------------------------------------------------------------------ */
+/* Embedding density of atom i from the Morse list (eam_d <= m_rc). */
+static double eam_rho(const orc_state* st, int i) {
+  double rho = 0.0;
+  for (int k = st->mo.off[i]; k < st->mo.off[i + 1]; ++k) {
+    double d[3];
+    min_image(st, i, st->mo.j[k], d);
+    rho += eam_f(&st->p, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+  }
+  return rho;
+}
+
 static void compute_forces(orc_state* st) {
   int n = st->n;
   if (st->p.hamiltonian == 1 && st->ml) {
@@ -679,7 +710,9 @@ static void compute_forces(orc_state* st) {
       double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       const double* sj = st->s + 3 * j;
       double sij = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
-      double c = -st->exdJ[k] * sij / r;        /* F_i -= J'(r) s_i.s_j (r_j - r_i)/r */
+      /* F_i -= J'(r) s_i.s_j (r_j - r_i)/r; the ground-state subtraction
+       * + J(r) adds J'(r) (r_j - r_i)/r */
+      double c = -st->exdJ[k] * (st->p.ground_sub ? sij - 1.0 : sij) / r;
       f[0] += c * d[0]; f[1] += c * d[1]; f[2] += c * d[2];
       const double* e = st->exE + 3 * k;
       if (has_neel(&st->p)) {
@@ -703,6 +736,24 @@ static void compute_forces(orc_state* st) {
         for (int q = 0; q < 3; ++q) f[q] += dp * eX * e[q] + dm / r * (X[q] - e[q] * eX);
       }
     }
+  }
+  if (has_eam(&st->p)) {
+    /* E = sum_i F(rho_i): F_i = sum_j (F'(rho_i) + F'(rho_j)) f'(r) (r_j - r_i)/r */
+    double* dF = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!dF) { if (st->err == ORC_OK) st->err = ORC_ERR_OOM; return; }
+    for (int i = 0; i < n; ++i) dF[i] = eam_dF(&st->p, eam_rho(st, i));
+    for (int i = 0; i < n; ++i) {
+      double* f = st->F + 3 * i;
+      for (int k = st->mo.off[i]; k < st->mo.off[i + 1]; ++k) {
+        int j = st->mo.j[k];
+        double d[3];
+        min_image(st, i, j, d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double c = (dF[i] + dF[j]) * eam_df(&st->p, r) / r;
+        f[0] += c * d[0]; f[1] += c * d[1]; f[2] += c * d[2];
+      }
+    }
+    free(dF);
   }
 }
 
@@ -759,7 +810,9 @@ orc_state* orc_create(const orc_params* p, const double* r, const double* v, con
   if (!p || p->n_atoms < 0 || p->mass <= 0.0 || p->hamiltonian < 0 || p->hamiltonian > 1 ||
       (p->hamiltonian == 1 && p->rotation != 0) || !(p->lat_gamma >= 0.0) || !(p->lat_temperature >= 0.0) ||
       (p->an_K != 0.0 && !(fabs(p->an_axis[0] * p->an_axis[0] + p->an_axis[1] * p->an_axis[1] +
-                                p->an_axis[2] * p->an_axis[2] - 1.0) <= 1e-12))) {
+                                p->an_axis[2] * p->an_axis[2] - 1.0) <= 1e-12)) ||
+      (p->eam_A != 0.0 && !(p->eam_d > 0.0 && p->eam_d <= p->m_rc)) ||
+      ((p->eam_A != 0.0 || p->ground_sub) && p->hamiltonian != 0)) {
     *err = ORC_ERR_ARG;
     return NULL;
   }
@@ -946,7 +999,10 @@ void orc_energy(const orc_state* st, double out[8]) {
       const double* si = st->s + 3 * i;
       const double* sj = st->s + 3 * j;
       ex -= st->exJ[k] * (si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2]);
+      if (st->p.ground_sub) em += st->exJ[k];
     }
+  if (has_eam(&st->p))
+    for (int i = 0; i < n; ++i) em += eam_F(&st->p, eam_rho(st, i));
   }
   double zf = st->p.mu_s * ORC_MUB;
   for (int i = 0; i < n; ++i) {
@@ -1018,6 +1074,8 @@ int orc_potential_energy(const orc_params* p, const double* r, const double* s, 
   int n = q.n_atoms;
   double em = 0.0, ex = 0.0, ez = 0.0, eo = 0.0;
   double vshift = q.morse_shift ? morse_V(&q, q.m_rc) : 0.0;
+  double* rho = (double*)calloc((size_t)(n ? n : 1), sizeof(double));
+  if (!rho) return ORC_ERR_OOM;
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j) {
       double d[3];
@@ -1027,11 +1085,16 @@ int orc_potential_energy(const orc_params* p, const double* r, const double* s, 
       }
       double rr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
       if (rr < q.m_rc) em += morse_V(&q, rr) - vshift;
+      if (rr < q.m_rc && has_eam(&q)) {
+        rho[i] += eam_f(&q, rr);
+        rho[j] += eam_f(&q, rr);
+      }
       if (rr < q.ex_rc) {
         const double* si = s + 3 * i;
         const double* sj = s + 3 * j;
         double sij = si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
         ex -= bs_J(&q, rr) * sij;
+        if (q.ground_sub) em += bs_J(&q, rr);
         double e[3] = {d[0] / rr, d[1] / rr, d[2] / rr};
         if (has_neel(&q)) {
           double a = e[0] * sj[0] + e[1] * sj[1] + e[2] * sj[2], b = e[0] * si[0] + e[1] * si[1] + e[2] * si[2];
@@ -1049,6 +1112,8 @@ int orc_potential_energy(const orc_params* p, const double* r, const double* s, 
     double sn = s[3 * i] * q.an_axis[0] + s[3 * i + 1] * q.an_axis[1] + s[3 * i + 2] * q.an_axis[2];
     eo -= q.an_K * sn * sn;
   }
+  for (int i = 0; i < n; ++i) em += eam_F(&q, rho[i]);
+  free(rho);
   out[0] = em; out[1] = ex; out[2] = ez; out[3] = em + ex + ez + eo; out[4] = eo;
   return ORC_OK;
 }
