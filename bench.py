@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=["fe_bcc_64x64x64_nve", "fe_bcc_10x10x10_nve", "fe_bcc_100x100x100_nve",
-                             "fe_bcc_batch256"])
+                             "fe_bcc_batch256", "fe_bcc_64x64x64_spin_orbit", "fe_bcc_64x64x64_eam"])
     ap.add_argument("--no-forms", action="store_true", help="skip the extra per-form measurements")
     ap.add_argument("--no-learned", action="store_true", help="skip training and judging the learned Hamiltonian")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
@@ -205,9 +205,13 @@ def build_workload(name, rank=0):
         return p, r, v, s, ("256 bcc-Fe replicas, sizes drawn from {8,12,16,20,24}^3 cells, Langevin spin "
                             "bath 50..1200 K (lambda 0.01), lattice NVE, dt 0.1 fs, one batched context")
     w = inputs.WORKLOADS[name]
-    p, r, v, s = inputs.bcc_fe_system(w["ncells"], w["seed"] + rank, T=w["T"], spins=w["spins"])
+    p, r, v, s = inputs.bcc_fe_system(w["ncells"], w["seed"] + rank, T=w["T"], spins=w["spins"],
+                                      **w.get("params", {}))
+    extra = w.get("params", {})
+    so = (" + uniaxial anisotropy, Neel and DMI terms" if "aniso_K_eV" in extra else "") + \
+         (" + Finnis-Sinclair embedding, ground-state exchange subtracted" if "eam_A_eV" in extra else "")
     return p, r, v, s, (f"bcc Fe {w['ncells']}^3 cells ({p['n_atoms']} atoms), Morse + Bethe-Slater exchange + "
-                        f"1 T Zeeman, {w['T']:.0f} K, {w['spins']} spins, NVE, dt 0.1 fs")
+                        f"1 T Zeeman{so}, {w['T']:.0f} K, {w['spins']} spins, NVE, dt 0.1 fs")
 
 
 def run_reference(args):
@@ -378,7 +382,8 @@ def run_ours(args):
     forms = None
     if rank == 0 and world == 1 and not args.no_forms and args.workload == DEFAULT_WORKLOAD:
         forms = {}
-        for name, steps in (("fe_bcc_batch256", 10), ("fe_bcc_10x10x10_nve", 100)):
+        for name, steps in (("fe_bcc_batch256", 10), ("fe_bcc_10x10x10_nve", 100),
+                            ("fe_bcc_64x64x64_spin_orbit", 50), ("fe_bcc_64x64x64_eam", 50)):
             fp, fr, fv, fs, fdesc = build_workload(name, 0)
             fn = int(sum(q["n_atoms"] for q in fp)) if isinstance(fp, list) else fp["n_atoms"]
             fsys = System(fp, fr, fv, fs, device=dev)
@@ -391,8 +396,13 @@ def run_ours(args):
             f1.record(fsys.stream)
             torch.cuda.synchronize()
             fms = f0.elapsed_time(f1) / steps
+            fsys.set_timing(True)
+            fsys.step(5)
+            fph = fsys.timing()
+            fsys.set_timing(False)
             forms[name] = {"value": fn / (fms * 1e-3), "unit": UNIT, "ms_per_step": fms, "steps": steps,
-                           "n_atoms": fn, "workload": fdesc, "launch_shape": ftune}
+                           "n_atoms": fn, "workload": fdesc, "launch_shape": ftune,
+                           "phase_ms_per_step": {k: v_[0] / max(1, v_[1]) for k, v_ in fph.items()}}
             fsys.close()
             del fsys
         if not args.no_learned:

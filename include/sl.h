@@ -117,6 +117,18 @@ typedef struct sl_params {
   double aniso_axis[3];
   double neel_alpha_eV, neel_gamma, neel_delta_A;
   double dmi_alpha_eV, dmi_gamma, dmi_delta_A;
+  /* Mechanical potential beyond the Morse pairs (App. B), analytic Hamiltonian
+   * only; zero turns each off.  Embedding term sum_i F(rho_i) of the embedded-atom
+   * method in the Finnis-Sinclair form: F(rho) = -eam_A_eV sqrt(rho) (0 at
+   * rho = 0), rho_i = sum_j f(r_ij), f(r) = (r - d)^2 + beta (r - d)^3 / d for
+   * r < d = eam_d_A (0 < d <= morse_rc_A, else SL_ERR_ARG), 0 beyond.  With
+   * subtract_ground_exchange = 1 the collinear magnetic ground state is taken
+   * out of the mechanical energy (Eq. app:mech1): + J(r_ij) per unordered pair,
+   * so the exchange adds neither energy nor force to a collinear state.  Both
+   * are reported in E_morse (the mechanical energy) by sl_energy. */
+  double eam_A_eV, eam_d_A, eam_beta;
+  int32_t subtract_ground_exchange;
+  int32_t reserved2;
 } sl_params;
 
 typedef struct sl_ctx sl_ctx;  /* opaque, owned by the library */
@@ -173,7 +185,8 @@ int sl_step(sl_ctx* ctx, int32_t n_steps);
 int sl_set_dt(sl_ctx* ctx, double dt_ps);
 int sl_set_field(sl_ctx* ctx, const double H_tesla[3]);
 
-/* out[8] (host) = E_kin, E_morse, E_exchange, E_zeeman, E_total (eV),
+/* out[8] (host) = E_kin, E_morse (the mechanical energy: Morse, embedding and
+ * ground-state subtraction), E_exchange, E_zeeman, E_total (eV),
  * T_L (Eq. lattice_temperature, K), T_S (Eq. spin_temperature, K), E_spin_orbit
  * (anisotropy + Neel + DMI, eV; part of E_total).
  * Pair energies count each unordered pair once.  For a batch: energies summed
@@ -307,8 +320,8 @@ int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void*
  *   omega(s) = (mu_s mu_B H - sum_j (P_ij + 2 Q_ij s.s_j) s_j) / hbar,
  *   P_ij = sum_k (G_i+G_j)[3k+1] g_k(r_ij),  Q_ij = sum_k (G_i+G_j)[3k+2] g_k(r_ij),
  * with the current neighbour spins.  The spin bath (lambda, temperature_K),
- * the Cayley propagator and the spin-orbit terms are not available in this
- * mode (SL_ERR_ARG).
+ * the Cayley propagator, the spin-orbit terms, the embedding term and the
+ * ground-state subtraction are not available in this mode (SL_ERR_ARG).
  * ------------------------------------------------------------------------ */
 #define SL_ML_NF 48
 #define SL_ML_NH 64

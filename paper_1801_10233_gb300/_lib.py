@@ -57,6 +57,8 @@ class sl_params(ctypes.Structure):
         ("aniso_K_eV", ctypes.c_double), ("aniso_axis", ctypes.c_double * 3),
         ("neel_alpha_eV", ctypes.c_double), ("neel_gamma", ctypes.c_double), ("neel_delta_A", ctypes.c_double),
         ("dmi_alpha_eV", ctypes.c_double), ("dmi_gamma", ctypes.c_double), ("dmi_delta_A", ctypes.c_double),
+        ("eam_A_eV", ctypes.c_double), ("eam_d_A", ctypes.c_double), ("eam_beta", ctypes.c_double),
+        ("subtract_ground_exchange", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -171,6 +173,10 @@ def make_params(p: dict) -> sl_params:
     q.dmi_alpha_eV = float(p.get("dmi_alpha_eV", 0.0))
     q.dmi_gamma = float(p.get("dmi_gamma", 0.0))
     q.dmi_delta_A = float(p.get("dmi_delta_A", 1.0))
+    q.eam_A_eV = float(p.get("eam_A_eV", 0.0))
+    q.eam_d_A = float(p.get("eam_d_A", 1.0))
+    q.eam_beta = float(p.get("eam_beta", 0.0))
+    q.subtract_ground_exchange = int(p.get("subtract_ground_exchange", 0))
     return q
 
 

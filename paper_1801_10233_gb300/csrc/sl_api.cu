@@ -93,6 +93,11 @@ int validate(const sl_params* p) {
   }
   if (p->neel_alpha_eV != 0.0 && !(p->neel_delta_A > 0.0)) return SL_ERR_ARG;
   if (p->dmi_alpha_eV != 0.0 && !(p->dmi_delta_A > 0.0)) return SL_ERR_ARG;
+  // embedding term and ground-state subtraction: analytic Hamiltonian only
+  if (!std::isfinite(p->eam_A_eV) || !std::isfinite(p->eam_beta)) return SL_ERR_ARG;
+  if (p->subtract_ground_exchange != 0 && p->subtract_ground_exchange != 1) return SL_ERR_ARG;
+  if ((p->eam_A_eV != 0.0 || p->subtract_ground_exchange) && p->hamiltonian != SL_HAM_ANALYTIC) return SL_ERR_ARG;
+  if (p->eam_A_eV != 0.0 && !(p->eam_d_A > 0.0 && p->eam_d_A <= p->morse_rc_A)) return SL_ERR_ARG;
   double rc = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
   for (int a = 0; a < 3; ++a)
     if (!(p->box[a] >= 2.0 * rc)) return SL_ERR_BOX;
@@ -121,7 +126,9 @@ int validate_batch(const sl_params* p, int nrep) {
                 a.lambda == b.lambda && a.seed == b.seed && a.hamiltonian == b.hamiltonian &&
                 a.aniso_K_eV == b.aniso_K_eV && a.neel_alpha_eV == b.neel_alpha_eV &&
                 a.neel_gamma == b.neel_gamma && a.neel_delta_A == b.neel_delta_A &&
-                a.dmi_alpha_eV == b.dmi_alpha_eV && a.dmi_gamma == b.dmi_gamma && a.dmi_delta_A == b.dmi_delta_A;
+                a.dmi_alpha_eV == b.dmi_alpha_eV && a.dmi_gamma == b.dmi_gamma && a.dmi_delta_A == b.dmi_delta_A &&
+                a.eam_A_eV == b.eam_A_eV && a.eam_d_A == b.eam_d_A && a.eam_beta == b.eam_beta &&
+                a.subtract_ground_exchange == b.subtract_ground_exchange;
     for (int c = 0; c < 3; ++c) same = same && a.H_tesla[c] == b.H_tesla[c] && a.aniso_axis[c] == b.aniso_axis[c];
     if (!same) return SL_ERR_ARG;
   }
@@ -265,6 +272,15 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   }
   d.an_c_f = split_f2(2.0 * p->aniso_K_eV / SL_HBAR);
   d.an_cl_f = split_f2(2.0 * p->aniso_K_eV / SL_HBAR / (1.0 + p->lambda * p->lambda));
+  // embedding term and ground-state subtraction
+  d.mech = (p->eam_A_eV != 0.0 ? SL_MECH_EAM : 0) | (p->subtract_ground_exchange ? SL_MECH_GROUND : 0);
+  d.em_A = p->eam_A_eV;
+  d.em_d = p->eam_A_eV != 0.0 ? p->eam_d_A : 1.0;
+  d.em_beta = p->eam_beta;
+  d.em_d_f = split_f2(d.em_d);
+  d.em_d2_f = split_f2(d.em_d * d.em_d);
+  d.em_bd_f = split_f2(p->eam_beta / d.em_d);
+  d.em_hA_f = split_f2(0.5 * p->eam_A_eV);
   {
     const double nd = p->neel_alpha_eV != 0.0 ? p->neel_delta_A : 1.0;
     const double dd = p->dmi_alpha_eV != 0.0 ? p->dmi_delta_A : 1.0;
@@ -292,6 +308,8 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_exJ = L.take<float2>(nn * d.max_ex);
   const bool so_pairs = d.so != 0;   // the spin-orbit sweep reads the tables whenever a term is on
   size_t o_exso = so_pairs ? L.take<float2>(5 * nn * d.max_ex) : 0;
+  const bool eam = (d.mech & SL_MECH_EAM) != 0;
+  size_t o_emfp = eam ? L.take<float2>(nn) : 0;
   size_t o_rh = L.take<float4>(nn), o_rm = L.take<float4>(nn), o_rl = L.take<float4>(nn);
   size_t o_sdf = L.take<float4>(2 * nn);
   size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
@@ -340,6 +358,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn); d.exin = (int*)(base + o_exin);
     d.exJ = (float2*)(base + o_exJ);
     d.exso = so_pairs ? (float2*)(base + o_exso) : nullptr;
+    d.em_fp = eam ? (float2*)(base + o_emfp) : nullptr;
     d.rh = (float4*)(base + o_rh); d.rm = (float4*)(base + o_rm); d.rl = (float4*)(base + o_rl);
     d.sdf = (float4*)(base + o_sdf);
     d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);

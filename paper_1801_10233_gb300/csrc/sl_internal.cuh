@@ -51,6 +51,8 @@ struct SlRep {
 
 // Spin-orbit term bits of SlDev::so.
 enum { SL_SO_ANISO = 1, SL_SO_NEEL = 2, SL_SO_DMI = 4 };
+// Mechanical-potential bits of SlDev::mech: embedding term, ground-state subtraction.
+enum { SL_MECH_EAM = 1, SL_MECH_GROUND = 2 };
 
 // Double-float constants of one f(r) = 4 alpha x (1 - gamma x) e^{-x},
 // x = r^2/delta^2 (Eq. BSfunction): 1/delta^2, 4 alpha, gamma, 8 alpha/delta^2.
@@ -97,6 +99,12 @@ struct SlDev {
   float2 an_c_f, an_cl_f, an_n_f[3];          // 2K/hbar, 2K/(hbar (1 + lambda^2)), n
   SlBsF ne_bs, dm_bs;                         // double-float constants of g1 and d
 
+  // mechanical potential beyond the Morse pairs (App. B): mech = SL_MECH_EAM |
+  // SL_MECH_GROUND bits; F(rho) = -A sqrt(rho), f(r) = (r - d)^2 + beta (r - d)^3 / d
+  int mech;
+  double em_A, em_d, em_beta;
+  float2 em_d_f, em_d2_f, em_bd_f, em_hA_f;   // d, d^2, beta/d, A/2
+
   const SlRep* reps;        // [nrep]
   int* arep;                // replica of each sorted atom
   int* tarep;               // rebuild scratch
@@ -116,6 +124,8 @@ struct SlDev {
   // [5][max_ex][n] g1, d, e_x, e_y, e_z (hi, lo) at current r, e = (r_j - r_i)/r;
   // zero beyond ex_rc (NULL when so == 0)
   float2 *exso;
+  // [n] F'(rho_i) (hi, lo) at current r, sorted order (NULL unless mech has SL_MECH_EAM)
+  float2 *em_fp;
   int *mj, *mn;             // [max_m][n] neighbour-major, counts
   // sweep scratch for blocks whose atoms exceed shared memory: [3 n] each
   float2 *hbuf, *sbuf, *ebuf;

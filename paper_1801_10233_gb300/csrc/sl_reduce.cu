@@ -21,6 +21,7 @@ __global__ void k_obs_atoms(SlDev d) {
   q[0] = 0.5 * d.mass * (v.x * v.x + v.y * v.y + v.z * v.z) / SL_FTOA;
   double em = 0.0;
   const int nm = (d.ham == SL_HAM_LEARNED && d.ctrl->ml_use) ? 0 : d.mn[i];
+  double rho = 0.0;
   for (int k = 0; k < nm; ++k) {
     const int j = d.mj[(size_t)k * d.n + i];
     const double3 dd = sl_min_image(R, ri, d.r[j]);
@@ -29,8 +30,14 @@ __global__ void k_obs_atoms(SlDev d) {
       const double e = exp(-d.m_alpha * (sqrt(r2) - d.m_r0));
       em += d.m_D0 * (e * e - 2.0 * e) - d.m_vshift;
     }
+    if ((d.mech & SL_MECH_EAM) && r2 < d.em_d * d.em_d) {
+      const double x = sqrt(r2) - d.em_d;
+      rho += x * x + d.em_beta * x * x * x / d.em_d;
+    }
   }
   q[1] = 0.5 * em;
+  // embedding energy F(rho_i) = -A sqrt(rho_i), one per atom
+  if (d.mech & SL_MECH_EAM) q[1] += rho > 0.0 ? -d.em_A * sqrt(rho) : 0.0;
   double hx = d.zee[0], hy = d.zee[1], hz = d.zee[2];
   double ex = 0.0;
   const bool learned = d.ham == SL_HAM_LEARNED && d.ctrl->ml_use;
@@ -48,6 +55,7 @@ __global__ void k_obs_atoms(SlDev d) {
     const double J = double_from_float(J2.x) + double_from_float(J2.y);
     const double4_32a sj = d.s[d.exj[e]];
     ex += J * (si.x * sj.x + si.y * sj.y + si.z * sj.z);
+    if (d.mech & SL_MECH_GROUND) q[1] += 0.5 * J;   // + J(r) per unordered pair
     hx = fma(J, sj.x, hx); hy = fma(J, sj.y, hy); hz = fma(J, sj.z, hz);
     if (d.exso) {
       so_field_d(d, e, sj, hx, hy, hz);

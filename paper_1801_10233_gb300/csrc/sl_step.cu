@@ -434,6 +434,45 @@ __global__ void k_jtable(SlDev d) {
   }
 }
 
+// Embedding density rho_i = sum_j f(r_ij) over the Morse list (r < d),
+// f(r) = x^2 (1 + (beta/d) x), x = r - d, and F'(rho_i) = -(A/2)/sqrt(rho_i)
+// (0 at rho = 0), at the current positions: recomputed with the exchange
+// table after every drift, read by the force kernel for both atoms of a pair.
+__global__ void k_density(SlDev d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n) return;
+  const p3 pi = load_pos(d, i);
+  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
+  const int nm = d.mn[i];
+  const df dc = F2(d.em_d_f), d2 = F2(d.em_d2_f), bd = F2(d.em_bd_f);
+  const float d2_hi = d2.hi * 1.0001f;
+  float h = 0.0f, l = 0.0f;
+  for (int k = 0; k < nm; ++k) {
+    const int j = __ldg(d.mj + (size_t)k * d.n + i);
+    const df3 dd = pair_sep(B, pi, load_pos(d, j));
+    const float r2f = dd.x.hi * dd.x.hi + dd.y.hi * dd.y.hi + dd.z.hi * dd.z.hi;
+    if (r2f > d2_hi) continue;
+    float a = 0.0f, b = 0.0f;
+    acc_prod(a, b, dd.x, dd.x);
+    acc_prod(a, b, dd.y, dd.y);
+    acc_prod(a, b, dd.z, dd.z);
+    const df r2 = acc_done(a, b);
+    if (!df_lt(r2, d2)) continue;
+    const df x = df_sub(df_mul(r2, df_rsqrt(r2)), dc);
+    acc_prod(h, l, df_sqr(x), df_add_f(df_mul(bd, x), 1.0f));
+  }
+  const df rho = acc_done(h, l);
+  const df fp = rho.hi > 0.0f ? df_neg(df_mul(F2(d.em_hA_f), df_rsqrt(rho))) : df_f(0.0f);
+  d.em_fp[i] = D2(fp);
+}
+
+// (F'(rho_i) + F'(rho_j)) f'(r)/r of the embedding term, f'(r) = x (2 + 3 (beta/d) x).
+__device__ __forceinline__ df eam_coeff(const SlDev& d, df r2, df rinv, df fpij) {
+  const df x = df_sub(df_mul(r2, rinv), F2(d.em_d_f));
+  const df fpr = df_mul(x, df_add_f(df_mul(df_mul_f(F2(d.em_bd_f), 3.0f), x), 2.0f));
+  return df_mul(fpij, df_mul(fpr, rinv));
+}
+
 // Forces at the current state, Eq. p_advance written as -dH/dr_i:
 //   F_i = sum_j [V'(r) - J'(r) (s_i.s_j)] (r_j - r_i)/r
 // with V'(r)/r = 2 a D0 e (1 - e)/r, e = exp(-a (r - r0)) (Morse, r < morse_rc)
@@ -447,7 +486,8 @@ __device__ __forceinline__ df morse_coeff(df r2, df na, df r0, df c2, df& rinv) 
   return df_mul(df_mul(c2, rinv), df_mul(e, df_add_f(df_neg(e), 1.0f)));   // V'(r)/r
 }
 
-template <bool SO>
+// MECH: also the embedding term and the ground-state subtraction.
+template <bool SO, bool MECH>
 __global__ void k_force(SlDev d, int kick) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
@@ -460,6 +500,9 @@ __global__ void k_force(SlDev d, int kick) {
   const df na = F2(d.m_nalpha_f), r0 = F2(d.m_r0_f), c2 = F2(d.m_c2_f), rc2 = F2(d.m_rc2_f);
   const df ix = F2(d.ex_ix_f), g = F2(d.ex_g_f), a8 = F2(d.ex_8ad2_f), xrc2 = F2(d.ex_rc2_f);
   const float rc2_hi = rc2.hi * 1.0001f;
+  const bool eam = MECH && (d.mech & SL_MECH_EAM);
+  const df ed2 = F2(d.em_d2_f);
+  const df fpi = eam ? F2(__ldg(d.em_fp + i)) : df_f(0.0f);
   // entries 0..ne-1: exchange neighbours (also inside the Morse cutoff)
   for (int k = 0; k < ne; ++k) {
     const int j = __ldg(d.mj + (size_t)k * d.n + i);
@@ -471,6 +514,7 @@ __global__ void k_force(SlDev d, int kick) {
     const df r2 = acc_done(h, l);
     df rinv;
     df c = df_lt(r2, rc2) ? morse_coeff(r2, na, r0, c2, rinv) : df_f(0.0f);
+    if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
     if (df_lt(r2, xrc2)) {
       const df x = df_mul(r2, ix);
       const df ex = df_exp(df_neg(x));
@@ -481,6 +525,7 @@ __global__ void k_force(SlDev d, int kick) {
       const df3 sj = load_spin(d, j);
       const df sij = dot3(si, sj);
       c = df_sub(c, df_mul(dJr, sij));
+      if (MECH && (d.mech & SL_MECH_GROUND)) c = df_add(c, dJr);   // + J(r): -dJr (s_i.s_j - 1)
       if (SO && (d.so & (SL_SO_NEEL | SL_SO_DMI))) {
         // Neel, U = -g1 Q, Q = (e.s_i)(e.s_j) - s_i.s_j/3 (A = e.s_j, B = e.s_i):
         //   F_i = -g1' Q e - (g1/r) (A s_i + B s_j - 2 A B e);
@@ -535,7 +580,8 @@ __global__ void k_force(SlDev d, int kick) {
     const df r2 = acc_done(h, l);
     if (!df_lt(r2, rc2)) continue;
     df rinv;
-    const df c = morse_coeff(r2, na, r0, c2, rinv);
+    df c = morse_coeff(r2, na, r0, c2, rinv);
+    if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
     acc_prod(fxh, fxl, c, dd.x);
     acc_prod(fyh, fyl, c, dd.y);
     acc_prod(fzh, fzl, c, dd.z);
@@ -561,8 +607,21 @@ void launch_jtable(const SlDev& d, int grid, int block, cudaStream_t st) {
 }
 
 void launch_force(const SlDev& d, int grid, int block, cudaStream_t st, int kick) {
-  if (d.so) k_force<true><<<grid, block, 0, st>>>(d, kick);
-  else k_force<false><<<grid, block, 0, st>>>(d, kick);
+  if (d.so && d.mech) k_force<true, true><<<grid, block, 0, st>>>(d, kick);
+  else if (d.so) k_force<true, false><<<grid, block, 0, st>>>(d, kick);
+  else if (d.mech) k_force<false, true><<<grid, block, 0, st>>>(d, kick);
+  else k_force<false, false><<<grid, block, 0, st>>>(d, kick);
+}
+
+// The per-step tables at the current positions: J (and the spin-orbit
+// tables), then the embedding density.  Returns the kernels launched.
+int launch_tables(const SlDev& d, int grid, int block, cudaStream_t st) {
+  launch_jtable(d, grid, block, st);
+  if (d.mech & SL_MECH_EAM) {
+    k_density<<<grid, block, 0, st>>>(d);
+    return 2;
+  }
+  return 1;
 }
 
 // The 16 passes of a spin half-op: colours 0..7 forward, then 7..0 backward.
@@ -675,7 +734,7 @@ int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild) {
 
 // Exchange table and forces at the current state (after init/rebuild/set_state).
 int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick) {
-  launch_jtable(d, grid_tb(d), tb(d), st);
+  launch_tables(d, grid_tb(d), tb(d), st);
   launch_force(d, grid_tb(d), tb(d), st, kick);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
@@ -720,7 +779,7 @@ static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark
   k_jtable<false><<<gn, SL_BLOCK, 0, st>>>(d);
   nk += 5;
   if (lat) {
-    k_force<false><<<gn, SL_BLOCK, 0, st>>>(d, 1);
+    k_force<false, false><<<gn, SL_BLOCK, 0, st>>>(d, 1);
     nk += 1;
   }
   phase(SL_PHASE_FORCE, 1);
@@ -754,9 +813,9 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
     if (e) return e;
     phase(SL_PHASE_DRIFT, 1);
     phase(SL_PHASE_JTABLE, 0);
-    launch_jtable(d, grid_tb(d), tb(d), st);
+    const int ntab = launch_tables(d, grid_tb(d), tb(d), st);
     phase(SL_PHASE_JTABLE, 1);
-    nk += 2 + SL_REBUILD_KERNELS + 1;
+    nk += 2 + SL_REBUILD_KERNELS + ntab;
   }
   phase(SL_PHASE_SPIN2, 0);
   launch_half_op(d, st, 2);

@@ -137,9 +137,16 @@ def bcc_fe_system(ncells, seed, T=200.0, sigma=0.01, spins="uniform", a=LATTICE_
 SPIN_ORBIT = dict(aniso_K_eV=1e-4, aniso_axis=[0.0, 0.0, 1.0], neel_alpha_eV=1e-3, neel_gamma=0.1,
                   neel_delta_A=1.7, dmi_alpha_eV=1e-3, dmi_gamma=0.3, dmi_delta_A=1.9)
 
-# The six workloads: plain 10^3 cells, plain 64^3 cells, 256 batched
+# Embedding term of the 64^3-cell embedded-atom workload (App. B): the
+# Finnis-Sinclair form F(rho) = -A sqrt(rho), f(r) = (r - d)^2 + beta (r - d)^3/d
+# on top of the Morse pairs, with the collinear magnetic ground state
+# subtracted (Eq. app:mech1).  d = 3.57 A takes the first two bcc shells;
+# A and beta are chosen to exercise and time the terms, not fitted.
+EMBEDDING = dict(eam_A_eV=0.5, eam_d_A=3.569745, eam_beta=1.8, subtract_ground_exchange=1)
+
+# The seven workloads: plain 10^3 cells, plain 64^3 cells, 256 batched
 # replicas, learned 40^3 cells, large 100^3 cells, 64^3 cells with the
-# spin-orbit terms.
+# spin-orbit terms, 64^3 cells with the embedding term.
 WORKLOADS = {
     "fe_bcc_10x10x10_nve": dict(ncells=10, seed=18010, T=200.0, spins="uniform", steps=1000),
     "fe_bcc_64x64x64_nve": dict(ncells=64, seed=18011, T=200.0, spins="cone10", steps=200),
@@ -147,6 +154,7 @@ WORKLOADS = {
     "fe_bcc_100x100x100_nve": dict(ncells=100, seed=18014, T=300.0, spins="uniform", steps=1000),
     "fe_bcc_64x64x64_spin_orbit": dict(ncells=64, seed=18017, T=200.0, spins="cone10", steps=200,
                                        params=SPIN_ORBIT),
+    "fe_bcc_64x64x64_eam": dict(ncells=64, seed=18018, T=200.0, spins="cone10", steps=200, params=EMBEDDING),
 }
 
 

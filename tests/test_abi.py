@@ -127,3 +127,23 @@ def test_spin_orbit_validation_on_host(lib):
     plist, *_ = inputs.replica_systems([5, 6], [100.0, 200.0], seed=3)
     with pytest.raises(lib.SlError):
         lib.workspace_bytes([dict(plist[0], dmi_alpha_eV=0.01), dict(plist[1])])
+
+
+def test_embedding_validation_on_host(lib):
+    """Embedding term: 0 < d <= morse_rc, analytic Hamiltonian only, a 0/1
+    subtraction flag, the same in every replica; it adds one per-atom table."""
+    from paper_1801_10233_gb300 import inputs
+    p, *_ = inputs.workload("fe_bcc_10x10x10_nve")
+    b0 = lib.workspace_bytes(p)
+    e = dict(p, eam_A_eV=0.5, eam_d_A=3.57, eam_beta=1.8)
+    assert lib.workspace_bytes(e) > b0
+    assert lib.workspace_bytes(dict(p, subtract_ground_exchange=1)) == b0
+    for bad in (dict(e, eam_d_A=0.0), dict(e, eam_d_A=6.5), dict(e, hamiltonian=1),
+                dict(p, subtract_ground_exchange=2), dict(p, subtract_ground_exchange=1, hamiltonian=1),
+                dict(e, eam_beta=float("inf"))):
+        with pytest.raises(lib.SlError) as err:
+            lib.workspace_bytes(bad)
+        assert err.value.code == lib.SL_ERR_ARG
+    plist, *_ = inputs.replica_systems([5, 6], [100.0, 200.0], seed=3)
+    with pytest.raises(lib.SlError):
+        lib.workspace_bytes([dict(plist[0], eam_A_eV=0.5), dict(plist[1])])
