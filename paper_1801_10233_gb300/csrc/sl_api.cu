@@ -274,6 +274,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   d.an_cl_f = split_f2(2.0 * p->aniso_K_eV / SL_HBAR / (1.0 + p->lambda * p->lambda));
   // embedding term and ground-state subtraction
   d.mech = (p->eam_A_eV != 0.0 ? SL_MECH_EAM : 0) | (p->subtract_ground_exchange ? SL_MECH_GROUND : 0);
+  d.em_fused = p->eam_A_eV != 0.0 && p->eam_d_A <= p->ex_rc_A;
   d.em_A = p->eam_A_eV;
   d.em_d = p->eam_A_eV != 0.0 ? p->eam_d_A : 1.0;
   d.em_beta = p->eam_beta;

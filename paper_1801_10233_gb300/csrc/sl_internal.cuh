@@ -102,6 +102,7 @@ struct SlDev {
   // mechanical potential beyond the Morse pairs (App. B): mech = SL_MECH_EAM |
   // SL_MECH_GROUND bits; F(rho) = -A sqrt(rho), f(r) = (r - d)^2 + beta (r - d)^3 / d
   int mech;
+  int em_fused;                               // d <= ex_rc: the density comes from the exchange entries
   double em_A, em_d, em_beta;
   float2 em_d_f, em_d2_f, em_bd_f, em_hA_f;   // d, d^2, beta/d, A/2
 

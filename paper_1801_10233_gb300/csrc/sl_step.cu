@@ -383,9 +383,24 @@ __global__ void k_decide(SlDev d) {
 // Exchange coefficients at the current positions (recomputed after every
 // drift, Sec. 3): J_ij = 4 alpha x (1 - gamma x) e^{-x}, x = r_ij^2/delta^2
 // (Eq. BSfunction), zero beyond the cutoff.
-// SO: also the spin-orbit tables (g1, d, e); the plain instance carries none
-// of that code.
-template <bool SO>
+// Embedding density: (h, l) += f(r) = x^2 (1 + (beta/d) x), x = r - d, for r^2 < d^2.
+__device__ __forceinline__ void eam_f_acc(const SlDev& d, df r2, float& h, float& l) {
+  if (!df_lt(r2, F2(d.em_d2_f))) return;
+  const df x = df_sub(df_mul(r2, df_rsqrt(r2)), F2(d.em_d_f));
+  acc_prod(h, l, df_sqr(x), df_add_f(df_mul(F2(d.em_bd_f), x), 1.0f));
+}
+
+// F'(rho_i) = -(A/2)/sqrt(rho_i) (0 at rho = 0) into the per-atom table.
+__device__ __forceinline__ void eam_store_fp(const SlDev& d, int i, float h, float l) {
+  const df rho = acc_done(h, l);
+  const df fp = rho.hi > 0.0f ? df_neg(df_mul(F2(d.em_hA_f), df_rsqrt(rho))) : df_f(0.0f);
+  d.em_fp[i] = D2(fp);
+}
+
+// SO: also the spin-orbit tables (g1, d, e); DENS: also the embedding density
+// (when its cutoff d is within the exchange cutoff, the exchange entries hold
+// every pair it needs).  The plain instance carries none of that code.
+template <bool SO, bool DENS>
 __global__ void k_jtable(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
@@ -396,6 +411,7 @@ __global__ void k_jtable(SlDev d) {
   const size_t n = (size_t)d.n;
   const df ix = F2(d.ex_ix_f), a4 = F2(d.ex_4a_f), g = F2(d.ex_g_f);
   const df rc2 = F2(d.ex_rc2_f);
+  float rh = 0.0f, rl = 0.0f;   // embedding density
   for (int k = 0; k < ne; ++k) {
     const size_t e = (size_t)k * n + i;
     const int j = __ldg(d.exj + e);
@@ -405,6 +421,7 @@ __global__ void k_jtable(SlDev d) {
     acc_prod(h, l, dd.y, dd.y);
     acc_prod(h, l, dd.z, dd.z);
     const df r2 = acc_done(h, l);
+    if (DENS) eam_f_acc(d, r2, rh, rl);
     df J = df_f(0.0f);
     const bool in = df_lt(r2, rc2);
     if (in) {
@@ -432,20 +449,20 @@ __global__ void k_jtable(SlDev d) {
       d.exso[4 * P + e] = D2(u.z);
     }
   }
+  if (DENS) eam_store_fp(d, i, rh, rl);
 }
 
-// Embedding density rho_i = sum_j f(r_ij) over the Morse list (r < d),
-// f(r) = x^2 (1 + (beta/d) x), x = r - d, and F'(rho_i) = -(A/2)/sqrt(rho_i)
-// (0 at rho = 0), at the current positions: recomputed with the exchange
-// table after every drift, read by the force kernel for both atoms of a pair.
+// Embedding density rho_i = sum_j f(r_ij) over the Morse list (r < d) and
+// F'(rho_i), at the current positions, when d lies beyond the exchange cutoff
+// (otherwise k_jtable computes it): recomputed after every drift, read by
+// the force kernel for both atoms of a pair.
 __global__ void k_density(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const p3 pi = load_pos(d, i);
   const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
   const int nm = d.mn[i];
-  const df dc = F2(d.em_d_f), d2 = F2(d.em_d2_f), bd = F2(d.em_bd_f);
-  const float d2_hi = d2.hi * 1.0001f;
+  const float d2_hi = F2(d.em_d2_f).hi * 1.0001f;
   float h = 0.0f, l = 0.0f;
   for (int k = 0; k < nm; ++k) {
     const int j = __ldg(d.mj + (size_t)k * d.n + i);
@@ -456,14 +473,9 @@ __global__ void k_density(SlDev d) {
     acc_prod(a, b, dd.x, dd.x);
     acc_prod(a, b, dd.y, dd.y);
     acc_prod(a, b, dd.z, dd.z);
-    const df r2 = acc_done(a, b);
-    if (!df_lt(r2, d2)) continue;
-    const df x = df_sub(df_mul(r2, df_rsqrt(r2)), dc);
-    acc_prod(h, l, df_sqr(x), df_add_f(df_mul(bd, x), 1.0f));
+    eam_f_acc(d, acc_done(a, b), h, l);
   }
-  const df rho = acc_done(h, l);
-  const df fp = rho.hi > 0.0f ? df_neg(df_mul(F2(d.em_hA_f), df_rsqrt(rho))) : df_f(0.0f);
-  d.em_fp[i] = D2(fp);
+  eam_store_fp(d, i, h, l);
 }
 
 // (F'(rho_i) + F'(rho_j)) f'(r)/r of the embedding term, f'(r) = x (2 + 3 (beta/d) x).
@@ -601,9 +613,11 @@ __global__ void k_force(SlDev d, int kick) {
 
 __global__ void k_end_step(SlDev d) { d.ctrl->step += 1; }
 
-void launch_jtable(const SlDev& d, int grid, int block, cudaStream_t st) {
-  if (d.so) k_jtable<true><<<grid, block, 0, st>>>(d);
-  else k_jtable<false><<<grid, block, 0, st>>>(d);
+void launch_jtable(const SlDev& d, int grid, int block, cudaStream_t st, bool dens) {
+  if (d.so && dens) k_jtable<true, true><<<grid, block, 0, st>>>(d);
+  else if (d.so) k_jtable<true, false><<<grid, block, 0, st>>>(d);
+  else if (dens) k_jtable<false, true><<<grid, block, 0, st>>>(d);
+  else k_jtable<false, false><<<grid, block, 0, st>>>(d);
 }
 
 void launch_force(const SlDev& d, int grid, int block, cudaStream_t st, int kick) {
@@ -616,8 +630,9 @@ void launch_force(const SlDev& d, int grid, int block, cudaStream_t st, int kick
 // The per-step tables at the current positions: J (and the spin-orbit
 // tables), then the embedding density.  Returns the kernels launched.
 int launch_tables(const SlDev& d, int grid, int block, cudaStream_t st) {
-  launch_jtable(d, grid, block, st);
-  if (d.mech & SL_MECH_EAM) {
+  const bool eam = (d.mech & SL_MECH_EAM) != 0;
+  launch_jtable(d, grid, block, st, eam && d.em_fused);
+  if (eam && !d.em_fused) {
     k_density<<<grid, block, 0, st>>>(d);
     return 2;
   }
@@ -767,7 +782,7 @@ static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark
   }
   phase(SL_PHASE_JTABLE, 0);
   if (!e) e = sl_ml_launch_point(d, st, 0);
-  k_jtable<false><<<gn, SL_BLOCK, 0, st>>>(d);
+  k_jtable<false, false><<<gn, SL_BLOCK, 0, st>>>(d);
   phase(SL_PHASE_JTABLE, 1);
   nk += 5;
   phase(SL_PHASE_SPIN2, 0);
@@ -776,7 +791,7 @@ static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark
   nk += 16;
   phase(SL_PHASE_FORCE, 0);
   if (!e) e = sl_ml_launch_point(d, st, lat ? 3 : 0);
-  k_jtable<false><<<gn, SL_BLOCK, 0, st>>>(d);
+  k_jtable<false, false><<<gn, SL_BLOCK, 0, st>>>(d);
   nk += 5;
   if (lat) {
     k_force<false, false><<<gn, SL_BLOCK, 0, st>>>(d, 1);

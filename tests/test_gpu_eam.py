@@ -38,6 +38,11 @@ CASES = {
                                                             subtract_ground_exchange=1, **EAM),
     "eam_wide_d_rebuild_3": lambda: inputs.bcc_fe_system(6, 54, T=600.0, sigma=0.05, rebuild_every=3,
                                                          eam_A_eV=0.3, eam_d_A=4.6, eam_beta=0.5),
+    "eam_within_exchange_cutoff": lambda: inputs.bcc_fe_system(6, 57, T=300.0, sigma=0.05,
+                                                               eam_A_eV=0.4, eam_d_A=3.3, eam_beta=1.2),
+    "eam_at_exchange_cutoff_so": lambda: inputs.bcc_fe_system(6, 58, T=300.0, sigma=0.05,
+                                                              subtract_ground_exchange=1, eam_A_eV=0.5,
+                                                              eam_d_A=3.4, eam_beta=1.8, **SO),
     "eam_ground_spin_orbit": lambda: inputs.bcc_fe_system(6, 55, T=300.0, sigma=0.05,
                                                           subtract_ground_exchange=1, **EAM, **SO),
 }
