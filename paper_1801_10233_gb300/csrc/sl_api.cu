@@ -246,6 +246,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   }
   d.list_ex2 = (p->ex_rc_A + p->skin_A) * (p->ex_rc_A + p->skin_A);
   d.list_m2 = (p->morse_rc_A + p->skin_A) * (p->morse_rc_A + p->skin_A);
+  d.sure_m2 = p->morse_rc_A > p->skin_A ? (p->morse_rc_A - p->skin_A) * (p->morse_rc_A - p->skin_A) : 0.0;
   d.half_skin2 = 0.25 * p->skin_A * p->skin_A;
   d.lambda = p->lambda;
   d.seed = p->seed;
@@ -315,7 +316,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_sdf = L.take<float4>(2 * nn);
   size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
   size_t o_p0 = L.take<float2>(3 * nn), o_p1 = L.take<float2>(3 * nn);
-  size_t o_mj = L.take<int>(nn * d.max_m), o_mn = L.take<int>(nn);
+  size_t o_mj = L.take<int>(nn * d.max_m), o_mn = L.take<int>(nn), o_mnc = L.take<int>(nn);
   size_t o_oa = L.take<double>(nn * SL_NOBS), o_or = L.take<double>((size_t)nrep * SL_NOBS);
   size_t o_reps = L.take<SlRep>((size_t)nrep);
   size_t o_stage = L.take<double>(nn * 9);
@@ -364,7 +365,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.sdf = (float4*)(base + o_sdf);
     d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);
     d.hpart[0] = (float2*)(base + o_p0); d.hpart[1] = (float2*)(base + o_p1);
-    d.mj = (int*)(base + o_mj); d.mn = (int*)(base + o_mn);
+    d.mj = (int*)(base + o_mj); d.mn = (int*)(base + o_mn); d.mnc = (int*)(base + o_mnc);
     d.obs_atom = (double*)(base + o_oa); d.obs_rep = (double*)(base + o_or);
     d.reps = (const SlRep*)(base + o_reps);
     d.stage = (double*)(base + o_stage);

@@ -126,7 +126,14 @@ __global__ void k_rb_copyback(SlDev d) {
 // other sectors' field in parallel and only these in sequence.  The Morse
 // list starts with the exchange list (same order) followed by the
 // Morse-only neighbours, so the force loop takes the magneto-elastic branch
-// only for its first exn[i] entries.  Requires morse_rc >= ex_rc.
+// only for its first exn[i] entries.  Requires morse_rc >= ex_rc.  The
+// Morse-only neighbours come in three groups, each in loop order: those
+// closer than morse_rc - skin at the build, which stay inside the cutoff
+// until the next rebuild (no atom moves more than skin/2 before one); then
+// those inside morse_rc at the build; then those outside it.  mnc[i] marks
+// the end of the first group.  In a lattice every atom of a warp reaches the
+// same group at the same entry, so the force loop's cutoff test takes the
+// same branch across the warp.
 // Membership uses float distances from the split positions with a relative
 // margin of 1e-4 on r^2 (far above their rounding): a list may hold a pair
 // marginally outside its radius, which is harmless because every kernel
@@ -140,12 +147,18 @@ __global__ void k_rb_nbr(SlDev d) {
   const float Lx = (float)R.box[0], Ly = (float)R.box[1], Lz = (float)R.box[2];
   const float iLx = R.inv_box_f[0], iLy = R.inv_box_f[1], iLz = R.inv_box_f[2];
   const float lm2 = (float)d.list_m2 * 1.0001f, le2 = (float)d.list_ex2 * 1.0001f;
+  const float lc2 = (float)d.sure_m2 * 0.9999f;     // (morse_rc - skin)^2, margin inward
   int sx, sy, sz;
   sl_sector_coords(d, R, d.secq[i], sx, sy, sz);
   int lox = (2 * R.mx + 1 >= R.nx) ? 0 : -R.mx, hix = (2 * R.mx + 1 >= R.nx) ? R.nx - 1 : R.mx;
   int loy = (2 * R.my + 1 >= R.ny) ? 0 : -R.my, hiy = (2 * R.my + 1 >= R.ny) ? R.ny - 1 : R.my;
   int loz = (2 * R.mz + 1 >= R.nz) ? 0 : -R.mz, hiz = (2 * R.mz + 1 >= R.nz) ? R.nz - 1 : R.mz;
-  int ce = 0, cm = 0;
+  const float lr2 = (float)d.m_rc2;
+  int ce = 0, cm = 0, cc = 0;
+  // pass 0: exchange entries and the Morse-only entries certain to stay
+  // inside the cutoff; pass 1: other Morse-only entries inside it at the
+  // build; pass 2: the rest
+  for (int pass = 0; pass < 3; ++pass)
   for (int oz = loz; oz <= hiz; ++oz) {
     int tz = (sz + oz + 2 * R.nz) % R.nz;
     for (int oy = loy; oy <= hiy; ++oy) {
@@ -165,12 +178,15 @@ __global__ void k_rb_nbr(SlDev d) {
           dz -= Lz * rintf(dz * iLz);
           const float r2 = dx * dx + dy * dy + dz * dz;
           if (r2 < le2) {
-            if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;
-            ++ce;
-          } else if (r2 < lm2) {
+            if (pass == 0) {
+              if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;
+              ++ce;
+            }
+          } else if (r2 < lm2 && (r2 < lc2 ? 0 : (r2 < lr2 ? 1 : 2)) == pass) {
             // Morse-only entries go after a gap of max_ex rows for now
             if (d.max_ex + cm < d.max_m) d.mj[(size_t)(d.max_ex + cm) * d.n + i] = j;
             ++cm;
+            if (pass == 0) ++cc;
           }
         }
       }
@@ -180,6 +196,7 @@ __global__ void k_rb_nbr(SlDev d) {
   const int ne = min(ce, d.max_ex);
   const int nmo = min(cm, d.max_m - d.max_ex);
   d.mn[i] = ne + nmo;
+  d.mnc[i] = ne + min(cc, nmo);
   d.exn[i] = ne;
   // stable partition: same-sector neighbours first
   const int qi = d.secq[i];

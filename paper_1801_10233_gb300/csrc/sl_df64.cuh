@@ -199,6 +199,25 @@ __device__ __forceinline__ double df_to_double(df a) {
 // k = rint((b - a)/L), to df accuracy relative to d itself: the large pieces
 // are differenced (and k L subtracted) with error-free two_sum before any
 // rounding, so the cancellation across the periodic boundary is exact.
+// The periodic shift k of b - a and the float separation (b.h - a.h) - k L.h
+// (within a few ulps of the exact one): the cheap cutoff test before f3_sep_k.
+__device__ __forceinline__ float f3_pre(f3 b, f3 a, f3 L, float invL, float& k) {
+  const float s = __fadd_rn(b.h, -a.h);
+  k = rintf(s * invL);
+  return __fmaf_rn(-k, L.h, s);
+}
+// Exact b - a - k L (k from f3_pre) rounded to df.
+__device__ __forceinline__ df f3_sep_k(f3 b, f3 a, f3 L, float k) {
+  df hs = two_sum(b.h, -a.h);
+  df h2 = two_sum(hs.hi, -k * L.h);                 // k L.h exact: |k| <= 1
+  df ms = two_sum(b.m, -a.m);
+  df m2 = two_sum(ms.hi, -k * L.m);
+  float small = __fadd_rn(__fsub_rn(b.l, a.l), -k * L.l);
+  df r = df_add(h2, m2);
+  r = df_add_f(r, hs.lo);
+  r = df_add_f(r, ms.lo);
+  return df_add_f(r, small);
+}
 __device__ __forceinline__ df f3_sep(f3 b, f3 a, f3 L, float invL) {
   df hs = two_sum(b.h, -a.h);
   float k = rintf(hs.hi * invL);

@@ -78,6 +78,7 @@ struct SlDev {
   double ex_alpha, ex_gamma, ex_delta, ex_rc2;
   double m_D0, m_alpha, m_r0, m_rc2, m_vshift;
   double list_ex2, list_m2; // (cutoff + skin)^2
+  double sure_m2;           // (morse_rc - skin)^2 (0 if skin >= morse_rc)
   double half_skin2;
   double lambda;
   int any_noise;            // some replica has a bath temperature
@@ -128,6 +129,7 @@ struct SlDev {
   // [n] F'(rho_i) (hi, lo) at current r, sorted order (NULL unless mech has SL_MECH_EAM)
   float2 *em_fp;
   int *mj, *mn;             // [max_m][n] neighbour-major, counts
+  int *mnc;                 // [n] end of the entries certain to be inside morse_rc until the next rebuild
   // sweep scratch for blocks whose atoms exceed shared memory: [3 n] each
   float2 *hbuf, *sbuf, *ebuf;
   // partial external fields precomputed for the next colour pass (ping-pong)

@@ -60,6 +60,30 @@ __device__ __forceinline__ df3 pair_sep(const box3& B, const p3& a, const p3& b)
   return r;
 }
 
+// Float separation of a pair and its periodic shifts, for a cutoff test
+// before the exact separation: |float r^2 - exact r^2| is a few ulps of
+// r * L, far inside the 1e-4 relative margin the callers allow.
+struct pre3 {
+  float r2;
+  float kx, ky, kz;
+};
+__device__ __forceinline__ pre3 pair_pre(const box3& B, const p3& a, const p3& b) {
+  pre3 q;
+  const float x = f3_pre(b.x, a.x, B.L[0], B.inv[0], q.kx);
+  const float y = f3_pre(b.y, a.y, B.L[1], B.inv[1], q.ky);
+  const float z = f3_pre(b.z, a.z, B.L[2], B.inv[2], q.kz);
+  q.r2 = x * x + y * y + z * z;
+  return q;
+}
+// The exact separation with the shifts of pair_pre: the same value as pair_sep.
+__device__ __forceinline__ df3 pair_sep_k(const box3& B, const p3& a, const p3& b, const pre3& q) {
+  df3 r;
+  r.x = f3_sep_k(b.x, a.x, B.L[0], q.kx);
+  r.y = f3_sep_k(b.y, a.y, B.L[1], q.ky);
+  r.z = f3_sep_k(b.z, a.z, B.L[2], q.kz);
+  return r;
+}
+
 __device__ __forceinline__ df dot3(const df3& a, const df3& b) {
   float h = 0.0f, l = 0.0f;
   acc_prod(h, l, a.x, b.x);

@@ -466,9 +466,10 @@ __global__ void k_density(SlDev d) {
   float h = 0.0f, l = 0.0f;
   for (int k = 0; k < nm; ++k) {
     const int j = __ldg(d.mj + (size_t)k * d.n + i);
-    const df3 dd = pair_sep(B, pi, load_pos(d, j));
-    const float r2f = dd.x.hi * dd.x.hi + dd.y.hi * dd.y.hi + dd.z.hi * dd.z.hi;
-    if (r2f > d2_hi) continue;
+    const p3 pj = load_pos(d, j);
+    const pre3 q = pair_pre(B, pi, pj);
+    if (q.r2 > d2_hi) continue;
+    const df3 dd = pair_sep_k(B, pi, pj, q);
     float a = 0.0f, b = 0.0f;
     acc_prod(a, b, dd.x, dd.x);
     acc_prod(a, b, dd.y, dd.y);
@@ -578,13 +579,31 @@ __global__ void k_force(SlDev d, int kick) {
     acc_prod(fyh, fyl, c, dd.y);
     acc_prod(fzh, fzl, c, dd.z);
   }
-  // entries ne..nm-1: Morse only
-  for (int k = ne; k < nm; ++k) {
+  // entries ne..mc-1: Morse only, inside the cutoff until the next rebuild
+  const int mc = d.mnc[i];
+  for (int k = ne; k < mc; ++k) {
     const int j = __ldg(d.mj + (size_t)k * d.n + i);
     const df3 dd = pair_sep(B, pi, load_pos(d, j));
-    // float pre-check: pairs clearly outside the cutoff skip the df test
-    const float r2f = dd.x.hi * dd.x.hi + dd.y.hi * dd.y.hi + dd.z.hi * dd.z.hi;
-    if (r2f > rc2_hi) continue;
+    float h = 0.0f, l = 0.0f;
+    acc_prod(h, l, dd.x, dd.x);
+    acc_prod(h, l, dd.y, dd.y);
+    acc_prod(h, l, dd.z, dd.z);
+    const df r2 = acc_done(h, l);
+    df rinv;
+    df c = morse_coeff(r2, na, r0, c2, rinv);
+    if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
+    acc_prod(fxh, fxl, c, dd.x);
+    acc_prod(fyh, fyl, c, dd.y);
+    acc_prod(fzh, fzl, c, dd.z);
+  }
+  // entries mc..nm-1: Morse only, possibly outside the cutoff
+  for (int k = mc; k < nm; ++k) {
+    const int j = __ldg(d.mj + (size_t)k * d.n + i);
+    const p3 pj = load_pos(d, j);
+    // float pre-check: pairs clearly outside the cutoff skip the exact separation
+    const pre3 q = pair_pre(B, pi, pj);
+    if (q.r2 > rc2_hi) continue;
+    const df3 dd = pair_sep_k(B, pi, pj, q);
     float h = 0.0f, l = 0.0f;
     acc_prod(h, l, dd.x, dd.x);
     acc_prod(h, l, dd.y, dd.y);
