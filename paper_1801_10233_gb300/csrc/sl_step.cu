@@ -41,8 +41,8 @@ inline int grid_for(int n) { return (n + SL_BLOCK - 1) / SL_BLOCK; }
 // Tile shapes (sectors per block SPB <= 32, threads per block): the
 // variants the autotuner chooses from (sl_autotune), variant 0 the default.
 // A block stages up to 12 atoms per sector in shared memory.
-constexpr int SW_MAXIN = 12;   // same-sector neighbours staged per atom
-constexpr int SW_BATCH = 4;    // external neighbours gathered per batch
+constexpr int SW_MAXIN = 6;    // same-sector neighbours staged per atom (more: read from global memory)
+constexpr int SW_BATCH = 2;    // external neighbours gathered per batch
 
 // Dynamic shared memory of one block with up to maxa atoms: H, S (and E
 // with noise) as float2 [3 maxa], same-sector lists J [SW_MAXIN maxa]
@@ -106,7 +106,7 @@ __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1,
 }
 
 template <int SW_SPB, int SW_THREADS, bool SO>
-__global__ void __launch_bounds__(SW_THREADS, 576 / SW_THREADS)
+__global__ void __launch_bounds__(SW_THREADS, 768 / SW_THREADS)
 k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, int next_colour, int pin, int pout) {
   constexpr int SW_MAXA = 12 * SW_SPB;
   extern __shared__ float2 smem[];
