@@ -56,7 +56,7 @@ enum {
   SL_OK = 0,
   SL_ERR_ARG = -1,          /* invalid argument or parameter */
   SL_ERR_CUDA = -2,         /* a CUDA runtime call failed */
-  SL_ERR_BOX = -3,          /* box < 2 (cutoff + skin), or < 2 sectors per edge */
+  SL_ERR_BOX = -3,          /* box < 2 (cutoff + skin), < 2 sectors per edge, or an edge >= 4096 A */
   SL_ERR_SPIN_NORM = -4,    /* an input spin is not unit length (|1 - |s|| > 1e-12) */
   SL_ERR_SKIN = -5,         /* an atom moved > skin/2 with no rebuild scheduled */
   SL_ERR_TIMEOUT = -6,      /* an in-kernel wait ran out of its iteration budget */
@@ -136,7 +136,8 @@ typedef struct sl_ctx sl_ctx;  /* opaque, owned by the library */
 /* Bytes of device workspace sl_init needs for these parameters.
  * Errors: SL_ERR_ARG (NULL pointer, n_atoms < 1, non-positive mass,
  * morse_rc_A < ex_rc_A, max_ex_neighbors above 64),
- * SL_ERR_BOX (box too small for the cutoffs or for 2 sectors per edge). */
+ * SL_ERR_BOX (box too small for the cutoffs or for 2 sectors per edge, or an
+ * edge of 4096 A or more: positions are held in 64-bit fixed point too). */
 int sl_workspace_bytes(const sl_params* params, size_t* bytes);
 
 /* Create a context: copies r, v, s (device, [n][3] doubles, caller order)

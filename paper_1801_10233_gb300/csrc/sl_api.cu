@@ -1,5 +1,6 @@
 // C ABI of libsl: context lifecycle, workspace layout, state transfer and
 // the per-step launch sequence (captured once into a CUDA graph).
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -100,7 +101,7 @@ int validate(const sl_params* p) {
   if (p->eam_A_eV != 0.0 && !(p->eam_d_A > 0.0 && p->eam_d_A <= p->morse_rc_A)) return SL_ERR_ARG;
   double rc = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
   for (int a = 0; a < 3; ++a)
-    if (!(p->box[a] >= 2.0 * rc)) return SL_ERR_BOX;
+    if (!(p->box[a] >= 2.0 * rc) || !(p->box[a] < SL_FX_MAX_BOX)) return SL_ERR_BOX;
   int n[3]; double e[3];
   return sector_grid(p, n, e);
 }
@@ -154,13 +155,6 @@ float2 split_f2(double x) {
   return make_float2(hi, lo);
 }
 
-// x = h + m + l exactly (three floats; the FP64 value has 53 bits).
-void split_f3(double x, float* h, float* m, float* l) {
-  *h = (float)x;
-  double r = x - (double)*h;
-  *m = (float)r;
-  *l = (float)(r - (double)*m);
-}
 
 // Double-float constants that depend on dt or H.
 void fill_df_constants(SlDev& d) {
@@ -188,12 +182,19 @@ void fill_noise(std::vector<SlRep>& reps, const sl_params* ps, double dt) {
 
 // Fill d's scalars, the replica table and (if base != NULL) d's pointers;
 // returns the workspace bytes needed.
+// Fixed-point positions X = rint(r 2^F) with one F for every context, so a
+// replica's trajectory does not depend on the batch it is in: F = 48 rounds
+// positions below 16 A by at most 2^-49 A (above, FP64 is coarser) and keeps
+// |X| < 2^61 for positions within one box length of boxes up to SL_FX_MAX_BOX.
+int fixed_point_bits(const sl_params*, int) { return SL_FX_BITS; }
+
 size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, char* base) {
   std::memset(&d, 0, sizeof(d));
   const sl_params* p = ps;
   reps.assign(nrep, SlRep());
   double reach = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
   int atom0 = 0, sec8 = 0, noise = 0;
+  const int fx = fixed_point_bits(ps, nrep);
   for (int r = 0; r < nrep; ++r) {
     SlRep& R = reps[r];
     std::memset(&R, 0, sizeof(R));
@@ -207,8 +208,8 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
       R.inv_box[a] = 1.0 / ps[r].box[a];
       R.edge[a] = e[a];
       *mm[a] = (int)std::ceil(reach / e[a]);
-      split_f3(ps[r].box[a], &R.box_h[a], &R.box_m[a], &R.box_l[a]);
-      R.inv_box_f[a] = (float)(1.0 / ps[r].box[a]);
+      R.boxX[a] = std::llrint(std::ldexp(ps[r].box[a], fx));
+      R.halfX[a] = R.boxX[a] / 2;
     }
     R.sec8_off = sec8;
     R.atom0 = atom0;
@@ -246,6 +247,11 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   }
   d.list_ex2 = (p->ex_rc_A + p->skin_A) * (p->ex_rc_A + p->skin_A);
   d.list_m2 = (p->morse_rc_A + p->skin_A) * (p->morse_rc_A + p->skin_A);
+  d.fx_F = fx;
+  d.fx_scale = std::ldexp(1.0, fx);
+  d.fx_s40 = std::ldexp(1.0f, 40 - fx);
+  d.fx_s20 = std::ldexp(1.0f, 20 - fx);
+  d.fx_s0 = std::ldexp(1.0f, -fx);
   d.sure_m2 = p->morse_rc_A > p->skin_A ? (p->morse_rc_A - p->skin_A) * (p->morse_rc_A - p->skin_A) : 0.0;
   d.half_skin2 = 0.25 * p->skin_A * p->skin_A;
   d.lambda = p->lambda;
@@ -312,7 +318,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_exso = so_pairs ? L.take<float2>(5 * nn * d.max_ex) : 0;
   const bool eam = (d.mech & SL_MECH_EAM) != 0;
   size_t o_emfp = eam ? L.take<float2>(nn) : 0;
-  size_t o_rh = L.take<float4>(nn), o_rm = L.take<float4>(nn), o_rl = L.take<float4>(nn);
+  size_t o_rx = L.take<SlFix>(nn);
   size_t o_sdf = L.take<float4>(2 * nn);
   size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
   size_t o_p0 = L.take<float2>(3 * nn), o_p1 = L.take<float2>(3 * nn);
@@ -361,7 +367,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.exJ = (float2*)(base + o_exJ);
     d.exso = so_pairs ? (float2*)(base + o_exso) : nullptr;
     d.em_fp = eam ? (float2*)(base + o_emfp) : nullptr;
-    d.rh = (float4*)(base + o_rh); d.rm = (float4*)(base + o_rm); d.rl = (float4*)(base + o_rl);
+    d.rx = (SlFix*)(base + o_rx);
     d.sdf = (float4*)(base + o_sdf);
     d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);
     d.hpart[0] = (float2*)(base + o_p0); d.hpart[1] = (float2*)(base + o_p1);

@@ -13,6 +13,8 @@
 // sequence can sit in the step's launch sequence (and in a CUDA graph) and
 // costs one early-exit per kernel when no rebuild is due.
 #include "sl_internal.cuh"
+#include "sl_df64.cuh"
+#include "sl_pair.cuh"
 
 namespace {
 
@@ -134,18 +136,17 @@ __global__ void k_rb_copyback(SlDev d) {
 // the end of the first group.  In a lattice every atom of a warp reaches the
 // same group at the same entry, so the force loop's cutoff test takes the
 // same branch across the warp.
-// Membership uses float distances from the split positions with a relative
-// margin of 1e-4 on r^2 (far above their rounding): a list may hold a pair
+// Membership uses float distances from the fixed-point positions with a
+// relative margin of 1e-4 on r^2 (far above their rounding): a list may hold a pair
 // marginally outside its radius, which is harmless because every kernel
 // applies the exact cutoff to the pairs it reads.
 __global__ void k_rb_nbr(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
-  const float4 rih = d.rh[i], rim = d.rm[i];
   const SlRep& R = d.reps[d.arep[i]];
-  const float Lx = (float)R.box[0], Ly = (float)R.box[1], Lz = (float)R.box[2];
-  const float iLx = R.inv_box_f[0], iLy = R.inv_box_f[1], iLz = R.inv_box_f[2];
+  const p3 pi = load_pos(d, i);
+  const box3 B = load_box(d, R);
   const float lm2 = (float)d.list_m2 * 1.0001f, le2 = (float)d.list_ex2 * 1.0001f;
   const float lc2 = (float)d.sure_m2 * 0.9999f;     // (morse_rc - skin)^2, margin inward
   int sx, sy, sz;
@@ -169,14 +170,7 @@ __global__ void k_rb_nbr(SlDev d) {
         int a = d.sec_start[q], b = d.sec_start[q + 1];
         for (int j = a; j < b; ++j) {
           if (j == i) continue;
-          const float4 jh = __ldg(d.rh + j), jm = __ldg(d.rm + j);
-          float dx = (jh.x - rih.x) + (jm.x - rim.x);
-          float dy = (jh.y - rih.y) + (jm.y - rim.y);
-          float dz = (jh.z - rih.z) + (jm.z - rim.z);
-          dx -= Lx * rintf(dx * iLx);
-          dy -= Ly * rintf(dy * iLy);
-          dz -= Lz * rintf(dz * iLz);
-          const float r2 = dx * dx + dy * dy + dz * dz;
+          const float r2 = pair_pre(B, pi, load_pos(d, j)).r2;
           if (r2 < le2) {
             if (pass == 0) {
               if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;

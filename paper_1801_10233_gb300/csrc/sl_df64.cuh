@@ -153,30 +153,6 @@ __device__ __forceinline__ df df_from_double(double x) {
 }
 
 // Exact three-piece split of a double: x = h + m + l (all floats, exact).
-struct f3 {
-  float h, m, l;
-};
-__device__ __forceinline__ f3 f3_from_double(double x) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  int e = (int)((b >> 52) & 0x7ff);
-  f3 r;
-  r.h = r.m = r.l = 0.0f;
-  int ef = e - 1023 + 127;
-  if (e == 0 || ef <= 52) return r;                     // |x| < 2^-74: treat as zero
-  if (ef >= 255) { r.h = __int_as_float(0x7fffffff); return r; }   // out of float range: NaN
-  unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
-  r.h = __uint_as_float(sign | ((unsigned)ef << 23) | (unsigned)(mant >> 29));
-  unsigned mid = (unsigned)((mant >> 5) & 0xFFFFFFu);   // next 24 bits, units 2^(e-1023-47)
-  unsigned low = (unsigned)(mant & 0x1Fu);              // last 5 bits, units 2^(e-1023-52)
-  float sm = __int_as_float((ef - 47) << 23);
-  float sl = __int_as_float((ef - 52) << 23);
-  r.m = __fmaf_rn(u23_to_float(mid >> 1), 2.0f, u23_to_float(mid & 1u)) * sm;  // exact: < 2^24
-  r.l = u23_to_float(low) * sl;
-  if (sign) { r.m = -r.m; r.l = -r.l; }
-  return r;
-}
-
 // Exact float -> double by bit operations (finite, normal or zero inputs).
 __device__ __forceinline__ double double_from_float(float f) {
   unsigned u = __float_as_uint(f);
@@ -193,42 +169,6 @@ __device__ __forceinline__ double double_from_float(float f) {
 // hi + lo as a double: two exact conversions and one FP64 add.
 __device__ __forceinline__ double df_to_double(df a) {
   return double_from_float(a.hi) + double_from_float(a.lo);
-}
-
-// Minimum-image separation d = b - a - k L of exactly split coordinates,
-// k = rint((b - a)/L), to df accuracy relative to d itself: the large pieces
-// are differenced (and k L subtracted) with error-free two_sum before any
-// rounding, so the cancellation across the periodic boundary is exact.
-// The periodic shift k of b - a and the float separation (b.h - a.h) - k L.h
-// (within a few ulps of the exact one): the cheap cutoff test before f3_sep_k.
-__device__ __forceinline__ float f3_pre(f3 b, f3 a, f3 L, float invL, float& k) {
-  const float s = __fadd_rn(b.h, -a.h);
-  k = rintf(s * invL);
-  return __fmaf_rn(-k, L.h, s);
-}
-// Exact b - a - k L (k from f3_pre) rounded to df.
-__device__ __forceinline__ df f3_sep_k(f3 b, f3 a, f3 L, float k) {
-  df hs = two_sum(b.h, -a.h);
-  df h2 = two_sum(hs.hi, -k * L.h);                 // k L.h exact: |k| <= 1
-  df ms = two_sum(b.m, -a.m);
-  df m2 = two_sum(ms.hi, -k * L.m);
-  float small = __fadd_rn(__fsub_rn(b.l, a.l), -k * L.l);
-  df r = df_add(h2, m2);
-  r = df_add_f(r, hs.lo);
-  r = df_add_f(r, ms.lo);
-  return df_add_f(r, small);
-}
-__device__ __forceinline__ df f3_sep(f3 b, f3 a, f3 L, float invL) {
-  df hs = two_sum(b.h, -a.h);
-  float k = rintf(hs.hi * invL);
-  df h2 = two_sum(hs.hi, -k * L.h);                 // k L.h exact: |k| <= 1
-  df ms = two_sum(b.m, -a.m);
-  df m2 = two_sum(ms.hi, -k * L.m);
-  float small = __fadd_rn(__fsub_rn(b.l, a.l), -k * L.l);
-  df r = df_add(h2, m2);
-  r = df_add_f(r, hs.lo);
-  r = df_add_f(r, ms.lo);
-  return df_add_f(r, small);
 }
 
 // Running sum of products (h, l) += a * b, renormalised after every term so

@@ -16,6 +16,8 @@
 // Sectors per block of the colour-pass tile shapes (threads: 192, 256, 128, 192, 128).
 static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8};
 #define SL_MAX_EX_CAP 64   // largest accepted max_ex_neighbors
+#define SL_FX_BITS 48       // fixed-point positions: X = rint(r 2^48)
+#define SL_FX_MAX_BOX 4096.0  // box edges below 2^(60 - SL_FX_BITS) A
 
 // Control block in device memory: sticky status, rebuild flag, counters.
 struct SlCtrl {
@@ -37,7 +39,7 @@ struct SlCtrl {
 // One system of a batch: its box, sector grid, atom range and spin bath.
 struct SlRep {
   double box[3], inv_box[3], edge[3];
-  float box_h[3], box_m[3], box_l[3], inv_box_f[3];   // exact 3-float split of the box
+  long long boxX[3], halfX[3];   // box and half box in fixed point (units 2^-F A)
   int nx, ny, nz;           // sectors per edge (even, >= 2)
   int s8;                   // sectors per colour
   int mx, my, mz;           // sector layers searched for Morse neighbours
@@ -60,6 +62,11 @@ struct SlBsF {
   float2 ix, a4, g, a8d2;
 };
 
+// A position in fixed point (units 2^-F A), one 32-byte load.
+struct __align__(32) SlFix {
+  long long x, y, z, w;
+};
+
 // Everything a kernel needs, passed by value.  Scalars used by the
 // double-float kernels are given as (hi, lo) float pairs split on the host.
 // Sector ranks are global and colour-major: rank = colour * s8 + sec8_off of
@@ -78,6 +85,9 @@ struct SlDev {
   double ex_alpha, ex_gamma, ex_delta, ex_rc2;
   double m_D0, m_alpha, m_r0, m_rc2, m_vshift;
   double list_ex2, list_m2; // (cutoff + skin)^2
+  int fx_F;                 // fixed-point positions: X = rint(r 2^F)
+  double fx_scale;          // 2^F
+  float fx_s40, fx_s20, fx_s0;   // 2^(40-F), 2^(20-F), 2^-F
   double sure_m2;           // (morse_rc - skin)^2 (0 if skin >= morse_rc)
   double half_skin2;
   double lambda;
@@ -114,7 +124,7 @@ struct SlDev {
   // state, sector-sorted (FP64, authoritative)
   double4_32a *r, *v, *s, *F, *rb;
   // split copies for the double-float kernels
-  float4 *rh, *rm, *rl;     // r = rh + rm + rl exactly
+  SlFix *rx;                // r in fixed point, rint(r 2^F)
   float4 *sdf;              // s = hi + lo to ~48 bits: sdf[2i] = hi, sdf[2i+1] = lo
   // rebuild scratch
   double4_32a *tr, *tv, *ts, *tF;

@@ -149,7 +149,7 @@ __global__ void k_ml_desc(SlDev d, int count_gate, float* raw, double* draw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const p3 pi = load_pos(d, i);
-  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
+  const box3 B = load_box(d, d.reps[__ldg(d.arep + i)]);
   const float3 si = spin_f(d, i);
   float D[NF];
 #pragma unroll
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(128) k_ml_pair(SlDev d, int fmode, int force, 
   if (i >= d.n) return;
   if (!force && !d.ctrl->ml_use) return;
   const p3 pi = load_pos(d, i);
-  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
+  const box3 B = load_box(d, d.reps[__ldg(d.arep + i)]);
   const float3 si = spin_f(d, i);
   float Gi[NF];
   {
@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(128) k_ml_gbar(SlDev d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const p3 pi = load_pos(d, i);
-  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
+  const box3 B = load_box(d, d.reps[__ldg(d.arep + i)]);
   const float3 si = spin_f(d, i);
   const float4 gFi = d.ml_gF[i], gBi = d.ml_gB[i];
   float Gb[NF];

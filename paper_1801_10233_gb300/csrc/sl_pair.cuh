@@ -15,18 +15,22 @@ __device__ __forceinline__ float2 D2(df a) { return make_float2(a.hi, a.lo); }
 struct df3 {
   df x, y, z;
 };
+// Positions in fixed point for the pair kernels: X = rint(r 2^F), 64-bit
+// integers, F (SlDev::fx_F) chosen on the host so that |X| < 2^61 for every
+// position within a box length of the box.  The difference of two positions
+// and its periodic shift by the integer box length are exact integer
+// operations; the separation is then rounded once to double-float.
 struct p3 {
-  f3 x, y, z;
+  long long x, y, z;
 };
 
 // Positions, lists and tables are read-only in every kernel that gathers
 // them; their loads go through the read-only path and may be issued early.
 __device__ __forceinline__ p3 load_pos(const SlDev& d, int j) {
-  float4 h = __ldg(d.rh + j), m = __ldg(d.rm + j), l = __ldg(d.rl + j);
+  const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(d.rx + j));
+  const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(d.rx + j) + 1);
   p3 p;
-  p.x.h = h.x; p.x.m = m.x; p.x.l = l.x;
-  p.y.h = h.y; p.y.m = m.y; p.y.l = l.y;
-  p.z.h = h.z; p.z.m = m.z; p.z.l = l.z;
+  p.x = a.x; p.y = a.y; p.z = b.x;
   return p;
 }
 
@@ -37,50 +41,82 @@ __device__ __forceinline__ df3 load_spin(const SlDev& d, int j) {
   return s;
 }
 
-// The replica's box as exact three-float pieces.
+// The replica's box and half box in fixed point, and the scales that bring
+// the 20-bit pieces of a fixed-point difference back to Angstrom.
 struct box3 {
-  f3 L[3];
-  float inv[3];
+  long long L[3], H[3];
+  float s40, s20, s0;
 };
-__device__ __forceinline__ box3 load_box(const SlRep& R) {
+__device__ __forceinline__ box3 load_box(const SlDev& d, const SlRep& R) {
   box3 b;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    b.L[a].h = R.box_h[a]; b.L[a].m = R.box_m[a]; b.L[a].l = R.box_l[a];
-    b.inv[a] = R.inv_box_f[a];
+    b.L[a] = R.boxX[a];
+    b.H[a] = R.halfX[a];
   }
+  b.s40 = d.fx_s40; b.s20 = d.fx_s20; b.s0 = d.fx_s0;
   return b;
+}
+
+// Minimum-image difference b - a in fixed point (|b - a| < 1.5 L before the shift).
+__device__ __forceinline__ long long fx_diff(long long b, long long a, long long L, long long H) {
+  long long D = b - a;
+  D = D > H ? D - L : D;
+  D = D < -H ? D + L : D;
+  return D;
+}
+
+// D 2^-F (|D| < 2^61) as df: D = A 2^40 + B 2^20 + C with |A| < 2^21 and
+// B, C < 2^20, each exact in a float; two error-free additions round the sum.
+__device__ __forceinline__ df fx_to_df(long long D, const box3& B) {
+  const int A = (int)(D >> 40);
+  const unsigned Bm = (unsigned)(D >> 20) & 0xFFFFFu, Cm = (unsigned)D & 0xFFFFFu;
+  const float fa = __fsub_rn(u23_to_float((unsigned)(A + (1 << 21))), 2097152.0f) * B.s40;
+  const float fb = u23_to_float(Bm) * B.s20;
+  const float fc = u23_to_float(Cm) * B.s0;
+  const df s = fast_two_sum(fa, fb);          // |fa| >= |fb| unless A = 0
+  const df t = two_sum(s.hi, fc);
+  return fast_two_sum(t.hi, __fadd_rn(t.lo, s.lo));
+}
+// The same value to about float precision (the cutoff pre-checks).
+__device__ __forceinline__ float fx_to_float(long long D, const box3& B) {
+  const int A = (int)(D >> 40);
+  const unsigned Bm = (unsigned)(D >> 20) & 0xFFFFFu;
+  return __fmaf_rn(__fsub_rn(u23_to_float((unsigned)(A + (1 << 21))), 2097152.0f), B.s40,
+                   u23_to_float(Bm) * B.s20);
 }
 
 __device__ __forceinline__ df3 pair_sep(const box3& B, const p3& a, const p3& b) {
   df3 r;
-  r.x = f3_sep(b.x, a.x, B.L[0], B.inv[0]);
-  r.y = f3_sep(b.y, a.y, B.L[1], B.inv[1]);
-  r.z = f3_sep(b.z, a.z, B.L[2], B.inv[2]);
+  r.x = fx_to_df(fx_diff(b.x, a.x, B.L[0], B.H[0]), B);
+  r.y = fx_to_df(fx_diff(b.y, a.y, B.L[1], B.H[1]), B);
+  r.z = fx_to_df(fx_diff(b.z, a.z, B.L[2], B.H[2]), B);
   return r;
 }
 
-// Float separation of a pair and its periodic shifts, for a cutoff test
-// before the exact separation: |float r^2 - exact r^2| is a few ulps of
-// r * L, far inside the 1e-4 relative margin the callers allow.
+// Minimum-image difference of a pair and its float r^2, for a cutoff test
+// before the exact separation: the float value is within 2^-20 A of the
+// exact one per component, far inside the 1e-4 relative margin the callers
+// allow on r^2.
 struct pre3 {
   float r2;
-  float kx, ky, kz;
+  long long dx, dy, dz;
 };
 __device__ __forceinline__ pre3 pair_pre(const box3& B, const p3& a, const p3& b) {
   pre3 q;
-  const float x = f3_pre(b.x, a.x, B.L[0], B.inv[0], q.kx);
-  const float y = f3_pre(b.y, a.y, B.L[1], B.inv[1], q.ky);
-  const float z = f3_pre(b.z, a.z, B.L[2], B.inv[2], q.kz);
+  q.dx = fx_diff(b.x, a.x, B.L[0], B.H[0]);
+  q.dy = fx_diff(b.y, a.y, B.L[1], B.H[1]);
+  q.dz = fx_diff(b.z, a.z, B.L[2], B.H[2]);
+  const float x = fx_to_float(q.dx, B), y = fx_to_float(q.dy, B), z = fx_to_float(q.dz, B);
   q.r2 = x * x + y * y + z * z;
   return q;
 }
-// The exact separation with the shifts of pair_pre: the same value as pair_sep.
+// The exact separation from pair_pre's differences: the same value as pair_sep.
 __device__ __forceinline__ df3 pair_sep_k(const box3& B, const p3& a, const p3& b, const pre3& q) {
   df3 r;
-  r.x = f3_sep_k(b.x, a.x, B.L[0], q.kx);
-  r.y = f3_sep_k(b.y, a.y, B.L[1], q.ky);
-  r.z = f3_sep_k(b.z, a.z, B.L[2], q.kz);
+  r.x = fx_to_df(q.dx, B);
+  r.y = fx_to_df(q.dy, B);
+  r.z = fx_to_df(q.dz, B);
   return r;
 }
 
@@ -101,11 +137,15 @@ __device__ __forceinline__ df3 cross3(const df3& a, const df3& b) {
   return c;
 }
 
+// Fixed-point copy of a position (out-of-range values saturate; they occur
+// only before the first wrap into the box, when no pair kernel reads them).
 __device__ __forceinline__ void store_pos_split(const SlDev& d, int k, double4_32a r) {
-  f3 x = f3_from_double(r.x), y = f3_from_double(r.y), z = f3_from_double(r.z);
-  d.rh[k] = make_float4(x.h, y.h, z.h, 0.0f);
-  d.rm[k] = make_float4(x.m, y.m, z.m, 0.0f);
-  d.rl[k] = make_float4(x.l, y.l, z.l, 0.0f);
+  SlFix x;
+  x.x = __double2ll_rn(r.x * d.fx_scale);
+  x.y = __double2ll_rn(r.y * d.fx_scale);
+  x.z = __double2ll_rn(r.z * d.fx_scale);
+  x.w = 0;
+  d.rx[k] = x;
 }
 
 __device__ __forceinline__ void store_spin_split(const SlDev& d, int k, double4_32a s) {

@@ -406,7 +406,7 @@ __global__ void k_jtable(SlDev d) {
   if (i >= d.n) return;
   if (d.ham == SL_HAM_LEARNED && d.ctrl->ml_use) return;   // the network is in effect here
   const p3 pi = load_pos(d, i);
-  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
+  const box3 B = load_box(d, d.reps[__ldg(d.arep + i)]);
   const int ne = d.exn[i];
   const size_t n = (size_t)d.n;
   const df ix = F2(d.ex_ix_f), a4 = F2(d.ex_4a_f), g = F2(d.ex_g_f);
@@ -460,7 +460,7 @@ __global__ void k_density(SlDev d) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n) return;
   const p3 pi = load_pos(d, i);
-  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
+  const box3 B = load_box(d, d.reps[__ldg(d.arep + i)]);
   const int nm = d.mn[i];
   const float d2_hi = F2(d.em_d2_f).hi * 1.0001f;
   float h = 0.0f, l = 0.0f;
@@ -506,7 +506,7 @@ __global__ void k_force(SlDev d, int kick) {
   if (i >= d.n) return;
   if (d.ham == SL_HAM_LEARNED && d.ctrl->ml_use) return;   // the network is in effect here
   const p3 pi = load_pos(d, i);
-  const box3 B = load_box(d.reps[__ldg(d.arep + i)]);
+  const box3 B = load_box(d, d.reps[__ldg(d.arep + i)]);
   const df3 si = load_spin(d, i);
   float fxh = 0.0f, fxl = 0.0f, fyh = 0.0f, fyl = 0.0f, fzh = 0.0f, fzl = 0.0f;
   const int nm = d.mn[i], ne = d.exn[i];
