@@ -147,3 +147,14 @@ def test_embedding_validation_on_host(lib):
     plist, *_ = inputs.replica_systems([5, 6], [100.0, 200.0], seed=3)
     with pytest.raises(lib.SlError):
         lib.workspace_bytes([dict(plist[0], eam_A_eV=0.5), dict(plist[1])])
+
+
+def test_box_limit_of_fixed_point_positions(lib):
+    """Positions are also held as rint(r 2^48) in 64-bit integers: box edges
+    of 4096 A or more are rejected on the host."""
+    from paper_1801_10233_gb300 import inputs
+    p, *_ = inputs.workload("fe_bcc_10x10x10_nve")
+    assert lib.workspace_bytes(dict(p, box=[4000.0, 30.0, 30.0])) > 0
+    with pytest.raises(lib.SlError) as e:
+        lib.workspace_bytes(dict(p, box=[4096.0, 30.0, 30.0]))
+    assert e.value.code == lib.SL_ERR_BOX
