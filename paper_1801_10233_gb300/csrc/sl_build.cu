@@ -125,7 +125,9 @@ __global__ void k_rb_copyback(SlDev d) {
 // neighbour-major.  Neighbour order is the fixed loop order, so rebuilds are
 // deterministic.  Each exchange list is reordered stably so that neighbours
 // in the atom's own sector come first (exin[i] of them): the sweep sums the
-// other sectors' field in parallel and only these in sequence.  The Morse
+// other sectors' field in parallel and only these in sequence.  The other
+// neighbours follow grouped by their sector's colour (exc[i] holds the group
+// starts), so a colour pass reads just the colour it needs.  The Morse
 // list starts with the exchange list (same order) followed by the
 // Morse-only neighbours, so the force loop takes the magneto-elastic branch
 // only for its first exn[i] entries.  Requires morse_rc >= ex_rc.  The
@@ -198,13 +200,24 @@ __global__ void k_rb_nbr(SlDev d) {
   int* col = d.exj + i;     // entry k at col[k * n]
   const size_t n = (size_t)d.n;
   int tmp[SL_MAX_EX_CAP];
+  unsigned char tcol[SL_MAX_EX_CAP];
   int nin = 0, nout = 0;
   for (int k = 0; k < ne; ++k) {
     const int j = col[k * n];
     if (j >= sa && j < sb) col[(nin++) * n] = j;
     else tmp[nout++] = j;
   }
-  for (int k = 0; k < nout; ++k) col[(nin + k) * n] = tmp[k];
+  // the other neighbours grouped by their sector's colour (stable); group c
+  // starts at entry byte c of exc[i] (group 8 ends at exn[i])
+  for (int k = 0; k < nout; ++k) tcol[k] = (unsigned char)(d.secq[tmp[k]] / d.s8);
+  unsigned st[8];
+  int w = nin;
+  for (int c = 0; c < 8; ++c) {
+    st[c] = (unsigned)w;
+    for (int k = 0; k < nout; ++k)
+      if (tcol[k] == c) col[(w++) * n] = tmp[k];
+  }
+  d.exc[i] = make_uint2(st[0] | st[1] << 8 | st[2] << 16 | st[3] << 24, st[4] | st[5] << 8 | st[6] << 16 | st[7] << 24);
   d.exin[i] = nin;
   // Morse list: the exchange list, then the Morse-only entries moved down
   int* mcol = d.mj + i;

@@ -132,6 +132,7 @@ struct SlDev {
   int *sec_count, *sec_start, *sec_fill;
   // neighbour lists
   int *exj, *exn, *exin;    // [max_ex][n] neighbour-major (same-sector entries first), counts
+  uint2 *exc;               // [n] start of each colour's group of the other entries, one byte per colour
   float2 *exJ;              // [max_ex][n] J_ij (hi, lo) at current r
   // [5][max_ex][n] g1, d, e_x, e_y, e_z (hi, lo) at current r, e = (r_j - r_i)/r;
   // zero beyond ex_rc (NULL when so == 0)

@@ -53,48 +53,39 @@ size_t sweep_smem_bytes(bool noise, int maxa) {
 }
 
 // (h, l) += sum of J_ij s_j (with SO: the field of the exchange, Neel and DMI
-// terms of the pair) over external entries [k0, k1) of atom i whose
-// neighbour index lies inside [lo, hi) (take = 1) or outside it (take = 0).
+// terms of the pair) over entries [k0, k1) of atom i's exchange list.
 template <bool SO>
-__device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1, int lo, int hi, int take,
-                                          float& hx, float& lx, float& hy, float& ly, float& hz, float& lz) {
+__device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1, float& hx, float& lx, float& hy,
+                                          float& ly, float& hz, float& lz) {
   const size_t n = (size_t)d.n;
   for (int kb = k0; kb < k1; kb += SW_BATCH) {
     int jj[SW_BATCH];
     float2 JJ[SW_BATCH];
     float4 vh[SW_BATCH], vl[SW_BATCH];
-    bool use[SW_BATCH];
 #pragma unroll
     for (int q = 0; q < SW_BATCH; ++q) {
-      use[q] = false;
       if (kb + q < k1) {
         const size_t e = (size_t)(kb + q) * n + i;
         jj[q] = __ldg(d.exj + e);
-        JJ[q] = __ldg(d.exJ + e);
-        use[q] = ((jj[q] >= lo && jj[q] < hi) == (take != 0));
+        if (!SO) JJ[q] = __ldg(d.exJ + e);
       }
     }
 #pragma unroll
     for (int q = 0; q < SW_BATCH; ++q) {
-      if (use[q]) {
+      if (kb + q < k1) {
         vh[q] = __ldg(d.sdf + 2 * (size_t)jj[q]);
         vl[q] = __ldg(d.sdf + 2 * (size_t)jj[q] + 1);
       }
     }
-    if constexpr (SO) {
 #pragma unroll
-      for (int q = 0; q < SW_BATCH; ++q) {
-        if (use[q]) {
+    for (int q = 0; q < SW_BATCH; ++q) {
+      if (kb + q < k1) {
+        if constexpr (SO) {
           const SoEntry so = load_so(d, (size_t)(kb + q) * n + i);
           df3 sj;
           sj.x = df_make(vh[q].x, vl[q].x); sj.y = df_make(vh[q].y, vl[q].y); sj.z = df_make(vh[q].z, vl[q].z);
           so_field_acc(so, sj, hx, lx, hy, ly, hz, lz);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < SW_BATCH; ++q) {
-        if (use[q]) {
+        } else {
           const df J = F2(JJ[q]);
           acc_prod(hx, lx, J, df_make(vh[q].x, vl[q].x));
           acc_prod(hy, ly, J, df_make(vh[q].y, vl[q].y));
@@ -103,6 +94,13 @@ __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1,
       }
     }
   }
+}
+
+// Start of colour c's group among atom i's other-sector entries (c = 8: the end).
+__device__ __forceinline__ int group_start(uint2 g, int c, int ne) {
+  if (c >= 8) return ne;
+  const unsigned w = c < 4 ? g.x : g.y;
+  return (int)((w >> (8 * (c & 3))) & 0xFFu);
 }
 
 template <int SW_SPB, int SW_THREADS, bool SO>
@@ -133,8 +131,6 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
   const size_t n = (size_t)d.n;
   const int kin = SO ? 0 : min(SW_MAXIN, d.max_ex);   // SO: same-sector lists read from global memory
   const float2* P = pin >= 0 ? d.hpart[pin] : nullptr;
-  int plo = 0, phi = 0;
-  if (P) { plo = d.sec_start[prev_colour * s8]; phi = d.sec_start[(prev_colour + 1) * s8]; }
 
   // phase 1
   for (int t = threadIdx.x; t < na; t += blockDim.x) {
@@ -159,13 +155,16 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
     S[3 * t + 2] = make_float2(s4h.z, s4l.z);
     float hx, lx, hy, ly, hz, lz;
     if (P) {
+      // the partial field of every other colour, plus the colour the previous pass turned
       hx = p0.x; lx = p0.y; hy = p1.x; ly = p1.y; hz = p2.x; lz = p2.y;
-      ext_field<SO>(d, i, ni, ne, plo, phi, 1, hx, lx, hy, ly, hz, lz);
+      const uint2 g = __ldg(d.exc + i);
+      ext_field<SO>(d, i, group_start(g, prev_colour, ne), group_start(g, prev_colour + 1, ne), hx, lx, hy, ly, hz,
+                    lz);
     } else {
       hx = d.zee_f[0].x; lx = d.zee_f[0].y;
       hy = d.zee_f[1].x; ly = d.zee_f[1].y;
       hz = d.zee_f[2].x; lz = d.zee_f[2].y;
-      ext_field<SO>(d, i, ni, ne, 0, 0, 0, hx, lx, hy, ly, hz, lz);
+      ext_field<SO>(d, i, ni, ne, hx, lx, hy, ly, hz, lz);
     }
     H[3 * t] = D2(acc_done(hx, lx));
     H[3 * t + 1] = D2(acc_done(hy, ly));
@@ -307,7 +306,6 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
   } else if (pout >= 0) {
     // precompute the next pass's partial external field (all neighbours not
     // of this pass's colour) for block b's sectors of the next colour
-    const int clo = d.sec_start[colour * s8], chi = d.sec_start[(colour + 1) * s8];
     const int nq0 = next_colour * s8 + blockIdx.x * SW_SPB;
     const int nq1 = min(nq0 + SW_SPB, (next_colour + 1) * s8);
     const int n0 = d.sec_start[nq0], n1 = d.sec_start[nq1];
@@ -317,7 +315,11 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
       float hx = d.zee_f[0].x, lx = d.zee_f[0].y;
       float hy = d.zee_f[1].x, ly = d.zee_f[1].y;
       float hz = d.zee_f[2].x, lz = d.zee_f[2].y;
-      ext_field<SO>(d, i, __ldg(d.exin + i), __ldg(d.exn + i), clo, chi, 0, hx, lx, hy, ly, hz, lz);
+      // every other-sector neighbour not of this pass's colour: two ranges
+      const int ne = __ldg(d.exn + i);
+      const uint2 g = __ldg(d.exc + i);
+      ext_field<SO>(d, i, __ldg(d.exin + i), group_start(g, colour, ne), hx, lx, hy, ly, hz, lz);
+      ext_field<SO>(d, i, group_start(g, colour + 1, ne), ne, hx, lx, hy, ly, hz, lz);
       Q[3 * (size_t)i] = make_float2(hx, lx);
       Q[3 * (size_t)i + 1] = make_float2(hy, ly);
       Q[3 * (size_t)i + 2] = make_float2(hz, lz);
