@@ -314,7 +314,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_cnt = L.take<int>(d.nsec), o_start = L.take<int>(d.nsec + 1), o_fill = L.take<int>(d.nsec);
   size_t o_exj = L.take<int>(nn * d.max_ex), o_exn = L.take<int>(nn), o_exin = L.take<int>(nn);
   size_t o_exc = L.take<uint2>(nn);
-  size_t o_exJ = L.take<float2>(nn * d.max_ex);
+  size_t o_exJ = L.take<float2>(nn * d.max_ex), o_exdJ = L.take<float2>(nn * d.max_ex);
   const bool so_pairs = d.so != 0;   // the spin-orbit sweep reads the tables whenever a term is on
   size_t o_exso = so_pairs ? L.take<float2>(5 * nn * d.max_ex) : 0;
   const bool eam = (d.mech & SL_MECH_EAM) != 0;
@@ -366,7 +366,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.sec_count = (int*)(base + o_cnt); d.sec_start = (int*)(base + o_start); d.sec_fill = (int*)(base + o_fill);
     d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn); d.exin = (int*)(base + o_exin);
     d.exc = (uint2*)(base + o_exc);
-    d.exJ = (float2*)(base + o_exJ);
+    d.exJ = (float2*)(base + o_exJ); d.exdJ = (float2*)(base + o_exdJ);
     d.exso = so_pairs ? (float2*)(base + o_exso) : nullptr;
     d.em_fp = eam ? (float2*)(base + o_emfp) : nullptr;
     d.rx = (SlFix*)(base + o_rx);

@@ -134,6 +134,7 @@ struct SlDev {
   int *exj, *exn, *exin;    // [max_ex][n] neighbour-major (same-sector entries first), counts
   uint2 *exc;               // [n] start of each colour's group of the other entries, one byte per colour
   float2 *exJ;              // [max_ex][n] J_ij (hi, lo) at current r
+  float2 *exdJ;             // [max_ex][n] J'(r_ij)/r_ij (hi, lo) at current r, for the forces
   // [5][max_ex][n] g1, d, e_x, e_y, e_z (hi, lo) at current r, e = (r_j - r_i)/r;
   // zero beyond ex_rc (NULL when so == 0)
   float2 *exso;

@@ -411,7 +411,7 @@ __global__ void k_jtable(SlDev d) {
   const box3 B = load_box(d, d.reps[__ldg(d.arep + i)]);
   const int ne = d.exn[i];
   const size_t n = (size_t)d.n;
-  const df ix = F2(d.ex_ix_f), a4 = F2(d.ex_4a_f), g = F2(d.ex_g_f);
+  const df ix = F2(d.ex_ix_f), a4 = F2(d.ex_4a_f), g = F2(d.ex_g_f), a8 = F2(d.ex_8ad2_f);
   const df rc2 = F2(d.ex_rc2_f);
   float rh = 0.0f, rl = 0.0f;   // embedding density
   for (int k = 0; k < ne; ++k) {
@@ -424,14 +424,19 @@ __global__ void k_jtable(SlDev d) {
     acc_prod(h, l, dd.z, dd.z);
     const df r2 = acc_done(h, l);
     if (DENS) eam_f_acc(d, r2, rh, rl);
-    df J = df_f(0.0f);
+    df J = df_f(0.0f), dJr = df_f(0.0f);
     const bool in = df_lt(r2, rc2);
     if (in) {
       const df x = df_mul(r2, ix);
       const df ex = df_exp(df_neg(x));
-      J = df_mul(df_mul(a4, x), df_mul(df_add_f(df_neg(df_mul(g, x)), 1.0f), ex));
+      const df gx = df_mul(g, x);
+      J = df_mul(df_mul(a4, x), df_mul(df_add_f(df_neg(gx), 1.0f), ex));
+      // J'(r)/r = 8 alpha/delta^2 e^{-x} (1 - x (1 + 2 g - g x)) for the forces
+      const df poly = df_add_f(df_neg(df_mul(x, df_add_f(df_sub(df_scale(g, 2.0f), gx), 1.0f))), 1.0f);
+      dJr = df_mul(df_mul(a8, ex), poly);
     }
     d.exJ[e] = D2(J);
+    d.exdJ[e] = D2(dJr);
     if (SO && d.exso) {
       // g1(r), d(r) and e = (r_j - r_i)/r of the spin-orbit pair terms
       const size_t P = (size_t)d.max_ex * n;
@@ -492,7 +497,8 @@ __device__ __forceinline__ df eam_coeff(const SlDev& d, df r2, df rinv, df fpij)
 //   F_i = sum_j [V'(r) - J'(r) (s_i.s_j)] (r_j - r_i)/r
 // with V'(r)/r = 2 a D0 e (1 - e)/r, e = exp(-a (r - r0)) (Morse, r < morse_rc)
 // and J'(r)/r = 8 alpha/delta^2 e^{-x} (1 - 2 gamma x - x + gamma x^2),
-// x = r^2/delta^2 (Eq. BSfunction, r < ex_rc).  One loop over the Morse list;
+// x = r^2/delta^2 (Eq. BSfunction, r < ex_rc), read from the exchange table
+// that k_jtable filled at the same positions.  Loops over the Morse list;
 // stored in FP64, then optionally v += (dt/2) F / m (the closing half-kick).
 __device__ __forceinline__ df morse_coeff(df r2, df na, df r0, df c2, df& rinv) {
   rinv = df_rsqrt(r2);
@@ -513,7 +519,7 @@ __global__ void k_force(SlDev d, int kick) {
   float fxh = 0.0f, fxl = 0.0f, fyh = 0.0f, fyl = 0.0f, fzh = 0.0f, fzl = 0.0f;
   const int nm = d.mn[i], ne = d.exn[i];
   const df na = F2(d.m_nalpha_f), r0 = F2(d.m_r0_f), c2 = F2(d.m_c2_f), rc2 = F2(d.m_rc2_f);
-  const df ix = F2(d.ex_ix_f), g = F2(d.ex_g_f), a8 = F2(d.ex_8ad2_f), xrc2 = F2(d.ex_rc2_f);
+  const df xrc2 = F2(d.ex_rc2_f);
   const float rc2_hi = rc2.hi * 1.0001f;
   const bool eam = MECH && (d.mech & SL_MECH_EAM);
   const df ed2 = F2(d.em_d2_f);
@@ -531,12 +537,8 @@ __global__ void k_force(SlDev d, int kick) {
     df c = df_lt(r2, rc2) ? morse_coeff(r2, na, r0, c2, rinv) : df_f(0.0f);
     if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
     if (df_lt(r2, xrc2)) {
-      const df x = df_mul(r2, ix);
-      const df ex = df_exp(df_neg(x));
-      const df gxm = df_mul(g, x);
-      // 1 - 2 g x - x + g x^2 = 1 - x (1 + 2 g - g x)
-      const df poly = df_add_f(df_neg(df_mul(x, df_add_f(df_sub(df_scale(g, 2.0f), gxm), 1.0f))), 1.0f);
-      const df dJr = df_mul(df_mul(a8, ex), poly);
+      // J'(r)/r from the exchange table (same positions, same entry order)
+      const df dJr = F2(__ldg(d.exdJ + (size_t)k * d.n + i));
       const df3 sj = load_spin(d, j);
       const df sij = dot3(si, sj);
       c = df_sub(c, df_mul(dJr, sij));
