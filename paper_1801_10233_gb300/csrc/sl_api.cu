@@ -8,6 +8,8 @@
 #include <vector>
 
 #include "sl_internal.cuh"
+#include "sl_df64.cuh"
+#include "sl_pair.cuh"
 
 struct sl_ctx {
   sl_params p;              // fields shared by every replica (replica 0's copy)
@@ -305,7 +307,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   Layout L;
   size_t nn = (size_t)n;
   size_t o_r = L.take<double4_32a>(nn), o_v = L.take<double4_32a>(nn), o_s = L.take<double4_32a>(nn);
-  size_t o_F = L.take<double4_32a>(nn), o_rb = L.take<double4_32a>(nn);
+  size_t o_F = L.take<double4_32a>(nn), o_rb = L.take<SlFix>(nn);
   size_t o_tr = L.take<double4_32a>(nn), o_tv = L.take<double4_32a>(nn), o_ts = L.take<double4_32a>(nn);
   size_t o_tF = L.take<double4_32a>(nn);
   size_t o_perm = L.take<int>(nn), o_rank = L.take<int>(nn), o_secq = L.take<int>(nn);
@@ -357,7 +359,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   }
   if (base) {
     d.r = (double4_32a*)(base + o_r); d.v = (double4_32a*)(base + o_v); d.s = (double4_32a*)(base + o_s);
-    d.F = (double4_32a*)(base + o_F); d.rb = (double4_32a*)(base + o_rb);
+    d.F = (double4_32a*)(base + o_F); d.rbx = (SlFix*)(base + o_rb);
     d.tr = (double4_32a*)(base + o_tr); d.tv = (double4_32a*)(base + o_tv); d.ts = (double4_32a*)(base + o_ts);
     d.tF = (double4_32a*)(base + o_tF);
     d.perm = (int*)(base + o_perm); d.rank = (int*)(base + o_rank); d.secq = (int*)(base + o_secq);
@@ -424,9 +426,8 @@ __global__ void k_check(SlDev d) {
 __global__ void k_disp_flag(SlDev d) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= d.n) return;
-  double4_32a r = d.r[k], b = d.rb[k];
-  double x = r.x - b.x, y = r.y - b.y, z = r.z - b.z;
-  if (x * x + y * y + z * z > d.half_skin2) d.ctrl->need_rebuild = 1;
+  const float m = fx_dist2(fx_pos(d.r[k]), d.rbx[k]);
+  if ((double)m > d.half_skin2) d.ctrl->need_rebuild = 1;
 }
 
 int cuda_err(sl_ctx* c) {
@@ -558,6 +559,12 @@ int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, 
   plan(params, n_replicas, c->d, c->reps, (char*)workspace);
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return SL_ERR_CUDA; }
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return SL_ERR_CUDA;
+  }
+  c->d.rb_cap = 8 * nsm;
   if (sl_prepare_kernels() != SL_OK || (c->d.ham == SL_HAM_LEARNED && sl_ml_prepare_kernels() != SL_OK)) {
     sl_destroy(c);
     return SL_ERR_CUDA;

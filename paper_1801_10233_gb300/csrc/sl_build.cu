@@ -12,6 +12,8 @@
 // Every kernel here runs only while ctrl->need_rebuild is set, so the whole
 // sequence can sit in the step's launch sequence (and in a CUDA graph) and
 // costs one early-exit per kernel when no rebuild is due.
+#include <algorithm>
+
 #include "sl_internal.cuh"
 #include "sl_df64.cuh"
 #include "sl_pair.cuh"
@@ -29,20 +31,20 @@ __global__ void k_rb_zero(SlDev d) {
 // Wrap positions into their replica's box and find each atom's sector rank.
 __global__ void k_rb_assign(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n) return;
-  const SlRep& R = d.reps[d.arep[k]];
-  double4_32a p = d.r[k];
-  p.x = sl_wrap(p.x, R.box[0]);
-  p.y = sl_wrap(p.y, R.box[1]);
-  p.z = sl_wrap(p.z, R.box[2]);
-  d.r[k] = p;
-  int sx = sl_sector_coord(p.x, R.edge[0], R.nx);
-  int sy = sl_sector_coord(p.y, R.edge[1], R.ny);
-  int sz = sl_sector_coord(p.z, R.edge[2], R.nz);
-  int q = sl_sector_rank(d, R, sx, sy, sz);
-  d.tsecq[k] = q;
-  atomicAdd(&d.sec_count[q], 1);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
+    const SlRep& R = d.reps[d.arep[k]];
+    double4_32a p = d.r[k];
+    p.x = sl_wrap(p.x, R.box[0]);
+    p.y = sl_wrap(p.y, R.box[1]);
+    p.z = sl_wrap(p.z, R.box[2]);
+    d.r[k] = p;
+    int sx = sl_sector_coord(p.x, R.edge[0], R.nx);
+    int sy = sl_sector_coord(p.y, R.edge[1], R.ny);
+    int sz = sl_sector_coord(p.z, R.edge[2], R.nz);
+    int q = sl_sector_rank(d, R, sx, sy, sz);
+    d.tsecq[k] = q;
+    atomicAdd(&d.sec_count[q], 1);
+  }
 }
 
 // Exclusive scan of the sector counts (one block; rebuild-only).
@@ -68,56 +70,56 @@ __global__ void k_rb_scan(SlDev d) {
 
 __global__ void k_rb_scatter(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n) return;
-  int q = d.tsecq[k];
-  int pos = d.sec_start[q] + atomicAdd(&d.sec_fill[q], 1);
-  d.src[pos] = k;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
+    int q = d.tsecq[k];
+    int pos = d.sec_start[q] + atomicAdd(&d.sec_fill[q], 1);
+    d.src[pos] = k;
+  }
 }
 
 // Order each sector's atoms by atom id (insertion sort; sectors hold ~10).
 __global__ void k_rb_sort(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= d.nsec) return;
-  int a = d.sec_start[q], b = d.sec_start[q + 1];
-  for (int x = a + 1; x < b; ++x) {
-    int v = d.src[x];
-    int id = d.perm[v];
-    int y = x - 1;
-    while (y >= a && d.perm[d.src[y]] > id) { d.src[y + 1] = d.src[y]; --y; }
-    d.src[y + 1] = v;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.nsec; q += gridDim.x * blockDim.x) {
+    int a = d.sec_start[q], b = d.sec_start[q + 1];
+    for (int x = a + 1; x < b; ++x) {
+      int v = d.src[x];
+      int id = d.perm[v];
+      int y = x - 1;
+      while (y >= a && d.perm[d.src[y]] > id) { d.src[y + 1] = d.src[y]; --y; }
+      d.src[y + 1] = v;
+    }
   }
 }
 
 __global__ void k_rb_gather(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n) return;
-  int o = d.src[k];
-  d.tr[k] = d.r[o];
-  d.tv[k] = d.v[o];
-  d.ts[k] = d.s[o];
-  d.tF[k] = d.F[o];
-  d.tperm[k] = d.perm[o];
-  d.tarep[k] = d.arep[o];
-  d.secq[k] = d.tsecq[o];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
+    int o = d.src[k];
+    d.tr[k] = d.r[o];
+    d.tv[k] = d.v[o];
+    d.ts[k] = d.s[o];
+    d.tF[k] = d.F[o];
+    d.tperm[k] = d.perm[o];
+    d.tarep[k] = d.arep[o];
+    d.secq[k] = d.tsecq[o];
+  }
 }
 
 __global__ void k_rb_copyback(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n) return;
-  double4_32a p = d.tr[k];
-  d.r[k] = p;
-  d.rb[k] = p;
-  d.v[k] = d.tv[k];
-  d.s[k] = d.ts[k];
-  d.F[k] = d.tF[k];
-  int id = d.tperm[k];
-  d.perm[k] = id;
-  d.rank[id] = k;
-  d.arep[k] = d.tarep[k];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
+    double4_32a p = d.tr[k];
+    d.r[k] = p;
+    d.rbx[k] = fx_pos(p);
+    d.v[k] = d.tv[k];
+    d.s[k] = d.ts[k];
+    d.F[k] = d.tF[k];
+    int id = d.tperm[k];
+    d.perm[k] = id;
+    d.rank[id] = k;
+    d.arep[k] = d.tarep[k];
+  }
 }
 
 // Full Verlet lists (both directions) from the sectors around each atom:
@@ -144,87 +146,87 @@ __global__ void k_rb_copyback(SlDev d) {
 // applies the exact cutoff to the pairs it reads.
 __global__ void k_rb_nbr(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n) return;
-  const SlRep& R = d.reps[d.arep[i]];
-  const p3 pi = load_pos(d, i);
-  const box3 B = load_box(d, R);
-  const float lm2 = (float)d.list_m2 * 1.0001f, le2 = (float)d.list_ex2 * 1.0001f;
-  const float lc2 = (float)d.sure_m2 * 0.9999f;     // (morse_rc - skin)^2, margin inward
-  int sx, sy, sz;
-  sl_sector_coords(d, R, d.secq[i], sx, sy, sz);
-  int lox = (2 * R.mx + 1 >= R.nx) ? 0 : -R.mx, hix = (2 * R.mx + 1 >= R.nx) ? R.nx - 1 : R.mx;
-  int loy = (2 * R.my + 1 >= R.ny) ? 0 : -R.my, hiy = (2 * R.my + 1 >= R.ny) ? R.ny - 1 : R.my;
-  int loz = (2 * R.mz + 1 >= R.nz) ? 0 : -R.mz, hiz = (2 * R.mz + 1 >= R.nz) ? R.nz - 1 : R.mz;
-  const float lr2 = (float)d.m_rc2;
-  int ce = 0, cm = 0, cc = 0;
-  // pass 0: exchange entries and the Morse-only entries certain to stay
-  // inside the cutoff; pass 1: other Morse-only entries inside it at the
-  // build; pass 2: the rest
-  for (int pass = 0; pass < 3; ++pass)
-  for (int oz = loz; oz <= hiz; ++oz) {
-    int tz = (sz + oz + 2 * R.nz) % R.nz;
-    for (int oy = loy; oy <= hiy; ++oy) {
-      int ty = (sy + oy + 2 * R.ny) % R.ny;
-      for (int ox = lox; ox <= hix; ++ox) {
-        int tx = (sx + ox + 2 * R.nx) % R.nx;
-        int q = sl_sector_rank(d, R, tx, ty, tz);
-        int a = d.sec_start[q], b = d.sec_start[q + 1];
-        for (int j = a; j < b; ++j) {
-          if (j == i) continue;
-          const float r2 = pair_pre(B, pi, load_pos(d, j)).r2;
-          if (r2 < le2) {
-            if (pass == 0) {
-              if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;
-              ++ce;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
+    const SlRep& R = d.reps[d.arep[i]];
+    const p3 pi = load_pos(d, i);
+    const box3 B = load_box(d, R);
+    const float lm2 = (float)d.list_m2 * 1.0001f, le2 = (float)d.list_ex2 * 1.0001f;
+    const float lc2 = (float)d.sure_m2 * 0.9999f;     // (morse_rc - skin)^2, margin inward
+    int sx, sy, sz;
+    sl_sector_coords(d, R, d.secq[i], sx, sy, sz);
+    int lox = (2 * R.mx + 1 >= R.nx) ? 0 : -R.mx, hix = (2 * R.mx + 1 >= R.nx) ? R.nx - 1 : R.mx;
+    int loy = (2 * R.my + 1 >= R.ny) ? 0 : -R.my, hiy = (2 * R.my + 1 >= R.ny) ? R.ny - 1 : R.my;
+    int loz = (2 * R.mz + 1 >= R.nz) ? 0 : -R.mz, hiz = (2 * R.mz + 1 >= R.nz) ? R.nz - 1 : R.mz;
+    const float lr2 = (float)d.m_rc2;
+    int ce = 0, cm = 0, cc = 0;
+    // pass 0: exchange entries and the Morse-only entries certain to stay
+    // inside the cutoff; pass 1: other Morse-only entries inside it at the
+    // build; pass 2: the rest
+    for (int pass = 0; pass < 3; ++pass)
+    for (int oz = loz; oz <= hiz; ++oz) {
+      int tz = (sz + oz + 2 * R.nz) % R.nz;
+      for (int oy = loy; oy <= hiy; ++oy) {
+        int ty = (sy + oy + 2 * R.ny) % R.ny;
+        for (int ox = lox; ox <= hix; ++ox) {
+          int tx = (sx + ox + 2 * R.nx) % R.nx;
+          int q = sl_sector_rank(d, R, tx, ty, tz);
+          int a = d.sec_start[q], b = d.sec_start[q + 1];
+          for (int j = a; j < b; ++j) {
+            if (j == i) continue;
+            const float r2 = pair_pre(B, pi, load_pos(d, j)).r2;
+            if (r2 < le2) {
+              if (pass == 0) {
+                if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;
+                ++ce;
+              }
+            } else if (r2 < lm2 && (r2 < lc2 ? 0 : (r2 < lr2 ? 1 : 2)) == pass) {
+              // Morse-only entries go after a gap of max_ex rows for now
+              if (d.max_ex + cm < d.max_m) d.mj[(size_t)(d.max_ex + cm) * d.n + i] = j;
+              ++cm;
+              if (pass == 0) ++cc;
             }
-          } else if (r2 < lm2 && (r2 < lc2 ? 0 : (r2 < lr2 ? 1 : 2)) == pass) {
-            // Morse-only entries go after a gap of max_ex rows for now
-            if (d.max_ex + cm < d.max_m) d.mj[(size_t)(d.max_ex + cm) * d.n + i] = j;
-            ++cm;
-            if (pass == 0) ++cc;
           }
         }
       }
     }
+    if (d.max_ex + cm > d.max_m || ce > d.max_ex) sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW);
+    const int ne = min(ce, d.max_ex);
+    const int nmo = min(cm, d.max_m - d.max_ex);
+    d.mn[i] = ne + nmo;
+    d.mnc[i] = ne + min(cc, nmo);
+    d.exn[i] = ne;
+    // stable partition: same-sector neighbours first
+    const int qi = d.secq[i];
+    const int sa = d.sec_start[qi], sb = d.sec_start[qi + 1];
+    int* col = d.exj + i;     // entry k at col[k * n]
+    const size_t n = (size_t)d.n;
+    int tmp[SL_MAX_EX_CAP];
+    unsigned char tcol[SL_MAX_EX_CAP];
+    int nin = 0, nout = 0;
+    for (int k = 0; k < ne; ++k) {
+      const int j = col[k * n];
+      if (j >= sa && j < sb) col[(nin++) * n] = j;
+      else tmp[nout++] = j;
+    }
+    // the other neighbours grouped by their sector's colour (stable); group c
+    // starts at entry byte c of exc[i] (group 8 ends at exn[i])
+    for (int k = 0; k < nout; ++k) tcol[k] = (unsigned char)(d.secq[tmp[k]] / d.s8);
+    unsigned st[8];
+    int w = nin;
+    for (int c = 0; c < 8; ++c) {
+      st[c] = (unsigned)w;
+      for (int k = 0; k < nout; ++k)
+        if (tcol[k] == c) col[(w++) * n] = tmp[k];
+    }
+    d.exc[i] = make_uint2(st[0] | st[1] << 8 | st[2] << 16 | st[3] << 24, st[4] | st[5] << 8 | st[6] << 16 | st[7] << 24);
+    d.exin[i] = nin;
+    // Morse list: the exchange list, then the Morse-only entries moved down
+    int* mcol = d.mj + i;
+    for (int k = 0; k < nmo; ++k) mcol[(ne + k) * n] = mcol[(d.max_ex + k) * n];
+    for (int k = 0; k < ne; ++k) mcol[k * n] = col[k * n];
+    atomicMax(&d.ctrl->max_m_seen, ce + cm);
+    atomicMax(&d.ctrl->max_ex_seen, ce);
   }
-  if (d.max_ex + cm > d.max_m || ce > d.max_ex) sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW);
-  const int ne = min(ce, d.max_ex);
-  const int nmo = min(cm, d.max_m - d.max_ex);
-  d.mn[i] = ne + nmo;
-  d.mnc[i] = ne + min(cc, nmo);
-  d.exn[i] = ne;
-  // stable partition: same-sector neighbours first
-  const int qi = d.secq[i];
-  const int sa = d.sec_start[qi], sb = d.sec_start[qi + 1];
-  int* col = d.exj + i;     // entry k at col[k * n]
-  const size_t n = (size_t)d.n;
-  int tmp[SL_MAX_EX_CAP];
-  unsigned char tcol[SL_MAX_EX_CAP];
-  int nin = 0, nout = 0;
-  for (int k = 0; k < ne; ++k) {
-    const int j = col[k * n];
-    if (j >= sa && j < sb) col[(nin++) * n] = j;
-    else tmp[nout++] = j;
-  }
-  // the other neighbours grouped by their sector's colour (stable); group c
-  // starts at entry byte c of exc[i] (group 8 ends at exn[i])
-  for (int k = 0; k < nout; ++k) tcol[k] = (unsigned char)(d.secq[tmp[k]] / d.s8);
-  unsigned st[8];
-  int w = nin;
-  for (int c = 0; c < 8; ++c) {
-    st[c] = (unsigned)w;
-    for (int k = 0; k < nout; ++k)
-      if (tcol[k] == c) col[(w++) * n] = tmp[k];
-  }
-  d.exc[i] = make_uint2(st[0] | st[1] << 8 | st[2] << 16 | st[3] << 24, st[4] | st[5] << 8 | st[6] << 16 | st[7] << 24);
-  d.exin[i] = nin;
-  // Morse list: the exchange list, then the Morse-only entries moved down
-  int* mcol = d.mj + i;
-  for (int k = 0; k < nmo; ++k) mcol[(ne + k) * n] = mcol[(d.max_ex + k) * n];
-  for (int k = 0; k < ne; ++k) mcol[k * n] = col[k * n];
-  atomicMax(&d.ctrl->max_m_seen, ce + cm);
-  atomicMax(&d.ctrl->max_ex_seen, ce);
 }
 
 __global__ void k_rb_end(SlDev d) {
@@ -248,8 +250,11 @@ int sl_launch_force_rebuild_flag(const SlDev& d, cudaStream_t st) {
 }
 
 // The rebuild sequence; each kernel returns at once unless need_rebuild is set.
+// The per-atom and per-sector kernels loop over a grid of at most rb_cap
+// blocks: on the many steps without a rebuild they only launch and return.
 int sl_launch_rebuild(const SlDev& d, cudaStream_t st) {
-  int gn = grid_for(d.n), gs = grid_for(d.nsec);
+  const int cap = d.rb_cap > 0 ? d.rb_cap : 1 << 30;
+  int gn = std::min(grid_for(d.n), cap), gs = std::min(grid_for(d.nsec), cap);
   int gz = gs < 1024 ? gs : 1024;
   k_rb_zero<<<gz, SL_BLOCK, 0, st>>>(d);
   k_rb_assign<<<gn, SL_BLOCK, 0, st>>>(d);

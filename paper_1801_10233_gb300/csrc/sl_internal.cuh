@@ -97,6 +97,7 @@ struct SlDev {
   int ham;                  // SL_HAM_ANALYTIC or SL_HAM_LEARNED
   int tune_sweep;           // colour-pass tile shape variant (0 .. SL_SWEEP_VARIANTS-1)
   int tune_block;           // threads per block of the per-atom kernels (0: SL_BLOCK)
+  int rb_cap;               // most blocks of a rebuild kernel (grid-stride loops)
 
   // double-float constants (hi, lo)
   float2 zee_f[3], inv_hbar_f, tau_f;        // tau = dt/4
@@ -122,7 +123,8 @@ struct SlDev {
   int* tarep;               // rebuild scratch
 
   // state, sector-sorted (FP64, authoritative)
-  double4_32a *r, *v, *s, *F, *rb;
+  double4_32a *r, *v, *s, *F;
+  SlFix *rbx;               // positions at the last rebuild, fixed point
   // split copies for the double-float kernels
   SlFix *rx;                // r in fixed point, rint(r 2^F)
   float4 *sdf;              // s = hi + lo to ~48 bits: sdf[2i] = hi, sdf[2i+1] = lo

@@ -137,15 +137,56 @@ __device__ __forceinline__ df3 cross3(const df3& a, const df3& b) {
   return c;
 }
 
-// Fixed-point copy of a position (out-of-range values saturate; they occur
-// only before the first wrap into the box, when no pair kernel reads them).
-__device__ __forceinline__ void store_pos_split(const SlDev& d, int k, double4_32a r) {
+// rint(x 2^48), ties to even, from the IEEE-754 fields of x by integer
+// operations (GB300's FP64 pipe is slow): x 2^48 = m 2^(e - 1027) with the
+// 53-bit significand m and biased exponent e.  Values of 2^14 A or more (and
+// non-finite ones) saturate to +-2^62; they occur only before the first wrap
+// into the box, when no pair kernel reads them.
+__device__ __forceinline__ long long fx_from_double(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return 0;
+  const long long m = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+  const int sh = e - 1075 + SL_FX_BITS;
+  long long X;
+  if (sh >= 10) {
+    X = 1ll << 62;
+  } else if (sh >= 0) {
+    X = m << sh;
+  } else if (sh > -54) {
+    const int s = -sh;
+    const long long q = m >> s, rem = m & ((1ll << s) - 1), half = 1ll << (s - 1);
+    X = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+  } else {
+    X = 0;
+  }
+  return b < 0 ? -X : X;
+}
+
+// Fixed-point copy of a position.
+__device__ __forceinline__ SlFix fx_pos(double4_32a r) {
   SlFix x;
-  x.x = __double2ll_rn(r.x * d.fx_scale);
-  x.y = __double2ll_rn(r.y * d.fx_scale);
-  x.z = __double2ll_rn(r.z * d.fx_scale);
+  x.x = fx_from_double(r.x);
+  x.y = fx_from_double(r.y);
+  x.z = fx_from_double(r.z);
   x.w = 0;
-  d.rx[k] = x;
+  return x;
+}
+__device__ __forceinline__ void store_pos_split(const SlDev& d, int k, double4_32a r) { d.rx[k] = fx_pos(r); }
+
+// |a - b|^2 in A^2 (float) of two fixed-point positions (no periodic shift).
+__device__ __forceinline__ float fx_dist2(const SlFix& a, const SlFix& b) {
+  const float s = 3.5527136788005009e-15f;   // 2^-48
+  const float x = (float)(a.x - b.x) * s, y = (float)(a.y - b.y) * s, z = (float)(a.z - b.z) * s;
+  return x * x + y * y + z * z;
+}
+
+// r has finite components (exponent field not all ones).
+__device__ __forceinline__ bool finite3(double4_32a r) {
+  const unsigned hx = (unsigned)(__double_as_longlong(r.x) >> 32), hy = (unsigned)(__double_as_longlong(r.y) >> 32),
+                 hz = (unsigned)(__double_as_longlong(r.z) >> 32);
+  return ((hx & 0x7ff00000u) != 0x7ff00000u) && ((hy & 0x7ff00000u) != 0x7ff00000u) &&
+         ((hz & 0x7ff00000u) != 0x7ff00000u);
 }
 
 __device__ __forceinline__ void store_spin_split(const SlDev& d, int k, double4_32a s) {

@@ -9,6 +9,8 @@
 // runs in double-float on the FP32 pipes (sl_df64.cuh) from split copies of r
 // (exact three-float pieces) and s (float pairs), and each result is added to
 // the FP64 state once per atom.
+#include <algorithm>
+
 #include "sl_internal.cuh"
 #include "sl_df64.cuh"
 #include "sl_pair.cuh"
@@ -349,22 +351,25 @@ __global__ void k_kick(SlDev d, double h) {
   d.v[k] = v;
 }
 
-// r += dt v, the largest displacement since the last rebuild, split copy of r.
+// r += dt v, the fixed-point copy of r, the largest displacement since the
+// last rebuild (float, from the exact fixed-point difference) and a
+// finiteness check on the bits: the only FP64 arithmetic is the drift itself.
 __global__ void k_drift(SlDev d) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  double m = 0.0;
+  float m = 0.0f;
   if (k < d.n) {
-    double4_32a r = d.r[k], v = d.v[k], b = d.rb[k];
+    double4_32a r = d.r[k];
+    const double4_32a v = d.v[k];
     r.x = fma(d.dt, v.x, r.x); r.y = fma(d.dt, v.y, r.y); r.z = fma(d.dt, v.z, r.z);
     d.r[k] = r;
-    store_pos_split(d, k, r);
-    double x = r.x - b.x, y = r.y - b.y, z = r.z - b.z;
-    m = x * x + y * y + z * z;
-    if (!(m == m) || !(fabs(r.x) + fabs(r.y) + fabs(r.z) < 1e300)) sl_set_error(d.ctrl, SL_ERR_NONFINITE);
+    const SlFix x = fx_pos(r);
+    d.rx[k] = x;
+    m = fx_dist2(x, d.rbx[k]);
+    if (!finite3(r) || !(m == m)) sl_set_error(d.ctrl, SL_ERR_NONFINITE);
   }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.0)
-    atomicMax(&d.ctrl->maxdisp2_bits, (unsigned long long)__double_as_longlong(m));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0f)
+    atomicMax(&d.ctrl->maxdisp2_bits, (unsigned long long)__double_as_longlong((double)m));
 }
 
 // Decide whether this step re-sectors (displacement trigger or schedule).
@@ -735,10 +740,10 @@ __global__ void k_omega_all(SlDev d, double* out) {
 // rebuild when `only_if_rebuild` is set).
 __global__ void k_split_all(SlDev d, int only_if_rebuild) {
   if (only_if_rebuild && !d.ctrl->need_rebuild) return;
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= d.n) return;
-  store_pos_split(d, k, d.r[k]);
-  store_spin_split(d, k, d.s[k]);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.n; k += gridDim.x * blockDim.x) {
+    store_pos_split(d, k, d.r[k]);
+    store_spin_split(d, k, d.s[k]);
+  }
 }
 
 // Allow the sweep's dynamic shared memory (above the 48 KB default).
@@ -766,7 +771,8 @@ int sl_prepare_kernels() {
 }
 
 int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild) {
-  k_split_all<<<grid_for(d.n), SL_BLOCK, 0, st>>>(d, only_if_rebuild);
+  const int g = only_if_rebuild && d.rb_cap > 0 ? std::min(grid_for(d.n), d.rb_cap) : grid_for(d.n);
+  k_split_all<<<g, SL_BLOCK, 0, st>>>(d, only_if_rebuild);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 
