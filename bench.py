@@ -44,15 +44,15 @@ SAMPLE_CELLS = 16
 MORSE_PAIR_FLOPS = 3 + 5 + 10 + 2 + 20 + 3 + 10 + 6      # dr, r^2, sqrt, arg, exp, V'/r, accumulate
 EXCH_FORCE_FLOPS = 5 + 6                                # s_i.s_j, accumulate
 JTABLE_PAIR_FLOPS = 3 + 5 + 2 + 20 + 6                  # dr, r^2, x, exp, J
-EXCH_DJ_FLOPS = 10 + 5                                  # J'/r from the shared exponential
+EXCH_DJ_FLOPS = 10 + 5                                  # J'/r from the same exponential (tabulated with J)
 ROTATION_FLOPS = 14 * 6 + 3 + 5 + 20 + 20 + 9 + 12 + 6  # field, u, |w|, sincos, A/B, cross, increment
 PHASE_FLOPS_PER_ATOM = {
     "kick": 6,
     "spin_half_op_1": 2 * ROTATION_FLOPS,
     "drift_rebuild": 6 + 8,
-    "exchange_table": 7 * JTABLE_PAIR_FLOPS,
+    "exchange_table": 7 * (JTABLE_PAIR_FLOPS + EXCH_DJ_FLOPS),
     "spin_half_op_2": 2 * ROTATION_FLOPS,
-    "force_kick": 32 * MORSE_PAIR_FLOPS + 7 * (20 + EXCH_DJ_FLOPS + EXCH_FORCE_FLOPS) + 6,
+    "force_kick": 32 * MORSE_PAIR_FLOPS + 7 * EXCH_FORCE_FLOPS + 6,
 }
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 pipe, nominal at 2070 MHz
 # The kernels run the FP64-accurate arithmetic as double-float on the FP32
@@ -64,7 +64,7 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 20 * 2 / 1e12
 # DRAM bytes (read + write) of one launch of each phase's kernel from an ncu
 # capture of the current kernels on the 64^3-cell workload
 # (profiles/force_fe_bcc_64x64x64_nve.md, profiles/jtable_fe_bcc_64x64x64_nve.md).
-NCU_TRAFFIC_64CUBED = {"force_kick": 305.9e6, "exchange_table": 86.1e6}
+NCU_TRAFFIC_64CUBED = {"force_kick": 327.4e6, "exchange_table": 120.6e6}
 
 
 def parse():
