@@ -81,19 +81,23 @@ __device__ __forceinline__ df df_fma(df a, df b, df c) { return df_add(df_mul(a,
 // Multiply by an exact power of two.
 __device__ __forceinline__ df df_scale(df a, float p2) { return df_make(a.hi * p2, a.lo * p2); }
 
-// 1/sqrt(a), a > 0: hardware estimate, one Newton step with float
-// corrections (~2^-44), then one in df (~2^-48).
+// 1/sqrt(a), a > 0: hardware estimate, one Newton step in float (~2^-23),
+// then one correction with the residual 1 - a y^2 in df: relative error
+// below 5e-14 (measured over r^2 in [3, 45] against FP64).
 __device__ __forceinline__ df df_rsqrt(df a) {
   float y = rsqrtf(a.hi);
-  df y2 = two_prod(y, y);
-  df e = df_add_f(df_neg(df_mul(a, y2)), 1.0f);          // 1 - a y^2
-  df yd = df_add_f(df_f(y), 0.5f * y * e.hi);
-  df e2 = df_add_f(df_neg(df_mul(a, df_sqr(yd))), 1.0f);  // 1 - a yd^2
-  return df_add(yd, df_mul_f(yd, 0.5f * e2.hi));
+  y = y * __fmaf_rn(-0.5f * a.hi * y, y, 1.5f);
+  const df e = df_add_f(df_neg(df_mul(a, two_prod(y, y))), 1.0f);   // 1 - a y^2
+  return fast_two_sum(y, 0.5f * y * e.hi);
 }
 
-// exp(x) for |x| < 80: x = n ln2/64 + r, n = 64 m + j, |r| <= ln2/128;
-// exp(x) = 2^m * T[j] * (1 + p(r)), p(r) = r + r^2/2 + r^3 (1/6 + r/24 + r^2/120).
+// exp(x): x = n ln2/64 + r, n = 64 m + j, |r| <= ln2/128; n ln2/64 is exact in
+// its first 14-bit piece for |n| < 1024 (|x| < 11; beyond, the relative error
+// grows to ~1e-7, where every caller's exp(x) is below 2e-5 of its largest
+// value or x is out of its range); exp(x) = 2^m T[j] (1 + p(r)),
+// p(r) = r + q, q = r^2/2 + r^3 (1/6 + r/24 + r^2/120): r^2/2 from the exact
+// square of r.hi plus r.hi r.lo, the cubic tail (< 2.7e-8) in float.
+// Relative error below 4e-14 (measured over x in [-12, 6] against FP64).
 __device__ __forceinline__ df df_exp(df x) {
   float nf = rintf(x.hi * SL_64_LN2);
   int n = (int)nf;
@@ -101,12 +105,10 @@ __device__ __forceinline__ df df_exp(df x) {
   float r1 = __fsub_rn(x.hi, nf * SL_LN2_64_C1);
   df r = df_add(df_make(r1, x.lo), df_neg(df_add_f(two_prod(nf, SL_LN2_64_C2), nf * SL_LN2_64_C3)));
   r = fast_two_sum(r.hi, r.lo);
-  const df c6 = df_make(SL_INV_FACT3_HI, SL_INV_FACT3_LO);  // 1/6 = hi + lo
-  float tail = __fmaf_rn(r.hi, __fmaf_rn(r.hi, 1.0f / 120.0f, 1.0f / 24.0f), 0.0f);
-  df c = df_add_f(c6, tail);
-  df r2 = df_sqr(r);
-  df r3 = df_mul(r2, r);
-  df p = df_add(df_add(r, df_scale(r2, 0.5f)), df_mul(r3, c));
+  const df P = two_prod(r.hi, r.hi);
+  const float tail = r.hi * P.hi * __fmaf_rn(r.hi, __fmaf_rn(r.hi, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f);
+  const df q = df_make(0.5f * P.hi, __fmaf_rn(r.hi, r.lo, __fmaf_rn(0.5f, P.lo, tail)));
+  const df p = df_add(r, q);
   int j = n & 63, m = n >> 6;
   float2 t = __ldg(kSlExp2Table + j);
   df T = df_make(t.x, t.y);

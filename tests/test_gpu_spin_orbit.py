@@ -171,11 +171,14 @@ def test_time_reversal(System):
 
 def test_energy_conservation(System):
     """NVE with all three terms: energy drift over 2000 steps stays at the
-    level of the plain path."""
+    level of the plain path.  Each single-spin factor is three double-float
+    rotations here (two anisotropy half turns and the main turn), each exact
+    in |s| to ~2^-48; over 24,000 of them per spin the norm error walks to a
+    few 1e-14, so the bar is 5e-14 (1e-14 on the plain path's 4,000)."""
     p, r, v, s = inputs.bcc_fe_system(8, 43, T=200.0, sigma=0.02, **ALL)
     gpu = System(p, r, v, s)
     E0 = gpu.energy()[4]
     gpu.step(2000)
     s1 = _np(gpu.state()[2])
-    assert np.abs(np.linalg.norm(s1, axis=1) - 1).max() < 1e-14
+    assert np.abs(np.linalg.norm(s1, axis=1) - 1).max() < 5e-14
     assert abs(gpu.energy()[4] - E0) / p["n_atoms"] < 1e-6
