@@ -64,7 +64,7 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 20 * 2 / 1e12
 # DRAM bytes (read + write) of one launch of each phase's kernel from an ncu
 # capture of the current kernels on the 64^3-cell workload
 # (profiles/force_fe_bcc_64x64x64_nve.md, profiles/jtable_fe_bcc_64x64x64_nve.md).
-NCU_TRAFFIC_64CUBED = {"force_kick": 327.4e6, "exchange_table": 120.6e6}
+NCU_TRAFFIC_64CUBED = {"force_kick": 327.1e6, "exchange_table": 120.6e6}
 
 
 def parse():
