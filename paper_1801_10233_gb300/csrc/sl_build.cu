@@ -158,16 +158,35 @@ __global__ void k_rb_nbr(SlDev d) {
     int loy = (2 * R.my + 1 >= R.ny) ? 0 : -R.my, hiy = (2 * R.my + 1 >= R.ny) ? R.ny - 1 : R.my;
     int loz = (2 * R.mz + 1 >= R.nz) ? 0 : -R.mz, hiz = (2 * R.mz + 1 >= R.nz) ? R.nz - 1 : R.mz;
     const float lr2 = (float)d.m_rc2;
-    int ce = 0, cm = 0, cc = 0;
+    // the atom's place inside its own sector, for skipping whole sectors
+    // beyond the list radius (only where the search range is a true offset
+    // range, and with a margin far above float rounding)
+    const double4_32a ri = d.r[i];
+    const float ux = (float)(ri.x - sx * R.edge[0]), uy = (float)(ri.y - sy * R.edge[1]),
+                uz = (float)(ri.z - sz * R.edge[2]);
+    const float ex = (float)R.edge[0], ey = (float)R.edge[1], ez = (float)R.edge[2];
+    const bool cx = 2 * R.mx + 1 < R.nx, cy = 2 * R.my + 1 < R.ny, cz = 2 * R.mz + 1 < R.nz;
+    const float cut2 = lm2 * 1.001f;
+    auto gap = [](bool on, int o, float u, float e) {
+      if (!on || o == 0) return 0.0f;
+      return o > 0 ? (float)o * e - u : u + (float)(-o - 1) * e;
+    };
+    int ce = 0, cc = 0, n1 = 0, c1 = 0, c2 = 0;
     // pass 0: exchange entries and the Morse-only entries certain to stay
-    // inside the cutoff; pass 1: other Morse-only entries inside it at the
-    // build; pass 2: the rest
-    for (int pass = 0; pass < 3; ++pass)
+    // inside the cutoff (counting those inside it at the build); pass 1: the
+    // others, inside the cutoff at the build first, then beyond it
+    for (int pass = 0; pass < 2; ++pass)
     for (int oz = loz; oz <= hiz; ++oz) {
+      const float gz = gap(cz, oz, uz, ez);
+      if (gz * gz > cut2) continue;
       int tz = (sz + oz + 2 * R.nz) % R.nz;
       for (int oy = loy; oy <= hiy; ++oy) {
+        const float gy = gap(cy, oy, uy, ey);
+        if (gz * gz + gy * gy > cut2) continue;
         int ty = (sy + oy + 2 * R.ny) % R.ny;
         for (int ox = lox; ox <= hix; ++ox) {
+          const float gx = gap(cx, ox, ux, ex);
+          if (gz * gz + gy * gy + gx * gx > cut2) continue;
           int tx = (sx + ox + 2 * R.nx) % R.nx;
           int q = sl_sector_rank(d, R, tx, ty, tz);
           int a = d.sec_start[q], b = d.sec_start[q + 1];
@@ -179,16 +198,25 @@ __global__ void k_rb_nbr(SlDev d) {
                 if (ce < d.max_ex) d.exj[(size_t)ce * d.n + i] = j;
                 ++ce;
               }
-            } else if (r2 < lm2 && (r2 < lc2 ? 0 : (r2 < lr2 ? 1 : 2)) == pass) {
+            } else if (r2 < lm2) {
+              const int cls = r2 < lc2 ? 0 : (r2 < lr2 ? 1 : 2);
               // Morse-only entries go after a gap of max_ex rows for now
-              if (d.max_ex + cm < d.max_m) d.mj[(size_t)(d.max_ex + cm) * d.n + i] = j;
-              ++cm;
-              if (pass == 0) ++cc;
+              int row = -1;
+              if (pass == 0) {
+                if (cls == 0) row = d.max_ex + cc++;
+                else if (cls == 1) ++n1;
+              } else if (cls == 1) {
+                row = d.max_ex + cc + c1++;
+              } else if (cls == 2) {
+                row = d.max_ex + cc + n1 + c2++;
+              }
+              if (row >= 0 && row < d.max_m) d.mj[(size_t)row * d.n + i] = j;
             }
           }
         }
       }
     }
+    const int cm = cc + c1 + c2;
     if (d.max_ex + cm > d.max_m || ce > d.max_ex) sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW);
     const int ne = min(ce, d.max_ex);
     const int nmo = min(cm, d.max_m - d.max_ex);
