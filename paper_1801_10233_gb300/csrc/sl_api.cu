@@ -186,11 +186,6 @@ void fill_noise(std::vector<SlRep>& reps, const sl_params* ps, double dt) {
 
 // Fill d's scalars, the replica table and (if base != NULL) d's pointers;
 // returns the workspace bytes needed.
-// Fixed-point positions X = rint(r 2^F) with one F for every context, so a
-// replica's trajectory does not depend on the batch it is in: F = 48 rounds
-// positions below 16 A by at most 2^-49 A (above, FP64 is coarser) and keeps
-// |X| < 2^61 for positions within one box length of boxes up to SL_FX_MAX_BOX.
-int fixed_point_bits(const sl_params*, int) { return SL_FX_BITS; }
 
 size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, char* base) {
   std::memset(&d, 0, sizeof(d));
@@ -198,7 +193,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   reps.assign(nrep, SlRep());
   double reach = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
   int atom0 = 0, sec8 = 0, noise = 0;
-  const int fx = fixed_point_bits(ps, nrep);
+  const int fx = SL_FX_BITS;   // fixed-point positions X = rint(r 2^48)
   for (int r = 0; r < nrep; ++r) {
     SlRep& R = reps[r];
     std::memset(&R, 0, sizeof(R));
@@ -251,8 +246,6 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   }
   d.list_ex2 = (p->ex_rc_A + p->skin_A) * (p->ex_rc_A + p->skin_A);
   d.list_m2 = (p->morse_rc_A + p->skin_A) * (p->morse_rc_A + p->skin_A);
-  d.fx_F = fx;
-  d.fx_scale = std::ldexp(1.0, fx);
   d.fx_s40 = std::ldexp(1.0f, 40 - fx);
   d.fx_s20 = std::ldexp(1.0f, 20 - fx);
   d.fx_s0 = std::ldexp(1.0f, -fx);

@@ -16,7 +16,11 @@
 // Sectors per block of the colour-pass tile shapes (threads: 192, 256, 128, 192, 128).
 static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8};
 #define SL_MAX_EX_CAP 64   // largest accepted max_ex_neighbors
-#define SL_FX_BITS 48       // fixed-point positions: X = rint(r 2^48)
+// Fixed-point positions X = rint(r 2^48), one scale for every context so a
+// replica's trajectory does not depend on the batch it is in: positions
+// below 16 A are rounded by at most 2^-49 A (above, FP64 is coarser), and
+// |X| < 2^61 for positions within one box length of boxes below SL_FX_MAX_BOX.
+#define SL_FX_BITS 48
 #define SL_FX_MAX_BOX 4096.0  // box edges below 2^(60 - SL_FX_BITS) A
 
 // Control block in device memory: sticky status, rebuild flag, counters.
@@ -85,8 +89,6 @@ struct SlDev {
   double ex_alpha, ex_gamma, ex_delta, ex_rc2;
   double m_D0, m_alpha, m_r0, m_rc2, m_vshift;
   double list_ex2, list_m2; // (cutoff + skin)^2
-  int fx_F;                 // fixed-point positions: X = rint(r 2^F)
-  double fx_scale;          // 2^F
   float fx_s40, fx_s20, fx_s0;   // 2^(40-F), 2^(20-F), 2^-F
   double sure_m2;           // (morse_rc - skin)^2 (0 if skin >= morse_rc)
   double half_skin2;

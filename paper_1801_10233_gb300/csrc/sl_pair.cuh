@@ -16,8 +16,8 @@ struct df3 {
   df x, y, z;
 };
 // Positions in fixed point for the pair kernels: X = rint(r 2^F), 64-bit
-// integers, F (SlDev::fx_F) chosen on the host so that |X| < 2^61 for every
-// position within a box length of the box.  The difference of two positions
+// integers, F = SL_FX_BITS, so that |X| < 2^61 for every position within a
+// box length of the box.  The difference of two positions
 // and its periodic shift by the integer box length are exact integer
 // operations; the separation is then rounded once to double-float.
 struct p3 {
