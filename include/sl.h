@@ -235,7 +235,7 @@ int sl_counters(sl_ctx* ctx, int64_t out[8]);
 
 /* Per-phase timing.  With enable = 1, sl_step launches each step's kernels
  * directly (no graph) and records a CUDA event pair on the context's stream
- * around each phase: 0 half-kick, 1 first spin half-op (16 colour passes),
+ * around each phase: 0 half-kick, 1 first spin half-op (15 colour passes),
  * 2 drift + rebuild check (+ rebuild), 3 exchange table, 4 second spin
  * half-op, 5 forces (Morse + magneto-elastic) + closing half-kick.
  * sl_get_timing synchronises and returns ms[k] = total milliseconds and

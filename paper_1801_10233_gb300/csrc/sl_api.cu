@@ -319,6 +319,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_rx = L.take<SlFix>(nn);
   size_t o_sdf = L.take<float4>(2 * nn);
   size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
+  size_t o_xb = L.take<float2>(3 * nn), o_eb2 = L.take<float2>(3 * nn);
   size_t o_p0 = L.take<float2>(3 * nn), o_p1 = L.take<float2>(3 * nn);
   size_t o_mj = L.take<int>(nn * d.max_m), o_mn = L.take<int>(nn), o_mnc = L.take<int>(nn);
   size_t o_oa = L.take<double>(nn * SL_NOBS), o_or = L.take<double>((size_t)nrep * SL_NOBS);
@@ -369,6 +370,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.rx = (SlFix*)(base + o_rx);
     d.sdf = (float4*)(base + o_sdf);
     d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);
+    d.xbuf = (float2*)(base + o_xb); d.ebuf2 = (float2*)(base + o_eb2);
     d.hpart[0] = (float2*)(base + o_p0); d.hpart[1] = (float2*)(base + o_p1);
     d.mj = (int*)(base + o_mj); d.mn = (int*)(base + o_mn); d.mnc = (int*)(base + o_mnc);
     d.obs_atom = (double*)(base + o_oa); d.obs_rep = (double*)(base + o_or);

@@ -149,6 +149,7 @@ struct SlDev {
   int *mnc;                 // [n] end of the entries certain to be inside morse_rc until the next rebuild
   // sweep scratch for blocks whose atoms exceed shared memory: [3 n] each
   float2 *hbuf, *sbuf, *ebuf;
+  float2 *xbuf, *ebuf2;     // the fused pass's external field and second noise
   // partial external fields precomputed for the next colour pass (ping-pong)
   float2 *hpart[2];         // [3 n] each
   // per-atom observables in caller order [n][SL_NOBS], per-replica sums

@@ -3,12 +3,13 @@
 //   spin half-op, forces + half-kick.
 // The spin half-op e^{Ls dt/2} is 8 colour passes forward then 8 backward
 // (Eq. spin_ST_sectoring, Sec. 5.1); each pass updates every sector of one
-// colour concurrently, the spins inside a sector one after another.
+// colour concurrently, the spins inside a sector one after another.  The two
+// passes of colour 7 in the middle run as one launch.
 //
 // The FP64 state (r, v, s, F) is authoritative.  Pair and rotation arithmetic
-// runs in double-float on the FP32 pipes (sl_df64.cuh) from split copies of r
-// (exact three-float pieces) and s (float pairs), and each result is added to
-// the FP64 state once per atom.
+// runs in double-float on the FP32 pipes (sl_df64.cuh) from copies of r (64-bit
+// fixed point, exact differences) and s (float pairs), and each result is
+// added to the FP64 state once per atom.
 #include <algorithm>
 
 #include "sl_internal.cuh"
@@ -49,9 +50,12 @@ constexpr int SW_BATCH = 2;    // external neighbours gathered per batch
 // Dynamic shared memory of one block with up to maxa atoms: H, S (and E
 // with noise) as float2 [3 maxa], same-sector lists J [SW_MAXIN maxa]
 // float2, local index [SW_MAXIN maxa] short, counts [maxa] int.
-size_t sweep_smem_bytes(bool noise, int maxa) {
+// A fused pass (one colour forward then backward) also keeps the external
+// field X [3 maxa] and, with noise, the second pass's noise [3 maxa].
+size_t sweep_smem_bytes(bool noise, int maxa, bool fused = false) {
   return (size_t)(noise ? 3 : 2) * 3 * maxa * sizeof(float2) + (size_t)SW_MAXIN * maxa * sizeof(float2) +
-         (size_t)SW_MAXIN * maxa * sizeof(short) + (size_t)maxa * sizeof(int);
+         (size_t)SW_MAXIN * maxa * sizeof(short) + (size_t)maxa * sizeof(int) +
+         (fused ? (size_t)(noise ? 2 : 1) * 3 * maxa * sizeof(float2) : 0);
 }
 
 // (h, l) += sum of J_ij s_j (with SO: the field of the exchange, Neel and DMI
@@ -118,6 +122,12 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
   float2* sh_ij = sh_e + (noise ? 3 * SW_MAXA : 0);
   short* sh_iu = (short*)(sh_ij + SW_MAXIN * SW_MAXA);
   int* sh_in = (int*)(sh_iu + SW_MAXIN * SW_MAXA);
+  // backward = 2: the fused pass, this colour forward then backward with the
+  // same external field (no other colour turns in between), noise of
+  // sub-passes `subpass` and `subpass + 1`
+  const bool both = backward == 2;
+  float2* sh_x = (float2*)(sh_in + SW_MAXA);
+  float2* sh_e2 = sh_x + 3 * SW_MAXA;
 
   const int s8 = d.s8;
   const int q0 = colour * s8 + blockIdx.x * SW_SPB;
@@ -128,6 +138,9 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
   float2* H = fits ? sh_h : d.hbuf + 3 * (size_t)a0;
   float2* S = fits ? sh_s : d.sbuf + 3 * (size_t)a0;
   float2* E = fits ? sh_e : d.ebuf + 3 * (size_t)a0;
+  float2* X = fits ? sh_x : d.xbuf + 3 * (size_t)a0;     // fused pass only
+  float2* E2 = fits ? sh_e2 : d.ebuf2 + 3 * (size_t)a0;  // fused pass with noise only
+  float2* Fx = both ? X : H;                              // where phase 1 puts the external field
   const long long step = d.ctrl->step;
   const df tau = F2(d.tau_f);
   const size_t n = (size_t)d.n;
@@ -168,23 +181,26 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
       hz = d.zee_f[2].x; lz = d.zee_f[2].y;
       ext_field<SO>(d, i, ni, ne, hx, lx, hy, ly, hz, lz);
     }
-    H[3 * t] = D2(acc_done(hx, lx));
-    H[3 * t + 1] = D2(acc_done(hy, ly));
-    H[3 * t + 2] = D2(acc_done(hz, lz));
+    Fx[3 * t] = D2(acc_done(hx, lx));
+    Fx[3 * t + 1] = D2(acc_done(hy, ly));
+    Fx[3 * t + 2] = D2(acc_done(hz, lz));
     if (noise) {
       // eta ~ N(0, 2 D_S / |tau|), D_S = lambda (1 + lambda^2) k_B T / hbar;
       // counter (atom id within its replica, step, sub-pass, replica)
       const SlRep& R = d.reps[__ldg(d.arep + i)];
-      df3 g;
-      g.x = g.y = g.z = df_f(0.0f);
-      df sig = df_f(0.0f);
-      if (R.temperature > 0.0) {
-        g = gauss3_df(d.seed, R.replica, step, subpass, d.perm[i] - R.atom0);
-        sig = F2(R.noise_sig);
+      for (int h = 0; h < (both ? 2 : 1); ++h) {
+        df3 g;
+        g.x = g.y = g.z = df_f(0.0f);
+        df sig = df_f(0.0f);
+        if (R.temperature > 0.0) {
+          g = gauss3_df(d.seed, R.replica, step, subpass + h, d.perm[i] - R.atom0);
+          sig = F2(R.noise_sig);
+        }
+        float2* Eh = h ? E2 : E;
+        Eh[3 * t] = D2(df_mul(sig, g.x));
+        Eh[3 * t + 1] = D2(df_mul(sig, g.y));
+        Eh[3 * t + 2] = D2(df_mul(sig, g.z));
       }
-      E[3 * t] = D2(df_mul(sig, g.x));
-      E[3 * t + 1] = D2(df_mul(sig, g.y));
-      E[3 * t + 2] = D2(df_mul(sig, g.z));
     }
   }
   __syncthreads();
@@ -196,10 +212,11 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
       const int sa = d.sec_start[q], sb = d.sec_start[q + 1];
       const int m = sb - sa;
       const df ih = F2(d.inv_hbar_f);
+      for (int dir = 0; dir < (both ? 2 : 1); ++dir)
       for (int c = 0; c < m; ++c) {
-        const int i = backward ? sb - 1 - c : sa + c;
+        const int i = (both ? dir : backward) ? sb - 1 - c : sa + c;
         const int t = i - a0;
-        const float2 f0 = H[3 * t], f1 = H[3 * t + 1], f2 = H[3 * t + 2];
+        const float2 f0 = Fx[3 * t], f1 = Fx[3 * t + 1], f2 = Fx[3 * t + 2];
         float hx = f0.x, lx = f0.y, hy = f1.x, ly = f1.y, hz = f2.x, lz = f2.y;
         float gx = 0.0f, kx = 0.0f, gy = 0.0f, ky = 0.0f, gz = 0.0f, kz = 0.0f;
         const int ni = fits ? sh_in[t] : d.exin[i];
@@ -277,9 +294,10 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
           df3 sxw = cross3(s, wt);
           const df lam = F2(d.lam_f), inv = F2(d.inv1pl2_f);
           if (noise) {
-            w.x = df_add(w.x, F2(E[3 * t]));
-            w.y = df_add(w.y, F2(E[3 * t + 1]));
-            w.z = df_add(w.z, F2(E[3 * t + 2]));
+            const float2* Ed = dir ? E2 : E;
+            w.x = df_add(w.x, F2(Ed[3 * t]));
+            w.y = df_add(w.y, F2(Ed[3 * t + 1]));
+            w.z = df_add(w.z, F2(Ed[3 * t + 2]));
           }
           w.x = df_mul(df_add(w.x, df_mul(lam, sxw.x)), inv);
           w.y = df_mul(df_add(w.y, df_mul(lam, sxw.y)), inv);
@@ -300,9 +318,15 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
           S[3 * t + 1] = D2(df_add(s.y, inc.y));
           S[3 * t + 2] = D2(df_add(s.z, inc.z));
         }
-        H[3 * t] = D2(inc.x);
-        H[3 * t + 1] = D2(inc.y);
-        H[3 * t + 2] = D2(inc.z);
+        if (both && dir) {   // the fused pass's second chain: total increment
+          H[3 * t] = D2(df_add(F2(H[3 * t]), inc.x));
+          H[3 * t + 1] = D2(df_add(F2(H[3 * t + 1]), inc.y));
+          H[3 * t + 2] = D2(df_add(F2(H[3 * t + 2]), inc.z));
+        } else {
+          H[3 * t] = D2(inc.x);
+          H[3 * t + 1] = D2(inc.y);
+          H[3 * t + 2] = D2(inc.z);
+        }
       }
     }
   } else if (pout >= 0) {
@@ -669,21 +693,26 @@ int launch_tables(const SlDev& d, int grid, int block, cudaStream_t st) {
   return 1;
 }
 
-// The 16 passes of a spin half-op: colours 0..7 forward, then 7..0 backward.
-// Pass p reads the partial field written by pass p - 1 (none for p = 0).
+// The passes of a spin half-op: colours 0..6 forward, colour 7 forward then
+// backward in one fused pass (nothing of another colour turns between the
+// two), colours 6..0 backward.  Pass p reads the partial field written by
+// pass p - 1 (none for p = 0) and precomputes the next pass's.
+constexpr int SL_SWEEP_PASSES = 15;
 template <int SPB, int THREADS, bool SO>
 void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
   int g = (d.s8 + SPB - 1) / SPB;
-  size_t sm = sweep_smem_bytes(d.any_noise != 0, 12 * SPB);
-  int col[16], bwd[16];
-  for (int p = 0; p < 8; ++p) { col[p] = p; bwd[p] = 0; col[15 - p] = p; bwd[15 - p] = 1; }
-  for (int p = 0; p < 16; ++p) {
+  const bool noise = d.any_noise != 0;
+  int col[SL_SWEEP_PASSES], bwd[SL_SWEEP_PASSES];
+  for (int p = 0; p < 7; ++p) { col[p] = p; bwd[p] = 0; col[14 - p] = p; bwd[14 - p] = 1; }
+  col[7] = 7; bwd[7] = 2;
+  for (int p = 0; p < SL_SWEEP_PASSES; ++p) {
     const int prev = p > 0 ? col[p - 1] : -1;
-    const int next = p < 15 ? col[p + 1] : -1;
+    const int next = p < SL_SWEEP_PASSES - 1 ? col[p + 1] : -1;
     const int pin = p > 0 ? (p - 1) & 1 : -1;
-    const int pout = p < 15 ? p & 1 : -1;
-    k_sweep_pass<SPB, THREADS, SO><<<g, THREADS, sm, st>>>(d, col[p], bwd[p], subpass0 + bwd[p], prev, next, pin,
-                                                           pout);
+    const int pout = p < SL_SWEEP_PASSES - 1 ? p & 1 : -1;
+    const size_t sm = sweep_smem_bytes(noise, 12 * SPB, bwd[p] == 2);
+    k_sweep_pass<SPB, THREADS, SO><<<g, THREADS, sm, st>>>(d, col[p], bwd[p], subpass0 + (bwd[p] == 1), prev, next,
+                                                           pin, pout);
   }
 }
 
@@ -753,15 +782,15 @@ template <bool SO>
 bool prepare_sweep() {
   bool ok = true;
   ok &= cudaFuncSetAttribute(k_sweep_pass<32, 192, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 32)) == cudaSuccess;
+                             (int)sweep_smem_bytes(true, 12 * 32, true)) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_sweep_pass<32, 256, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 32)) == cudaSuccess;
+                             (int)sweep_smem_bytes(true, 12 * 32, true)) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_sweep_pass<16, 128, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 16)) == cudaSuccess;
+                             (int)sweep_smem_bytes(true, 12 * 16, true)) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_sweep_pass<16, 192, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 16)) == cudaSuccess;
+                             (int)sweep_smem_bytes(true, 12 * 16, true)) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_sweep_pass<8, 128, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 8)) == cudaSuccess;
+                             (int)sweep_smem_bytes(true, 12 * 8, true)) == cudaSuccess;
   return ok;
 }
 
@@ -865,7 +894,7 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
   phase(SL_PHASE_SPIN1, 0);
   launch_half_op(d, st, 0);
   phase(SL_PHASE_SPIN1, 1);
-  nk += 16;
+  nk += SL_SWEEP_PASSES;
   if (lat) {
     phase(SL_PHASE_DRIFT, 0);
     k_drift<<<grid_tb(d), tb(d), 0, st>>>(d);
@@ -881,7 +910,7 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
   phase(SL_PHASE_SPIN2, 0);
   launch_half_op(d, st, 2);
   phase(SL_PHASE_SPIN2, 1);
-  nk += 16;
+  nk += SL_SWEEP_PASSES;
   if (lat) {
     phase(SL_PHASE_FORCE, 0);
     launch_force(d, grid_tb(d), tb(d), st, 1);
