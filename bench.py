@@ -70,7 +70,7 @@ NCU_TRAFFIC_64CUBED = {"force_kick": 327.1e6, "exchange_table": 120.6e6}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200, help="timed steps (200: the 64^3-cell workload's run)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
@@ -382,8 +382,10 @@ def run_ours(args):
     forms = None
     if rank == 0 and world == 1 and not args.no_forms and args.workload == DEFAULT_WORKLOAD:
         forms = {}
-        for name, steps in (("fe_bcc_batch256", 10), ("fe_bcc_10x10x10_nve", 100),
-                            ("fe_bcc_64x64x64_spin_orbit", 50), ("fe_bcc_64x64x64_eam", 50)):
+        # timed steps as in each workload's run (the batch's 500 and the
+        # 2,000-atom system's 1,000), 200 for the spin-orbit and embedding forms
+        for name, steps in (("fe_bcc_batch256", 500), ("fe_bcc_10x10x10_nve", 1000),
+                            ("fe_bcc_64x64x64_spin_orbit", 200), ("fe_bcc_64x64x64_eam", 200)):
             fp, fr, fv, fs, fdesc = build_workload(name, 0)
             fn = int(sum(q["n_atoms"] for q in fp)) if isinstance(fp, list) else fp["n_atoms"]
             fsys = System(fp, fr, fv, fs, device=dev)
