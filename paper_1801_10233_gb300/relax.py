@@ -50,14 +50,18 @@ def _tau(ts, temps, target):
 
 
 def run(cells=10, T=300.0, ps=20.0, dt=5e-4, every=None, gamma=10.0, lam=0.01, prep_ps=2.0, seed=18016,
-        device=None):
-    """Both runs; returns a dict of their T_L and T_S series and e-folding times."""
+        device=None, extra=None):
+    """Both runs; returns a dict of their T_L and T_S series and e-folding times.
+    `extra`: further Hamiltonian parameters for both runs (for instance the
+    Neel pair term, which lets lattice motion torque collinear spins)."""
+    extra = dict(extra or {})
     steps = int(round(ps / dt))
     every = every or max(1, steps // 100)
-    out = {"cells": cells, "T_K": T, "dt_ps": dt, "ps": ps, "lambda": lam, "lattice_gamma_ps": gamma}
+    out = {"cells": cells, "T_K": T, "dt_ps": dt, "ps": ps, "lambda": lam, "lattice_gamma_ps": gamma,
+           "extra": extra}
 
     # run A: spin bath only; spins first equilibrated at T on the frozen perfect lattice
-    p, r, v, s = inputs.bcc_fe_system(cells, seed, T=T, sigma=0.0, spins="uniform", dt_ps=dt)
+    p, r, v, s = inputs.bcc_fe_system(cells, seed, T=T, sigma=0.0, spins="uniform", dt_ps=dt, **extra)
     pa = dict(p, **{"lambda": lam, "temperature_K": T, "seed": seed})
     prep = System(dict(pa, fix_lattice=1), r, np.zeros_like(v), s, device=device)
     prep.step(int(round(prep_ps / dt)))
@@ -70,7 +74,7 @@ def run(cells=10, T=300.0, ps=20.0, dt=5e-4, every=None, gamma=10.0, lam=0.01, p
     out["spin_bath"] = {"t_ps": ts, "T_L": tl, "T_S": tsp, "tau_L_ps": _tau(ts, tl, T)}
 
     # run B: lattice bath only; spins within 2-degree cones about the field
-    p, r, v, s = inputs.bcc_fe_system(cells, seed + 1, T=T, sigma=0.0, spins="cone2", dt_ps=dt)
+    p, r, v, s = inputs.bcc_fe_system(cells, seed + 1, T=T, sigma=0.0, spins="cone2", dt_ps=dt, **extra)
     pb = dict(p, lattice_gamma_ps=gamma, lattice_temperature_K=T, seed=seed + 1)
     b = System(pb, r, v, s, device=device)
     ts, tl, tsp = _series(b, steps, every, dt)
@@ -89,10 +93,13 @@ def main(argv=None):
     ap.add_argument("--dt", type=float, default=5e-4)
     ap.add_argument("--gamma", type=float, default=10.0, help="lattice damping rate gamma_L/m, 1/ps")
     ap.add_argument("--lam", type=float, default=0.01)
+    ap.add_argument("--neel", type=float, default=0.0,
+                    help="Neel pair term alpha in eV (gamma 0.1, delta 1.7 A; 0: none)")
     args = ap.parse_args(argv)
+    extra = dict(neel_alpha_eV=args.neel, neel_gamma=0.1, neel_delta_A=1.7) if args.neel else None
     from . import build
     build.build()
-    print(json.dumps(run(args.cells, args.T, args.ps, args.dt, gamma=args.gamma, lam=args.lam)))
+    print(json.dumps(run(args.cells, args.T, args.ps, args.dt, gamma=args.gamma, lam=args.lam, extra=extra)))
 
 
 if __name__ == "__main__":
