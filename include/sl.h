@@ -226,11 +226,8 @@ int sl_get_omega(sl_ctx* ctx, double* omega);
 int sl_get_order(sl_ctx* ctx, int32_t* order_dev, int32_t colour_start[9], int32_t nsec[3]);
 
 /* out[8] (host) = steps done, rebuilds done, largest exchange-list length
- * seen, largest Morse-list length seen, kernel launches per step without a
- * rebuild, 1 if steps run as a captured CUDA graph, 1 if that graph runs the
- * rebuild sequence under a conditional node (its kernels then launch only on
- * steps that rebuild; otherwise they launch every step and return at once,
- * and the count includes them), 0.  Synchronises. */
+ * seen, largest Morse-list length seen, kernel launches per step, 1 if steps
+ * run as a captured CUDA graph, 0, 0.  Synchronises. */
 int sl_counters(sl_ctx* ctx, int64_t out[8]);
 
 /* Per-phase timing.  With enable = 1, sl_step launches each step's kernels

@@ -18,8 +18,6 @@ struct sl_ctx {
   SlDev d;
   cudaStream_t stream;
   cudaStream_t cap;         // private stream for graph capture
-  cudaStream_t cap2;        // second capture stream (the rebuild body)
-  int graph_cond;           // the graph's rebuild section is a conditional node
   cudaGraphExec_t graph;
   int graph_ok;
   int device;
@@ -451,85 +449,20 @@ void drop_graph(sl_ctx* c) {
   c->graph_ok = 0;
 }
 
-// Graph-capture hook for the rebuild section: an IF node on the handle that
-// k_decide sets, whose body is the rebuild sequence captured on a second
-// stream.  On the many steps without a rebuild none of its kernels launch.
-int cond_rebuild(const SlDev& d, cudaStream_t st, void* user, int* kernels) {
-  sl_ctx* c = (sl_ctx*)user;
-  *kernels = 0;
-  cudaStreamCaptureStatus cs;
-  cudaGraph_t cg = nullptr;
-  const cudaGraphNode_t* deps = nullptr;
-  size_t nd = 0;
-  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess ||
-      cs != cudaStreamCaptureStatusActive)
-    return SL_ERR_CUDA;
-  // the parameter struct has no default constructor (a union): zeroed storage
-  alignas(cudaGraphNodeParams) unsigned char buf[sizeof(cudaGraphNodeParams)];
-  std::memset(buf, 0, sizeof(buf));
-  cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(buf);
-  np->type = cudaGraphNodeTypeConditional;
-  np->conditional.handle = d.rb_cond;
-  np->conditional.type = cudaGraphCondTypeIf;
-  np->conditional.size = 1;
-  cudaGraphNode_t node;
-  if (cudaGraphAddNode(&node, cg, deps, nullptr, nd, np) != cudaSuccess) return SL_ERR_CUDA;
-  cudaGraph_t body = np->conditional.phGraph_out[0];
-  if (cudaStreamBeginCaptureToGraph(c->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
-      cudaSuccess)
-    return SL_ERR_CUDA;
-  const int e = sl_launch_rebuild(d, c->cap2);
-  cudaGraph_t out = nullptr;
-  if (cudaStreamEndCapture(c->cap2, &out) != cudaSuccess || e) return SL_ERR_CUDA;
-  if (cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
-    return SL_ERR_CUDA;
-  return SL_OK;
-}
-
-// Capture one step's launch sequence into a graph on a private stream: with
-// the rebuild under a conditional node if the runtime takes it, else as
-// plain kernels that return at once when no rebuild is pending.
-int capture_step(sl_ctx* c, bool cond, cudaGraph_t* g) {
-  *g = nullptr;
-  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SL_ERR_CUDA;
-  SlDev d = c->d;
-  d.rb_cond = 0;
-  int e = SL_OK;
-  if (cond) {
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t cg = nullptr;
-    cudaGraphConditionalHandle h = 0;
-    if (cudaStreamGetCaptureInfo(c->cap, &cs, nullptr, &cg, nullptr, nullptr, nullptr) != cudaSuccess ||
-        cudaGraphConditionalHandleCreate(&h, cg, 0, 0) != cudaSuccess)
-      e = SL_ERR_CUDA;
-    d.rb_cond = h;
-  }
-  if (!e) e = sl_launch_step(d, c->cap, nullptr, nullptr, &c->kernels_per_step, cond ? cond_rebuild : nullptr, c);
-  cudaError_t ce = cudaStreamEndCapture(c->cap, g);
-  if (e || ce != cudaSuccess || !*g) {
-    if (*g) cudaGraphDestroy(*g);
-    *g = nullptr;
-    cudaGetLastError();
-    return SL_ERR_CUDA;
-  }
-  return SL_OK;
-}
-
+// Capture one step's launch sequence into a graph on a private stream.
 int build_graph(sl_ctx* c) {
   drop_graph(c);
   if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
-  if (!c->cap2 && cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
-  for (int cond = 1; cond >= 0; --cond) {
-    cudaGraph_t g = nullptr;
-    if (capture_step(c, cond != 0, &g)) continue;
-    cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (ie != cudaSuccess) { c->graph = nullptr; cudaGetLastError(); continue; }
-    c->graph_ok = 1;
-    c->graph_cond = cond;
-    return SL_OK;
-  }
-  return SL_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SL_ERR_CUDA;
+  int e = sl_launch_step(c->d, c->cap, nullptr, nullptr, &c->kernels_per_step);
+  cudaError_t ce = cudaStreamEndCapture(c->cap, &g);
+  if (e || ce != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return SL_ERR_CUDA; }
+  cudaError_t ie = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) { c->graph = nullptr; cudaGetLastError(); return SL_ERR_CUDA; }
+  c->graph_ok = 1;
+  return SL_OK;
 }
 
 // Record a timing event at a phase boundary on the phase's stream (the pool
@@ -906,7 +839,7 @@ int sl_counters(sl_ctx* c, int64_t out[8]) {
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return cuda_err(c);
   out[0] = h.step; out[1] = h.rebuilds; out[2] = h.max_ex_seen; out[3] = h.max_m_seen;
-  out[4] = c->kernels_per_step; out[5] = c->graph_ok; out[6] = c->graph_ok && c->graph_cond; out[7] = 0;
+  out[4] = c->kernels_per_step; out[5] = c->graph_ok; out[6] = 0; out[7] = 0;
   if (h.status && !c->sticky) c->sticky = h.status;
   return c->sticky;
 }
@@ -1127,7 +1060,6 @@ void sl_destroy(sl_ctx* c) {
   cudaStreamSynchronize(c->stream);
   drop_graph(c);
   if (c->cap) cudaStreamDestroy(c->cap);
-  if (c->cap2) cudaStreamDestroy(c->cap2);
   for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   delete c;
 }

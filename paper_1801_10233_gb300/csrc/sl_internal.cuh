@@ -100,7 +100,6 @@ struct SlDev {
   int tune_sweep;           // colour-pass tile shape variant (0 .. SL_SWEEP_VARIANTS-1)
   int tune_block;           // threads per block of the per-atom kernels (0: SL_BLOCK)
   int rb_cap;               // most blocks of a rebuild kernel (grid-stride loops)
-  unsigned long long rb_cond;   // graph conditional handle k_decide sets (0: none)
 
   // double-float constants (hi, lo)
   float2 zee_f[3], inv_hbar_f, tau_f;        // tau = dt/4
@@ -245,12 +244,7 @@ enum { SL_PHASE_KICK = 0, SL_PHASE_SPIN1 = 1, SL_PHASE_DRIFT = 2, SL_PHASE_JTABL
        SL_PHASE_FORCE = 5, SL_NPHASE = 6 };
 #define SL_REBUILD_KERNELS 10
 typedef void (*SlPhaseMark)(void* user, int phase, int end, cudaStream_t st);
-// The rebuild section of a step: by default sl_launch_rebuild; a graph
-// capture passes a hook that puts it under a conditional node.  Returns an
-// error code and the kernels it launches on every step in *kernels.
-typedef int (*SlRebuildHook)(const SlDev& d, cudaStream_t st, void* user, int* kernels);
-int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels,
-                   SlRebuildHook rebuild = nullptr, void* rebuild_user = nullptr);
+int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels);
 int sl_launch_observables(const SlDev& d, cudaStream_t st);
 int sl_launch_force_rebuild_flag(const SlDev& d, cudaStream_t st);
 int sl_launch_omega_all(const SlDev& d, double* out, cudaStream_t st);

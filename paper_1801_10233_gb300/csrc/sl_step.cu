@@ -409,8 +409,6 @@ __global__ void k_decide(SlDev d) {
   }
   c->need_rebuild = need;
   c->maxdisp2_bits = 0ull;
-  // inside the step's CUDA graph: run the rebuild body only when needed
-  if (d.rb_cond) cudaGraphSetConditional(d.rb_cond, need ? 1u : 0u);
 }
 
 // Exchange coefficients at the current positions (recomputed after every
@@ -817,21 +815,7 @@ int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick) {
 // One step with the learned Hamiltonian: the network is evaluated after the
 // first half-op (and drift) and after the second; each evaluation point
 // either uses the network or, if the gate closed, the analytic kernels.
-// The rebuild section: the hook if given, else the rebuild kernels (which
-// return at once when no rebuild is pending).
-static int rebuild_section(const SlDev& d, cudaStream_t st, SlRebuildHook hook, void* hook_user, int* nk) {
-  if (hook) {
-    int k = 0;
-    const int e = hook(d, st, hook_user, &k);
-    *nk += k;
-    return e;
-  }
-  *nk += SL_REBUILD_KERNELS;
-  return sl_launch_rebuild(d, st);
-}
-
-static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels,
-                               SlRebuildHook hook, void* hook_user) {
+static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels) {
   int gn = grid_for(d.n);
   const int lat = !d.fix_lattice;
   int nk = 0;
@@ -850,9 +834,9 @@ static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark
     phase(SL_PHASE_DRIFT, 0);
     k_drift<<<gn, SL_BLOCK, 0, st>>>(d);
     k_decide<<<1, 1, 0, st>>>(d);
-    if (!e) e = rebuild_section(d, st, hook, hook_user, &nk);
+    if (!e) e = sl_launch_rebuild(d, st);
     phase(SL_PHASE_DRIFT, 1);
-    nk += 2;
+    nk += 2 + SL_REBUILD_KERNELS;
   }
   phase(SL_PHASE_JTABLE, 0);
   if (!e) e = sl_ml_launch_point(d, st, 0);
@@ -879,9 +863,8 @@ static int launch_step_learned(const SlDev& d, cudaStream_t st, SlPhaseMark mark
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 
-int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels,
-                   SlRebuildHook hook, void* hook_user) {
-  if (d.ham == SL_HAM_LEARNED) return launch_step_learned(d, st, mark, user, kernels, hook, hook_user);
+int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels) {
+  if (d.ham == SL_HAM_LEARNED) return launch_step_learned(d, st, mark, user, kernels);
   const int lat = !d.fix_lattice;
   int nk = 0;
   auto phase = [&](int ph, int end) { if (mark) mark(user, ph, end, st); };
@@ -899,13 +882,13 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
     phase(SL_PHASE_DRIFT, 0);
     k_drift<<<grid_tb(d), tb(d), 0, st>>>(d);
     k_decide<<<1, 1, 0, st>>>(d);
-    int e = rebuild_section(d, st, hook, hook_user, &nk);
+    int e = sl_launch_rebuild(d, st);
     if (e) return e;
     phase(SL_PHASE_DRIFT, 1);
     phase(SL_PHASE_JTABLE, 0);
     const int ntab = launch_tables(d, grid_tb(d), tb(d), st);
     phase(SL_PHASE_JTABLE, 1);
-    nk += 2 + ntab;
+    nk += 2 + SL_REBUILD_KERNELS + ntab;
   }
   phase(SL_PHASE_SPIN2, 0);
   launch_half_op(d, st, 2);

@@ -112,7 +112,7 @@ class System:
         out = (ctypes.c_int64 * 8)()
         check(self._L.sl_counters(self._h, out), "sl_counters")
         return dict(steps=out[0], rebuilds=out[1], max_ex_seen=out[2], max_morse_seen=out[3],
-                    kernels_per_step=out[4], graph=bool(out[5]), graph_conditional_rebuild=bool(out[6]))
+                    kernels_per_step=out[4], graph=bool(out[5]))
 
     def set_timing(self, enable: bool):
         """Per-phase CUDA-event timing of each step (direct launches)."""

@@ -254,23 +254,3 @@ def test_full_size_64cubed(System):
     gpu.step(2)
     ref.step(2)
     assert_state_parity(gpu, ref, p)
-
-
-def test_rebuild_under_graph_conditional(System):
-    """Steps run as one CUDA graph whose rebuild sequence sits under a
-    conditional node that k_decide sets: rebuilds still happen exactly when
-    the oracle's do, and a graph step without a rebuild launches no rebuild
-    kernel."""
-    import oracle
-    p, r, v, s = inputs.bcc_fe_system(6, 12, T=200.0)
-    v = v.copy()
-    v[17] = [900.0, -300.0, 100.0]
-    gpu = System(p, r, v, s)
-    ref = oracle.Oracle(p, r, v, s)
-    gpu.step(6)
-    ref.step(6)
-    c = gpu.counters()
-    assert c["graph"] and c["graph_conditional_rebuild"]
-    assert ref.rebuilds >= 2 and c["rebuilds"] == ref.rebuilds
-    assert c["kernels_per_step"] < 40
-    assert_state_parity(gpu, ref, p)
