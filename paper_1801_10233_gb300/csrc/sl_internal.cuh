@@ -127,8 +127,8 @@ struct SlDev {
   // state, sector-sorted (FP64, authoritative)
   double4_32a *r, *v, *s, *F;
   SlFix *rbx;               // positions at the last rebuild, fixed point
-  // split copies for the double-float kernels
-  SlFix *rx;                // r in fixed point, rint(r 2^F)
+  // copies for the pair and double-float kernels
+  SlFix *rx;                // r in fixed point, rint(r 2^48)
   float4 *sdf;              // s = hi + lo to ~48 bits: sdf[2i] = hi, sdf[2i+1] = lo
   // rebuild scratch
   double4_32a *tr, *tv, *ts, *tF;

@@ -26,16 +26,16 @@ inline int grid_for(int n) { return (n + SL_BLOCK - 1) / SL_BLOCK; }
 //   phase 1 (all warps, parallel over atoms): the exchange field from atoms
 //           outside the atom's own sector -- either in full, or as the
 //           partial field precomputed during the previous pass plus the
-//           contribution of the colour that pass updated -- the noise of the
-//           spin bath, and a copy of the atom's same-sector list (local
-//           index, J) into shared memory;
+//           previous pass's colour group of the atom's exchange list -- the
+//           noise of the spin bath, and up to SW_MAXIN entries of the atom's
+//           same-sector list (local index, J) in shared memory;
 //   phase 2 (warp 0, one lane per sector, sequential): for each spin in
 //           order, add the field of the already-updated spins of its own
 //           sector, form omega and rotate -- shared memory only.
 //           Meanwhile warps 1.. precompute, for block b's sectors of the
 //           next colour in the sweep, the external field of every
 //           neighbour not of this pass's colour (those spins are final for
-//           this pass);
+//           this pass: two contiguous ranges of the colour-grouped list);
 //   phase 3 (all warps, parallel over atoms): add each increment to the
 //           FP64 spin once and refresh its float split.
 // Blocks with more than SW_MAXA atoms use workspace scratch and read their
