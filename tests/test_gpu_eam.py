@@ -127,3 +127,29 @@ def test_time_reversal_and_energy(System):
     gpu.set_dt(p["dt_ps"])
     gpu.step(2000)
     assert abs(gpu.energy()[4] - E0) / p["n_atoms"] < 1e-6
+
+
+def test_full_size_embedding_workload(System):
+    """The 524,288-atom embedding benchmark workload (density inside the
+    exchange-table kernel) in the bench's launch shape: initial forces and
+    energies of every atom, then two steps, against the oracle."""
+    import oracle
+    p, r, v, s = inputs.workload("fe_bcc_64x64x64_eam")
+    gpu = System(p, r, v, s)
+    gpu.set_launch_shape(1, 128)
+    ref = oracle.Oracle(p, r, v, s)
+    Fg, Fo = _np(gpu.forces()), ref.forces()
+    assert np.abs(Fg - Fo).max() <= TOL * np.abs(Fo).max()
+    eg, eo = gpu.energy(), ref.energy()
+    assert abs(eg[1] - eo[1]) <= TOL * abs(eo[1])
+    gpu.step(2)
+    ref.step(2)
+    rg, vg, sg = (_np(t) for t in gpu.state())
+    ro, vo, so = ref.state()
+    L = np.asarray(p["box"])
+    dr = rg - ro
+    dr -= L * np.round(dr / L)
+    assert np.abs(dr).max() <= TOL * L.max()
+    assert np.abs(sg - so).max() <= TOL
+    assert np.abs(vg - vo).max() <= TOL * math.sqrt(float((vo * vo).mean()))
+    assert abs(gpu.energy()[4] - ref.energy()[4]) <= TOL * abs(ref.energy()[4])

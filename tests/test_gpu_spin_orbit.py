@@ -182,3 +182,21 @@ def test_energy_conservation(System):
     s1 = _np(gpu.state()[2])
     assert np.abs(np.linalg.norm(s1, axis=1) - 1).max() < 5e-14
     assert abs(gpu.energy()[4] - E0) / p["n_atoms"] < 1e-6
+
+
+def test_full_size_spin_orbit_workload(System):
+    """The 524,288-atom spin-orbit benchmark workload in the bench's launch
+    shape: initial forces, fields and energies of every atom, then two
+    steps, against the oracle."""
+    import oracle
+    p, r, v, s = inputs.workload("fe_bcc_64x64x64_spin_orbit")
+    gpu = System(p, r, v, s)
+    gpu.set_launch_shape(1, 128)
+    ref = oracle.Oracle(p, r, v, s)
+    Fg, Fo = _np(gpu.forces()), ref.forces()
+    assert np.abs(Fg - Fo).max() <= TOL * np.abs(Fo).max()
+    wg, wo = _np(gpu.omega()), ref.omega()
+    assert np.abs(wg - wo).max() <= TOL * np.abs(wo).max()
+    gpu.step(2)
+    ref.step(2)
+    _state_parity(gpu, ref, p)
