@@ -79,6 +79,8 @@ def lib():
         L.orc_get_rebuilds.argtypes = [ctypes.c_void_p]
         L.orc_get_error.restype = ctypes.c_int
         L.orc_get_error.argtypes = [ctypes.c_void_p]
+        L.orc_set_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_count_pairs.restype = ctypes.c_int
         L.orc_count_pairs.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_energy.argtypes = [ctypes.c_void_p, _c_double_p]
@@ -189,7 +191,8 @@ class OracleError(RuntimeError):
 class Oracle:
     """Plain FP64 reference of one coupled spin-lattice system."""
 
-    def __init__(self, params: dict, r, v, s, brute_force=False, lam=0.0, temperature=0.0, seed=0, replica=0):
+    def __init__(self, params: dict, r, v, s, brute_force=False, lam=0.0, temperature=0.0, seed=0, replica=0,
+                 threads=1):
         self._L = lib()
         self.params = dict(params)
         self.n = int(params["n_atoms"])
@@ -202,6 +205,13 @@ class Oracle:
         if not h:
             raise OracleError(err.value)
         self._h = ctypes.c_void_p(h)
+        self.threads = self.set_threads(threads)
+
+    def set_threads(self, threads):
+        """Threads for later steps (1 = serial); returns the number used.
+        Any number gives results bit-identical to one thread."""
+        self.threads = int(self._L.orc_set_threads(self._h, int(threads)))
+        return self.threads
 
     def __del__(self):
         h = getattr(self, "_h", None)

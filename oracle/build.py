@@ -20,7 +20,10 @@ def build(force: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            *SRCS, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP only splits independent work (orc_set_threads); without it the
+    # oracle runs on one thread with the same results
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB
 

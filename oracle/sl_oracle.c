@@ -36,8 +36,13 @@
  *                 pseudo-dipolar -g1(r)((e.s_i)(e.s_j) - s_i.s_j/3) and DMI
  *                 d(r) e_ij.(s_i x s_j) per unordered pair inside the exchange
  *                 cutoff, g1 and d of the form of Eq. BSfunction; the
- *                 anisotropy makes omega_i depend on s_i, so its factor
- *                 rotates about omega at the midpoint s + (tau/2) omega x s.
+ *                 anisotropy makes omega_i depend on s_i, so each
+ *                 single-spin factor is split symmetrically: an exact half
+ *                 turn under the anisotropy alone (it keeps s.n), the turn
+ *                 under the rest of omega, another anisotropy half turn.
+ *   Embedding     (Sec. 2, Eq. app:mech1) optional Finnis-Sinclair term
+ *                 sum_i -A sqrt(rho_i), rho_i = sum_j f(r_ij), and optional
+ *                 subtraction of the collinear exchange ground state.
  *   Observables   kinetic, Morse, exchange, Zeeman energies; T_L
  *                 (Eq. lattice_temperature), T_S (Eq. spin_temperature),
  *                 magnetisation M = (1/N) sum_i s_i.
@@ -69,6 +74,14 @@
  * through the sector assignment, which is redone when an atom has moved more
  * than skin/2 since the last assignment (or on a fixed schedule), because the
  * colour order of the sweep depends on it.
+ *
+ * Threads (orc_set_threads, default 1): the sweep can turn the sectors of
+ * one colour side by side, since they are further apart than every cutoff
+ * while no atom has moved more than skin/2 (Sec. 5.1); the pair search, the
+ * pair tables and the forces are sums per atom.  Each is split over OpenMP
+ * threads without changing any operation or its order, so every thread
+ * count gives the serial result bit for bit.  After a skin error the sweep
+ * runs serially.
  *
  * Compiled with -ffp-contract=off so that every a*b+c rounds twice, as written.
  */
@@ -144,6 +157,10 @@ typedef struct {
   int *colour;             /* colour 0..7 per atom */
   int *order;              /* atom ids in sweep order: colour, sector, id */
   int colour_start[9];
+  int *run;                /* starts of the sectors' runs in the sweep order, nrun + 1 */
+  int nrun;
+  int colour_run[9];       /* first run of each colour */
+  int threads;             /* > 1: same-colour sectors, atoms and rows split over OpenMP threads */
   orc_list ex, mo;         /* exchange pairs (r < ex_rc), Morse pairs (r < m_rc) */
   double *exJ, *exdJ;      /* J(r_ij), J'(r_ij) per exchange list entry */
   double *exG1, *exDm;     /* g1(r_ij), d(r_ij) per exchange list entry */
@@ -274,6 +291,48 @@ static int list_push(orc_list* L, int* cnt, int j) {
   return ORC_OK;
 }
 
+static int list_reserve(orc_list* L, int need) {
+  if (need <= L->cap) return ORC_OK;
+  int nc = L->cap ? L->cap : 1024;
+  while (nc < need) nc *= 2;
+  int* nj = (int*)realloc(L->j, (size_t)nc * sizeof(int));
+  if (!nj) return ORC_ERR_OOM;
+  L->j = nj; L->cap = nc;
+  return ORC_OK;
+}
+
+typedef struct {
+  int nx, ny, nz;
+  const int *head, *next, *cellof;   /* chained cell lists, cell of each atom */
+} cell_grid;
+
+/* Row i of the list from the 27 cells around atom i: with pop given, only a
+ * bound (the atoms in those cells); else the number of j != i within the
+ * cutoff, written to out (sorted by j) when out is not NULL. */
+static int cell_row(const orc_state* st, const cell_grid* g, int i, double rc2, const int* pop, int* out) {
+  int m = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int x = (g->cellof[3 * i] + dx + g->nx) % g->nx;
+        int y = (g->cellof[3 * i + 1] + dy + g->ny) % g->ny;
+        int z = (g->cellof[3 * i + 2] + dz + g->nz) % g->nz;
+        int c = x + g->nx * (y + g->ny * z);
+        if (pop) { m += pop[c]; continue; }
+        for (int j = g->head[c]; j >= 0; j = g->next[j]) {
+          if (j == i) continue;
+          double d[3];
+          min_image(st, i, j, d);
+          if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2) {
+            if (out) out[m] = j;
+            m += 1;
+          }
+        }
+      }
+  if (out) qsort(out, (size_t)m, sizeof(int), cmp_int);
+  return m;
+}
+
 /* All j != i with |min_image(r_j - r_i)| < rc, rows sorted by j. */
 static int build_list(orc_state* st, double rc, orc_list* L) {
   int n = st->n;
@@ -303,9 +362,10 @@ static int build_list(orc_state* st, double rc, orc_list* L) {
   /* cell list: cell edge >= rc, at least 3 cells per dimension */
   int ncell = nc[0] * nc[1] * nc[2];
   int* head = (int*)malloc((size_t)ncell * sizeof(int));
+  int* pop = (int*)calloc((size_t)ncell, sizeof(int));
   int* next = (int*)malloc((size_t)n * sizeof(int));
   int* cellof = (int*)malloc((size_t)n * 3 * sizeof(int));
-  if (!head || !next || !cellof) { free(head); free(next); free(cellof); return ORC_ERR_OOM; }
+  if (!head || !pop || !next || !cellof) { free(head); free(pop); free(next); free(cellof); return ORC_ERR_OOM; }
   for (int c = 0; c < ncell; ++c) head[c] = -1;
   for (int i = n - 1; i >= 0; --i) {
     int cc[3];
@@ -320,28 +380,33 @@ static int build_list(orc_state* st, double rc, orc_list* L) {
     int c = cc[0] + nc[0] * (cc[1] + nc[1] * cc[2]);
     next[i] = head[c];
     head[c] = i;
+    pop[c] += 1;
   }
-  for (int i = 0; i < n; ++i) {
-    L->off[i] = cnt;
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          int x = (cellof[3 * i] + dx + nc[0]) % nc[0];
-          int y = (cellof[3 * i + 1] + dy + nc[1]) % nc[1];
-          int z = (cellof[3 * i + 2] + dz + nc[2]) % nc[2];
-          for (int j = head[x + nc[0] * (y + nc[1] * z)]; j >= 0; j = next[j]) {
-            if (j == i) continue;
-            double d[3];
-            min_image(st, i, j, d);
-            if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rc2)
-              if (list_push(L, &cnt, j)) { free(head); free(next); free(cellof); return ORC_ERR_OOM; }
-          }
-        }
-    qsort(L->j + L->off[i], (size_t)(cnt - L->off[i]), sizeof(int), cmp_int);
+  const cell_grid g = {nc[0], nc[1], nc[2], head, next, cellof};
+  int e = ORC_OK;
+  if (st->threads <= 1) {
+    for (int i = 0; i < n; ++i) {
+      L->off[i] = cnt;
+      if (list_reserve(L, cnt + cell_row(st, &g, i, rc2, pop, NULL))) { e = ORC_ERR_OOM; break; }
+      cnt += cell_row(st, &g, i, rc2, NULL, L->j + cnt);
+    }
+  } else {
+    /* the same rows, counted in one parallel pass and written in a second */
+    int nt = st->threads;
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 256)
+    for (int i = 0; i < n; ++i) L->off[i + 1] = cell_row(st, &g, i, rc2, NULL, NULL);
+    L->off[0] = 0;
+    for (int i = 0; i < n; ++i) L->off[i + 1] += L->off[i];
+    cnt = L->off[n];
+    if (list_reserve(L, cnt)) e = ORC_ERR_OOM;
+    if (!e) {
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 256)
+      for (int i = 0; i < n; ++i) cell_row(st, &g, i, rc2, NULL, L->j + L->off[i]);
+    }
   }
   L->off[n] = cnt;
-  free(head); free(next); free(cellof);
-  return ORC_OK;
+  free(head); free(pop); free(next); free(cellof);
+  return e;
 }
 
 /* Pair lists and the exchange coefficients at the current positions
@@ -363,6 +428,8 @@ static int refresh_pairs(orc_state* st) {
   st->exDm = (double*)malloc((size_t)(np ? np : 1) * sizeof(double));
   st->exE = (double*)malloc((size_t)(np ? np : 1) * 3 * sizeof(double));
   if (!st->exJ || !st->exdJ || !st->exG1 || !st->exDm || !st->exE) return ORC_ERR_OOM;
+  int nt = st->threads > 1 ? st->threads : 1;
+#pragma omp parallel for num_threads(nt) schedule(static) if (nt > 1)
   for (int i = 0; i < st->n; ++i)
     for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
       double d[3];
@@ -432,6 +499,16 @@ static int assign_sectors(orc_state* st) {
   }
   for (int c = 7; c >= 0; --c)
     if (st->colour_start[c] > st->colour_start[c + 1]) st->colour_start[c] = st->colour_start[c + 1];
+  /* the sweep order holds each sector as one run of consecutive entries */
+  st->nrun = 0;
+  for (int c = 0; c < 8; ++c) {
+    st->colour_run[c] = st->nrun;
+    for (int k = st->colour_start[c]; k < st->colour_start[c + 1]; ++k)
+      if (k == st->colour_start[c] || st->sector[st->order[k]] != st->sector[st->order[k - 1]])
+        st->run[st->nrun++] = k;
+  }
+  st->colour_run[8] = st->nrun;
+  st->run[st->nrun] = n;
   memcpy(st->rb, st->r, (size_t)n * 3 * sizeof(double));
   free(keys);
   st->rebuilds += 1;
@@ -626,8 +703,26 @@ static int ml_point(orc_state* st, double* F) {
 /* The palindromic sweep: forward over the sweep order with h/2 per spin, then backward. */
 static void sweep(orc_state* st, double h, int subpass0) {
   int n = st->n;
-  for (int k = 0; k < n; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
-  for (int k = n - 1; k >= 0; --k) rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
+  if (st->threads <= 1 || st->err != ORC_OK) {
+    for (int k = 0; k < n; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
+    for (int k = n - 1; k >= 0; --k) rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
+    return;
+  }
+  /* The same order with the sectors of one colour side by side: while every
+   * atom stays within skin/2 of where the sectors were assigned, atoms of two
+   * sectors of one colour are further apart than every cutoff (Sec. 5.1), so
+   * no rotation reads a spin that another sector of its colour turns. */
+  int nt = st->threads;
+  for (int c = 0; c < 8; ++c) {
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
+    for (int q = st->colour_run[c]; q < st->colour_run[c + 1]; ++q)
+      for (int k = st->run[q]; k < st->run[q + 1]; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
+  }
+  for (int c = 7; c >= 0; --c) {
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
+    for (int q = st->colour_run[c]; q < st->colour_run[c + 1]; ++q)
+      for (int k = st->run[q + 1] - 1; k >= st->run[q]; --k) rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
+  }
 }
 
 /* e^{L_s h}.  Learned Hamiltonian: predictor sweep, field coefficients at the
@@ -693,6 +788,8 @@ static void compute_forces(orc_state* st) {
     free(F);
   }
   memset(st->F, 0, (size_t)n * 3 * sizeof(double));
+  int nt = st->threads > 1 ? st->threads : 1;   /* each atom's sum is its own: any split gives the same F */
+#pragma omp parallel for num_threads(nt) schedule(static) if (nt > 1)
   for (int i = 0; i < n; ++i) {
     double* f = st->F + 3 * i;
     for (int k = st->mo.off[i]; k < st->mo.off[i + 1]; ++k) {
@@ -741,7 +838,9 @@ static void compute_forces(orc_state* st) {
     /* E = sum_i F(rho_i): F_i = sum_j (F'(rho_i) + F'(rho_j)) f'(r) (r_j - r_i)/r */
     double* dF = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     if (!dF) { if (st->err == ORC_OK) st->err = ORC_ERR_OOM; return; }
+#pragma omp parallel for num_threads(nt) schedule(static) if (nt > 1)
     for (int i = 0; i < n; ++i) dF[i] = eam_dF(&st->p, eam_rho(st, i));
+#pragma omp parallel for num_threads(nt) schedule(static) if (nt > 1)
     for (int i = 0; i < n; ++i) {
       double* f = st->F + 3 * i;
       for (int k = st->mo.off[i]; k < st->mo.off[i + 1]; ++k) {
@@ -795,7 +894,7 @@ static double max_disp2(const orc_state* st) {
 void orc_destroy(orc_state* st) {
   if (!st) return;
   free(st->r); free(st->v); free(st->s); free(st->F); free(st->rb);
-  free(st->sector); free(st->colour); free(st->order);
+  free(st->sector); free(st->colour); free(st->order); free(st->run);
   free(st->ex.off); free(st->ex.j); free(st->mo.off); free(st->mo.j);
   free(st->exJ); free(st->exdJ); free(st->exG1); free(st->exDm); free(st->exE);
   free(st->ml); free(st->mll.off); free(st->mll.j); free(st->mlP); free(st->mlQ);
@@ -832,7 +931,9 @@ orc_state* orc_create(const orc_params* p, const double* r, const double* v, con
   st->sector = (int*)malloc((size_t)(n ? n : 1) * sizeof(int));
   st->colour = (int*)malloc((size_t)(n ? n : 1) * sizeof(int));
   st->order = (int*)malloc((size_t)(n ? n : 1) * sizeof(int));
-  if (!st->r || !st->v || !st->s || !st->F || !st->rb || !st->sector || !st->colour || !st->order) {
+  st->run = (int*)malloc((size_t)(n + 1) * sizeof(int));
+  st->threads = 1;
+  if (!st->r || !st->v || !st->s || !st->F || !st->rb || !st->sector || !st->colour || !st->order || !st->run) {
     orc_destroy(st); *err = ORC_ERR_OOM; return NULL;
   }
   memcpy(st->r, r, (size_t)n * 3 * sizeof(double));
@@ -960,6 +1061,19 @@ void orc_get_order(const orc_state* st, int* order, int* colour_start, int* sect
 
 long orc_get_step(const orc_state* st) { return st->step; }
 int orc_get_rebuilds(const orc_state* st) { return st->rebuilds; }
+
+/* Threads for the sweep, the pair search, the pair tables and the forces
+ * (default 1).  Every split gives results bit-identical to one thread.
+ * Returns the number used: 1 when built without OpenMP. */
+int orc_set_threads(orc_state* st, int threads) {
+#ifdef _OPENMP
+  st->threads = threads > 1 ? threads : 1;
+#else
+  (void)threads;
+  st->threads = 1;
+#endif
+  return st->threads;
+}
 int orc_get_error(const orc_state* st) { return st->err; }
 int orc_count_pairs(const orc_state* st, int which) {
   return which == 0 ? st->ex.off[st->n] : st->mo.off[st->n];
