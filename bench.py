@@ -421,7 +421,7 @@ def run_ours(args):
             forms["learned"] = learned_forms(args, dev, torch)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ost, ost1 = 160, 40
+        ost, ost1 = 1000, 40
         val, secs, ns, nt = time_oracle(ost, 1, host_cores())
         val1, secs1, _, _ = time_oracle(ost1, 1, 1)
         cpu = {"value": val, "unit": UNIT, "cores": nt, "kind": "oracle",
