@@ -272,15 +272,7 @@ __device__ __forceinline__ double4_32a lattice_bath(const SlDev& d, int i, doubl
 // are summed in df, beyond that A and B come from FP64 sin).  Cayley map of
 // Sec. 3: A = 1/(1 + u/4), B = A/2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau, int cayley) {
-  float h = 0.0f, l = 0.0f;
-  acc_prod(h, l, w.x, w.x);
-  acc_prod(h, l, w.y, w.y);
-  acc_prod(h, l, w.z, w.z);
-  df w2 = acc_done(h, l);
-  df tau2 = df_sqr(tau);
-  df u = df_mul(w2, tau2);
-  df A, B;
+__device__ __forceinline__ void rot_coeffs(df u, int cayley, df& A, df& B) {
   if (cayley) {
     df den = df_add_f(df_scale(u, 0.25f), 1.0f);
     float y0 = __frcp_rn(den.hi);
@@ -314,6 +306,18 @@ __device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau,
     A = df_from_double(sin(th) / th);
     B = df_from_double(2.0 * hs * hs / ud);
   }
+}
+
+__device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau, int cayley) {
+  float h = 0.0f, l = 0.0f;
+  acc_prod(h, l, w.x, w.x);
+  acc_prod(h, l, w.y, w.y);
+  acc_prod(h, l, w.z, w.z);
+  df w2 = acc_done(h, l);
+  df tau2 = df_sqr(tau);
+  df u = df_mul(w2, tau2);
+  df A, B;
+  rot_coeffs(u, cayley, A, B);
   df uB = df_mul(u, B);
   df tA = df_mul(tau, A);
   df tBws = df_mul(df_mul(tau2, B), dot3(w, s));
@@ -381,6 +385,32 @@ __device__ __forceinline__ df3 aniso_vec(const SlDev& d, const df3& s, df c) {
   df3 a;
   a.x = df_mul(k, n.x); a.y = df_mul(k, n.y); a.z = df_mul(k, n.z);
   return a;
+}
+
+// The increment of one anisotropy turn over tau: rot_increment with
+// w = c (s.n) n and |n| = 1, i.e. theta = c (s.n) tau, u = theta^2 and
+//   s' - s = -u B (s - (s.n) n) + theta A (n x s).
+__device__ __forceinline__ df3 aniso_increment(const SlDev& d, const df3& s, df c, df tau, int cayley) {
+  df3 n;
+  n.x = F2(d.an_n_f[0]); n.y = F2(d.an_n_f[1]); n.z = F2(d.an_n_f[2]);
+  const df sn = dot3(s, n);
+  const df th = df_mul(df_mul(c, sn), tau);
+  const df u = df_sqr(th);
+  df A, B;
+  rot_coeffs(u, cayley, A, B);
+  const df nuB = df_neg(df_mul(u, B)), tA = df_mul(th, A);
+  const df3 x = cross3(n, s);
+  df3 inc;
+  float h = 0.0f, l = 0.0f;
+  acc_prod(h, l, nuB, df_sub(s.x, df_mul(sn, n.x))); acc_prod(h, l, tA, x.x);
+  inc.x = acc_done(h, l);
+  h = l = 0.0f;
+  acc_prod(h, l, nuB, df_sub(s.y, df_mul(sn, n.y))); acc_prod(h, l, tA, x.y);
+  inc.y = acc_done(h, l);
+  h = l = 0.0f;
+  acc_prod(h, l, nuB, df_sub(s.z, df_mul(sn, n.z))); acc_prod(h, l, tA, x.z);
+  inc.z = acc_done(h, l);
+  return inc;
 }
 
 // FP64 versions for the observables: the spin-orbit field of one entry and

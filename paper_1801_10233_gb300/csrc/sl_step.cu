@@ -280,7 +280,7 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
         df3 inc_a;
         inc_a.x = inc_a.y = inc_a.z = df_f(0.0f);
         if (aniso) {
-          inc_a = rot_increment(aniso_vec(d, s, F2(bath ? d.an_cl_f : d.an_c_f)), s, df_scale(tau, 0.5f), cayley);
+          inc_a = aniso_increment(d, s, F2(bath ? d.an_cl_f : d.an_c_f), df_scale(tau, 0.5f), cayley);
           s.x = df_add(s.x, inc_a.x); s.y = df_add(s.y, inc_a.y); s.z = df_add(s.z, inc_a.z);
         }
         if (bath) {
@@ -306,8 +306,7 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
         df3 inc = rot_increment(w, s, tau, cayley);
         if (aniso) {
           s.x = df_add(s.x, inc.x); s.y = df_add(s.y, inc.y); s.z = df_add(s.z, inc.z);
-          const df3 i2 =
-              rot_increment(aniso_vec(d, s, F2(bath ? d.an_cl_f : d.an_c_f)), s, df_scale(tau, 0.5f), cayley);
+          const df3 i2 = aniso_increment(d, s, F2(bath ? d.an_cl_f : d.an_c_f), df_scale(tau, 0.5f), cayley);
           s.x = df_add(s.x, i2.x); s.y = df_add(s.y, i2.y); s.z = df_add(s.z, i2.z);
           inc.x = df_add(df_add(inc_a.x, inc.x), i2.x);
           inc.y = df_add(df_add(inc_a.y, inc.y), i2.y);
