@@ -61,6 +61,8 @@ def fe_params(box, n_atoms, **overrides):
         eam_d_A=3.569745,
         eam_beta=1.8,
         subtract_ground_exchange=0,
+        max_ex_neighbors=0,
+        max_morse_neighbors=0,
     )
     for k, v in overrides.items():
         if k not in p:

@@ -65,6 +65,11 @@ CASES = {
     "rebuild_every_3": lambda: inputs.bcc_fe_system(6, 8, T=600.0, sigma=0.05, rebuild_every=3),
     "tilted_field_5T": lambda: inputs.bcc_fe_system(6, 9, T=200.0, H_tesla=[2.0, -3.0, 3.0]),
     "cone10": lambda: inputs.bcc_fe_system(8, 10, T=200.0, spins="cone10"),
+    # other sector grids (Sec. 5.1): 4^3 and 8^3 sectors instead of 6^3; the
+    # 1.5 A skin lists up to 54 exchange and 168 Morse neighbours
+    "wide_skin_4_sectors": lambda: inputs.bcc_fe_system(10, 14, T=300.0, sigma=0.03, skin_A=1.5,
+                                                        max_ex_neighbors=64, max_morse_neighbors=192),
+    "narrow_skin_8_sectors": lambda: inputs.bcc_fe_system(10, 15, T=300.0, sigma=0.03, skin_A=0.1),
 }
 
 
