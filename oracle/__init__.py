@@ -79,6 +79,9 @@ def lib():
         L.orc_get_rebuilds.argtypes = [ctypes.c_void_p]
         L.orc_get_error.restype = ctypes.c_int
         L.orc_get_error.argtypes = [ctypes.c_void_p]
+        L.orc_create_threads.restype = ctypes.c_void_p
+        L.orc_create_threads.argtypes = [ctypes.POINTER(_Params), _c_double_p, _c_double_p, _c_double_p, ctypes.c_int,
+                                         _c_int_p]
         L.orc_set_threads.restype = ctypes.c_int
         L.orc_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.orc_count_pairs.restype = ctypes.c_int
@@ -201,7 +204,7 @@ class Oracle:
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(self.n, 3)
         s = np.ascontiguousarray(s, dtype=np.float64).reshape(self.n, 3)
         err = ctypes.c_int(0)
-        h = self._L.orc_create(ctypes.byref(self._p), _dp(r), _dp(v), _dp(s), ctypes.byref(err))
+        h = self._L.orc_create_threads(ctypes.byref(self._p), _dp(r), _dp(v), _dp(s), int(threads), ctypes.byref(err))
         if not h:
             raise OracleError(err.value)
         self._h = ctypes.c_void_p(h)

@@ -903,8 +903,21 @@ void orc_destroy(orc_state* st) {
 
 int orc_params_size(void) { return (int)sizeof(orc_params); }
 
-/* r, v, s: [n][3] in atom-id order.  Returns NULL and sets *err on failure. */
-orc_state* orc_create(const orc_params* p, const double* r, const double* v, const double* s, int* err) {
+static int set_threads(orc_state* st, int threads) {
+#ifdef _OPENMP
+  st->threads = threads > 1 ? threads : 1;
+#else
+  (void)threads;
+  st->threads = 1;
+#endif
+  return st->threads;
+}
+
+/* r, v, s: [n][3] in atom-id order; threads as for orc_set_threads (the
+ * initial lists and forces use them too).  Returns NULL and sets *err on
+ * failure. */
+orc_state* orc_create_threads(const orc_params* p, const double* r, const double* v, const double* s, int threads,
+                              int* err) {
   *err = ORC_OK;
   if (!p || p->n_atoms < 0 || p->mass <= 0.0 || p->hamiltonian < 0 || p->hamiltonian > 1 ||
       (p->hamiltonian == 1 && p->rotation != 0) || !(p->lat_gamma >= 0.0) || !(p->lat_temperature >= 0.0) ||
@@ -932,7 +945,7 @@ orc_state* orc_create(const orc_params* p, const double* r, const double* v, con
   st->colour = (int*)malloc((size_t)(n ? n : 1) * sizeof(int));
   st->order = (int*)malloc((size_t)(n ? n : 1) * sizeof(int));
   st->run = (int*)malloc((size_t)(n + 1) * sizeof(int));
-  st->threads = 1;
+  set_threads(st, threads);
   if (!st->r || !st->v || !st->s || !st->F || !st->rb || !st->sector || !st->colour || !st->order || !st->run) {
     orc_destroy(st); *err = ORC_ERR_OOM; return NULL;
   }
@@ -950,6 +963,10 @@ orc_state* orc_create(const orc_params* p, const double* r, const double* v, con
   if (e) { orc_destroy(st); *err = e; return NULL; }
   compute_forces(st);
   return st;
+}
+
+orc_state* orc_create(const orc_params* p, const double* r, const double* v, const double* s, int* err) {
+  return orc_create_threads(p, r, v, s, 1, err);
 }
 
 /* Install the learned model (float params[ML_NPARAM], norm[ML_NNORM]) and
@@ -1065,15 +1082,7 @@ int orc_get_rebuilds(const orc_state* st) { return st->rebuilds; }
 /* Threads for the sweep, the pair search, the pair tables and the forces
  * (default 1).  Every split gives results bit-identical to one thread.
  * Returns the number used: 1 when built without OpenMP. */
-int orc_set_threads(orc_state* st, int threads) {
-#ifdef _OPENMP
-  st->threads = threads > 1 ? threads : 1;
-#else
-  (void)threads;
-  st->threads = 1;
-#endif
-  return st->threads;
-}
+int orc_set_threads(orc_state* st, int threads) { return set_threads(st, threads); }
 int orc_get_error(const orc_state* st) { return st->err; }
 int orc_count_pairs(const orc_state* st, int which) {
   return which == 0 ? st->ex.off[st->n] : st->mo.off[st->n];
