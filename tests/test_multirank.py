@@ -58,7 +58,7 @@ def test_two_gloo_ranks_reduce_and_count():
 def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
-    args = type("A", (), dict(steps=1, warmup=0, gpus=2, workload="fe_bcc_64x64x64_nve"))()
+    args = type("A", (), dict(steps=1, warmup=0, gpus=2, workload="fe_bcc_64x64x64_nve", full_workload=False))()
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.run_reference(args)
@@ -69,3 +69,19 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_full_workload(capsys, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    args = type("A", (), dict(steps=2, warmup=1, gpus=1, workload="fe_bcc_10x10x10_nve", full_workload=True))()
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["config"]["sample_atoms"] == 2000 and line["value"] > 0
+    assert "whole workload" in line["cpu_baseline"]["sample"]
+    args.workload = "fe_bcc_batch256"
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "unavailable" in line
