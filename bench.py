@@ -65,6 +65,9 @@ DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 20 * 2 / 1e12
 # capture of the current kernels on the 64^3-cell workload
 # (profiles/force_fe_bcc_64x64x64_nve.md, profiles/jtable_fe_bcc_64x64x64_nve.md).
 NCU_TRAFFIC_64CUBED = {"force_kick": 327.1e6, "exchange_table": 120.6e6}
+# DRAM bytes per atom-step of the whole step on the same workload, warm L2
+# (ncu --cache-control none, one pass per launch; profiles/dram_per_step_fe_bcc_64x64x64_nve.md)
+NCU_DRAM_PER_ATOM_STEP_64CUBED = 2139.0
 
 
 def parse():
@@ -385,6 +388,12 @@ def run_ours(args):
     # compulsory state traffic: r, v, s read and written once per step (144 B/atom)
     if hbm:
         roofline["hbm_frac_state_traffic"] = 144.0 * n / (ms / args.steps * 1e-3) / 1e9 / hbm
+    if args.workload == DEFAULT_WORKLOAD:
+        # measured DRAM traffic of a whole step (ncu), and its rate at this run's step time
+        roofline["dram_bytes_per_atom_step"] = NCU_DRAM_PER_ATOM_STEP_64CUBED
+        if hbm:
+            roofline["hbm_frac_measured_traffic"] = (NCU_DRAM_PER_ATOM_STEP_64CUBED * n /
+                                                     (ms / args.steps * 1e-3) / 1e9 / hbm)
 
     # end to end through the public API with host buffers: per step, upload the
     # state from pinned memory, advance one step, read the state back
