@@ -447,10 +447,15 @@ static int refresh_pairs(orc_state* st) {
 /* ------------------------------------------------------------------ */
 /* Sector assignment (Sec. 5.1) and the sweep order                   */
 /* ------------------------------------------------------------------ */
+/* The largest even number of sectors per edge whose edge exceeds the reach
+ * of a spin's interactions plus the skin, by a relative margin of 1e-6: atoms
+ * of two sectors of one colour stay further apart than the reach while none
+ * has moved more than skin/2, with room to spare for a list built from
+ * rounded distances. */
 static int sector_grid(const orc_params* p, int nsec[3], double edge[3]) {
   double reach = p->ex_rc;
   if (p->hamiltonian == 1 && ML_RC > reach) reach = ML_RC;
-  double w = reach + p->skin;
+  double w = (reach + p->skin) * (1.0 + 1e-6);
   for (int a = 0; a < 3; ++a) {
     int n = (int)floor(p->box[a] / w);
     if (n % 2) n -= 1;
