@@ -140,6 +140,15 @@ typedef struct sl_ctx sl_ctx;  /* opaque, owned by the library */
  * edge of 4096 A or more: positions are held in 64-bit fixed point too). */
 int sl_workspace_bytes(const sl_params* params, size_t* bytes);
 
+/* Sector grid of the sectored sweep (Sec. 5.1) for these parameters, on the
+ * host (no device call): nsec (host, 3) sectors per edge, the largest even
+ * counts whose edges edge (host, 3, A) exceed the spin reach (ex_rc_A, or
+ * the learned model's 6 A cutoff, plus skin_A) by a relative margin of 1e-6.
+ * Sectors of one colour are then more than the reach apart while no atom has
+ * moved more than skin/2, so their spins never interact within a pass.
+ * Errors: those of sl_workspace_bytes. */
+int sl_sector_grid(const sl_params* params, int32_t nsec[3], double edge[3]);
+
 /* Create a context: copies r, v, s (device, [n][3] doubles, caller order)
  * into the library's sector-sorted layout inside `workspace` (device,
  * >= sl_workspace_bytes, 256-byte aligned, owned by the caller and kept
@@ -277,7 +286,10 @@ int sl_set_launch_shape(sl_ctx* ctx, int32_t sweep_variant, int32_t block);
  * using different streams) race and may return wrong results.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress,
  * done once per device, with that device current); make that first call
- * before any stream capture.  Stream-ordered on cuda_stream; no host sync.
+ * before any stream capture.  The address is kept for the life of the
+ * process: do not call this after cudaDeviceReset on that device.
+ * cuda_stream must belong to the current device (SL_ERR_ARG otherwise,
+ * before any launch).  Stream-ordered on cuda_stream; no host sync.
  * Errors: SL_ERR_ARG, SL_ERR_CUDA. */
 int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void* cuda_stream);
 

@@ -28,7 +28,7 @@ SL_ML_NPARAM, SL_ML_NNORM = 7361, 192
 
 # Every exported symbol of include/sl.h.
 EXPORTS = (
-    "sl_workspace_bytes", "sl_init", "sl_build_neighbors", "sl_step", "sl_set_dt", "sl_set_field",
+    "sl_workspace_bytes", "sl_sector_grid", "sl_init", "sl_build_neighbors", "sl_step", "sl_set_dt", "sl_set_field",
     "sl_energy", "sl_magnetization", "sl_get_state", "sl_set_state", "sl_get_state_host",
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
     "sl_get_timing", "sl_magnetization_static", "sl_status", "sl_strerror", "sl_destroy",
@@ -78,6 +78,7 @@ def load():
     P = ctypes.POINTER(sl_params)
     sig = {
         "sl_workspace_bytes": ([P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+        "sl_sector_grid": ([P, ctypes.POINTER(ctypes.c_int32), _dp], ctypes.c_int),
         "sl_init": ([P, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
         "sl_build_neighbors": ([_vp], ctypes.c_int),
         "sl_step": ([_vp, ctypes.c_int32], ctypes.c_int),
@@ -196,6 +197,15 @@ def workspace_bytes(p) -> int:
     b = ctypes.c_size_t(0)
     check(L.sl_workspace_bytes_batch(arr, len(arr), ctypes.byref(b)), "sl_workspace_bytes_batch")
     return int(b.value)
+
+
+def sector_grid(p):
+    """(sectors per edge, sector edges in A) of the sectored sweep for the
+    parameter dict p, computed on the host."""
+    n = (ctypes.c_int32 * 3)()
+    e = (ctypes.c_double * 3)()
+    check(load().sl_sector_grid(ctypes.byref(make_params(p)), n, e), "sl_sector_grid")
+    return [int(x) for x in n], [float(x) for x in e]
 
 
 def strerror(code: int) -> str:

@@ -53,12 +53,14 @@ struct DeviceGuard {
 };
 
 // Sector grid of Sec. 5.1: the largest even count per edge with sector edge
-// >= exchange cutoff + skin (the network's cutoff + skin for the learned
-// Hamiltonian, whose spins interact up to that distance).
+// >= (exchange cutoff + skin)(1 + SL_SECTOR_MARGIN) (the network's cutoff +
+// skin for the learned Hamiltonian, whose spins interact up to that
+// distance).  The margin keeps two atoms of same-colour sectors more than
+// the list radius apart by more than a float distance test can misjudge.
 int sector_grid(const sl_params* p, int n[3], double e[3]) {
   double reach = p->ex_rc_A;
   if (p->hamiltonian == SL_HAM_LEARNED && SL_ML_RC > reach) reach = SL_ML_RC;
-  double w = reach + p->skin_A;
+  double w = (reach + p->skin_A) * (1.0 + SL_SECTOR_MARGIN);
   for (int a = 0; a < 3; ++a) {
     int k = (int)std::floor(p->box[a] / w);
     if (k % 2) k -= 1;
@@ -96,6 +98,17 @@ int validate(const sl_params* p) {
   }
   if (p->neel_alpha_eV != 0.0 && !(p->neel_delta_A > 0.0)) return SL_ERR_ARG;
   if (p->dmi_alpha_eV != 0.0 && !(p->dmi_delta_A > 0.0)) return SL_ERR_ARG;
+  // every exponential the pair kernels take inside a cutoff stays within the
+  // double-float exp's accurate range: e^{-r^2/delta^2} for r < ex_rc
+  // (Eq. BSfunction, also the Neel and DMI ranges) and e^{-a (r - r0)} for
+  // 0 < r < morse_rc (also the fallback of the learned Hamiltonian)
+  auto sq = [](double x) { return x * x; };
+  if (!(sq(p->ex_rc_A / p->ex_delta_A) <= SL_DF_EXP_XMAX)) return SL_ERR_ARG;
+  if (p->neel_alpha_eV != 0.0 && !(sq(p->ex_rc_A / p->neel_delta_A) <= SL_DF_EXP_XMAX)) return SL_ERR_ARG;
+  if (p->dmi_alpha_eV != 0.0 && !(sq(p->ex_rc_A / p->dmi_delta_A) <= SL_DF_EXP_XMAX)) return SL_ERR_ARG;
+  if (!(std::fabs(p->morse_alpha_invA) * std::fmax(std::fabs(p->morse_rc_A - p->morse_r0_A),
+                                                   std::fabs(p->morse_r0_A)) <= SL_DF_EXP_XMAX))
+    return SL_ERR_ARG;
   // embedding term and ground-state subtraction: analytic Hamiltonian only
   if (!std::isfinite(p->eam_A_eV) || !std::isfinite(p->eam_beta)) return SL_ERR_ARG;
   if (p->subtract_ground_exchange != 0 && p->subtract_ground_exchange != 1) return SL_ERR_ARG;
@@ -528,6 +541,18 @@ int sl_workspace_bytes_batch(const sl_params* params, int32_t n_replicas, size_t
 
 int sl_workspace_bytes(const sl_params* params, size_t* bytes) {
   return sl_workspace_bytes_batch(params, 1, bytes);
+}
+
+int sl_sector_grid(const sl_params* params, int32_t nsec[3], double edge[3]) {
+  if (!nsec || !edge) return SL_ERR_ARG;
+  int e = validate(params);
+  if (e) return e;
+  int n[3];
+  double w[3];
+  e = sector_grid(params, n, w);
+  if (e) return e;
+  for (int a = 0; a < 3; ++a) { nsec[a] = n[a]; edge[a] = w[a]; }
+  return SL_OK;
 }
 
 int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, const double* v,

@@ -22,6 +22,14 @@ static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8};
 // |X| < 2^61 for positions within one box length of boxes below SL_FX_MAX_BOX.
 #define SL_FX_BITS 48
 #define SL_FX_MAX_BOX 4096.0  // box edges below 2^(60 - SL_FX_BITS) A
+// Largest |x| whose double-float exp(x) keeps its 4e-14 accuracy (the
+// reduction x = n ln2/64 + r is exact for |n| < 1024); parameter sets whose
+// exponentials reach beyond it inside a cutoff are rejected on the host.
+#define SL_DF_EXP_XMAX 11.0
+// Sector edges exceed the sector reach (cutoff + skin) by at least this
+// relative margin, so that a float distance test at the reach never lists a
+// pair from two sectors of one colour.
+#define SL_SECTOR_MARGIN 1e-6
 
 // Control block in device memory: sticky status, rebuild flag, counters.
 struct SlCtrl {

@@ -78,10 +78,19 @@ __global__ void k_mag_final(const double* part, int nblk, int n, double* out) {
 extern "C" int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void* cuda_stream) {
   if (!s || !out || n_atoms < 1) return SL_ERR_ARG;
   if (n_atoms > kStaticMaxAtoms) return SL_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the scratch address is the current device's: a stream of another device
+  // is a caller error, reported before any launch
+  int cur = 0, sdev = 0;
+  if (cudaGetDevice(&cur) != cudaSuccess) return SL_ERR_CUDA;
+  if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+    cudaGetLastError();
+    return SL_ERR_ARG;
+  }
+  if (sdev != cur) return SL_ERR_ARG;
   double* part = nullptr;
   int e = scratch_address(&part);
   if (e) return e;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   int nblk = (n_atoms + kStaticBlock - 1) / kStaticBlock;
   k_mag_partials<<<nblk, kStaticBlock, 0, st>>>(s, n_atoms, part);
   k_mag_final<<<1, 32, 0, st>>>(part, nblk, n_atoms, out);

@@ -158,3 +158,42 @@ def test_box_limit_of_fixed_point_positions(lib):
     with pytest.raises(lib.SlError) as e:
         lib.workspace_bytes(dict(p, box=[4096.0, 30.0, 30.0]))
     assert e.value.code == lib.SL_ERR_BOX
+
+
+def test_exponential_ranges_are_validated_on_host(lib):
+    """The pair kernels' double-float exp keeps its accuracy for |x| <= 11:
+    parameter sets whose exponentials inside a cutoff reach further
+    (e^{-r^2/delta^2} for r < ex_rc, e^{-a (r - r0)} for 0 < r < morse_rc)
+    are rejected."""
+    from paper_1801_10233_gb300 import inputs
+    p, *_ = inputs.workload("fe_bcc_10x10x10_nve")
+    assert lib.workspace_bytes(dict(p, ex_delta_A=3.4 / 11.0 ** 0.5 + 1e-6)) > 0
+    bad = (dict(p, ex_delta_A=0.3), dict(p, ex_delta_A=3.4 / 11.0 ** 0.5 - 1e-6),
+           dict(p, neel_alpha_eV=0.01, neel_delta_A=0.9), dict(p, dmi_alpha_eV=0.01, dmi_delta_A=0.5),
+           dict(p, morse_alpha_invA=4.0), dict(p, morse_r0_A=0.2, morse_alpha_invA=1.9))
+    for q in bad:
+        with pytest.raises(lib.SlError) as e:
+            lib.workspace_bytes(q)
+        assert e.value.code == lib.SL_ERR_ARG
+    # a small Neel/DMI range is fine while the term is off
+    assert lib.workspace_bytes(dict(p, neel_delta_A=0.1, dmi_delta_A=0.1)) > 0
+
+
+def test_sector_grid_of_a_commensurate_box(lib, orc):
+    """A box whose edge is an exact multiple of the spin reach (cutoff +
+    skin): the sectors must still be wider than the reach, so that no listed
+    exchange pair joins two sectors of one colour; library and oracle agree."""
+    import numpy as np
+    from paper_1801_10233_gb300 import inputs
+    p, r, v, s = inputs.bcc_fe_system(11, 21, T=100.0, a=32.0 / 11.0, ex_rc_A=3.5, skin_A=0.5)
+    p = dict(p, box=[32.0, 32.0, 32.0])
+    reach = p["ex_rc_A"] + p["skin_A"]
+    assert 32.0 / reach == 8.0
+    nsec, edge = lib.sector_grid(p)
+    assert nsec == [6, 6, 6]
+    assert all(e >= reach * (1 + 1e-6) for e in edge)
+    o = orc.Oracle(p, np.mod(r, 32.0), v, s)
+    assert list(o.order()["nsec"]) == nsec
+    # a box just wide enough for 8 sectors with the margin keeps 8
+    q = dict(p, box=[32.0 * (1 + 2e-6)] * 3)
+    assert lib.sector_grid(q)[0] == [8, 8, 8]
