@@ -1,11 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the coupled spin-lattice timestep (arXiv 1801.10233) on GB300.
 
-Default workload: bcc Fe, 64x64x64 cells (524,288 atoms), Morse lattice
-potential + Bethe-Slater exchange + 1 T Zeeman field, FP64 state, dt = 0.1 fs,
-seeded synthetic inputs.  One bench step = one full timestep of
+Default workload: bcc Fe, 100x100x100 cells (2,000,000 atoms), Morse
+lattice potential + Bethe-Slater exchange + 1 T Zeeman field, 300 K, random
+spins, FP64 state with double-float pair and rotation arithmetic, dt = 0.1
+fs, seeded synthetic inputs.  One bench step = one full timestep of
 Eq. general_ST_decomposition (half-kick, 16 colour passes, drift + rebuild
-check + exchange table, 16 colour passes, forces + half-kick).
+check + exchange table, 16 colour passes, forces + half-kick).  The other
+workloads (64^3 cells, 10^3 cells, the replica batch, the spin-orbit and
+embedding terms, the learned Hamiltonian) are reported as forms.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.  With torchrun (N > 1) every rank
@@ -30,50 +33,66 @@ if ROOT not in sys.path:
 
 METRIC = "spin-lattice atom-steps/s on 1 GB300 (plain vs learned/batched) + HBM roofline %"
 UNIT = "atom-steps/s"
-DEFAULT_WORKLOAD = "fe_bcc_64x64x64_nve"
+# The largest single-GPU workload: 100^3 cells, 2,000,000 atoms, 300 K,
+# random spins (the 64^3-cell workload is one of the forms).
+DEFAULT_WORKLOAD = "fe_bcc_100x100x100_nve"
+DEFAULT_STEPS = 1000
 # Oracle sample: the same recipe on a 16x16x16-cell box (8,192 atoms); the
 # oracle's cost per atom-step does not depend on the box size.
 SAMPLE_CELLS = 16
 
-# Algorithmic FP64 work per atom and step of each phase, counting add, mul
-# and fma-halves as 1, a square root or division as 10 and an exponential,
-# sine or cosine as 20.  Pair terms count each unordered pair once (bcc at
-# 6 A: 32 Morse pairs and 7 exchange pairs per atom), although the kernels
-# evaluate every pair from both atoms (deterministic per-atom sums without
-# atomics); the spin sweep needs all 14 exchange neighbours per update.
-MORSE_PAIR_FLOPS = 3 + 5 + 10 + 2 + 20 + 3 + 10 + 6      # dr, r^2, sqrt, arg, exp, V'/r, accumulate
-EXCH_FORCE_FLOPS = 5 + 6                                # s_i.s_j, accumulate
-JTABLE_PAIR_FLOPS = 3 + 5 + 2 + 20 + 6                  # dr, r^2, x, exp, J
-EXCH_DJ_FLOPS = 10 + 5                                  # J'/r from the same exponential (tabulated with J)
-ROTATION_FLOPS = 14 * 6 + 3 + 5 + 20 + 20 + 9 + 12 + 6  # field, u, |w|, sincos, A/B, cross, increment
-PHASE_FLOPS_PER_ATOM = {
-    "kick": 6,
-    "spin_half_op_1": 2 * ROTATION_FLOPS,
-    "drift_rebuild": 6 + 8,
-    "exchange_table": 7 * (JTABLE_PAIR_FLOPS + EXCH_DJ_FLOPS),
-    "spin_half_op_2": 2 * ROTATION_FLOPS,
-    "force_kick": 32 * MORSE_PAIR_FLOPS + 7 * EXCH_FORCE_FLOPS + 6,
+# Algorithmic FP64-equivalent arithmetic per atom-step of each kernel family,
+# with the scope table's per-unit estimates (an exponential ~20 ops, a square
+# root or division ~10, a sine or cosine ~40, a multiply-add 1; each
+# unordered pair once): Morse 32 pairs x ~45, exchange table 7 pairs x ~40,
+# spin rotations 4 per atom-step x (14 x 3 multiply-adds + ~60).
+KERNEL_OPS_PER_ATOM_STEP = {
+    "k_sweep_pass": 4 * (14 * 3 + 60),
+    "k_force": 32 * 45,
+    "k_jtable": 7 * 40,
+    "k_drift": 6,
+    "k_kick": 6,
 }
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 pipe, nominal at 2070 MHz
-# The kernels run the FP64-accurate arithmetic as double-float on the FP32
-# pipes: 152 SMs x 128 FP32 lanes x 2.07 GHz = 40.3e12 FP32 instructions/s;
-# a double-float multiply-add costs ~20 FP32 instructions (two_prod, two
-# corrections, two_sum, renormalisation), so FP64-accurate arithmetic peaks at
-# 40.3e12 / 20 x 2 flop = 4.03 TFLOP/s on this chip.
-DF_PEAK_TFLOPS = 152 * 128 * 2.07e9 / 20 * 2 / 1e12
-# DRAM bytes (read + write) of one launch of each phase's kernel from an ncu
-# capture of the current kernels on the 64^3-cell workload
-# (profiles/force_fe_bcc_64x64x64_nve.md, profiles/jtable_fe_bcc_64x64x64_nve.md).
-NCU_TRAFFIC_64CUBED = {"force_kick": 327.1e6, "exchange_table": 120.6e6}
-# DRAM bytes per atom-step of the whole step on the same workload, warm L2
-# (ncu --cache-control none, one pass per launch; profiles/dram_per_step_fe_bcc_64x64x64_nve.md)
-NCU_DRAM_PER_ATOM_STEP_64CUBED = 2139.0
+# Kernel family of each timed phase; launches per step of each family.
+PHASE_KERNEL = {"kick": "k_kick", "spin_half_op_1": "k_sweep_pass", "drift_rebuild": "k_drift",
+                "exchange_table": "k_jtable", "spin_half_op_2": "k_sweep_pass", "force_kick": "k_force"}
+KERNEL_LAUNCHES_PER_STEP = {"k_sweep_pass": 30, "k_force": 1, "k_jtable": 1, "k_drift": 1, "k_kick": 1}
+# What the path computes in: the bench line's dtype is "df64".
+ARITH = ("FP64 state (r, v, s, F), FP64 per-atom updates and energy sums; pair and rotation arithmetic "
+         "in double-float (unevaluated float pairs, ~48-bit significand, error-free transformations) on the "
+         "FP32 pipes, exp and rsqrt to <5e-14 relative; positions also in 64-bit fixed point for exact "
+         "separations")
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 pipe, nominal at 2070 MHz (context only)
+# Compulsory state traffic: r, v, s read and written once per step.
+STATE_BYTES_PER_ATOM_STEP = 144.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# kernel on a workload, from one ncu capture, with a hash of the kernel
+# sources it was taken on: a profile whose sources have changed since is
+# reported as null (stale), never reused.
+PROFILED_DRAM = {}
+PROFILED_SOURCES = ("sl_step.cu", "sl_pair.cuh", "sl_df64.cuh", "sl_internal.cuh", "sl_build.cu", "sl_api.cu")
+
+
+def kernel_sources_sha():
+    """sha256 (16 hex digits) of the kernel sources a profile depends on."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in PROFILED_SOURCES:
+        with open(os.path.join(ROOT, "paper_1801_10233_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled(workload, kernel):
+    """The current profile entry of (workload, kernel), or None if absent or stale."""
+    e = PROFILED_DRAM.get((workload, kernel))
+    return e if e and e.get("sources_sha") == kernel_sources_sha() else None
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200, help="timed steps (200: the 64^3-cell workload's run)")
+    ap.add_argument("--steps", type=int, default=DEFAULT_STEPS, help="timed steps (1000: the 100^3-cell workload's run)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
@@ -316,6 +335,47 @@ def learned_forms(args, dev, torch):
     return out
 
 
+def df_peak_tflops():
+    """Measured double-float multiply-add throughput of this GPU (TFLOP/s,
+    2 flop per multiply-add), from the library's own probe kernel."""
+    from paper_1801_10233_gb300 import _lib
+    f, _ = _lib.df_fma_rate(4096)
+    return f / 1e12
+
+
+def kernel_roofline(phases, n, workload, step_s_ms, peak=None):
+    """Roofline entry of the kernel family with the most device time per
+    step: achieved = its algorithmic ops per atom-step x atoms / its time per
+    step (the same per launch), against the measured double-float peak."""
+    per_kernel = {}
+    for ph, (tot, cnt) in phases.items():
+        k = PHASE_KERNEL[ph]
+        per_kernel[k] = per_kernel.get(k, 0.0) + tot / max(1, cnt)
+    dom = max((k for k in per_kernel if k in KERNEL_OPS_PER_ATOM_STEP), key=lambda k: per_kernel[k])
+    t = per_kernel[dom] * 1e-3
+    peak = peak if peak is not None else df_peak_tflops()
+    achieved = KERNEL_OPS_PER_ATOM_STEP[dom] * n / t / 1e12
+    launches = KERNEL_LAUNCHES_PER_STEP[dom]
+    prof = profiled(workload, dom)
+    traffic = prof["dram_bytes_per_launch"] if prof else None
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+           "traffic": traffic, "kernel": dom, "launches_per_step": launches,
+           "ms_per_launch": per_kernel[dom] / launches, "ops_per_atom_step": KERNEL_OPS_PER_ATOM_STEP[dom],
+           "peak_kind": "measured: double-float multiply-add throughput of the library's probe kernel "
+                        "(sl_df_fma_rate, 2 flop each), this GPU, this run",
+           "fp64_pipe_nominal_tflops": FP64_NOMINAL_TFLOPS,
+           "kernel_ms_per_step": per_kernel,
+           "phase_ms_per_step": {k: v_[0] / max(1, v_[1]) for k, v_ in phases.items()}}
+    hbm = measured_peaks().get("hbm_gbs")
+    if hbm:
+        out["hbm_peak_gbs"] = hbm
+        out["hbm_frac_state_traffic"] = STATE_BYTES_PER_ATOM_STEP * n / (step_s_ms * 1e-3) / 1e9 / hbm
+    if traffic:
+        out["traffic_profile"] = prof["profile"]
+        out["hbm_frac_kernel_traffic"] = traffic / (out["ms_per_launch"] * 1e-3) / 1e9 / hbm if hbm else None
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -346,6 +406,9 @@ def run_ours(args):
         tune = {"variant": sv, "block": sb, "set_by": "--launch-shape"}
     else:
         tune = None if args.no_autotune else sysm.autotune(3)
+    # the compute roof of the double-float kernels, measured on this GPU
+    # before the timed region (the probe kernel runs ~10 ms)
+    peak = df_peak_tflops()
     sysm.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -374,26 +437,7 @@ def run_ours(args):
     sysm.step(tsteps)
     phases = sysm.timing()
     sysm.set_timing(False)
-    dom = max(phases, key=lambda k: phases[k][0])
-    dom_ms = phases[dom][0] / max(1, phases[dom][1])
-    flops = PHASE_FLOPS_PER_ATOM[dom] * n
-    achieved = flops / (dom_ms * 1e-3) / 1e12
-    traffic = NCU_TRAFFIC_64CUBED.get(dom) if args.workload == DEFAULT_WORKLOAD else None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": DF_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / DF_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
-                "peak_kind": "FP64-accurate (double-float on FP32 pipes) peak derived from unit counts and clock",
-                "fp64_pipe_nominal_tflops": FP64_NOMINAL_TFLOPS,
-                "phase_ms_per_step": {k: v_[0] / max(1, v_[1]) for k, v_ in phases.items()}}
-    hbm = measured_peaks().get("hbm_gbs")
-    # compulsory state traffic: r, v, s read and written once per step (144 B/atom)
-    if hbm:
-        roofline["hbm_frac_state_traffic"] = 144.0 * n / (ms / args.steps * 1e-3) / 1e9 / hbm
-    if args.workload == DEFAULT_WORKLOAD:
-        # measured DRAM traffic of a whole step (ncu), and its rate at this run's step time
-        roofline["dram_bytes_per_atom_step"] = NCU_DRAM_PER_ATOM_STEP_64CUBED
-        if hbm:
-            roofline["hbm_frac_measured_traffic"] = (NCU_DRAM_PER_ATOM_STEP_64CUBED * n /
-                                                     (ms / args.steps * 1e-3) / 1e9 / hbm)
+    roofline = kernel_roofline(phases, n, args.workload, ms / args.steps, peak)
 
     # end to end through the public API with host buffers: per step, upload the
     # state from pinned memory, advance one step, read the state back
@@ -416,9 +460,10 @@ def run_ours(args):
     forms = None
     if rank == 0 and world == 1 and not args.no_forms and args.workload == DEFAULT_WORKLOAD:
         forms = {}
-        # timed steps as in each workload's run (the batch's 500 and the
-        # 2,000-atom system's 1,000), 200 for the spin-orbit and embedding forms
-        for name, steps in (("fe_bcc_batch256", 500), ("fe_bcc_10x10x10_nve", 1000),
+        # timed steps as in each workload's run (the 64^3-cell system's 200,
+        # the batch's 500 and the 2,000-atom system's 1,000), 200 for the
+        # spin-orbit and embedding forms
+        for name, steps in (("fe_bcc_64x64x64_nve", 200), ("fe_bcc_batch256", 500), ("fe_bcc_10x10x10_nve", 1000),
                             ("fe_bcc_64x64x64_spin_orbit", 200), ("fe_bcc_64x64x64_eam", 200)):
             fp, fr, fv, fs, fdesc = build_workload(name, 0)
             fn = int(sum(q["n_atoms"] for q in fp)) if isinstance(fp, list) else fp["n_atoms"]
@@ -438,7 +483,7 @@ def run_ours(args):
             fsys.set_timing(False)
             forms[name] = {"value": fn / (fms * 1e-3), "unit": UNIT, "ms_per_step": fms, "steps": steps,
                            "n_atoms": fn, "workload": fdesc, "launch_shape": ftune,
-                           "phase_ms_per_step": {k: v_[0] / max(1, v_[1]) for k, v_ in fph.items()}}
+                           "roofline": kernel_roofline(fph, fn, name, fms, peak)}
             fsys.close()
             del fsys
         if not args.no_learned:
@@ -458,7 +503,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+            "arith": ARITH,
             "config": {"workload": args.workload, "description": wdesc, "n_atoms": n, "dt_ps": p0["dt_ps"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "working set > 129 MB L2 (no flush needed)", "graph": counters["graph"],

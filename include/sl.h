@@ -293,6 +293,18 @@ int sl_set_launch_shape(sl_ctx* ctx, int32_t sweep_variant, int32_t block);
  * Errors: SL_ERR_ARG, SL_ERR_CUDA. */
 int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void* cuda_stream);
 
+/* Measured throughput of the library's double-float multiply-add (the
+ * FP64-accurate a*b + c on the FP32 pipes that the pair and rotation kernels
+ * are built from) on the current device: the compute roof those kernels are
+ * compared with.  The paper has no counterpart: this is a measurement
+ * service of the library.  Runs 4 blocks of 256 threads per SM, each thread
+ * `iters` (1 .. 2^20) rounds of 8 independent multiply-adds, on a private
+ * stream: one warm-up launch, then the best of three timed with CUDA events.
+ *   flop_per_s (host) 2 flop per multiply-add / best launch time
+ *   ms         (host, may be NULL) that launch's duration
+ * Synchronises.  Errors: SL_ERR_ARG, SL_ERR_CUDA. */
+int sl_df_fma_rate(int32_t iters, double* flop_per_s, double* ms);
+
 /* ------------------------------------------------------------------------
  * Learned per-atom Hamiltonian.  The paper has no learned model: this is an
  * extension of the library in which a small network stands in for the Morse

@@ -31,7 +31,7 @@ EXPORTS = (
     "sl_workspace_bytes", "sl_sector_grid", "sl_init", "sl_build_neighbors", "sl_step", "sl_set_dt", "sl_set_field",
     "sl_energy", "sl_magnetization", "sl_get_state", "sl_set_state", "sl_get_state_host",
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
-    "sl_get_timing", "sl_magnetization_static", "sl_status", "sl_strerror", "sl_destroy",
+    "sl_get_timing", "sl_magnetization_static", "sl_df_fma_rate", "sl_status", "sl_strerror", "sl_destroy",
     "sl_workspace_bytes_batch", "sl_init_batch", "sl_batch_size", "sl_energy_batch", "sl_magnetization_batch",
     "sl_ml_set_model", "sl_ml_get_model", "sl_ml_eval", "sl_ml_descriptor_stats", "sl_ml_gate", "sl_ml_vjp",
     "sl_ml_train_step", "sl_autotune", "sl_set_launch_shape",
@@ -97,6 +97,7 @@ def load():
         "sl_set_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
         "sl_get_timing": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "sl_magnetization_static": ([_vp, ctypes.c_int32, _vp, _vp], ctypes.c_int),
+        "sl_df_fma_rate": ([ctypes.c_int32, _dp, _dp], ctypes.c_int),
         "sl_status": ([_vp], ctypes.c_int),
         "sl_workspace_bytes_batch": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "sl_init_batch": ([P, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)],
@@ -206,6 +207,15 @@ def sector_grid(p):
     e = (ctypes.c_double * 3)()
     check(load().sl_sector_grid(ctypes.byref(make_params(p)), n, e), "sl_sector_grid")
     return [int(x) for x in n], [float(x) for x in e]
+
+
+def df_fma_rate(iters=4096):
+    """(flop/s, ms) of the double-float multiply-add on the current device
+    (2 flop per multiply-add), measured by the library."""
+    f = ctypes.c_double(0.0)
+    ms = ctypes.c_double(0.0)
+    check(load().sl_df_fma_rate(int(iters), ctypes.byref(f), ctypes.byref(ms)), "sl_df_fma_rate")
+    return f.value, ms.value
 
 
 def strerror(code: int) -> str:

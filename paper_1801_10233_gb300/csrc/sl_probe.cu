@@ -1,0 +1,74 @@
+// Measured throughput of the double-float multiply-add that the pair and
+// rotation kernels are built from (df_fma of sl_df64.cuh): the compute roof
+// of FP64-accurate arithmetic on the FP32 pipes of the current device.
+//
+// Every thread runs SL_PROBE_CHAINS independent chains a <- a b + c (the
+// chains give each warp enough independent instructions to fill the FP32
+// pipes), with |b| < 1 so the values stay finite; the grid is 4 blocks of
+// 256 threads per SM.  Each multiply-add counts as 2 flop.
+#include "sl_internal.cuh"
+#include "sl_df64.cuh"
+
+namespace {
+
+constexpr int SL_PROBE_CHAINS = 8;
+constexpr int SL_PROBE_THREADS = 256;
+
+// Written only when a result equals an improbable value, so the compiler
+// keeps the work without the kernel needing an output buffer.
+__device__ float2 g_probe_sink;
+
+__global__ void __launch_bounds__(SL_PROBE_THREADS) k_df_fma_rate(float2 bc0, float2 bc1, int iters) {
+  const df b = df_make(bc0.x, bc0.y), c = df_make(bc1.x, bc1.y);
+  df a[SL_PROBE_CHAINS];
+#pragma unroll
+  for (int j = 0; j < SL_PROBE_CHAINS; ++j) a[j] = df_make(1e-3f * (float)threadIdx.x + (float)j, 0.0f);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < SL_PROBE_CHAINS; ++j) a[j] = df_fma(a[j], b, c);
+  }
+  df s = a[0];
+#pragma unroll
+  for (int j = 1; j < SL_PROBE_CHAINS; ++j) s = df_add(s, a[j]);
+  if (s.hi == 12345.0f) g_probe_sink = make_float2(s.hi, s.lo);
+}
+
+}  // namespace
+
+extern "C" int sl_df_fma_rate(int32_t iters, double* flop_per_s, double* ms) {
+  if (!flop_per_s || iters < 1 || iters > (1 << 20)) return SL_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    return SL_ERR_CUDA;
+  const int blocks = 4 * sms;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = SL_ERR_CUDA;
+  float best = 0.0f;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
+  if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+    const float2 b = make_float2(0.99999988f, 1.3e-9f), c = make_float2(0.25f, -2.1e-10f);
+    rc = SL_OK;
+    // one warm-up launch, then the best of three timed launches
+    for (int rep = 0; rep < 4 && rc == SL_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      k_df_fma_rate<<<blocks, SL_PROBE_THREADS, 0, st>>>(b, c, iters);
+      cudaEventRecord(e1, st);
+      float t = 0.0f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess ||
+          cudaGetLastError() != cudaSuccess)
+        rc = SL_ERR_CUDA;
+      else if (rep > 0 && (best == 0.0f || t < best))
+        best = t;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  if (rc != SL_OK || !(best > 0.0f)) return rc != SL_OK ? rc : SL_ERR_CUDA;
+  const double fmas = (double)blocks * SL_PROBE_THREADS * (double)iters * SL_PROBE_CHAINS;
+  *flop_per_s = 2.0 * fmas / (best * 1e-3);
+  if (ms) *ms = best;
+  return SL_OK;
+}

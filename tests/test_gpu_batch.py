@@ -77,3 +77,36 @@ def test_batch_totals_are_sums(System):
     n = np.array([p["n_atoms"] for p in plist])
     mt = g.magnetization()
     assert np.abs(mt[:3] - (m[:, :3] * n[:, None]).sum(axis=0) / n.sum()).max() < 1e-14
+
+
+def test_batch_at_workload_sizes_matches_oracle(System):
+    """Replicas of the batched workload's sizes ({8, 12, 16, 20, 24}^3 cells,
+    1,024 to 27,648 atoms, two of 24^3) at bath temperatures spanning its
+    50..1200 K ends, lambda 0.01: every replica against its own oracle run
+    after 10 steps (same Philox draws), at 1e-12."""
+    import os
+    import oracle
+    cells = [24, 8, 12, 16, 20, 24, 12, 8]
+    temps = list(np.linspace(50.0, 1200.0, len(cells)))
+    plist, r, v, s = inputs.replica_systems(cells, temps, seed=18012, lam=0.01)
+    gpu = System(plist, r, v, s)
+    gpu.step(10)
+    rg, vg, sg = (_split(t.cpu().numpy(), plist) for t in gpu.state())
+    eg = gpu.energy_per_replica()
+    mg = gpu.magnetization_per_replica()
+    threads = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 1
+    for k, (p, rk, vk, sk) in enumerate(zip(plist, _split(r, plist), _split(v, plist), _split(s, plist))):
+        o = oracle.Oracle(p, rk, vk, sk, lam=p["lambda"], temperature=p["temperature_K"], seed=p["seed"],
+                          replica=p["replica"], threads=threads)
+        o.step(10)
+        ro, vo, so = o.state()
+        L = np.asarray(p["box"])
+        dr = rg[k] - ro
+        dr -= L * np.round(dr / L)
+        assert np.abs(dr).max() <= TOL * L.max(), (k, cells[k])
+        assert np.abs(sg[k] - so).max() <= TOL, (k, cells[k])
+        vrms = float(np.sqrt((vo * vo).mean()))
+        assert np.abs(vg[k] - vo).max() <= TOL * vrms, (k, cells[k])
+        eo = o.energy()
+        assert abs(eg[k, 4] - eo[4]) <= TOL * abs(eo[4]), (k, cells[k])
+        assert np.abs(mg[k] - o.magnetization()).max() <= TOL, (k, cells[k])

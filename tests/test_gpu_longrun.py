@@ -1,0 +1,113 @@
+"""Long runs: the GPU against the CPU oracle in the statistics of a
+10,000-step trajectory, and the invariants of long GPU runs.
+
+Sec. 5.2 compares serial and parallel runs of the method: with a different
+update order or rounding the trajectories separate, so what must agree is
+their statistics, not the positions.  Here the GPU (double-float pair and
+rotation arithmetic, FP64 state) and the FP64 oracle start from the same
+state and advance 10,000 steps of 0.1 fs; the means and standard deviations
+of the total energy per atom, |M| and the spin temperature must agree within
+their combined blocked standard errors.  Both runs must also keep every
+|s_i| = 1 to 1e-14 (Sec. 3: the rotations preserve the norm, no
+renormalisation) and drift by less than 1e-6 eV/atom/ps (the least-squares
+slope of E_tot/N against time).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1801_10233_gb300 import inputs  # noqa: E402
+
+DRIFT_MAX = 1e-6       # eV/atom/ps
+NORM_TOL = 1e-14
+NSIGMA = 4.0
+
+
+@pytest.fixture(scope="module")
+def System():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_10233_gb300.build import build
+    build()
+    from paper_1801_10233_gb300 import System as S
+    return S
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def _series(sysm, n, steps, every):
+    """E_tot/N, |M| and T_S every `every` steps, the first at t = 0."""
+    out = []
+    for k in range(steps // every + 1):
+        if k:
+            sysm.step(every)
+        e = sysm.energy()
+        m = sysm.magnetization()
+        out.append((e[4] / n, m[3], e[6]))
+    return np.array(out)
+
+
+def _blocked(x, nblocks=10):
+    """Mean, standard deviation, and the standard errors of both from the
+    spread of nblocks contiguous block estimates (correlated samples)."""
+    b = np.array_split(x, nblocks)
+    means = np.array([y.mean() for y in b])
+    sds = np.array([y.std() for y in b])
+    return x.mean(), x.std(), means.std(ddof=1) / math.sqrt(nblocks), sds.std(ddof=1) / math.sqrt(nblocks)
+
+
+def _drift(e, dt_ps, every):
+    t = np.arange(len(e)) * every * dt_ps
+    return np.polyfit(t, e, 1)[0]
+
+
+def test_long_run_statistics_match_the_oracle(System):
+    """10^3 cells (2,000 atoms, random spins, 200 K), 10,000 steps of 0.1 fs
+    on both sides from the same state, observables every 10 steps."""
+    import oracle
+    p, r, v, s = inputs.workload("fe_bcc_10x10x10_nve")
+    n, steps, every = p["n_atoms"], 10000, 10
+    gpu = System(p, r, v, s)
+    ref = oracle.Oracle(p, r, v, s, threads=_host_cores())
+    xg = _series(gpu, n, steps, every)
+    xo = _series(ref, n, steps, every)
+    # invariants of both runs
+    for st in ((t.cpu().numpy() for t in gpu.state()), ref.state()):
+        _, _, s1 = st
+        assert np.abs(np.linalg.norm(s1, axis=1) - 1.0).max() <= NORM_TOL
+    for x in (xg, xo):
+        assert abs(_drift(x[:, 0], p["dt_ps"], every)) <= DRIFT_MAX
+    # the energy is conserved along both runs to well inside the drift gate
+    assert np.abs(xg[:, 0] - xo[:, 0]).max() <= DRIFT_MAX
+    # statistics of E/N, |M|, T_S
+    floors = (1e-12, 1e-12, 1e-9)
+    for c, name in enumerate(("E_tot/N", "|M|", "T_S")):
+        mg, sg, emg, esg = _blocked(xg[:, c])
+        mo, so, emo, eso = _blocked(xo[:, c])
+        assert abs(mg - mo) <= NSIGMA * math.hypot(emg, emo) + floors[c] * max(1.0, abs(mo)), (name, mg, mo)
+        assert abs(sg - so) <= NSIGMA * math.hypot(esg, eso) + floors[c] * max(1.0, so), (name, sg, so)
+    assert gpu.counters()["steps"] == steps == ref.steps_done
+
+
+def test_long_run_invariants_64cubed(System):
+    """The 64^3-cell workload (524,288 atoms) over 1,000 steps: |s_i| = 1 to
+    1e-14, total momentum conserved, energy drift below 1e-6 eV/atom/ps."""
+    p, r, v, s = inputs.workload("fe_bcc_64x64x64_nve")
+    n, steps, every = p["n_atoms"], 1000, 100
+    gpu = System(p, r, v, s)
+    P0 = v.sum(axis=0)
+    x = _series(gpu, n, steps, every)
+    _, v1, s1 = (t.cpu().numpy() for t in gpu.state())
+    assert np.abs(np.linalg.norm(s1, axis=1) - 1.0).max() <= NORM_TOL
+    assert np.abs(v1.sum(axis=0) - P0).max() <= 1e-7
+    assert abs(_drift(x[:, 0], p["dt_ps"], every)) <= DRIFT_MAX
