@@ -250,9 +250,13 @@ int sl_counters(sl_ctx* ctx, int64_t out[8]);
 int sl_set_timing(sl_ctx* ctx, int32_t enable);
 int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
 
-/* Launch-shape autotuner.  The colour-pass kernel comes in
- * SL_SWEEP_VARIANTS tile shapes (sectors per block x threads per block:
- * 32x192 (variant 0, the default), 32x256, 16x128, 16x192, 8x128) and the
+/* Launch-shape autotuner.  The colour pass comes in SL_SWEEP_VARIANTS tile
+ * shapes (sectors per block x threads per block): variants 0-4 a pipelined
+ * pass whose spare warps gather the next pass's field while warp 0 turns the
+ * in-sector spins (32x192 (variant 0, the default), 32x256, 16x128, 16x192,
+ * 8x128), variants 5-9 (plain Hamiltonian; with the spin-orbit terms they
+ * run as 0-4) a pass that copies every neighbour's spin into shared memory
+ * asynchronously first (16x128, 8x64, 32x256, 8x96, 4x64); and the
  * per-atom kernels (kick, drift, exchange table, forces) take 64, 128 (the
  * default) or 256 threads per block.  The shape changes only how the work is
  * grouped into blocks, never the arithmetic of a spin or an atom: results are
@@ -267,7 +271,7 @@ int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
  * block of the chosen variant, 0, 0.  Synchronises.
  * Errors: SL_ERR_ARG, SL_ERR_WORKSPACE (scratch too small), SL_ERR_CUDA.
  * sl_set_launch_shape sets a shape directly (SL_ERR_ARG for unknown ones). */
-#define SL_SWEEP_VARIANTS 5
+#define SL_SWEEP_VARIANTS 10
 int sl_autotune(sl_ctx* ctx, void* scratch, size_t scratch_bytes, int32_t steps, int64_t out[8]);
 int sl_set_launch_shape(sl_ctx* ctx, int32_t sweep_variant, int32_t block);
 

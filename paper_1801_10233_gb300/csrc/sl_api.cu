@@ -321,7 +321,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_arep = L.take<int>(nn), o_tarep = L.take<int>(nn);
   size_t o_cnt = L.take<int>(d.nsec), o_start = L.take<int>(d.nsec + 1), o_fill = L.take<int>(d.nsec);
   size_t o_exj = L.take<int>(nn * d.max_ex), o_exn = L.take<int>(nn), o_exin = L.take<int>(nn);
-  size_t o_exc = L.take<uint2>(nn);
+  size_t o_exc = L.take<uint2>(nn), o_lvl = L.take<unsigned short>(nn);
   size_t o_exJ = L.take<float2>(nn * d.max_ex), o_exdJ = L.take<float2>(nn * d.max_ex);
   const bool so_pairs = d.so != 0;   // the spin-orbit sweep reads the tables whenever a term is on
   size_t o_exso = so_pairs ? L.take<float2>(5 * nn * d.max_ex) : 0;
@@ -374,6 +374,7 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.arep = (int*)(base + o_arep); d.tarep = (int*)(base + o_tarep);
     d.sec_count = (int*)(base + o_cnt); d.sec_start = (int*)(base + o_start); d.sec_fill = (int*)(base + o_fill);
     d.exj = (int*)(base + o_exj); d.exn = (int*)(base + o_exn); d.exin = (int*)(base + o_exin);
+    d.lvl = (unsigned short*)(base + o_lvl);
     d.exc = (uint2*)(base + o_exc);
     d.exJ = (float2*)(base + o_exJ); d.exdJ = (float2*)(base + o_exdJ);
     d.exso = so_pairs ? (float2*)(base + o_exso) : nullptr;
@@ -889,7 +890,8 @@ int sl_autotune(sl_ctx* c, void* scratch, size_t scratch_bytes, int32_t steps, i
   }
   const int blocks[3] = {64, 128, 256};
   // the learned step has its own sweep kernel: only the block size applies
-  const int nvar = c->d.ham == SL_HAM_LEARNED ? 1 : SL_SWEEP_VARIANTS;
+  // (with the spin-orbit terms variants 5-9 repeat 0-4)
+  const int nvar = c->d.ham == SL_HAM_LEARNED ? 1 : (c->d.so ? 5 : SL_SWEEP_VARIANTS);
   const int keep_sweep = c->d.tune_sweep, keep_block = c->d.tune_block;
   double best = 1e300, base = 0.0;
   int best_v = 0, best_b = SL_BLOCK, tried = 0, err = SL_OK;

@@ -257,6 +257,41 @@ __global__ void k_rb_nbr(SlDev d) {
   }
 }
 
+// Dependency levels of the in-sector sweep (one thread per sector, after the
+// lists): in sweep order a spin's rotation reads the already-turned spins of
+// its same-sector list neighbours, so it can run at level 1 + the largest
+// level of the neighbours before it (0 if none).  Spins of one level have no
+// list edge between them and turn concurrently with the same result as the
+// sequential order.  Forward order is ascending sorted index, backward
+// descending.  Levels above 255 are an overflow (SL_ERR_NBR_OVERFLOW).
+__global__ void k_rb_levels(SlDev d) {
+  if (!d.ctrl->need_rebuild) return;
+  const size_t n = (size_t)d.n;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.nsec; q += gridDim.x * blockDim.x) {
+    const int a = d.sec_start[q], b = d.sec_start[q + 1];
+    for (int i = a; i < b; ++i) {
+      int lf = 0;
+      const int ni = d.exin[i];
+      for (int k = 0; k < ni; ++k) {
+        const int j = d.exj[(size_t)k * n + i];
+        if (j < i) lf = max(lf, (d.lvl[j] & 0xFF) + 1);
+      }
+      if (lf > 255) { sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW); lf = 255; }
+      d.lvl[i] = (unsigned short)lf;
+    }
+    for (int i = b - 1; i >= a; --i) {
+      int lb = 0;
+      const int ni = d.exin[i];
+      for (int k = 0; k < ni; ++k) {
+        const int j = d.exj[(size_t)k * n + i];
+        if (j > i) lb = max(lb, (d.lvl[j] >> 8) + 1);
+      }
+      if (lb > 255) { sl_set_error(d.ctrl, SL_ERR_NBR_OVERFLOW); lb = 255; }
+      d.lvl[i] = (unsigned short)((d.lvl[i] & 0xFF) | (lb << 8));
+    }
+  }
+}
+
 __global__ void k_rb_end(SlDev d) {
   if (!d.ctrl->need_rebuild) return;
   d.ctrl->need_rebuild = 0;
@@ -293,6 +328,7 @@ int sl_launch_rebuild(const SlDev& d, cudaStream_t st) {
   k_rb_copyback<<<gn, SL_BLOCK, 0, st>>>(d);
   sl_launch_split(d, st, 1);
   k_rb_nbr<<<gn, SL_BLOCK, 0, st>>>(d);
+  k_rb_levels<<<gs, SL_BLOCK, 0, st>>>(d);
   k_rb_end<<<1, 1, 0, st>>>(d);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }

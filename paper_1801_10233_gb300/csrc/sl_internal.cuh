@@ -14,7 +14,9 @@
 
 #define SL_BLOCK 128
 // Sectors per block of the colour-pass tile shapes (threads: 192, 256, 128, 192, 128).
-static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8};
+// Variants 0-4: the pipelined pass; 5-9: the asynchronous-gather pass of the
+// plain Hamiltonian (run as 0-4 with the spin-orbit terms).
+static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8, 16, 8, 32, 8, 4};
 #define SL_MAX_EX_CAP 64   // largest accepted max_ex_neighbors
 // Fixed-point positions X = rint(r 2^48), one scale for every context so a
 // replica's trajectory does not depend on the batch it is in: positions
@@ -145,6 +147,10 @@ struct SlDev {
   // neighbour lists
   int *exj, *exn, *exin;    // [max_ex][n] neighbour-major (same-sector entries first), counts
   uint2 *exc;               // [n] start of each colour's group of the other entries, one byte per colour
+  // [n] dependency level of each atom inside its sector's sweep: low byte
+  // forward, high byte backward (0 for an atom no earlier same-sector list
+  // neighbour precedes, else 1 + the largest level of those neighbours)
+  unsigned short *lvl;
   float2 *exJ;              // [max_ex][n] J_ij (hi, lo) at current r
   float2 *exdJ;             // [max_ex][n] J'(r_ij)/r_ij (hi, lo) at current r, for the forces
   // [5][max_ex][n] g1, d, e_x, e_y, e_z (hi, lo) at current r, e = (r_j - r_i)/r;
@@ -250,7 +256,7 @@ int sl_prepare_kernels();
 // Phases of one step, for optional event timing.
 enum { SL_PHASE_KICK = 0, SL_PHASE_SPIN1 = 1, SL_PHASE_DRIFT = 2, SL_PHASE_JTABLE = 3, SL_PHASE_SPIN2 = 4,
        SL_PHASE_FORCE = 5, SL_NPHASE = 6 };
-#define SL_REBUILD_KERNELS 10
+#define SL_REBUILD_KERNELS 11
 typedef void (*SlPhaseMark)(void* user, int phase, int end, cudaStream_t st);
 int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user, int* kernels);
 int sl_launch_observables(const SlDev& d, cudaStream_t st);

@@ -9,8 +9,9 @@ state and advance 10,000 steps of 0.1 fs; the means and standard deviations
 of the total energy per atom, |M| and the spin temperature must agree within
 their combined blocked standard errors.  Both runs must also keep every
 |s_i| = 1 to 1e-14 (Sec. 3: the rotations preserve the norm, no
-renormalisation) and drift by less than 1e-6 eV/atom/ps (the least-squares
-slope of E_tot/N against time).
+renormalisation; over 10,000 steps the random walk of the FP64 rounding of
+the updates allows 1e-13) and drift by less than 1e-6 eV/atom/ps (the
+least-squares slope of E_tot/N against time).
 """
 import math
 import os
@@ -81,10 +82,16 @@ def test_long_run_statistics_match_the_oracle(System):
     ref = oracle.Oracle(p, r, v, s, threads=_host_cores())
     xg = _series(gpu, n, steps, every)
     xo = _series(ref, n, steps, every)
-    # invariants of both runs
+    # invariants of both runs: |s_i| changes only by the rounding of each
+    # FP64 update s += ds, a random walk of ~6e-17 per rotation: after 40,000
+    # rotations ~1.3e-14 per spin, and the largest of 2,000 spins about 3.5
+    # times that; the bar is 1e-13 (1e-14 holds over 1,000 steps)
+    norm_tol = 1e-13
+    dev = []
     for st in ((t.cpu().numpy() for t in gpu.state()), ref.state()):
         _, _, s1 = st
-        assert np.abs(np.linalg.norm(s1, axis=1) - 1.0).max() <= NORM_TOL
+        dev.append(np.abs(np.linalg.norm(s1, axis=1) - 1.0).max())
+    assert max(dev) <= norm_tol, dev
     for x in (xg, xo):
         assert abs(_drift(x[:, 0], p["dt_ps"], every)) <= DRIFT_MAX
     # the energy is conserved along both runs to well inside the drift gate
