@@ -115,6 +115,16 @@ __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1,
   }
 }
 
+// Programmatic dependent launch: each colour pass loads what the previous
+// pass does not write (lists, levels, its own spins, noise) before it waits
+// for that pass's results (pdl_wait), and lets the next pass's blocks be
+// scheduled only after that wait (pdl_trigger): the pass before the previous
+// one, which turned the next pass's colour in the fused sweep order 6, 7, 6,
+// is then complete, so the next pass's early loads see its results.  Both
+// are no-ops for a launch without the programmatic dependency.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Start of colour c's group among atom i's other-sector entries (c = 8: the end).
 __device__ __forceinline__ int group_start(uint2 g, int c, int ne) {
   if (c >= 8) return ne;
@@ -311,7 +321,8 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
   for (int w = threadIdx.x; w < SW_LWORDS; w += blockDim.x) sh_lc[w] = 0;
   __syncthreads();
 
-  // phase 1
+  // phase 1, before the previous pass's results: levels, own spins,
+  // same-sector lists, noise
   for (int t = threadIdx.x; t < na; t += blockDim.x) {
     const int i = a0 + t;
     if (fits) {
@@ -327,9 +338,7 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
       }
     }
     const float4 s4h = __ldg(d.sdf + 2 * (size_t)i), s4l = __ldg(d.sdf + 2 * (size_t)i + 1);
-    const int ni = __ldg(d.exin + i), ne = __ldg(d.exn + i);
-    float2 p0, p1, p2;
-    if (P) { p0 = __ldg(P + 3 * (size_t)i); p1 = __ldg(P + 3 * (size_t)i + 1); p2 = __ldg(P + 3 * (size_t)i + 2); }
+    const int ni = __ldg(d.exin + i);
     if (fits) {
       // all of the atom's same-sector entries go to the block's staging pool
       // when they fit (read-only loads: free to run ahead of the stores)
@@ -351,22 +360,6 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
     S[3 * t] = make_float2(s4h.x, s4l.x);
     S[3 * t + 1] = make_float2(s4h.y, s4l.y);
     S[3 * t + 2] = make_float2(s4h.z, s4l.z);
-    float hx, lx, hy, ly, hz, lz;
-    if (P) {
-      // the partial field of every other colour, plus the colour the previous pass turned
-      hx = p0.x; lx = p0.y; hy = p1.x; ly = p1.y; hz = p2.x; lz = p2.y;
-      const uint2 g = __ldg(d.exc + i);
-      ext_field<SO>(d, i, group_start(g, prev_colour, ne), group_start(g, prev_colour + 1, ne), hx, lx, hy, ly, hz,
-                    lz);
-    } else {
-      hx = d.zee_f[0].x; lx = d.zee_f[0].y;
-      hy = d.zee_f[1].x; ly = d.zee_f[1].y;
-      hz = d.zee_f[2].x; lz = d.zee_f[2].y;
-      ext_field<SO>(d, i, ni, ne, hx, lx, hy, ly, hz, lz);
-    }
-    Fx[3 * t] = D2(acc_done(hx, lx));
-    Fx[3 * t + 1] = D2(acc_done(hy, ly));
-    Fx[3 * t + 2] = D2(acc_done(hz, lz));
     if (noise) {
       // eta ~ N(0, 2 D_S / |tau|), D_S = lambda (1 + lambda^2) k_B T / hbar;
       // counter (atom id within its replica, step, sub-pass, replica)
@@ -385,6 +378,32 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
         Eh[3 * t + 2] = D2(df_mul(sig, g.z));
       }
     }
+  }
+  pdl_wait();
+  pdl_trigger();
+
+  // phase 1, the external field: the partial field of every other colour
+  // plus the colour the previous pass turned (the first pass: all of it)
+  for (int t = threadIdx.x; t < na; t += blockDim.x) {
+    const int i = a0 + t;
+    const int ne = __ldg(d.exn + i);
+    float hx, lx, hy, ly, hz, lz;
+    if (P) {
+      const float2 p0 = __ldcg(P + 3 * (size_t)i), p1 = __ldcg(P + 3 * (size_t)i + 1),
+                   p2 = __ldcg(P + 3 * (size_t)i + 2);
+      hx = p0.x; lx = p0.y; hy = p1.x; ly = p1.y; hz = p2.x; lz = p2.y;
+      const uint2 g = __ldg(d.exc + i);
+      ext_field<SO>(d, i, group_start(g, prev_colour, ne), group_start(g, prev_colour + 1, ne), hx, lx, hy, ly, hz,
+                    lz);
+    } else {
+      hx = d.zee_f[0].x; lx = d.zee_f[0].y;
+      hy = d.zee_f[1].x; ly = d.zee_f[1].y;
+      hz = d.zee_f[2].x; lz = d.zee_f[2].y;
+      ext_field<SO>(d, i, __ldg(d.exin + i), ne, hx, lx, hy, ly, hz, lz);
+    }
+    Fx[3 * t] = D2(acc_done(hx, lx));
+    Fx[3 * t + 1] = D2(acc_done(hy, ly));
+    Fx[3 * t + 2] = D2(acc_done(hz, lz));
   }
   __syncthreads();
 
@@ -555,6 +574,7 @@ k_sweep_async(SlDev d, int colour, int backward, int subpass, int prev_colour) {
     const int cnt = fits ? ne - ni : 0;           // a block beyond SW_MAXA atoms reads global memory
     const int base = cnt > 0 ? atomicAdd(used, cnt) : SLOTS;
     const int nslot = max(0, min(cnt, SLOTS - base));
+    pdl_wait();                                   // the neighbours' spins are the previous pass's results
 #pragma unroll
     for (int q = 0; q < SW_JSPEC; ++q) {
       const int k = q - ni;                       // pool entry of list row q
@@ -620,6 +640,8 @@ k_sweep_async(SlDev d, int colour, int backward, int subpass, int prev_colour) {
       }
     }
   }
+  pdl_wait();                                     // (threads without an atom)
+  pdl_trigger();
   cp_async_wait_all();
 
   // phase 1b: each thread sums the external field of the atoms whose copies
@@ -1025,6 +1047,27 @@ int launch_tables(const SlDev& d, int grid, int block, cudaStream_t st) {
 // two), colours 6..0 backward.  Pass p reads the partial field written by
 // pass p - 1 (none for p = 0) and precomputes the next pass's.
 constexpr int SL_SWEEP_PASSES = 15;
+// Launch with programmatic stream serialization (pdl = true): the kernel may
+// start while the previous one finishes; it waits for it with
+// griddepcontrol.wait.  The first pass of a half-op is launched plainly: the
+// kernel before it may be the last pass of the other half-op, which turns the
+// same colour (spin-only dynamics), or any kernel of the step.
+template <typename... KArgs, typename... Args>
+void launch_pdl(bool pdl, void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <int SPB, int THREADS, bool SO>
 void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
   int g = (d.s8 + SPB - 1) / SPB;
@@ -1038,8 +1081,8 @@ void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
     const int pin = p > 0 ? (p - 1) & 1 : -1;
     const int pout = p < SL_SWEEP_PASSES - 1 ? p & 1 : -1;
     const size_t sm = sweep_smem_bytes(noise, 12 * SPB, bwd[p] == 2, true);
-    k_sweep_pass<SPB, THREADS, SO><<<g, THREADS, sm, st>>>(d, col[p], bwd[p], subpass0 + (bwd[p] == 1), prev, next,
-                                                           pin, pout);
+    launch_pdl(p > 0, k_sweep_pass<SPB, THREADS, SO>, g, THREADS, sm, st, d, col[p], bwd[p], subpass0 + (bwd[p] == 1),
+               prev, next, pin, pout);
   }
 }
 
@@ -1068,7 +1111,7 @@ void launch_half_op_async_t(const SlDev& d, cudaStream_t st, int subpass0) {
     const int col = p < 7 ? p : (p == 7 ? 7 : 14 - p);
     const int bwd = p < 7 ? 0 : (p == 7 ? 2 : 1);
     const int prev = p == 0 ? -1 : (p - 1 < 7 ? p - 1 : (p - 1 == 7 ? 7 : 14 - (p - 1)));
-    k_sweep_async<SPB, THREADS, MAXA><<<g, THREADS, sm, st>>>(d, col, bwd, subpass0 + (bwd == 1), prev);
+    launch_pdl(p > 0, k_sweep_async<SPB, THREADS, MAXA>, g, THREADS, sm, st, d, col, bwd, subpass0 + (bwd == 1), prev);
   }
 }
 
