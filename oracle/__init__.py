@@ -51,7 +51,7 @@ class _Params(ctypes.Structure):
         ("neel_alpha", ctypes.c_double), ("neel_gamma", ctypes.c_double), ("neel_delta", ctypes.c_double),
         ("dmi_alpha", ctypes.c_double), ("dmi_gamma", ctypes.c_double), ("dmi_delta", ctypes.c_double),
         ("eam_A", ctypes.c_double), ("eam_d", ctypes.c_double), ("eam_beta", ctypes.c_double),
-        ("ground_sub", ctypes.c_int32), ("pad2", ctypes.c_int32),
+        ("ground_sub", ctypes.c_int32), ("eam_tab", ctypes.c_int32),
     ]
 
 
@@ -114,6 +114,14 @@ def lib():
         L.orc_ml_eval_sample.argtypes = [ctypes.c_int, _c_double_p, _c_double_p, _c_double_p, _f_p, _f_p,
                                          ctypes.c_int, _c_int_p, _c_double_p, _c_double_p, _c_double_p,
                                          _c_double_p]
+        L.orc_set_eam_tables.restype = ctypes.c_int
+        L.orc_set_eam_tables.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _c_double_p, ctypes.c_int,
+                                         ctypes.c_double, _c_double_p, _c_double_p]
+        L.orc_potential_energy_state.restype = ctypes.c_int
+        L.orc_potential_energy_state.argtypes = [ctypes.c_void_p, _c_double_p, _c_double_p, _c_double_p]
+        L.orc_spline_eval.restype = ctypes.c_int
+        L.orc_spline_eval.argtypes = [ctypes.c_int, ctypes.c_double, _c_double_p, ctypes.c_int, _c_double_p,
+                                      _c_double_p, _c_double_p]
         L.orc_bf16_value.restype = ctypes.c_double
         L.orc_bf16_value.argtypes = [ctypes.c_float]
         L.orc_params_size.restype = ctypes.c_int
@@ -182,6 +190,7 @@ def make_params(p: dict, brute_force=False, lam=0.0, temperature=0.0, seed=0, re
     q.eam_A, q.eam_d = float(p.get("eam_A_eV", 0.0)), float(p.get("eam_d_A", 1.0))
     q.eam_beta = float(p.get("eam_beta", 0.0))
     q.ground_sub = int(p.get("subtract_ground_exchange", 0))
+    q.eam_tab = int(p.get("eam_tabulated", 0))
     return q
 
 
@@ -284,6 +293,29 @@ class Oracle:
         if e:
             raise OracleError(e)
 
+    def set_eam_tables(self, F, drho, rho, phi, dr):
+        """Tables of the tabulated embedded-atom potential (params
+        eam_tabulated = 1): F on rho = k drho, rho(r) and phi(r) on r = k dr."""
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        if rho.shape != phi.shape:
+            raise ValueError("rho and phi tables differ in length")
+        e = self._L.orc_set_eam_tables(self._h, len(F), float(drho), _dp(F), len(rho), float(dr), _dp(rho), _dp(phi))
+        if e:
+            raise OracleError(e)
+
+    def potential_energy(self, r, s):
+        """(E_mech, E_exch, E_zeeman, sum, E_spin_orbit) of arbitrary positions
+        and spins with this system's parameters and tables (brute-force pairs)."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        out = np.empty(5)
+        e = self._L.orc_potential_energy_state(self._h, _dp(r), _dp(s), _dp(out))
+        if e:
+            raise OracleError(e)
+        return out
+
     def gate(self):
         """(out-of-range atoms at the last learned evaluation point, points handed to the analytic H)."""
         out = np.zeros(2, dtype=np.int32)
@@ -302,6 +334,20 @@ def potential_energy(params: dict, r, s):
     out = np.empty(5)
     L.orc_potential_energy(ctypes.byref(p), _dp(r), _dp(s), _dp(out))
     return out
+
+
+def spline_eval(y, h, x):
+    """Natural cubic spline through (k h, y_k), evaluated at the points x:
+    (values, derivatives)."""
+    L = lib()
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.empty_like(x)
+    dv = np.empty_like(x)
+    e = L.orc_spline_eval(len(y), float(h), _dp(y), len(x), _dp(x), _dp(v), _dp(dv))
+    if e:
+        raise OracleError(e)
+    return v, dv
 
 
 def philox4x32_10(ctr, key):

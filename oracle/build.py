@@ -9,8 +9,8 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "sl_oracle.c")
-SRCS = [SRC, os.path.join(HERE, "sl_learned.c")]
-DEPS = SRCS + [os.path.join(HERE, "orc_learned.h")]
+SRCS = [SRC, os.path.join(HERE, "sl_learned.c"), os.path.join(HERE, "sl_eam_tab.c")]
+DEPS = SRCS + [os.path.join(HERE, "orc_learned.h"), os.path.join(HERE, "orc_eam_tab.h")]
 LIB = os.path.join(HERE, "libslorc.so")
 
 

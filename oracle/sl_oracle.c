@@ -42,7 +42,11 @@
  *                 under the rest of omega, another anisotropy half turn.
  *   Embedding     (Sec. 2, Eq. app:mech1) optional Finnis-Sinclair term
  *                 sum_i -A sqrt(rho_i), rho_i = sum_j f(r_ij), and optional
- *                 subtraction of the collinear exchange ground state.
+ *                 subtraction of the collinear exchange ground state; or
+ *                 (App. B) the tabulated embedded-atom potential: pair term
+ *                 phi(r) in place of Morse and embedding F(rho_i), rho_i =
+ *                 sum_j rho(r_ij), all three from tables on uniform grids
+ *                 through natural cubic splines (sl_eam_tab.c).
  *   Observables   kinetic, Morse, exchange, Zeeman energies; T_L
  *                 (Eq. lattice_temperature), T_S (Eq. spin_temperature),
  *                 magnetisation M = (1/N) sum_i s_i.
@@ -91,6 +95,7 @@
 #include <string.h>
 
 #include "orc_learned.h"
+#include "orc_eam_tab.h"
 
 /* Physical constants in the paper's "metal" unit set (A, ps, eV, amu, K, T). */
 #define ORC_HBAR 6.582119569e-4   /* eV ps / rad (Sec. 2.1 prints 1e3 too small) */
@@ -136,7 +141,12 @@ typedef struct {
    * mechanical energy (Eq. app:mech1): + sum_{i<j} J(r_ij) */
   double eam_A, eam_d, eam_beta;
   int32_t ground_sub;
-  int32_t pad2;
+  /* 1: the mechanical potential is the tabulated embedded-atom form of
+   * App. B instead of Morse (+ the Finnis-Sinclair term): pair term phi(r),
+   * embedding F(rho_i), rho_i = sum_j rho(r_ij), r < m_rc, each from a table on
+   * a uniform grid interpolated by a natural cubic spline (orc_set_eam_tables;
+   * eam_A must be 0) */
+  int32_t eam_tab;
 } orc_params;
 
 typedef struct {
@@ -168,6 +178,7 @@ typedef struct {
   long step;               /* completed steps */
   int err;
   int rebuilds;
+  orc_eam_tabs tabs;       /* tables of the tabulated embedded-atom potential */
   /* learned Hamiltonian */
   orc_ml_model* ml;        /* NULL until orc_ml_set_model */
   orc_list mll;            /* pairs with r < ML_RC */
@@ -249,7 +260,6 @@ static double morse_dV(const orc_params* p, double r) {
   return p->m_D0 * (-2.0 * p->m_alpha * e * e + 2.0 * p->m_alpha * e);
 }
 /* Embedding term: density contribution f(r), f'(r) (r < d), F(rho), F'(rho). */
-static int has_eam(const orc_params* p) { return p->eam_A != 0.0; }
 static double eam_f(const orc_params* p, double r) {
   double x = r - p->eam_d;
   return r < p->eam_d ? x * x + p->eam_beta * x * x * x / p->eam_d : 0.0;
@@ -260,6 +270,40 @@ static double eam_df(const orc_params* p, double r) {
 }
 static double eam_F(const orc_params* p, double rho) { return rho > 0.0 ? -p->eam_A * sqrt(rho) : 0.0; }
 static double eam_dF(const orc_params* p, double rho) { return rho > 0.0 ? -0.5 * p->eam_A / sqrt(rho) : 0.0; }
+
+/* The mechanical potential in either form (r < m_rc): pair term V(r) and
+ * dV/dr -- Morse, or phi(r) from its table -- and embedding F(rho) with the
+ * density contribution f(r) -- Finnis-Sinclair, or F(rho) and rho(r) from
+ * their tables.  Tables that are not set yet (T NULL or not ready) count as
+ * zero functions. */
+static int tab_on(const orc_params* p, const orc_eam_tabs* T) { return p->eam_tab && T && T->ready; }
+static int has_embed(const orc_params* p) { return p->eam_A != 0.0 || p->eam_tab; }
+static double mech_V(const orc_params* p, const orc_eam_tabs* T, double r, double* dVdr) {
+  if (p->eam_tab) {
+    if (!tab_on(p, T)) { if (dVdr) *dVdr = 0.0; return 0.0; }
+    return orc_spline_value(&T->phi, r, dVdr);
+  }
+  if (dVdr) *dVdr = morse_dV(p, r);
+  return morse_V(p, r);
+}
+static double embed_f(const orc_params* p, const orc_eam_tabs* T, double r, double* dfdr) {
+  if (p->eam_tab) {
+    if (!tab_on(p, T)) { if (dfdr) *dfdr = 0.0; return 0.0; }
+    return orc_spline_value(&T->rho, r, dfdr);
+  }
+  if (dfdr) *dfdr = eam_df(p, r);
+  return eam_f(p, r);
+}
+static double embed_F(const orc_params* p, const orc_eam_tabs* T, double rho, double* dFdrho) {
+  if (p->eam_tab) {
+    if (!tab_on(p, T)) { if (dFdrho) *dFdrho = 0.0; return 0.0; }
+    return orc_spline_value(&T->F, rho, dFdrho);
+  }
+  if (dFdrho) *dFdrho = eam_dF(p, rho);
+  return eam_F(p, rho);
+}
+/* The energy shift of each pair term: V(m_rc) with morse_shift (Morse only). */
+static double pair_shift(const orc_params* p) { return p->morse_shift && !p->eam_tab ? morse_V(p, p->m_rc) : 0.0; }
 
 /* Minimum-image separation d = r_j - r_i. */
 static void min_image(const orc_state* st, int i, int j, double d[3]) {
@@ -773,7 +817,7 @@ static double eam_rho(const orc_state* st, int i) {
   for (int k = st->mo.off[i]; k < st->mo.off[i + 1]; ++k) {
     double d[3];
     min_image(st, i, st->mo.j[k], d);
-    rho += eam_f(&st->p, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]));
+    rho += embed_f(&st->p, &st->tabs, sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), NULL);
   }
   return rho;
 }
@@ -801,7 +845,9 @@ static void compute_forces(orc_state* st) {
       double d[3];
       min_image(st, i, st->mo.j[k], d);
       double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      double c = morse_dV(&st->p, r) / r;       /* F_i += V'(r) (r_j - r_i)/r */
+      double dv;
+      mech_V(&st->p, &st->tabs, r, &dv);
+      double c = dv / r;                        /* F_i += V'(r) (r_j - r_i)/r */
       f[0] += c * d[0]; f[1] += c * d[1]; f[2] += c * d[2];
     }
     const double* si = st->s + 3 * i;
@@ -839,12 +885,12 @@ static void compute_forces(orc_state* st) {
       }
     }
   }
-  if (has_eam(&st->p)) {
+  if (has_embed(&st->p)) {
     /* E = sum_i F(rho_i): F_i = sum_j (F'(rho_i) + F'(rho_j)) f'(r) (r_j - r_i)/r */
     double* dF = (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     if (!dF) { if (st->err == ORC_OK) st->err = ORC_ERR_OOM; return; }
 #pragma omp parallel for num_threads(nt) schedule(static) if (nt > 1)
-    for (int i = 0; i < n; ++i) dF[i] = eam_dF(&st->p, eam_rho(st, i));
+    for (int i = 0; i < n; ++i) embed_F(&st->p, &st->tabs, eam_rho(st, i), dF + i);
 #pragma omp parallel for num_threads(nt) schedule(static) if (nt > 1)
     for (int i = 0; i < n; ++i) {
       double* f = st->F + 3 * i;
@@ -853,7 +899,9 @@ static void compute_forces(orc_state* st) {
         double d[3];
         min_image(st, i, j, d);
         double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        double c = (dF[i] + dF[j]) * eam_df(&st->p, r) / r;
+        double df;
+        embed_f(&st->p, &st->tabs, r, &df);
+        double c = (dF[i] + dF[j]) * df / r;
         f[0] += c * d[0]; f[1] += c * d[1]; f[2] += c * d[2];
       }
     }
@@ -903,6 +951,7 @@ void orc_destroy(orc_state* st) {
   free(st->ex.off); free(st->ex.j); free(st->mo.off); free(st->mo.j);
   free(st->exJ); free(st->exdJ); free(st->exG1); free(st->exDm); free(st->exE);
   free(st->ml); free(st->mll.off); free(st->mll.j); free(st->mlP); free(st->mlQ);
+  orc_spline_free(&st->tabs.F); orc_spline_free(&st->tabs.rho); orc_spline_free(&st->tabs.phi);
   free(st);
 }
 
@@ -929,7 +978,8 @@ orc_state* orc_create_threads(const orc_params* p, const double* r, const double
       (p->an_K != 0.0 && !(fabs(p->an_axis[0] * p->an_axis[0] + p->an_axis[1] * p->an_axis[1] +
                                 p->an_axis[2] * p->an_axis[2] - 1.0) <= 1e-12)) ||
       (p->eam_A != 0.0 && !(p->eam_d > 0.0 && p->eam_d <= p->m_rc)) ||
-      ((p->eam_A != 0.0 || p->ground_sub) && p->hamiltonian != 0)) {
+      ((p->eam_A != 0.0 || p->ground_sub || p->eam_tab) && p->hamiltonian != 0) ||
+      (p->eam_tab != 0 && p->eam_tab != 1) || (p->eam_tab && p->eam_A != 0.0)) {
     *err = ORC_ERR_ARG;
     return NULL;
   }
@@ -995,6 +1045,7 @@ void orc_ml_gate(const orc_state* st, int out[2]) {
 /* One or more timesteps of Eq. general_ST_decomposition. */
 int orc_step(orc_state* st, int nsteps) {
   if (st->p.hamiltonian == 1 && !st->ml) return ORC_ERR_ARG;
+  if (st->p.eam_tab && !st->tabs.ready) return ORC_ERR_ARG;
   for (int it = 0; it < nsteps; ++it) {
     double dt = st->p.dt;
     int lat = !st->p.fix_lattice;
@@ -1107,7 +1158,7 @@ void orc_energy(const orc_state* st, double out[8]) {
     const double* v = st->v + 3 * i;
     ek += 0.5 * st->p.mass * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / ORC_FTOA;
   }
-  double vshift = st->p.morse_shift ? morse_V(&st->p, st->p.m_rc) : 0.0;
+  double vshift = pair_shift(&st->p);
   if (learned) {
     for (int i = 0; i < n; ++i) em += eat[i];
   } else {
@@ -1118,7 +1169,7 @@ void orc_energy(const orc_state* st, double out[8]) {
       double d[3];
       min_image(st, i, j, d);
       double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      em += morse_V(&st->p, r) - vshift;
+      em += mech_V(&st->p, &st->tabs, r, NULL) - vshift;
     }
   for (int i = 0; i < n; ++i)
     for (int k = st->ex.off[i]; k < st->ex.off[i + 1]; ++k) {
@@ -1129,8 +1180,8 @@ void orc_energy(const orc_state* st, double out[8]) {
       ex -= st->exJ[k] * (si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2]);
       if (st->p.ground_sub) em += st->exJ[k];
     }
-  if (has_eam(&st->p))
-    for (int i = 0; i < n; ++i) em += eam_F(&st->p, eam_rho(st, i));
+  if (has_embed(&st->p))
+    for (int i = 0; i < n; ++i) em += embed_F(&st->p, &st->tabs, eam_rho(st, i), NULL);
   }
   double zf = st->p.mu_s * ORC_MUB;
   for (int i = 0; i < n; ++i) {
@@ -1196,12 +1247,13 @@ void orc_magnetization(const orc_state* st, double out[4]) {
 /* Energy of arbitrary (r, s) without building a state: used by the
  * finite-difference tests.  Same definitions as orc_energy (potential part
  * only: out[1..3]).  Brute-force pairs. */
-int orc_potential_energy(const orc_params* p, const double* r, const double* s, double out[5]) {
+static int potential_energy(const orc_params* p, const orc_eam_tabs* T, const double* r, const double* s,
+                            double out[5]) {
   orc_params q = *p;
   q.brute_force = 1;
   int n = q.n_atoms;
   double em = 0.0, ex = 0.0, ez = 0.0, eo = 0.0;
-  double vshift = q.morse_shift ? morse_V(&q, q.m_rc) : 0.0;
+  double vshift = pair_shift(&q);
   double* rho = (double*)calloc((size_t)(n ? n : 1), sizeof(double));
   if (!rho) return ORC_ERR_OOM;
   for (int i = 0; i < n; ++i)
@@ -1212,10 +1264,10 @@ int orc_potential_energy(const orc_params* p, const double* r, const double* s, 
         d[a] = x - q.box[a] * nearbyint(x / q.box[a]);
       }
       double rr = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-      if (rr < q.m_rc) em += morse_V(&q, rr) - vshift;
-      if (rr < q.m_rc && has_eam(&q)) {
-        rho[i] += eam_f(&q, rr);
-        rho[j] += eam_f(&q, rr);
+      if (rr < q.m_rc) em += mech_V(&q, T, rr, NULL) - vshift;
+      if (rr < q.m_rc && has_embed(&q)) {
+        rho[i] += embed_f(&q, T, rr, NULL);
+        rho[j] += embed_f(&q, T, rr, NULL);
       }
       if (rr < q.ex_rc) {
         const double* si = s + 3 * i;
@@ -1240,8 +1292,43 @@ int orc_potential_energy(const orc_params* p, const double* r, const double* s, 
     double sn = s[3 * i] * q.an_axis[0] + s[3 * i + 1] * q.an_axis[1] + s[3 * i + 2] * q.an_axis[2];
     eo -= q.an_K * sn * sn;
   }
-  for (int i = 0; i < n; ++i) em += eam_F(&q, rho[i]);
+  if (has_embed(&q))
+    for (int i = 0; i < n; ++i) em += embed_F(&q, T, rho[i], NULL);
   free(rho);
   out[0] = em; out[1] = ex; out[2] = ez; out[3] = em + ex + ez + eo; out[4] = eo;
   return ORC_OK;
+}
+
+int orc_potential_energy(const orc_params* p, const double* r, const double* s, double out[5]) {
+  return potential_energy(p, NULL, r, s, out);
+}
+
+/* The same with a state's parameters and tables (tabulated embedded-atom
+ * potential), for arbitrary positions and spins of its n atoms. */
+int orc_potential_energy_state(const orc_state* st, const double* r, const double* s, double out[5]) {
+  return potential_energy(&st->p, &st->tabs, r, s, out);
+}
+
+/* Tables of the tabulated embedded-atom potential (App. B): F on the grid
+ * rho = k drho (nrho points), rho(r) and phi(r) on r = k dr (nr points, the
+ * grid reaching m_rc); natural cubic splines through them.  Recomputes the
+ * forces. */
+int orc_set_eam_tables(orc_state* st, int nrho, double drho, const double* F, int nr, double dr, const double* rho,
+                       const double* phi) {
+  if (!st->p.eam_tab || nrho < 2 || nr < 2 || !(drho > 0.0) || !(dr > 0.0) || !((nr - 1) * dr >= st->p.m_rc))
+    return ORC_ERR_ARG;
+  orc_eam_tabs T;
+  T.ready = 0;
+  int e = orc_spline_build(&T.F, nrho, drho, F);
+  if (!e) e = orc_spline_build(&T.rho, nr, dr, rho);
+  if (!e) e = orc_spline_build(&T.phi, nr, dr, phi);
+  if (e) {
+    orc_spline_free(&T.F); orc_spline_free(&T.rho); orc_spline_free(&T.phi);
+    return e == -8 ? ORC_ERR_OOM : ORC_ERR_ARG;
+  }
+  orc_spline_free(&st->tabs.F); orc_spline_free(&st->tabs.rho); orc_spline_free(&st->tabs.phi);
+  st->tabs = T;
+  st->tabs.ready = 1;
+  compute_forces(st);
+  return st->err;
 }

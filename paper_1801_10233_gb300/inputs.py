@@ -61,6 +61,7 @@ def fe_params(box, n_atoms, **overrides):
         eam_d_A=3.569745,
         eam_beta=1.8,
         subtract_ground_exchange=0,
+        eam_tabulated=0,
         max_ex_neighbors=0,
         max_morse_neighbors=0,
     )
@@ -147,9 +148,44 @@ SPIN_ORBIT = dict(aniso_K_eV=1e-4, aniso_axis=[0.0, 0.0, 1.0], neel_alpha_eV=1e-
 # terms, not fitted.
 EMBEDDING = dict(eam_A_eV=0.5, eam_d_A=3.4, eam_beta=1.8, subtract_ground_exchange=1)
 
-# The seven workloads: plain 10^3 cells, plain 64^3 cells, 256 batched
+# Tabulated embedded-atom workload (App. B): the paper's potential comes as
+# tables of F(rho), rho(r) and phi(r); the Pun-Mishin tables are not
+# available here, so synthetic tables of smooth stand-in functions take their
+# place (eam_tables below).
+EMBEDDING_TABULATED = dict(eam_tabulated=1, subtract_ground_exchange=1)
+
+
+def eam_tables(nr=2003, dr=0.003, nrho=2001, drho=0.01, A=0.5, d=3.4, beta=1.8, shifted_force=True,
+               D0=0.4174, alpha=1.3885, r0=2.845, rc=6.0, cut=True):
+    """Synthetic tables for the tabulated embedded-atom form: (F, drho, rho,
+    phi, dr), F on rho = k drho (nrho points), rho(r) and phi(r) on r = k dr
+    (nr points, reaching past rc).  Stand-in shapes, not a fitted potential:
+    F(rho) = -A sqrt(rho); rho(r) = (r - d)^2 + beta (r - d)^3 / d below d, 0
+    beyond; phi(r) the Morse pair energy D0 (e^{-2a(r-r0)} - 2 e^{-a(r-r0)}),
+    by default shifted in value and slope to vanish at rc and 0 beyond (with
+    cut = False the Morse form continues past rc)."""
+    r = np.arange(nr) * dr
+    x = r - d
+    rho = np.where(r < d, x * x + beta * x ** 3 / d, 0.0)
+    def morse(y):
+        e = np.exp(-alpha * (y - r0))
+        return D0 * (e * e - 2.0 * e)
+    def dmorse(y):
+        e = np.exp(-alpha * (y - r0))
+        return D0 * (-2.0 * alpha * e * e + 2.0 * alpha * e)
+    phi = morse(r)
+    if shifted_force:
+        phi = phi - morse(rc) - (r - rc) * dmorse(rc)
+    if cut:
+        phi = np.where(r < rc, phi, 0.0)
+    F = -A * np.sqrt(np.arange(nrho) * drho)
+    return F, drho, rho, phi, dr
+
+
+# The workloads: plain 10^3 cells, plain 64^3 cells, 256 batched
 # replicas, learned 40^3 cells, large 100^3 cells, 64^3 cells with the
-# spin-orbit terms, 64^3 cells with the embedding term.
+# spin-orbit terms, 64^3 cells with the embedding term in the Finnis-Sinclair
+# and in the tabulated form.
 WORKLOADS = {
     "fe_bcc_10x10x10_nve": dict(ncells=10, seed=18010, T=200.0, spins="uniform", steps=1000),
     "fe_bcc_64x64x64_nve": dict(ncells=64, seed=18011, T=200.0, spins="cone10", steps=200),
@@ -158,6 +194,8 @@ WORKLOADS = {
     "fe_bcc_64x64x64_spin_orbit": dict(ncells=64, seed=18017, T=200.0, spins="cone10", steps=200,
                                        params=SPIN_ORBIT),
     "fe_bcc_64x64x64_eam": dict(ncells=64, seed=18018, T=200.0, spins="cone10", steps=200, params=EMBEDDING),
+    "fe_bcc_64x64x64_eam_tab": dict(ncells=64, seed=18019, T=200.0, spins="cone10", steps=200,
+                                    params=EMBEDDING_TABULATED),
 }
 
 
