@@ -128,7 +128,14 @@ typedef struct sl_params {
    * are reported in E_morse (the mechanical energy) by sl_energy. */
   double eam_A_eV, eam_d_A, eam_beta;
   int32_t subtract_ground_exchange;
-  int32_t reserved2;
+  /* 1: the mechanical potential is the tabulated embedded-atom form of App. B
+   * instead of the Morse pairs (and eam_A_eV must be 0): pair term phi(r) and
+   * embedding F(rho_i), rho_i = sum_j rho(r_ij), over r < morse_rc_A, each a
+   * natural cubic spline through a table on a uniform grid given by
+   * sl_set_eam_tables (sl_step returns SL_ERR_ARG until then; the forces of
+   * sl_init have no mechanical part).  Analytic Hamiltonian only; the
+   * exchange and the ground-state subtraction combine with it as above. */
+  int32_t eam_tabulated;
 } sl_params;
 
 typedef struct sl_ctx sl_ctx;  /* opaque, owned by the library */
@@ -194,6 +201,30 @@ int sl_step(sl_ctx* ctx, int32_t n_steps);
 /* Change dt (negative runs the dynamics backwards) or the applied field. */
 int sl_set_dt(sl_ctx* ctx, double dt_ps);
 int sl_set_field(sl_ctx* ctx, const double H_tesla[3]);
+
+/* Tables of the tabulated embedded-atom potential (App. B; contexts created
+ * with eam_tabulated = 1), in the uniform-grid form such potentials are
+ * distributed in: F at rho = k drho (k = 0 .. nrho-1, eV), rho(r) and phi(r)
+ * (eV) at r = k dr (k = 0 .. nr-1), the r grid reaching at least morse_rc_A.
+ * Each function is the natural cubic spline through its table (zero second
+ * derivative at both ends; F is extended past its last point by its last
+ * cubic).  The arrays are host memory, read during the call.
+ * The library solves for the splines in FP64, keeps their coefficients in its
+ * workspace (FP64 for the energies, double-float for the force and density
+ * kernels), and recomputes the densities and forces at the current state.
+ * Applies to every replica of a batch.  Synchronises.
+ * Errors: SL_ERR_ARG (context without eam_tabulated, NULL arrays, fewer than
+ * 2 or more than SL_EAM_MAX_POINTS points, non-positive spacing, an r grid
+ * short of morse_rc_A, non-finite values), SL_ERR_CUDA. */
+#define SL_EAM_MAX_POINTS 16384
+typedef struct sl_eam_tables {
+  int32_t nrho, nr;
+  double drho, dr;
+  const double* F;     /* [nrho] */
+  const double* rho;   /* [nr] */
+  const double* phi;   /* [nr] */
+} sl_eam_tables;
+int sl_set_eam_tables(sl_ctx* ctx, const sl_eam_tables* tables);
 
 /* out[8] (host) = E_kin, E_morse (the mechanical energy: Morse, embedding and
  * ground-state subtraction), E_exchange, E_zeeman, E_total (eV),

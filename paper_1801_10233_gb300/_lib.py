@@ -31,12 +31,18 @@ EXPORTS = (
     "sl_workspace_bytes", "sl_sector_grid", "sl_init", "sl_build_neighbors", "sl_step", "sl_set_dt", "sl_set_field",
     "sl_energy", "sl_magnetization", "sl_get_state", "sl_set_state", "sl_get_state_host",
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
-    "sl_get_timing", "sl_magnetization_static", "sl_df_fma_rate", "sl_status", "sl_strerror", "sl_destroy",
+    "sl_get_timing", "sl_magnetization_static", "sl_df_fma_rate", "sl_set_eam_tables", "sl_status", "sl_strerror", "sl_destroy",
     "sl_workspace_bytes_batch", "sl_init_batch", "sl_batch_size", "sl_energy_batch", "sl_magnetization_batch",
     "sl_ml_set_model", "sl_ml_get_model", "sl_ml_eval", "sl_ml_descriptor_stats", "sl_ml_gate", "sl_ml_vjp",
     "sl_ml_train_step", "sl_autotune", "sl_set_launch_shape",
 )
 PHASES = ("kick", "spin_half_op_1", "drift_rebuild", "exchange_table", "spin_half_op_2", "force_kick")
+
+
+class sl_eam_tables(ctypes.Structure):
+    _fields_ = [("nrho", ctypes.c_int32), ("nr", ctypes.c_int32), ("drho", ctypes.c_double),
+                ("dr", ctypes.c_double), ("F", ctypes.POINTER(ctypes.c_double)),
+                ("rho", ctypes.POINTER(ctypes.c_double)), ("phi", ctypes.POINTER(ctypes.c_double))]
 
 
 class sl_params(ctypes.Structure):
@@ -58,7 +64,7 @@ class sl_params(ctypes.Structure):
         ("neel_alpha_eV", ctypes.c_double), ("neel_gamma", ctypes.c_double), ("neel_delta_A", ctypes.c_double),
         ("dmi_alpha_eV", ctypes.c_double), ("dmi_gamma", ctypes.c_double), ("dmi_delta_A", ctypes.c_double),
         ("eam_A_eV", ctypes.c_double), ("eam_d_A", ctypes.c_double), ("eam_beta", ctypes.c_double),
-        ("subtract_ground_exchange", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+        ("subtract_ground_exchange", ctypes.c_int32), ("eam_tabulated", ctypes.c_int32),
     ]
 
 
@@ -98,6 +104,7 @@ def load():
         "sl_get_timing": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "sl_magnetization_static": ([_vp, ctypes.c_int32, _vp, _vp], ctypes.c_int),
         "sl_df_fma_rate": ([ctypes.c_int32, _dp, _dp], ctypes.c_int),
+        "sl_set_eam_tables": ([_vp, ctypes.POINTER(sl_eam_tables)], ctypes.c_int),
         "sl_status": ([_vp], ctypes.c_int),
         "sl_workspace_bytes_batch": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
         "sl_init_batch": ([P, ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)],
@@ -179,6 +186,7 @@ def make_params(p: dict) -> sl_params:
     q.eam_d_A = float(p.get("eam_d_A", 1.0))
     q.eam_beta = float(p.get("eam_beta", 0.0))
     q.subtract_ground_exchange = int(p.get("subtract_ground_exchange", 0))
+    q.eam_tabulated = int(p.get("eam_tabulated", 0))
     return q
 
 

@@ -35,6 +35,7 @@ struct sl_ctx {
   size_t ws_bytes;
   std::vector<double> lat_gamma, lat_temp;   // per-replica lattice bath (for sl_set_dt)
   int ml_ready;             // a model has been set
+  int eam_ready;            // the tables of the tabulated embedded-atom form have been set
   int ml_stale;             // parameters changed since the last evaluation point
   long long ml_t;           // Adam steps taken
 };
@@ -114,6 +115,8 @@ int validate(const sl_params* p) {
   if (p->subtract_ground_exchange != 0 && p->subtract_ground_exchange != 1) return SL_ERR_ARG;
   if ((p->eam_A_eV != 0.0 || p->subtract_ground_exchange) && p->hamiltonian != SL_HAM_ANALYTIC) return SL_ERR_ARG;
   if (p->eam_A_eV != 0.0 && !(p->eam_d_A > 0.0 && p->eam_d_A <= p->morse_rc_A)) return SL_ERR_ARG;
+  if (p->eam_tabulated != 0 && p->eam_tabulated != 1) return SL_ERR_ARG;
+  if (p->eam_tabulated && (p->hamiltonian != SL_HAM_ANALYTIC || p->eam_A_eV != 0.0)) return SL_ERR_ARG;
   double rc = (p->morse_rc_A > p->ex_rc_A ? p->morse_rc_A : p->ex_rc_A) + p->skin_A;
   for (int a = 0; a < 3; ++a)
     if (!(p->box[a] >= 2.0 * rc) || !(p->box[a] < SL_FX_MAX_BOX)) return SL_ERR_BOX;
@@ -144,7 +147,7 @@ int validate_batch(const sl_params* p, int nrep) {
                 a.neel_gamma == b.neel_gamma && a.neel_delta_A == b.neel_delta_A &&
                 a.dmi_alpha_eV == b.dmi_alpha_eV && a.dmi_gamma == b.dmi_gamma && a.dmi_delta_A == b.dmi_delta_A &&
                 a.eam_A_eV == b.eam_A_eV && a.eam_d_A == b.eam_d_A && a.eam_beta == b.eam_beta &&
-                a.subtract_ground_exchange == b.subtract_ground_exchange;
+                a.subtract_ground_exchange == b.subtract_ground_exchange && a.eam_tabulated == b.eam_tabulated;
     for (int c = 0; c < 3; ++c) same = same && a.H_tesla[c] == b.H_tesla[c] && a.aniso_axis[c] == b.aniso_axis[c];
     if (!same) return SL_ERR_ARG;
   }
@@ -288,7 +291,8 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   d.an_c_f = split_f2(2.0 * p->aniso_K_eV / SL_HBAR);
   d.an_cl_f = split_f2(2.0 * p->aniso_K_eV / SL_HBAR / (1.0 + p->lambda * p->lambda));
   // embedding term and ground-state subtraction
-  d.mech = (p->eam_A_eV != 0.0 ? SL_MECH_EAM : 0) | (p->subtract_ground_exchange ? SL_MECH_GROUND : 0);
+  d.mech = (p->eam_A_eV != 0.0 ? SL_MECH_EAM : 0) | (p->subtract_ground_exchange ? SL_MECH_GROUND : 0) |
+           (p->eam_tabulated ? SL_MECH_EAM | SL_MECH_TAB : 0);
   d.em_fused = p->eam_A_eV != 0.0 && p->eam_d_A <= p->ex_rc_A;
   d.em_A = p->eam_A_eV;
   d.em_d = p->eam_A_eV != 0.0 ? p->eam_d_A : 1.0;
@@ -327,6 +331,12 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_exso = so_pairs ? L.take<float2>(5 * nn * d.max_ex) : 0;
   const bool eam = (d.mech & SL_MECH_EAM) != 0;
   size_t o_emfp = eam ? L.take<float2>(nn) : 0;
+  // spline coefficients of the tabulated form, room for the largest tables
+  const bool tab = (d.mech & SL_MECH_TAB) != 0;
+  const size_t tint = (size_t)SL_EAM_MAX_POINTS - 1;
+  size_t o_tabd[3] = {0, 0, 0}, o_tabf[3] = {0, 0, 0};
+  if (tab)
+    for (int t = 0; t < 3; ++t) { o_tabd[t] = L.take<double>(4 * tint); o_tabf[t] = L.take<float4>(2 * tint); }
   size_t o_rx = L.take<SlFix>(nn);
   size_t o_sdf = L.take<float4>(2 * nn);
   size_t o_hb = L.take<float2>(3 * nn), o_sb = L.take<float2>(3 * nn), o_eb = L.take<float2>(3 * nn);
@@ -379,6 +389,11 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.exJ = (float2*)(base + o_exJ); d.exdJ = (float2*)(base + o_exdJ);
     d.exso = so_pairs ? (float2*)(base + o_exso) : nullptr;
     d.em_fp = eam ? (float2*)(base + o_emfp) : nullptr;
+    for (int t = 0; t < 3; ++t) {
+      d.tab_d[t] = tab ? (double*)(base + o_tabd[t]) : nullptr;
+      d.tab_f[t] = tab ? (float4*)(base + o_tabf[t]) : nullptr;
+      d.tab_n[t] = 0;
+    }
     d.rx = (SlFix*)(base + o_rx);
     d.sdf = (float4*)(base + o_sdf);
     d.hbuf = (float2*)(base + o_hb); d.sbuf = (float2*)(base + o_sb); d.ebuf = (float2*)(base + o_eb);
@@ -622,6 +637,7 @@ int sl_step(sl_ctx* c, int32_t n_steps) {
   if (!c || n_steps < 0) return SL_ERR_ARG;
   if (c->sticky) return c->sticky;
   if (c->d.ham == SL_HAM_LEARNED && !c->ml_ready) return SL_ERR_ARG;
+  if ((c->d.mech & SL_MECH_TAB) && !c->eam_ready) return SL_ERR_ARG;
   DeviceGuard g(c->device);
   if (int e = ml_fresh(c)) return e;
   if (c->timing) {
@@ -686,6 +702,70 @@ int sl_set_dt(sl_ctx* c, double dt) {
   }
   drop_graph(c);
   return c->sticky;
+}
+
+// Natural cubic spline through (k h, y_k), k = 0 .. n-1: the knot second
+// derivatives M solve M_{k-1} + 4 M_k + M_{k+1} = 6 (y_{k+1} - 2 y_k + y_{k-1})/h^2
+// with M_0 = M_{n-1} = 0 (Thomas algorithm); interval k is then
+// y_k + u [(y_{k+1} - y_k) - h^2 (2 M_k + M_{k+1})/6] + u^2 h^2 M_k/2
+// + u^3 h^2 (M_{k+1} - M_k)/6, u = x/h - k.  coef: [n-1][4].
+static void natural_spline(int n, double h, const double* y, std::vector<double>& coef) {
+  std::vector<double> M(n, 0.0), piv(n, 0.0), rhs(n, 0.0);
+  for (int k = 1; k + 1 < n; ++k) {
+    const double b = 4.0 - (k > 1 ? 1.0 / piv[k - 1] : 0.0);
+    piv[k] = b;
+    rhs[k] = 6.0 * (y[k + 1] - 2.0 * y[k] + y[k - 1]) / (h * h) - (k > 1 ? rhs[k - 1] / piv[k - 1] : 0.0);
+  }
+  for (int k = n - 2; k >= 1; --k) M[k] = (rhs[k] - M[k + 1]) / piv[k];
+  coef.assign((size_t)(n - 1) * 4, 0.0);
+  const double h2 = h * h;
+  for (int k = 0; k + 1 < n; ++k) {
+    coef[4 * k] = y[k];
+    coef[4 * k + 1] = (y[k + 1] - y[k]) - h2 * (2.0 * M[k] + M[k + 1]) / 6.0;
+    coef[4 * k + 2] = h2 * M[k] / 2.0;
+    coef[4 * k + 3] = h2 * (M[k + 1] - M[k]) / 6.0;
+  }
+}
+
+int sl_set_eam_tables(sl_ctx* c, const sl_eam_tables* t) {
+  if (!c || !t || !(c->d.mech & SL_MECH_TAB)) return SL_ERR_ARG;
+  if (!t->F || !t->rho || !t->phi) return SL_ERR_ARG;
+  if (t->nrho < 2 || t->nr < 2 || t->nrho > SL_EAM_MAX_POINTS || t->nr > SL_EAM_MAX_POINTS) return SL_ERR_ARG;
+  if (!(t->drho > 0.0) || !(t->dr > 0.0) || !std::isfinite(t->drho) || !std::isfinite(t->dr)) return SL_ERR_ARG;
+  if (!((t->nr - 1) * t->dr >= c->p.morse_rc_A)) return SL_ERR_ARG;
+  for (int k = 0; k < t->nrho; ++k) if (!std::isfinite(t->F[k])) return SL_ERR_ARG;
+  for (int k = 0; k < t->nr; ++k) if (!std::isfinite(t->rho[k]) || !std::isfinite(t->phi[k])) return SL_ERR_ARG;
+  if (c->sticky) return c->sticky;
+  DeviceGuard g(c->device);
+  const int n[3] = {t->nrho, t->nr, t->nr};
+  const double h[3] = {t->drho, t->dr, t->dr};
+  const double* y[3] = {t->F, t->rho, t->phi};
+  for (int q = 0; q < 3; ++q) {
+    std::vector<double> coef;
+    natural_spline(n[q], h[q], y[q], coef);
+    std::vector<float4> cf((size_t)(n[q] - 1) * 2);
+    for (int k = 0; k + 1 < n[q]; ++k) {
+      const float2 a = split_f2(coef[4 * k]), b = split_f2(coef[4 * k + 1]);
+      const float2 e = split_f2(coef[4 * k + 2]), f = split_f2(coef[4 * k + 3]);
+      cf[2 * k] = make_float4(a.x, a.y, b.x, b.y);
+      cf[2 * k + 1] = make_float4(e.x, e.y, f.x, f.y);
+    }
+    if (cudaMemcpyAsync(c->d.tab_d[q], coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->d.tab_f[q], cf.data(), cf.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return cuda_err(c);
+    c->d.tab_n[q] = n[q];
+    c->d.tab_ih[q] = 1.0 / h[q];
+    c->d.tab_ih_f[q] = split_f2(1.0 / h[q]);
+  }
+  c->eam_ready = 1;
+  drop_graph(c);
+  // densities and forces of the current state with the new potential
+  int e = sl_launch_pairs_and_forces(c->d, c->stream, 0);
+  if (e) return e;
+  return sync_status(c);
 }
 
 int sl_set_field(sl_ctx* c, const double H[3]) {
@@ -878,6 +958,7 @@ int sl_autotune(sl_ctx* c, void* scratch, size_t scratch_bytes, int32_t steps, i
   if (c->sticky) return c->sticky;
   if (scratch_bytes < c->ws_bytes) return SL_ERR_WORKSPACE;
   if (c->d.ham == SL_HAM_LEARNED && !c->ml_ready) return SL_ERR_ARG;
+  if ((c->d.mech & SL_MECH_TAB) && !c->eam_ready) return SL_ERR_ARG;
   DeviceGuard g(c->device);
   if (int e = ml_fresh(c)) return e;
   cudaStream_t st = c->stream;

@@ -67,8 +67,12 @@ struct SlRep {
 
 // Spin-orbit term bits of SlDev::so.
 enum { SL_SO_ANISO = 1, SL_SO_NEEL = 2, SL_SO_DMI = 4 };
-// Mechanical-potential bits of SlDev::mech: embedding term, ground-state subtraction.
-enum { SL_MECH_EAM = 1, SL_MECH_GROUND = 2 };
+// Mechanical-potential bits of SlDev::mech: embedding term, ground-state
+// subtraction, tabulated form (pair term and embedding from splines; set with
+// SL_MECH_EAM).
+enum { SL_MECH_EAM = 1, SL_MECH_GROUND = 2, SL_MECH_TAB = 4 };
+// Tables of the tabulated embedded-atom potential.
+enum { SL_TAB_F = 0, SL_TAB_RHO = 1, SL_TAB_PHI = 2 };
 
 // Double-float constants of one f(r) = 4 alpha x (1 - gamma x) e^{-x},
 // x = r^2/delta^2 (Eq. BSfunction): 1/delta^2, 4 alpha, gamma, 8 alpha/delta^2.
@@ -129,6 +133,15 @@ struct SlDev {
   int em_fused;                               // d <= ex_rc: the density comes from the exchange entries
   double em_A, em_d, em_beta;
   float2 em_d_f, em_d2_f, em_bd_f, em_hA_f;   // d, d^2, beta/d, A/2
+  // tabulated form (SL_MECH_TAB): natural cubic splines of F(rho), rho(r),
+  // phi(r); interval k holds c0..c3 of c0 + u (c1 + u (c2 + u c3)), u = x/h - k,
+  // in FP64 (tab_d, [n-1][4]) and as double-float pairs (tab_f, [n-1][2]:
+  // (c0, c1), (c2, c3)); tab_n = 0 until the tables are set
+  int tab_n[3];
+  double tab_ih[3];                            // 1/h
+  float2 tab_ih_f[3];
+  double* tab_d[3];
+  float4* tab_f[3];
 
   const SlRep* reps;        // [nrep]
   int* arep;                // replica of each sorted atom

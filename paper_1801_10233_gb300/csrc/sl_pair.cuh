@@ -333,6 +333,61 @@ __device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau,
 }
 
 // ---------------------------------------------------------------------------
+// Tabulated embedded-atom potential (App. B): natural cubic splines on
+// uniform grids.  Interval k = floor(x/h) (clamped to the grid; a value just
+// below a knot may take the next interval at u ~ -1e-16, where the two cubics
+// agree to rounding), u = x/h - k, value c0 + u (c1 + u (c2 + u c3)), slope
+// (c1 + u (2 c2 + 3 u c3))/h.  A table not yet set (tab_n = 0) is zero.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int tab_interval(const SlDev& d, int t, float uhi) {
+  const int k = (int)floorf(uhi);
+  return max(0, min(k, d.tab_n[t] - 2));
+}
+
+// Value (double-float); *slope (if not NULL) the derivative.
+__device__ __forceinline__ df tab_value_df(const SlDev& d, int t, df x, df* slope) {
+  if (d.tab_n[t] < 2) {
+    if (slope) *slope = df_f(0.0f);
+    return df_f(0.0f);
+  }
+  const df ih = F2(d.tab_ih_f[t]);
+  const df ux = df_mul(x, ih);
+  const int k = tab_interval(d, t, ux.hi);
+  const df u = df_add_f(ux, -(float)k);
+  const float4 a = __ldg(d.tab_f[t] + 2 * (size_t)k), b = __ldg(d.tab_f[t] + 2 * (size_t)k + 1);
+  const df c0 = df_make(a.x, a.y), c1 = df_make(a.z, a.w), c2 = df_make(b.x, b.y), c3 = df_make(b.z, b.w);
+  if (slope) {
+    const df q = df_add(df_scale(c2, 2.0f), df_mul(df_mul_f(c3, 3.0f), u));
+    *slope = df_mul(df_add(c1, df_mul(u, q)), ih);
+  }
+  return df_add(c0, df_mul(u, df_add(c1, df_mul(u, df_add(c2, df_mul(u, c3))))));
+}
+
+// Slope only (the force kernel's pair terms).
+__device__ __forceinline__ df tab_slope_df(const SlDev& d, int t, df x) {
+  if (d.tab_n[t] < 2) return df_f(0.0f);
+  const df ih = F2(d.tab_ih_f[t]);
+  const df ux = df_mul(x, ih);
+  const int k = tab_interval(d, t, ux.hi);
+  const df u = df_add_f(ux, -(float)k);
+  const float4 a = __ldg(d.tab_f[t] + 2 * (size_t)k), b = __ldg(d.tab_f[t] + 2 * (size_t)k + 1);
+  const df c1 = df_make(a.z, a.w), c2 = df_make(b.x, b.y), c3 = df_make(b.z, b.w);
+  const df q = df_add(df_scale(c2, 2.0f), df_mul(df_mul_f(c3, 3.0f), u));
+  return df_mul(df_add(c1, df_mul(u, q)), ih);
+}
+
+// FP64 value (the energies).
+__device__ __forceinline__ double tab_value_d(const SlDev& d, int t, double x) {
+  if (d.tab_n[t] < 2) return 0.0;
+  const double ux = x * d.tab_ih[t];
+  int k = (int)floor(ux);
+  k = max(0, min(k, d.tab_n[t] - 2));
+  const double u = ux - (double)k;
+  const double* c = d.tab_d[t] + 4 * (size_t)k;
+  return c[0] + u * (c[1] + u * (c[2] + u * c[3]));
+}
+
+// ---------------------------------------------------------------------------
 // Spin-orbit terms (App. A.2)
 // ---------------------------------------------------------------------------
 // f(r) = 4 alpha x (1 - gamma x) e^{-x}, x = r^2/delta^2 (Eq. BSfunction), and

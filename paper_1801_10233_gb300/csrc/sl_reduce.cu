@@ -26,6 +26,15 @@ __global__ void k_obs_atoms(SlDev d) {
     const int j = d.mj[(size_t)k * d.n + i];
     const double3 dd = sl_min_image(R, ri, d.r[j]);
     const double r2 = dd.x * dd.x + dd.y * dd.y + dd.z * dd.z;
+    if (d.mech & SL_MECH_TAB) {
+      // tabulated form: phi(r) and rho(r) inside the Morse cutoff
+      if (r2 < d.m_rc2) {
+        const double r = sqrt(r2);
+        em += tab_value_d(d, SL_TAB_PHI, r);
+        rho += tab_value_d(d, SL_TAB_RHO, r);
+      }
+      continue;
+    }
     if (r2 < d.m_rc2) {
       const double e = exp(-d.m_alpha * (sqrt(r2) - d.m_r0));
       em += d.m_D0 * (e * e - 2.0 * e) - d.m_vshift;
@@ -36,8 +45,9 @@ __global__ void k_obs_atoms(SlDev d) {
     }
   }
   q[1] = 0.5 * em;
-  // embedding energy F(rho_i) = -A sqrt(rho_i), one per atom
-  if (d.mech & SL_MECH_EAM) q[1] += rho > 0.0 ? -d.em_A * sqrt(rho) : 0.0;
+  // embedding energy, one per atom: F(rho_i) = -A sqrt(rho_i), or the table's
+  if (d.mech & SL_MECH_TAB) q[1] += tab_value_d(d, SL_TAB_F, rho);
+  else if (d.mech & SL_MECH_EAM) q[1] += rho > 0.0 ? -d.em_A * sqrt(rho) : 0.0;
   double hx = d.zee[0], hy = d.zee[1], hz = d.zee[2];
   double ex = 0.0;
   const bool learned = d.ham == SL_HAM_LEARNED && d.ctrl->ml_use;

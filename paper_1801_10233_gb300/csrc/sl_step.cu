@@ -849,6 +849,30 @@ __global__ void k_density(SlDev d) {
   const p3 pi = load_pos(d, i);
   const box3 B = load_box(d, d.reps[__ldg(d.arep + i)]);
   const int nm = d.mn[i];
+  if (d.mech & SL_MECH_TAB) {
+    // tabulated form: rho_i = sum_j rho(r_ij) over r < morse_rc, then F'(rho_i)
+    const df rc2 = F2(d.m_rc2_f);
+    const float rc2_hi = rc2.hi * 1.0001f;
+    df rho = df_f(0.0f);
+    for (int k = 0; k < nm; ++k) {
+      const int j = __ldg(d.mj + (size_t)k * d.n + i);
+      const p3 pj = load_pos(d, j);
+      const pre3 q = pair_pre(B, pi, pj);
+      if (q.r2 > rc2_hi) continue;
+      const df3 dd = pair_sep_k(B, pi, pj, q);
+      float a = 0.0f, b = 0.0f;
+      acc_prod(a, b, dd.x, dd.x);
+      acc_prod(a, b, dd.y, dd.y);
+      acc_prod(a, b, dd.z, dd.z);
+      const df r2 = acc_done(a, b);
+      if (!df_lt(r2, rc2)) continue;
+      rho = df_add(rho, tab_value_df(d, SL_TAB_RHO, df_mul(r2, df_rsqrt(r2)), nullptr));
+    }
+    df fp;
+    tab_value_df(d, SL_TAB_F, rho, &fp);
+    d.em_fp[i] = D2(fp);
+    return;
+  }
   const float d2_hi = F2(d.em_d2_f).hi * 1.0001f;
   float h = 0.0f, l = 0.0f;
   for (int k = 0; k < nm; ++k) {
@@ -887,7 +911,16 @@ __device__ __forceinline__ df morse_coeff(df r2, df na, df r0, df c2, df& rinv) 
   return df_mul(df_mul(c2, rinv), df_mul(e, df_add_f(df_neg(e), 1.0f)));   // V'(r)/r
 }
 
-// MECH: also the embedding term and the ground-state subtraction.
+// phi'(r)/r + (F'(rho_i) + F'(rho_j)) rho'(r)/r of the tabulated form.
+__device__ __forceinline__ df tab_coeff(const SlDev& d, df r2, df fpij) {
+  const df rinv = df_rsqrt(r2);
+  const df r = df_mul(r2, rinv);
+  const df c = df_add(tab_slope_df(d, SL_TAB_PHI, r), df_mul(fpij, tab_slope_df(d, SL_TAB_RHO, r)));
+  return df_mul(c, rinv);
+}
+
+// MECH: also the embedding term (closed or tabulated form) and the
+// ground-state subtraction.
 template <bool SO, bool MECH>
 __global__ void k_force(SlDev d, int kick) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -902,6 +935,7 @@ __global__ void k_force(SlDev d, int kick) {
   const df xrc2 = F2(d.ex_rc2_f);
   const float rc2_hi = rc2.hi * 1.0001f;
   const bool eam = MECH && (d.mech & SL_MECH_EAM);
+  const bool tab = MECH && (d.mech & SL_MECH_TAB);   // tabulated pair term and embedding replace Morse + FS
   const df ed2 = F2(d.em_d2_f);
   const df fpi = eam ? F2(__ldg(d.em_fp + i)) : df_f(0.0f);
   // entries 0..ne-1: exchange neighbours (also inside the Morse cutoff)
@@ -914,8 +948,13 @@ __global__ void k_force(SlDev d, int kick) {
     acc_prod(h, l, dd.z, dd.z);
     const df r2 = acc_done(h, l);
     df rinv;
-    df c = df_lt(r2, rc2) ? morse_coeff(r2, na, r0, c2, rinv) : df_f(0.0f);
-    if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
+    df c = df_f(0.0f);
+    if (tab) {
+      if (df_lt(r2, rc2)) c = tab_coeff(d, r2, df_add(fpi, F2(__ldg(d.em_fp + j))));
+    } else {
+      c = df_lt(r2, rc2) ? morse_coeff(r2, na, r0, c2, rinv) : df_f(0.0f);
+      if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
+    }
     if (df_lt(r2, xrc2)) {
       // J'(r)/r from the exchange table (same positions, same entry order)
       const df dJr = F2(__ldg(d.exdJ + (size_t)k * d.n + i));
@@ -974,8 +1013,13 @@ __global__ void k_force(SlDev d, int kick) {
     acc_prod(h, l, dd.z, dd.z);
     const df r2 = acc_done(h, l);
     df rinv;
-    df c = morse_coeff(r2, na, r0, c2, rinv);
-    if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
+    df c;
+    if (tab) {
+      c = tab_coeff(d, r2, df_add(fpi, F2(__ldg(d.em_fp + j))));
+    } else {
+      c = morse_coeff(r2, na, r0, c2, rinv);
+      if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
+    }
     acc_prod(fxh, fxl, c, dd.x);
     acc_prod(fyh, fyl, c, dd.y);
     acc_prod(fzh, fzl, c, dd.z);
@@ -995,8 +1039,13 @@ __global__ void k_force(SlDev d, int kick) {
     const df r2 = acc_done(h, l);
     if (!df_lt(r2, rc2)) continue;
     df rinv;
-    df c = morse_coeff(r2, na, r0, c2, rinv);
-    if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
+    df c;
+    if (tab) {
+      c = tab_coeff(d, r2, df_add(fpi, F2(__ldg(d.em_fp + j))));
+    } else {
+      c = morse_coeff(r2, na, r0, c2, rinv);
+      if (eam && df_lt(r2, ed2)) c = df_add(c, eam_coeff(d, r2, rinv, df_add(fpi, F2(__ldg(d.em_fp + j)))));
+    }
     acc_prod(fxh, fxl, c, dd.x);
     acc_prod(fyh, fyl, c, dd.y);
     acc_prod(fzh, fzl, c, dd.z);

@@ -82,6 +82,18 @@ class System:
         h = np.ascontiguousarray(H, dtype=np.float64)
         check(self._L.sl_set_field(self._h, _lib._arr_ptr(h)), "sl_set_field")
 
+    def set_eam_tables(self, F, drho, rho, phi, dr):
+        """Tables of the tabulated embedded-atom potential (eam_tabulated = 1):
+        F on rho = k drho, rho(r) and phi(r) on r = k dr (host arrays)."""
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        if rho.shape != phi.shape:
+            raise ValueError("rho and phi tables differ in length")
+        t = _lib.sl_eam_tables(len(F), len(rho), float(drho), float(dr), _lib._arr_ptr(F), _lib._arr_ptr(rho),
+                               _lib._arr_ptr(phi))
+        check(self._L.sl_set_eam_tables(self._h, ctypes.byref(t)), "sl_set_eam_tables")
+
     # -- observables -------------------------------------------------------
     def energy(self) -> np.ndarray:
         """E_kin, E_morse, E_exch, E_zeeman, E_total (eV), T_L, T_S (K), 0."""
