@@ -56,6 +56,9 @@ class _Params(ctypes.Structure):
 
 
 _lib = None
+# observation point inside a step: (user, event, arg); event 0 after a colour's
+# pass (arg = colour), 1 after the drift
+HOOK = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_int)
 
 
 def lib():
@@ -122,6 +125,8 @@ def lib():
         L.orc_spline_eval.restype = ctypes.c_int
         L.orc_spline_eval.argtypes = [ctypes.c_int, ctypes.c_double, _c_double_p, ctypes.c_int, _c_double_p,
                                       _c_double_p, _c_double_p]
+        L.orc_set_hook.argtypes = [ctypes.c_void_p, HOOK, ctypes.c_void_p]
+        L.orc_set_atoms.argtypes = [ctypes.c_void_p, ctypes.c_int, _c_int_p, _c_double_p, _c_double_p]
         L.orc_bf16_value.restype = ctypes.c_double
         L.orc_bf16_value.argtypes = [ctypes.c_float]
         L.orc_params_size.restype = ctypes.c_int
@@ -315,6 +320,18 @@ class Oracle:
         if e:
             raise OracleError(e)
         return out
+
+    def set_hook(self, fn):
+        """Call fn(event, arg) at the step's observation points (None: off)."""
+        self._hook = None if fn is None else HOOK(lambda user, ev, arg: fn(int(ev), int(arg)))
+        self._L.orc_set_hook(self._h, self._hook if self._hook is not None else HOOK(), None)
+
+    def set_atoms(self, ids, r=None, s=None):
+        """Overwrite the positions and/or spins of the atoms `ids`."""
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        r = None if r is None else np.ascontiguousarray(r, dtype=np.float64).reshape(len(ids), 3)
+        s = None if s is None else np.ascontiguousarray(s, dtype=np.float64).reshape(len(ids), 3)
+        self._L.orc_set_atoms(self._h, len(ids), _ip(ids), _opt(r), _opt(s))
 
     def gate(self):
         """(out-of-range atoms at the last learned evaluation point, points handed to the analytic H)."""

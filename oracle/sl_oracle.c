@@ -179,6 +179,11 @@ typedef struct {
   int err;
   int rebuilds;
   orc_eam_tabs tabs;       /* tables of the tabulated embedded-atom potential */
+  /* observation points inside a step (orc_set_hook): after each colour's
+   * pass of a sweep (event 0, arg = colour) and after the drift (event 1);
+   * the decomposition tests exchange halo data there */
+  void (*hook)(void* user, int event, int arg);
+  void* hook_user;
   /* learned Hamiltonian */
   orc_ml_model* ml;        /* NULL until orc_ml_set_model */
   orc_list mll;            /* pairs with r < ML_RC */
@@ -750,11 +755,23 @@ static int ml_point(orc_state* st, double* F) {
 }
 
 /* The palindromic sweep: forward over the sweep order with h/2 per spin, then backward. */
+static void call_hook(orc_state* st, int event, int arg) {
+  if (st->hook) st->hook(st->hook_user, event, arg);
+}
+
 static void sweep(orc_state* st, double h, int subpass0) {
-  int n = st->n;
   if (st->threads <= 1 || st->err != ORC_OK) {
-    for (int k = 0; k < n; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
-    for (int k = n - 1; k >= 0; --k) rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
+    /* the order is colour-major: colour c's atoms are entries
+     * colour_start[c] .. colour_start[c+1]-1, forward then backward */
+    for (int c = 0; c < 8; ++c) {
+      for (int k = st->colour_start[c]; k < st->colour_start[c + 1]; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
+      call_hook(st, 0, c);
+    }
+    for (int c = 7; c >= 0; --c) {
+      for (int k = st->colour_start[c + 1] - 1; k >= st->colour_start[c]; --k)
+        rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
+      call_hook(st, 0, c);
+    }
     return;
   }
   /* The same order with the sectors of one colour side by side: while every
@@ -766,11 +783,13 @@ static void sweep(orc_state* st, double h, int subpass0) {
 #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
     for (int q = st->colour_run[c]; q < st->colour_run[c + 1]; ++q)
       for (int k = st->run[q]; k < st->run[q + 1]; ++k) rotate(st, st->order[k], 0.5 * h, subpass0);
+    call_hook(st, 0, c);
   }
   for (int c = 7; c >= 0; --c) {
 #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
     for (int q = st->colour_run[c]; q < st->colour_run[c + 1]; ++q)
       for (int k = st->run[q + 1] - 1; k >= st->run[q]; --k) rotate(st, st->order[k], 0.5 * h, subpass0 + 1);
+    call_hook(st, 0, c);
   }
 }
 
@@ -1056,6 +1075,7 @@ int orc_step(orc_state* st, int nsteps) {
     spin_half_op(st, 0.5 * dt, 0);
     if (lat) {
       for (int k = 0; k < 3 * st->n; ++k) st->r[k] += dt * st->v[k];
+      call_hook(st, 1, 0);
       double h = 0.5 * st->p.skin;
       double md2 = max_disp2(st);
       int resector;
@@ -1084,6 +1104,24 @@ int orc_step(orc_state* st, int nsteps) {
 }
 
 void orc_set_dt(orc_state* st, double dt) { st->p.dt = dt; }
+
+/* Observation points (see orc_state.hook); NULL removes them. */
+void orc_set_hook(orc_state* st, void (*fn)(void* user, int event, int arg), void* user) {
+  st->hook = fn;
+  st->hook_user = user;
+}
+
+/* Overwrite positions and/or spins (NULL: keep) of m atoms given by id. */
+void orc_set_atoms(orc_state* st, int m, const int* ids, const double* r, const double* s) {
+  for (int q = 0; q < m; ++q) {
+    int i = ids[q];
+    if (i < 0 || i >= st->n) continue;
+    for (int a = 0; a < 3; ++a) {
+      if (r) st->r[3 * i + a] = r[3 * q + a];
+      if (s) st->s[3 * i + a] = s[3 * q + a];
+    }
+  }
+}
 
 void orc_get_state(const orc_state* st, double* r, double* v, double* s) {
   size_t b = (size_t)st->n * 3 * sizeof(double);
