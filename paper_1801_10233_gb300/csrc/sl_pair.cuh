@@ -26,16 +26,27 @@ struct p3 {
 
 // Positions, lists and tables are read-only in every kernel that gathers
 // them; their loads go through the read-only path and may be issued early.
+// A position (32 bytes, fixed point) and a spin's float split (32 bytes: hi
+// then lo halves) each come in one 256-bit load.
 __device__ __forceinline__ p3 load_pos(const SlDev& d, int j) {
-  const longlong2 a = __ldg(reinterpret_cast<const longlong2*>(d.rx + j));
-  const longlong2 b = __ldg(reinterpret_cast<const longlong2*>(d.rx + j) + 1);
+  long long x, y, z, w;
+  asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(x), "=l"(y), "=l"(z), "=l"(w) : "l"(d.rx + j));
+  (void)w;
   p3 p;
-  p.x = a.x; p.y = a.y; p.z = b.x;
+  p.x = x; p.y = y; p.z = z;
   return p;
 }
 
+// sdf[2j] and sdf[2j + 1] (hi, lo float4) of spin j in one load.
+__device__ __forceinline__ void load_sdf(const float4* sdf, int j, float4& h, float4& l) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(h.x), "=f"(h.y), "=f"(h.z), "=f"(h.w), "=f"(l.x), "=f"(l.y), "=f"(l.z), "=f"(l.w)
+      : "l"(sdf + 2 * (size_t)j));
+}
+
 __device__ __forceinline__ df3 load_spin(const SlDev& d, int j) {
-  float4 h = __ldg(d.sdf + 2 * (size_t)j), l = __ldg(d.sdf + 2 * (size_t)j + 1);
+  float4 h, l;
+  load_sdf(d.sdf, j, h, l);
   df3 s;
   s.x = df_make(h.x, l.x); s.y = df_make(h.y, l.y); s.z = df_make(h.z, l.z);
   return s;

@@ -90,12 +90,8 @@ __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1,
       }
     }
 #pragma unroll
-    for (int q = 0; q < SW_BATCH; ++q) {
-      if (kb + q < k1) {
-        vh[q] = __ldg(d.sdf + 2 * (size_t)jj[q]);
-        vl[q] = __ldg(d.sdf + 2 * (size_t)jj[q] + 1);
-      }
-    }
+    for (int q = 0; q < SW_BATCH; ++q)
+      if (kb + q < k1) load_sdf(d.sdf, jj[q], vh[q], vl[q]);
 #pragma unroll
     for (int q = 0; q < SW_BATCH; ++q) {
       if (kb + q < k1) {
@@ -337,7 +333,8 @@ k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, in
         sh_lc[SW_LWORDS - 1] = 1;
       }
     }
-    const float4 s4h = __ldg(d.sdf + 2 * (size_t)i), s4l = __ldg(d.sdf + 2 * (size_t)i + 1);
+    float4 s4h, s4l;
+    load_sdf(d.sdf, i, s4h, s4l);
     const int ni = __ldg(d.exin + i);
     if (fits) {
       // all of the atom's same-sector entries go to the block's staging pool
@@ -617,7 +614,8 @@ k_sweep_async(SlDev d, int colour, int backward, int subpass, int prev_colour) {
     }
     atomicMax(used + 1, (int)(lv & 0xFFu));
     atomicMax(used + 2, (int)(lv >> 8));
-    const float4 s4h = __ldg(d.sdf + 2 * (size_t)i), s4l = __ldg(d.sdf + 2 * (size_t)i + 1);
+    float4 s4h, s4l;
+    load_sdf(d.sdf, i, s4h, s4l);
     S[3 * t] = make_float2(s4h.x, s4l.x);
     S[3 * t + 1] = make_float2(s4h.y, s4l.y);
     S[3 * t + 2] = make_float2(s4h.z, s4l.z);
@@ -671,7 +669,8 @@ k_sweep_async(SlDev d, int colour, int backward, int subpass, int prev_colour) {
       } else {
         const size_t e = (size_t)k * n + i;
         const int j = __ldg(d.exj + e);
-        vh = __ldg(d.sdf + 2 * (size_t)j); vl = __ldg(d.sdf + 2 * (size_t)j + 1); J = F2(__ldg(d.exJ + e));
+        load_sdf(d.sdf, j, vh, vl);
+        J = F2(__ldg(d.exJ + e));
       }
       acc_prod(hx, lx, J, df_make(vh.x, vl.x));
       acc_prod(hy, ly, J, df_make(vh.y, vl.y));
