@@ -69,7 +69,16 @@ STATE_BYTES_PER_ATOM_STEP = 144.0
 # kernel on a workload, from one ncu capture, with a hash of the kernel
 # sources it was taken on: a profile whose sources have changed since is
 # reported as null (stale), never reused.
-PROFILED_DRAM = {}
+PROFILED_DRAM = {
+    ("fe_bcc_100x100x100_nve", "k_sweep_pass"): {
+        "dram_bytes_per_launch": 174.6e6, "sources_sha": "072a7692a61beb25",
+        "profile": "ncu dram__bytes_read.sum + dram__bytes_write.sum, --cache-control none, mean of 2 launches "
+                   "of k_sweep_pass<16, 128, 0> (launch shape 2,128) inside 3-step runs"},
+    ("fe_bcc_100x100x100_nve", "k_force"): {
+        "dram_bytes_per_launch": 2400.4e6, "sources_sha": "072a7692a61beb25",
+        "profile": "ncu dram__bytes_read.sum + dram__bytes_write.sum, --cache-control none, mean of 2 launches "
+                   "of k_force<0, 0> (launch shape 2,128) inside 3-step runs"},
+}
 PROFILED_SOURCES = ("sl_step.cu", "sl_pair.cuh", "sl_df64.cuh", "sl_internal.cuh", "sl_build.cu", "sl_api.cu")
 
 
