@@ -284,8 +284,8 @@ int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
 /* Launch-shape autotuner.  The colour pass comes in SL_SWEEP_VARIANTS tile
  * shapes (sectors per block x threads per block): variants 0-4 a pipelined
  * pass whose spare warps gather the next pass's field while warp 0 turns the
- * in-sector spins (32x192 (variant 0, the default), 32x256, 16x128, 16x192,
- * 8x128), variants 5-9 (plain Hamiltonian; with the spin-orbit terms they
+ * in-sector spins (32x192 (variant 0, the default), 32x256, 16x128, 16x128 with
+ * registers for 1,024 resident threads per SM, 8x128), variants 5-9 (plain Hamiltonian; with the spin-orbit terms they
  * run as 0-4) a pass that copies every neighbour's spin into shared memory
  * asynchronously first (16x128, 8x64, 32x256, 8x96, 4x64); and the
  * per-atom kernels (kick, drift, exchange table, forces) take 64, 128 (the

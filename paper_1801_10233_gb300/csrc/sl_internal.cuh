@@ -13,7 +13,7 @@
 #define SL_FTOA 9648.533212       // (eV/A)/amu -> A/ps^2
 
 #define SL_BLOCK 128
-// Sectors per block of the colour-pass tile shapes (threads: 192, 256, 128, 192, 128).
+// Sectors per block of the colour-pass tile shapes (threads: 192, 256, 128, 128, 128).
 // Variants 0-4: the pipelined pass; 5-9: the asynchronous-gather pass of the
 // plain Hamiltonian (run as 0-4 with the spin-orbit terms).
 static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8, 16, 8, 32, 8, 4};

@@ -275,8 +275,10 @@ __device__ __forceinline__ void sweep_chain(const SlDev& d, int q, int a0, bool 
     }
 }
 
-template <int SW_SPB, int SW_THREADS, bool SO>
-__global__ void __launch_bounds__(SW_THREADS, 768 / SW_THREADS)
+// SW_RES: threads per SM the register budget is cut for (768: 80 registers;
+// 1024: 64, no spills for the plain instance).
+template <int SW_SPB, int SW_THREADS, bool SO, int SW_RES = 768>
+__global__ void __launch_bounds__(SW_THREADS, SW_RES / SW_THREADS)
 k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, int next_colour, int pin, int pout) {
   constexpr int SW_MAXA = 12 * SW_SPB;
   extern __shared__ float2 smem[];
@@ -1116,7 +1118,7 @@ void launch_pdl(bool pdl, void (*kern)(KArgs...), int grid, int block, size_t sm
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
-template <int SPB, int THREADS, bool SO>
+template <int SPB, int THREADS, bool SO, int RES = 768>
 void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
   int g = (d.s8 + SPB - 1) / SPB;
   const bool noise = d.any_noise != 0;
@@ -1129,8 +1131,8 @@ void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
     const int pin = p > 0 ? (p - 1) & 1 : -1;
     const int pout = p < SL_SWEEP_PASSES - 1 ? p & 1 : -1;
     const size_t sm = sweep_smem_bytes(noise, 12 * SPB, bwd[p] == 2, true);
-    launch_pdl(p > 0, k_sweep_pass<SPB, THREADS, SO>, g, THREADS, sm, st, d, col[p], bwd[p], subpass0 + (bwd[p] == 1),
-               prev, next, pin, pout);
+    launch_pdl(p > 0, k_sweep_pass<SPB, THREADS, SO, RES>, g, THREADS, sm, st, d, col[p], bwd[p],
+               subpass0 + (bwd[p] == 1), prev, next, pin, pout);
   }
 }
 
@@ -1139,7 +1141,7 @@ void launch_half_op_so(const SlDev& d, cudaStream_t st, int subpass0) {
   switch (d.tune_sweep % 5) {
     case 1: launch_half_op_t<32, 256, SO>(d, st, subpass0); break;
     case 2: launch_half_op_t<16, 128, SO>(d, st, subpass0); break;
-    case 3: launch_half_op_t<16, 192, SO>(d, st, subpass0); break;
+    case 3: launch_half_op_t<16, 128, SO, 1024>(d, st, subpass0); break;
     case 4: launch_half_op_t<8, 128, SO>(d, st, subpass0); break;
     default: launch_half_op_t<32, 192, SO>(d, st, subpass0); break;
   }
@@ -1164,7 +1166,8 @@ void launch_half_op_async_t(const SlDev& d, cudaStream_t st, int subpass0) {
 }
 
 // Tile shapes: variants 0-4 are the pipelined pass k_sweep_pass (sectors per
-// block 32, 32, 16, 16, 8 x 192, 256, 128, 192, 128 threads), for every
+// block 32, 32, 16, 16, 8 x 192, 256, 128, 128, 128 threads; variant 3 with
+// registers for 1,024 threads per SM, the others 768), for every
 // Hamiltonian; variants 5-9 the asynchronous-gather pass k_sweep_async of the
 // plain Hamiltonian (16, 8, 32, 8, 4 sectors x 128, 64, 256, 96, 64 threads,
 // up to 128, 64, 256, 96, 48 atoms per block in shared memory); with the
@@ -1239,7 +1242,7 @@ bool prepare_sweep() {
                              (int)sweep_smem_bytes(true, 12 * 32, true, true)) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_sweep_pass<16, 128, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sweep_smem_bytes(true, 12 * 16, true, true)) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_sweep_pass<16, 192, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  ok &= cudaFuncSetAttribute(k_sweep_pass<16, 128, SO, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sweep_smem_bytes(true, 12 * 16, true, true)) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_sweep_pass<8, 128, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sweep_smem_bytes(true, 12 * 8, true, true)) == cudaSuccess;
