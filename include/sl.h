@@ -340,6 +340,18 @@ int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void*
  * Synchronises.  Errors: SL_ERR_ARG, SL_ERR_CUDA. */
 int sl_df_fma_rate(int32_t iters, double* flop_per_s, double* ms);
 
+/* Check of the library's bounded in-kernel wait (the one the tensor-core
+ * kernels use for their MMA completion), on the current device: one thread
+ * waits on a shared-memory barrier of count 1 for at most limit_ns
+ * nanoseconds (0 .. 2e9) of the GPU's global timer; with arrive = 1 it first
+ * arrives itself, so the wait completes, with arrive = 0 nothing ever does.
+ * *status (host) receives SL_OK or SL_ERR_TIMEOUT, the code such a wait
+ * leaves in a context's sticky status.  The paper has no counterpart: this
+ * lets a caller confirm that a wait which never completes ends with an
+ * error status, leaving the GPU usable, instead of hanging it.
+ * Synchronises.  Errors: SL_ERR_ARG, SL_ERR_CUDA. */
+int sl_check_bounded_wait(int64_t limit_ns, int32_t arrive, int32_t* status);
+
 /* ------------------------------------------------------------------------
  * Learned per-atom Hamiltonian.  The paper has no learned model: this is an
  * extension of the library in which a small network stands in for the Morse

@@ -8,6 +8,7 @@
 // 256 threads per SM.  Each multiply-add counts as 2 flop.
 #include "sl_internal.cuh"
 #include "sl_df64.cuh"
+#include "sl_tc.cuh"
 
 namespace {
 
@@ -33,7 +34,36 @@ __global__ void __launch_bounds__(SL_PROBE_THREADS) k_df_fma_rate(float2 bc0, fl
   if (s.hi == 12345.0f) g_probe_sink = make_float2(s.hi, s.lo);
 }
 
+// The bounded wait of the tensor-core kernels (mbar_wait_ns) on a barrier
+// of count 1: completed by one arrival (arrive = 1) or by nothing.
+__device__ int g_wait_status;
+__global__ void k_bounded_wait(unsigned long long limit_ns, int arrive) {
+  __shared__ __align__(8) unsigned long long bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) mbar_init(b, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) mbar_arrive(b);
+    g_wait_status = mbar_wait_ns(b, 0, limit_ns) ? SL_OK : SL_ERR_TIMEOUT;
+  }
+}
+
 }  // namespace
+
+extern "C" int sl_check_bounded_wait(int64_t limit_ns, int32_t arrive, int32_t* status) {
+  if (!status || limit_ns < 0 || limit_ns > 2000000000LL) return SL_ERR_ARG;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
+  int rc = SL_OK;
+  int v = SL_ERR_CUDA;
+  k_bounded_wait<<<1, 32, 0, st>>>((unsigned long long)limit_ns, arrive ? 1 : 0);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess ||
+      cudaMemcpyFromSymbol(&v, g_wait_status, sizeof(int)) != cudaSuccess)
+    rc = SL_ERR_CUDA;
+  cudaStreamDestroy(st);
+  if (rc == SL_OK) *status = v;
+  return rc;
+}
 
 extern "C" int sl_df_fma_rate(int32_t iters, double* flop_per_s, double* ms) {
   if (!flop_per_s || iters < 1 || iters > (1 << 20)) return SL_ERR_ARG;

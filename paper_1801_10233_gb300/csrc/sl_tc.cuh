@@ -89,16 +89,25 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for the given phase parity for at most about one second; returns 0 if
-// the time ran out (the caller reports SL_ERR_TIMEOUT).
-__device__ __forceinline__ int mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the given phase parity for at most limit_ns nanoseconds of the
+// global timer; returns 0 if the time ran out (the caller reports
+// SL_ERR_TIMEOUT).
+__device__ __forceinline__ int mbar_wait_ns(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_test_wait(bar, parity)) return 1;
   const uint64_t t0 = global_ns();
-  while (global_ns() - t0 < 1000000000ull) {
+  while (global_ns() - t0 < limit_ns) {
     if (mbar_test_wait(bar, parity)) return 1;
     __nanosleep(64);
   }
   return mbar_test_wait(bar, parity);
+}
+// The kernels' waits: at most about one second.
+__device__ __forceinline__ int mbar_wait(uint32_t bar, uint32_t parity) {
+  return mbar_wait_ns(bar, parity, 1000000000ull);
+}
+// One thread arrives on the barrier (completes a phase of count 1).
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
 }
 
 // 16 consecutive float32 columns of this thread's tensor-memory lane (warp w
