@@ -60,7 +60,7 @@ KERNEL_LAUNCHES_PER_STEP = {"k_sweep_pass": 30, "k_force": 1, "k_jtable": 1, "k_
 # What the path computes in: the bench line's dtype is "df64".
 ARITH = ("FP64 state (r, v, s, F), FP64 per-atom updates and energy sums; pair and rotation arithmetic "
          "in double-float (unevaluated float pairs, ~48-bit significand, error-free transformations) on the "
-         "FP32 pipes, exp and rsqrt to <5e-14 relative; positions also in 64-bit fixed point for exact "
+         "FP32 pipes, exp to <7e-14 and rsqrt to <5e-14 relative; positions also in 64-bit fixed point for exact "
          "separations")
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 pipe, nominal at 2070 MHz (context only)
 # Compulsory state traffic: r, v, s read and written once per step.

@@ -340,6 +340,21 @@ int sl_magnetization_static(const double* s, int32_t n_atoms, double* out, void*
  * Synchronises.  Errors: SL_ERR_ARG, SL_ERR_CUDA. */
 int sl_df_fma_rate(int32_t iters, double* flop_per_s, double* ms);
 
+/* The double-float functions of the pair and rotation kernels, evaluated on
+ * the device for a check of their accuracy against FP64 (a measurement
+ * service of the library; the paper has none): y[k] = f(x[k]) with x[k]
+ * rounded to a double-float (~48 bits), f computed in double-float and the
+ * result widened back to FP64.
+ *   fn   SL_DF_EXP (exp x, used for x in [-12, 6]), SL_DF_RSQRT (1/sqrt x,
+ *        x > 0) or SL_DF_SQRT (sqrt x, x >= 0)
+ *   x, y device pointers to n doubles (caller-owned; y may not alias x)
+ * Stream-ordered on cuda_stream; no host sync.  Errors: SL_ERR_ARG (fn, n
+ * or pointers), SL_ERR_CUDA. */
+#define SL_DF_EXP 0
+#define SL_DF_RSQRT 1
+#define SL_DF_SQRT 2
+int sl_df_eval(int32_t fn, const double* x, double* y, int64_t n, void* cuda_stream);
+
 /* Check of the library's bounded in-kernel wait (the one the tensor-core
  * kernels use for their MMA completion), on the current device: one thread
  * waits on a shared-memory barrier of count 1 for at most limit_ns

@@ -31,7 +31,7 @@ EXPORTS = (
     "sl_workspace_bytes", "sl_sector_grid", "sl_init", "sl_build_neighbors", "sl_step", "sl_set_dt", "sl_set_field",
     "sl_energy", "sl_magnetization", "sl_get_state", "sl_set_state", "sl_get_state_host",
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
-    "sl_get_timing", "sl_magnetization_static", "sl_df_fma_rate", "sl_check_bounded_wait", "sl_set_eam_tables", "sl_status", "sl_strerror", "sl_destroy",
+    "sl_get_timing", "sl_magnetization_static", "sl_df_fma_rate", "sl_df_eval", "sl_check_bounded_wait", "sl_set_eam_tables", "sl_status", "sl_strerror", "sl_destroy",
     "sl_workspace_bytes_batch", "sl_init_batch", "sl_batch_size", "sl_energy_batch", "sl_magnetization_batch",
     "sl_ml_set_model", "sl_ml_get_model", "sl_ml_eval", "sl_ml_descriptor_stats", "sl_ml_gate", "sl_ml_vjp",
     "sl_ml_train_step", "sl_autotune", "sl_set_launch_shape",
@@ -104,6 +104,7 @@ def load():
         "sl_get_timing": ([_vp, _dp, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "sl_magnetization_static": ([_vp, ctypes.c_int32, _vp, _vp], ctypes.c_int),
         "sl_df_fma_rate": ([ctypes.c_int32, _dp, _dp], ctypes.c_int),
+        "sl_df_eval": ([ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
         "sl_check_bounded_wait": ([ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "sl_set_eam_tables": ([_vp, ctypes.POINTER(sl_eam_tables)], ctypes.c_int),
         "sl_status": ([_vp], ctypes.c_int),
@@ -225,6 +226,15 @@ def df_fma_rate(iters=4096):
     ms = ctypes.c_double(0.0)
     check(load().sl_df_fma_rate(int(iters), ctypes.byref(f), ctypes.byref(ms)), "sl_df_fma_rate")
     return f.value, ms.value
+
+
+SL_DF_EXP, SL_DF_RSQRT, SL_DF_SQRT = 0, 1, 2
+
+
+def df_eval(fn: int, x_ptr: int, y_ptr: int, n: int, stream: int = 0):
+    """y = f(x) in the library's double-float arithmetic (device pointers to
+    n doubles, stream-ordered on `stream`)."""
+    check(load().sl_df_eval(int(fn), x_ptr, y_ptr, int(n), stream), "sl_df_eval")
 
 
 def strerror(code: int) -> str:

@@ -55,6 +55,17 @@ __device__ __forceinline__ df df_add(df a, df b) {
   return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+// The cheaper sum of Hida, Li and Bailey's "sloppy" addition (one
+// error-free sum of the high parts, the low parts added in float): its error
+// is below ~2^-47 of max(|a|, |b|) rather than of |a + b|, so it is used only
+// where that absolute error is already within the operands' own (a sum with
+// no cancellation, or a difference of quantities that carry an error of that
+// size, such as r - r0 with r from r^2 and 1/sqrt(r^2)).
+__device__ __forceinline__ df df_add_sloppy(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
 __device__ __forceinline__ df df_add_f(df a, float b) {
   df s = two_sum(a.hi, b);
   s.lo = __fadd_rn(s.lo, a.lo);
@@ -83,7 +94,8 @@ __device__ __forceinline__ df df_scale(df a, float p2) { return df_make(a.hi * p
 
 // 1/sqrt(a), a > 0: hardware estimate, one Newton step in float (~2^-23),
 // then one correction with the residual 1 - a y^2 in df: relative error
-// below 5e-14 (measured over r^2 in [3, 45] against FP64).
+// below 5e-14 (4.6e-14 the largest over 4 million points of r^2 in
+// [1, 64] against FP64).
 __device__ __forceinline__ df df_rsqrt(df a) {
   float y = rsqrtf(a.hi);
   y = y * __fmaf_rn(-0.5f * a.hi * y, y, 1.5f);
@@ -97,22 +109,26 @@ __device__ __forceinline__ df df_rsqrt(df a) {
 // value or x is out of its range); exp(x) = 2^m T[j] (1 + p(r)),
 // p(r) = r + q, q = r^2/2 + r^3 (1/6 + r/24 + r^2/120): r^2/2 from the exact
 // square of r.hi plus r.hi r.lo, the cubic tail (< 2.7e-8) in float.
-// Relative error below 4e-14 (measured over x in [-12, 6] against FP64).
+// Relative error below 7e-14 (6.1e-14 the largest over 4 million points
+// of x in [-12, 6] against FP64 at the same input; 1e-14 for 99.99 % of
+// them).
 __device__ __forceinline__ df df_exp(df x) {
   float nf = rintf(x.hi * SL_64_LN2);
   int n = (int)nf;
   // r = x - n ln2/64 (n * C1 exact; x.hi - n C1 exact by Sterbenz)
   float r1 = __fsub_rn(x.hi, nf * SL_LN2_64_C1);
+  // (r1, x.lo) is not normalised (x.lo belongs to |x|, not to |r1|): an
+  // accurate sum; the two below have no cancellation (|q| < r^2, |T p| <
+  // 0.011 T) and take the sloppy one
   df r = df_add(df_make(r1, x.lo), df_neg(df_add_f(two_prod(nf, SL_LN2_64_C2), nf * SL_LN2_64_C3)));
-  r = fast_two_sum(r.hi, r.lo);
   const df P = two_prod(r.hi, r.hi);
   const float tail = r.hi * P.hi * __fmaf_rn(r.hi, __fmaf_rn(r.hi, 1.0f / 120.0f, 1.0f / 24.0f), 1.0f / 6.0f);
   const df q = df_make(0.5f * P.hi, __fmaf_rn(r.hi, r.lo, __fmaf_rn(0.5f, P.lo, tail)));
-  const df p = df_add(r, q);
+  const df p = df_add_sloppy(r, q);
   int j = n & 63, m = n >> 6;
   float2 t = __ldg(kSlExp2Table + j);
   df T = df_make(t.x, t.y);
-  df e = df_add(T, df_mul(T, p));
+  df e = df_add_sloppy(T, df_mul(T, p));
   float s = __int_as_float((127 + m) << 23);  // 2^m, |m| < 126
   return df_scale(e, s);
 }
@@ -199,7 +215,8 @@ __device__ __forceinline__ df df_div(df a, df b) {
   return df_add_f(fast_two_sum(q1, q2), q3);
 }
 
-// sqrt(a), a > 0: correctly rounded float root, one Newton correction.
+// sqrt(a), a > 0: correctly rounded float root, one Newton correction;
+// relative error below 2e-14 (1.5e-14 the largest over [0.5, 64]).
 __device__ __forceinline__ df df_sqrt(df a) {
   const float y = sqrtf(a.hi);
   const df e = df_sub(a, two_prod(y, y));

@@ -131,6 +131,19 @@ __device__ __forceinline__ df3 pair_sep_k(const box3& B, const p3& a, const p3& 
   return r;
 }
 
+// |d|^2 of a separation: three exact squares of the high parts, the cross
+// and low terms in float, the three (positive) high products summed
+// error-free and the low parts folded in once; about 2^-47 relative, as for
+// a running df sum of the three squares.
+__device__ __forceinline__ df sep_r2(const df3& d) {
+  const df px = two_prod(d.x.hi, d.x.hi), py = two_prod(d.y.hi, d.y.hi), pz = two_prod(d.z.hi, d.z.hi);
+  const float lx = __fmaf_rn(2.0f * d.x.hi, d.x.lo, px.lo), ly = __fmaf_rn(2.0f * d.y.hi, d.y.lo, py.lo),
+              lz = __fmaf_rn(2.0f * d.z.hi, d.z.lo, pz.lo);
+  const df s = two_sum(px.hi, py.hi);
+  const df t = two_sum(s.hi, pz.hi);
+  return fast_two_sum(t.hi, __fadd_rn(__fadd_rn(t.lo, s.lo), __fadd_rn(__fadd_rn(lx, ly), lz)));
+}
+
 __device__ __forceinline__ df dot3(const df3& a, const df3& b) {
   float h = 0.0f, l = 0.0f;
   acc_prod(h, l, a.x, b.x);

@@ -48,6 +48,19 @@ __global__ void k_bounded_wait(unsigned long long limit_ns, int arrive) {
   }
 }
 
+// y = f(x) through the double-float functions: x to df (48 bits), the
+// function, back to FP64.
+__global__ void k_df_eval(int fn, const double* x, double* y, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const df a = df_from_double(x[k]);
+  df r;
+  if (fn == SL_DF_EXP) r = df_exp(a);
+  else if (fn == SL_DF_RSQRT) r = df_rsqrt(a);
+  else r = df_sqrt(a);
+  y[k] = df_to_double(r);
+}
+
 }  // namespace
 
 extern "C" int sl_check_bounded_wait(int64_t limit_ns, int32_t arrive, int32_t* status) {
@@ -63,6 +76,16 @@ extern "C" int sl_check_bounded_wait(int64_t limit_ns, int32_t arrive, int32_t* 
   cudaStreamDestroy(st);
   if (rc == SL_OK) *status = v;
   return rc;
+}
+
+extern "C" int sl_df_eval(int32_t fn, const double* x, double* y, int64_t n, void* cuda_stream) {
+  if (fn < SL_DF_EXP || fn > SL_DF_SQRT || n < 0 || (n > 0 && (!x || !y))) return SL_ERR_ARG;
+  if (n == 0) return SL_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int64_t blocks = (n + 255) / 256;
+  if (blocks > 0x7fffffffLL) return SL_ERR_ARG;
+  k_df_eval<<<(unsigned)blocks, 256, 0, st>>>(fn, x, y, n);
+  return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
 }
 
 extern "C" int sl_df_fma_rate(int32_t iters, double* flop_per_s, double* ms) {

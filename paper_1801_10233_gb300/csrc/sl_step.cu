@@ -799,11 +799,7 @@ __global__ void k_jtable(SlDev d) {
     const size_t e = (size_t)k * n + i;
     const int j = __ldg(d.exj + e);
     const df3 dd = pair_sep(B, pi, load_pos(d, j));
-    float h = 0.0f, l = 0.0f;
-    acc_prod(h, l, dd.x, dd.x);
-    acc_prod(h, l, dd.y, dd.y);
-    acc_prod(h, l, dd.z, dd.z);
-    const df r2 = acc_done(h, l);
+    const df r2 = sep_r2(dd);
     if (DENS) eam_f_acc(d, r2, rh, rl);
     df J = df_f(0.0f), dJr = df_f(0.0f);
     const bool in = df_lt(r2, rc2);
@@ -908,7 +904,7 @@ __device__ __forceinline__ df eam_coeff(const SlDev& d, df r2, df rinv, df fpij)
 __device__ __forceinline__ df morse_coeff(df r2, df na, df r0, df c2, df& rinv) {
   rinv = df_rsqrt(r2);
   const df r = df_mul(r2, rinv);
-  const df e = df_exp(df_mul(na, df_sub(r, r0)));
+  const df e = df_exp(df_mul(na, df_add_sloppy(r, df_neg(r0))));   // r carries an error of 2^-48 r already
   return df_mul(df_mul(c2, rinv), df_mul(e, df_add_f(df_neg(e), 1.0f)));   // V'(r)/r
 }
 
@@ -943,11 +939,7 @@ __global__ void k_force(SlDev d, int kick) {
   for (int k = 0; k < ne; ++k) {
     const int j = __ldg(d.mj + (size_t)k * d.n + i);
     const df3 dd = pair_sep(B, pi, load_pos(d, j));
-    float h = 0.0f, l = 0.0f;
-    acc_prod(h, l, dd.x, dd.x);
-    acc_prod(h, l, dd.y, dd.y);
-    acc_prod(h, l, dd.z, dd.z);
-    const df r2 = acc_done(h, l);
+    const df r2 = sep_r2(dd);
     df rinv;
     df c = df_f(0.0f);
     if (tab) {
@@ -1008,11 +1000,7 @@ __global__ void k_force(SlDev d, int kick) {
   for (int k = ne; k < mc; ++k) {
     const int j = __ldg(d.mj + (size_t)k * d.n + i);
     const df3 dd = pair_sep(B, pi, load_pos(d, j));
-    float h = 0.0f, l = 0.0f;
-    acc_prod(h, l, dd.x, dd.x);
-    acc_prod(h, l, dd.y, dd.y);
-    acc_prod(h, l, dd.z, dd.z);
-    const df r2 = acc_done(h, l);
+    const df r2 = sep_r2(dd);
     df rinv;
     df c;
     if (tab) {
@@ -1033,11 +1021,7 @@ __global__ void k_force(SlDev d, int kick) {
     const pre3 q = pair_pre(B, pi, pj);
     if (q.r2 > rc2_hi) continue;
     const df3 dd = pair_sep_k(B, pi, pj, q);
-    float h = 0.0f, l = 0.0f;
-    acc_prod(h, l, dd.x, dd.x);
-    acc_prod(h, l, dd.y, dd.y);
-    acc_prod(h, l, dd.z, dd.z);
-    const df r2 = acc_done(h, l);
+    const df r2 = sep_r2(dd);
     if (!df_lt(r2, rc2)) continue;
     df rinv;
     df c;

@@ -10,7 +10,8 @@ of the total energy per atom, |M| and the spin temperature must agree within
 their combined blocked standard errors.  Both runs must also keep every
 |s_i| = 1 to 1e-14 (Sec. 3: the rotations preserve the norm, no
 renormalisation; over 10,000 steps the random walk of the FP64 rounding of
-the updates allows 1e-13) and drift by less than 1e-6 eV/atom/ps (the
+the updates allows 1e-13; over 1,000 steps 1e-14 for 2,000 spins, 3e-14 for
+524,288) and drift by less than 1e-6 eV/atom/ps (the
 least-squares slope of E_tot/N against time).
 """
 import math
@@ -25,7 +26,6 @@ pytestmark = pytest.mark.gpu
 from paper_1801_10233_gb300 import inputs  # noqa: E402
 
 DRIFT_MAX = 1e-6       # eV/atom/ps
-NORM_TOL = 1e-14
 NSIGMA = 4.0
 
 
@@ -108,13 +108,17 @@ def test_long_run_statistics_match_the_oracle(System):
 
 def test_long_run_invariants_64cubed(System):
     """The 64^3-cell workload (524,288 atoms) over 1,000 steps: |s_i| = 1 to
-    1e-14, total momentum conserved, energy drift below 1e-6 eV/atom/ps."""
+    3e-14, total momentum conserved, energy drift below 1e-6 eV/atom/ps.
+    The rotations preserve the norm (Sec. 3) up to the FP64 rounding of each
+    update s += ds, a random walk of ~6e-17 per rotation: after 4,000
+    rotations ~3.8e-15 per spin, and the largest of 524,288 spins about five
+    times that (1.0e-14 measured), hence the bar."""
     p, r, v, s = inputs.workload("fe_bcc_64x64x64_nve")
     n, steps, every = p["n_atoms"], 1000, 100
     gpu = System(p, r, v, s)
     P0 = v.sum(axis=0)
     x = _series(gpu, n, steps, every)
     _, v1, s1 = (t.cpu().numpy() for t in gpu.state())
-    assert np.abs(np.linalg.norm(s1, axis=1) - 1.0).max() <= NORM_TOL
+    assert np.abs(np.linalg.norm(s1, axis=1) - 1.0).max() <= 3e-14
     assert np.abs(v1.sum(axis=0) - P0).max() <= 1e-7
     assert abs(_drift(x[:, 0], p["dt_ps"], every)) <= DRIFT_MAX
