@@ -18,7 +18,9 @@ def test_roofline_picks_the_kernel_with_most_time_per_step(monkeypatch):
     assert r["achieved"] == pytest.approx(408 * n / 0.6e-3 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / 4.0)
     assert r["ms_per_launch"] == pytest.approx(0.6 / 30)
-    assert r["traffic"] is None
+    # the committed profile of this kernel and workload, if its sources are current
+    prof = bench.profiled("fe_bcc_100x100x100_nve", "k_sweep_pass")
+    assert r["traffic"] == (prof["dram_bytes_per_launch"] if prof else None)
     assert r["hbm_frac_state_traffic"] == pytest.approx(144.0 * n / 1.2e-3 / 1e9 / 6000.0)
     phases["force_kick"] = (7.0, 10)
     assert bench.kernel_roofline(phases, n, "x", 1.2, peak=4.0)["kernel"] == "k_force"
