@@ -332,27 +332,48 @@ __device__ __forceinline__ void rot_coeffs(df u, int cayley, df& A, df& B) {
   }
 }
 
+// a0 b0 + a1 b1 + a2 b2 and a0 b0 - a1 b1 with the products formed side by
+// side (exact high products, cross and low terms in float), the high parts
+// combined by error-free sums and the low parts folded in once: the same
+// accuracy as a running sum (about 2^-47 of the largest term, absolute) in
+// far fewer dependent steps, for the single-spin propagator, whose chain of
+// dependent rotations sets the colour pass's latency.
+__device__ __forceinline__ float prod_lo(df a, df b, float plo) {
+  return __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, plo));
+}
+__device__ __forceinline__ df sum3_prod(df a0, df b0, df a1, df b1, df a2, df b2) {
+  const df p0 = two_prod(a0.hi, b0.hi), p1 = two_prod(a1.hi, b1.hi), p2 = two_prod(a2.hi, b2.hi);
+  const float l = __fadd_rn(__fadd_rn(prod_lo(a0, b0, p0.lo), prod_lo(a1, b1, p1.lo)), prod_lo(a2, b2, p2.lo));
+  const df s = two_sum(p0.hi, p1.hi);
+  const df t = two_sum(s.hi, p2.hi);
+  return fast_two_sum(t.hi, __fadd_rn(__fadd_rn(t.lo, s.lo), l));
+}
+__device__ __forceinline__ df diff2_prod(df a0, df b0, df a1, df b1) {
+  const df p0 = two_prod(a0.hi, b0.hi), p1 = two_prod(a1.hi, b1.hi);
+  const float l = __fsub_rn(prod_lo(a0, b0, p0.lo), prod_lo(a1, b1, p1.lo));
+  const df s = two_sum(p0.hi, -p1.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, l));
+}
+
 __device__ __forceinline__ df3 rot_increment(const df3& w, const df3& s, df tau, int cayley) {
-  float h = 0.0f, l = 0.0f;
-  acc_prod(h, l, w.x, w.x);
-  acc_prod(h, l, w.y, w.y);
-  acc_prod(h, l, w.z, w.z);
-  df w2 = acc_done(h, l);
-  df tau2 = df_sqr(tau);
-  df u = df_mul(w2, tau2);
+  const df w2 = sum3_prod(w.x, w.x, w.y, w.y, w.z, w.z);
+  const df tau2 = df_sqr(tau);
+  const df u = df_mul(w2, tau2);
   df A, B;
   rot_coeffs(u, cayley, A, B);
-  df uB = df_mul(u, B);
-  df tA = df_mul(tau, A);
-  df tBws = df_mul(df_mul(tau2, B), dot3(w, s));
-  df3 c = cross3(w, s);
+  // w.s and w x s do not depend on A, B: they overlap rot_coeffs
+  const df ws = sum3_prod(w.x, s.x, w.y, s.y, w.z, s.z);
+  df3 c;
+  c.x = diff2_prod(w.y, s.z, w.z, s.y);
+  c.y = diff2_prod(w.z, s.x, w.x, s.z);
+  c.z = diff2_prod(w.x, s.y, w.y, s.x);
+  const df nuB = df_neg(df_mul(u, B));
+  const df tA = df_mul(tau, A);
+  const df tBws = df_mul(df_mul(tau2, B), ws);
   df3 inc;
-  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.x); acc_prod(h, l, tA, c.x); acc_prod(h, l, tBws, w.x);
-  inc.x = acc_done(h, l);
-  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.y); acc_prod(h, l, tA, c.y); acc_prod(h, l, tBws, w.y);
-  inc.y = acc_done(h, l);
-  h = l = 0.0f; acc_prod(h, l, df_neg(uB), s.z); acc_prod(h, l, tA, c.z); acc_prod(h, l, tBws, w.z);
-  inc.z = acc_done(h, l);
+  inc.x = sum3_prod(nuB, s.x, tA, c.x, tBws, w.x);
+  inc.y = sum3_prod(nuB, s.y, tA, c.y, tBws, w.y);
+  inc.z = sum3_prod(nuB, s.z, tA, c.z, tBws, w.z);
   return inc;
 }
 
