@@ -77,24 +77,36 @@ __device__ __forceinline__ long long fx_diff(long long b, long long a, long long
   return D;
 }
 
+// m 2^e exactly for an integer 0 <= m < 2^23 (E = the float bits of
+// 2^(23+e)): the float 2^(23+e) + m 2^e has m in its low mantissa bits, so
+// one subtraction of 2^(23+e) gives the scaled piece without a conversion
+// or a multiply.
+__device__ __forceinline__ float u23_scaled(unsigned m, unsigned E, float two23e) {
+  return __fsub_rn(__uint_as_float(E | m), two23e);
+}
+static_assert(SL_FX_BITS == 48, "the piece scales below are those of F = 48");
 // D 2^-F (|D| < 2^61) as df: D = A 2^40 + B 2^20 + C with |A| < 2^21 and
-// B, C < 2^20, each exact in a float; two error-free additions round the sum.
+// B, C < 2^20, each piece exact in a float (A 2^-8 from A + 2^21 under the
+// exponent of 2^15, B 2^-28 under 2^-5, C 2^-48 under 2^-25); two error-free
+// additions round the sum.
 __device__ __forceinline__ df fx_to_df(long long D, const box3& B) {
+  (void)B;
   const int A = (int)(D >> 40);
   const unsigned Bm = (unsigned)(D >> 20) & 0xFFFFFu, Cm = (unsigned)D & 0xFFFFFu;
-  const float fa = __fsub_rn(u23_to_float((unsigned)(A + (1 << 21))), 2097152.0f) * B.s40;
-  const float fb = u23_to_float(Bm) * B.s20;
-  const float fc = u23_to_float(Cm) * B.s0;
+  const float fa = u23_scaled((unsigned)(A + (1 << 21)), 0x47000000u, 40960.0f);   // 2^15 + 2^21 2^-8
+  const float fb = u23_scaled(Bm, 0x3D000000u, 0.03125f);                            // 2^-5
+  const float fc = u23_scaled(Cm, 0x33000000u, 2.98023223876953125e-8f);             // 2^-25
   const df s = fast_two_sum(fa, fb);          // |fa| >= |fb| unless A = 0
   const df t = two_sum(s.hi, fc);
   return fast_two_sum(t.hi, __fadd_rn(t.lo, s.lo));
 }
 // The same value to about float precision (the cutoff pre-checks).
 __device__ __forceinline__ float fx_to_float(long long D, const box3& B) {
+  (void)B;
   const int A = (int)(D >> 40);
   const unsigned Bm = (unsigned)(D >> 20) & 0xFFFFFu;
-  return __fmaf_rn(__fsub_rn(u23_to_float((unsigned)(A + (1 << 21))), 2097152.0f), B.s40,
-                   u23_to_float(Bm) * B.s20);
+  return __fadd_rn(u23_scaled((unsigned)(A + (1 << 21)), 0x47000000u, 40960.0f),
+                   u23_scaled(Bm, 0x3D000000u, 0.03125f));
 }
 
 __device__ __forceinline__ df3 pair_sep(const box3& B, const p3& a, const p3& b) {
