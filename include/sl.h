@@ -287,11 +287,7 @@ int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
  * in-sector spins (32x192 (variant 0, the default), 32x256, 16x128, 16x128 with
  * registers for 1,024 resident threads per SM, 8x128), variants 5-9 (plain Hamiltonian; with the spin-orbit terms they
  * run as 0-4) a pass that copies every neighbour's spin into shared memory
- * asynchronously first (16x128, 8x64, 32x256, 8x96, 4x64), variants 10
- * and 11 the pipelined pass's 16x128 (1,024 threads per SM) and 8x128 shapes
- * run as one persistent launch per half-op, whose blocks take (pass, block)
- * items in order and wait (one second at most; SL_ERR_TIMEOUT beyond) only
- * for the previous pass's blocks of the neighbouring super-cells; and the
+ * asynchronously first (16x128, 8x64, 32x256, 8x96, 4x64); and the
  * per-atom kernels (kick, drift, exchange table, forces) take 64, 128 (the
  * default) or 256 threads per block.  The shape changes only how the work is
  * grouped into blocks, never the arithmetic of a spin or an atom: results are
@@ -306,7 +302,7 @@ int sl_get_timing(sl_ctx* ctx, double ms[8], int64_t count[8]);
  * block of the chosen variant, 0, 0.  Synchronises.
  * Errors: SL_ERR_ARG, SL_ERR_WORKSPACE (scratch too small), SL_ERR_CUDA.
  * sl_set_launch_shape sets a shape directly (SL_ERR_ARG for unknown ones). */
-#define SL_SWEEP_VARIANTS 12
+#define SL_SWEEP_VARIANTS 10
 int sl_autotune(sl_ctx* ctx, void* scratch, size_t scratch_bytes, int32_t steps, int64_t out[8]);
 int sl_set_launch_shape(sl_ctx* ctx, int32_t sweep_variant, int32_t block);
 
@@ -370,16 +366,6 @@ int sl_df_eval(int32_t fn, const double* x, double* y, int64_t n, void* cuda_str
  * error status, leaving the GPU usable, instead of hanging it.
  * Synchronises.  Errors: SL_ERR_ARG, SL_ERR_CUDA. */
 int sl_check_bounded_wait(int64_t limit_ns, int32_t arrive, int32_t* status);
-
-/* Check of the dataflow colour pass's wait (sweep variants 10 and 11, whose
- * items wait for the done flags of the previous pass's neighbouring blocks
- * with a one-second bound), on the current device: one warp waits, bounded
- * by limit_ns (0 .. 2e9), for 40 flags that are all set (set = 1) or that
- * nothing sets (set = 0), on a private stream.
- * *status (host) receives SL_OK or SL_ERR_TIMEOUT, the code the pass reports
- * (sticky status) when a wait runs out; the GPU stays usable.
- * Synchronises.  Errors: SL_ERR_ARG, SL_ERR_CUDA. */
-int sl_check_sweep_wait(int64_t limit_ns, int32_t set, int32_t* status);
 
 /* ------------------------------------------------------------------------
  * Learned per-atom Hamiltonian.  The paper has no learned model: this is an

@@ -31,7 +31,7 @@ EXPORTS = (
     "sl_workspace_bytes", "sl_sector_grid", "sl_init", "sl_build_neighbors", "sl_step", "sl_set_dt", "sl_set_field",
     "sl_energy", "sl_magnetization", "sl_get_state", "sl_set_state", "sl_get_state_host",
     "sl_set_state_host", "sl_get_forces", "sl_get_omega", "sl_get_order", "sl_counters", "sl_set_timing",
-    "sl_get_timing", "sl_magnetization_static", "sl_df_fma_rate", "sl_df_eval", "sl_check_bounded_wait", "sl_check_sweep_wait", "sl_set_eam_tables", "sl_status", "sl_strerror", "sl_destroy",
+    "sl_get_timing", "sl_magnetization_static", "sl_df_fma_rate", "sl_df_eval", "sl_check_bounded_wait", "sl_set_eam_tables", "sl_status", "sl_strerror", "sl_destroy",
     "sl_workspace_bytes_batch", "sl_init_batch", "sl_batch_size", "sl_energy_batch", "sl_magnetization_batch",
     "sl_ml_set_model", "sl_ml_get_model", "sl_ml_eval", "sl_ml_descriptor_stats", "sl_ml_gate", "sl_ml_vjp",
     "sl_ml_train_step", "sl_autotune", "sl_set_launch_shape",
@@ -106,7 +106,6 @@ def load():
         "sl_df_fma_rate": ([ctypes.c_int32, _dp, _dp], ctypes.c_int),
         "sl_df_eval": ([ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
         "sl_check_bounded_wait": ([ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
-        "sl_check_sweep_wait": ([ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "sl_set_eam_tables": ([_vp, ctypes.POINTER(sl_eam_tables)], ctypes.c_int),
         "sl_status": ([_vp], ctypes.c_int),
         "sl_workspace_bytes_batch": ([P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),

@@ -198,43 +198,6 @@ void fill_noise(std::vector<SlRep>& reps, const sl_params* ps, double dt) {
   }
 }
 
-// Neighbour blocks of the dataflow colour pass: blocks of `spb` consecutive
-// super-cells (2x2x2 sectors, one per colour) in the colour-major sector
-// order, across replicas; for each block, the sorted blocks holding a
-// super-cell within one step (periodic in its replica) of any of its own,
-// itself included.  A sector's exchange neighbours lie in the sectors one
-// step away (sector edges are at least the exchange reach), so those blocks
-// hold every spin a block's pass reads.
-void build_sweep_nb(const std::vector<SlRep>& reps, int s8, int spb, std::vector<int>& start, std::vector<int>& list) {
-  const int nblk = (s8 + spb - 1) / spb;
-  start.assign((size_t)nblk + 1, 0);
-  list.clear();
-  std::vector<int> mark((size_t)nblk, -1);
-  size_t r = 0;
-  for (int b = 0; b < nblk; ++b) {
-    start[b] = (int)list.size();
-    for (int q = b * spb; q < std::min(s8, (b + 1) * spb); ++q) {
-      while (r + 1 < reps.size() && reps[r + 1].sec8_off <= q) ++r;
-      const SlRep& R = reps[r];
-      const int hxn = R.nx / 2, hyn = R.ny / 2, hzn = R.nz / 2;
-      const int loc = q - R.sec8_off;
-      const int hx = loc % hxn, hy = (loc / hxn) % hyn, hz = loc / (hxn * hyn);
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int x = (hx + dx + hxn) % hxn, y = (hy + dy + hyn) % hyn, z = (hz + dz + hzn) % hzn;
-            const int b2 = (R.sec8_off + x + hxn * (y + hyn * z)) / spb;
-            if (mark[b2] != b) {
-              mark[b2] = b;
-              list.push_back(b2);
-            }
-          }
-    }
-    std::sort(list.begin() + start[b], list.end());
-  }
-  start[nblk] = (int)list.size();
-}
-
 // Fill d's scalars, the replica table and (if base != NULL) d's pointers;
 // returns the workspace bytes needed.
 
@@ -380,16 +343,6 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
   size_t o_xb = L.take<float2>(3 * nn), o_eb2 = L.take<float2>(3 * nn);
   size_t o_p0 = L.take<float2>(3 * nn), o_p1 = L.take<float2>(3 * nn);
   size_t o_mj = L.take<int>(nn * d.max_m), o_mn = L.take<int>(nn), o_mnc = L.take<int>(nn);
-  // the dataflow colour pass: neighbour blocks for 16 and 8 sectors per block,
-  // ticket, abort word and done flags
-  std::vector<int> nb_start[2], nb_list[2];
-  size_t o_nbs[2], o_nbl[2];
-  for (int k = 0; k < 2; ++k) {
-    build_sweep_nb(reps, sec8, k == 0 ? 16 : 8, nb_start[k], nb_list[k]);
-    o_nbs[k] = L.take<int>(nb_start[k].size());
-    o_nbl[k] = L.take<int>(nb_list[k].size());
-  }
-  size_t o_swsync = L.take<int>(2 + (size_t)15 * ((sec8 + 7) / 8));
   size_t o_oa = L.take<double>(nn * SL_NOBS), o_or = L.take<double>((size_t)nrep * SL_NOBS);
   size_t o_reps = L.take<SlRep>((size_t)nrep);
   size_t o_stage = L.take<double>(nn * 9);
@@ -447,11 +400,6 @@ size_t plan(const sl_params* ps, int nrep, SlDev& d, std::vector<SlRep>& reps, c
     d.xbuf = (float2*)(base + o_xb); d.ebuf2 = (float2*)(base + o_eb2);
     d.hpart[0] = (float2*)(base + o_p0); d.hpart[1] = (float2*)(base + o_p1);
     d.mj = (int*)(base + o_mj); d.mn = (int*)(base + o_mn); d.mnc = (int*)(base + o_mnc);
-    for (int k = 0; k < 2; ++k) {
-      d.swnb_start[k] = (const int*)(base + o_nbs[k]);
-      d.swnb_list[k] = (const int*)(base + o_nbl[k]);
-    }
-    d.sw_sync = (int*)(base + o_swsync);
     d.obs_atom = (double*)(base + o_oa); d.obs_rep = (double*)(base + o_or);
     d.reps = (const SlRep*)(base + o_reps);
     d.stage = (double*)(base + o_stage);
@@ -653,7 +601,6 @@ int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, 
     return SL_ERR_CUDA;
   }
   c->d.rb_cap = 8 * nsm;
-  c->d.nsm = nsm;
   if (sl_prepare_kernels() != SL_OK || (c->d.ham == SL_HAM_LEARNED && sl_ml_prepare_kernels() != SL_OK)) {
     sl_destroy(c);
     return SL_ERR_CUDA;
@@ -661,13 +608,6 @@ int sl_init_batch(const sl_params* params, int32_t n_replicas, const double* r, 
   cudaMemsetAsync(c->d.ctrl, 0, sizeof(SlCtrl), c->stream);
   cudaMemcpyAsync((void*)c->d.reps, c->reps.data(), sizeof(SlRep) * n_replicas, cudaMemcpyHostToDevice,
                   c->stream);
-  for (int k = 0; k < 2; ++k) {
-    // pageable host sources: each copy has read them when it returns
-    std::vector<int> st, li;
-    build_sweep_nb(c->reps, c->d.s8, k == 0 ? 16 : 8, st, li);
-    cudaMemcpyAsync((void*)c->d.swnb_start[k], st.data(), sizeof(int) * st.size(), cudaMemcpyHostToDevice, c->stream);
-    cudaMemcpyAsync((void*)c->d.swnb_list[k], li.data(), sizeof(int) * li.size(), cudaMemcpyHostToDevice, c->stream);
-  }
   k_load<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d, r, v, s, 1);
   k_check<<<grid_for(c->d.n), SL_BLOCK, 0, c->stream>>>(c->d);
   sl_launch_force_rebuild_flag(c->d, c->stream);

@@ -15,9 +15,8 @@
 #define SL_BLOCK 128
 // Sectors per block of the colour-pass tile shapes (threads: 192, 256, 128, 128, 128).
 // Variants 0-4: the pipelined pass; 5-9: the asynchronous-gather pass of the
-// plain Hamiltonian (run as 0-4 with the spin-orbit terms); 10, 11: the
-// pipelined pass of variants 3 and 4 as one persistent launch per half-op.
-static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8, 16, 8, 32, 8, 4, 16, 8};
+// plain Hamiltonian (run as 0-4 with the spin-orbit terms).
+static const int kSlSweepSPB[SL_SWEEP_VARIANTS] = {32, 32, 16, 16, 8, 16, 8, 32, 8, 4};
 #define SL_MAX_EX_CAP 64   // largest accepted max_ex_neighbors
 // Fixed-point positions X = rint(r 2^48), one scale for every context so a
 // replica's trajectory does not depend on the batch it is in: positions
@@ -115,14 +114,6 @@ struct SlDev {
   int tune_sweep;           // colour-pass tile shape variant (0 .. SL_SWEEP_VARIANTS-1)
   int tune_block;           // threads per block of the per-atom kernels (0: SL_BLOCK)
   int rb_cap;               // most blocks of a rebuild kernel (grid-stride loops)
-  int nsm;                  // SMs of the device
-  // persistent colour pass (sweep variants 10 and 11): for blocks of 16 and
-  // of 8 sectors per colour (class 0, 1), the blocks whose 2x2x2 super-cells
-  // touch each block's (CSR: starts [nblk + 1], lists); and the launch's
-  // item ticket, abort word and done flags [2 + 15 * nblk(8)]
-  const int* swnb_start[2];
-  const int* swnb_list[2];
-  int* sw_sync;
 
   // double-float constants (hi, lo)
   float2 zee_f[3], inv_hbar_f, tau_f;        // tau = dt/4

@@ -52,7 +52,6 @@ constexpr int SW_MAXIN = 6;    // same-sector staging entries per atom slot (a b
                                // SW_MAXIN x SW_MAXA; an atom whose entries do not fit reads them
                                // from global memory)
 constexpr int SW_BATCH = 2;    // external neighbours gathered per batch
-constexpr int SL_SWEEP_PASSES = 15;
 // In-sector dependency levels handled per block: SW_LMAX per direction (a
 // block with a deeper sector runs its sectors' chains one spin at a time).
 // Shared words: starts [2][SW_LMAX + 1], cursors [2][SW_LMAX], the staged
@@ -72,28 +71,9 @@ size_t sweep_smem_bytes(bool noise, int maxa, bool fused = false, bool levels = 
          (fused ? (size_t)(noise ? 2 : 1) * 3 * maxa * sizeof(float2) : 0);
 }
 
-// sdf[2j], sdf[2j + 1] through L2 (ld.global.cg): for the persistent colour
-// pass, where other blocks of the same launch write the spins it reads (the
-// read-only path may not serve data written during a kernel).
-__device__ __forceinline__ void load_sdf_cg(const float4* sdf, int j, float4& h, float4& l) {
-  asm volatile("ld.global.cg.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=f"(h.x), "=f"(h.y), "=f"(h.z), "=f"(h.w), "=f"(l.x), "=f"(l.y), "=f"(l.z), "=f"(l.w)
-               : "l"(sdf + 2 * (size_t)j));
-}
-__device__ __forceinline__ double4_32a ld_cg_d4(const double4_32a* p) {
-  double4_32a r;
-  asm volatile("ld.global.cg.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(r.x), "=d"(r.y), "=d"(r.z), "=d"(r.w) : "l"(p));
-  return r;
-}
-template <bool CG>
-__device__ __forceinline__ void load_sdf_t(const float4* sdf, int j, float4& h, float4& l) {
-  if constexpr (CG) load_sdf_cg(sdf, j, h, l);
-  else load_sdf(sdf, j, h, l);
-}
-
 // (h, l) += sum of J_ij s_j (with SO: the field of the exchange, Neel and DMI
 // terms of the pair) over entries [k0, k1) of atom i's exchange list.
-template <bool SO, bool CG = false>
+template <bool SO>
 __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1, float& hx, float& lx, float& hy,
                                           float& ly, float& hz, float& lz) {
   const size_t n = (size_t)d.n;
@@ -111,7 +91,7 @@ __device__ __forceinline__ void ext_field(const SlDev& d, int i, int k0, int k1,
     }
 #pragma unroll
     for (int q = 0; q < SW_BATCH; ++q)
-      if (kb + q < k1) load_sdf_t<CG>(d.sdf, jj[q], vh[q], vl[q]);
+      if (kb + q < k1) load_sdf(d.sdf, jj[q], vh[q], vl[q]);
 #pragma unroll
     for (int q = 0; q < SW_BATCH; ++q) {
       if (kb + q < k1) {
@@ -295,14 +275,11 @@ __device__ __forceinline__ void sweep_chain(const SlDev& d, int q, int a0, bool 
     }
 }
 
-// One colour pass of block `blk`'s SW_SPB sectors.  PERSIST: inside the
-// persistent half-op kernel, which has already waited for the previous
-// pass's neighbouring blocks; the spins and the FP64 state, which other
-// blocks of that launch write, are read through L2, and there is no
-// programmatic-launch wait.
-template <int SW_SPB, int SW_THREADS, bool SO, bool PERSIST>
-__device__ __forceinline__ void sweep_item(const SlDev& d, int colour, int backward, int subpass, int prev_colour,
-                                           int next_colour, int pin, int pout, int blk) {
+// SW_RES: threads per SM the register budget is cut for (768: 80 registers;
+// 1024: 64, no spills for the plain instance).
+template <int SW_SPB, int SW_THREADS, bool SO, int SW_RES = 768>
+__global__ void __launch_bounds__(SW_THREADS, SW_RES / SW_THREADS)
+k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, int next_colour, int pin, int pout) {
   constexpr int SW_MAXA = 12 * SW_SPB;
   extern __shared__ float2 smem[];
   const bool noise = d.any_noise != 0;
@@ -324,8 +301,7 @@ __device__ __forceinline__ void sweep_item(const SlDev& d, int colour, int backw
   float2* sh_e2 = sh_x + 3 * SW_MAXA;
 
   const int s8 = d.s8;
-  // (blockIdx.x itself outside the persistent kernel: a special register costs no register)
-  const int q0 = colour * s8 + (PERSIST ? blk : blockIdx.x) * SW_SPB;
+  const int q0 = colour * s8 + blockIdx.x * SW_SPB;
   const int q1 = min(q0 + SW_SPB, (colour + 1) * s8);
   const int a0 = d.sec_start[q0], a1 = d.sec_start[q1];
   const int na = a1 - a0;
@@ -360,7 +336,7 @@ __device__ __forceinline__ void sweep_item(const SlDev& d, int colour, int backw
       }
     }
     float4 s4h, s4l;
-    load_sdf_t<PERSIST>(d.sdf, i, s4h, s4l);
+    load_sdf(d.sdf, i, s4h, s4l);
     const int ni = __ldg(d.exin + i);
     if (fits) {
       // all of the atom's same-sector entries go to the block's staging pool
@@ -402,10 +378,8 @@ __device__ __forceinline__ void sweep_item(const SlDev& d, int colour, int backw
       }
     }
   }
-  if constexpr (!PERSIST) {
-    pdl_wait();
-    pdl_trigger();
-  }
+  pdl_wait();
+  pdl_trigger();
 
   // phase 1, the external field: the partial field of every other colour
   // plus the colour the previous pass turned (the first pass: all of it)
@@ -418,13 +392,13 @@ __device__ __forceinline__ void sweep_item(const SlDev& d, int colour, int backw
                    p2 = __ldcg(P + 3 * (size_t)i + 2);
       hx = p0.x; lx = p0.y; hy = p1.x; ly = p1.y; hz = p2.x; lz = p2.y;
       const uint2 g = __ldg(d.exc + i);
-      ext_field<SO, PERSIST>(d, i, group_start(g, prev_colour, ne), group_start(g, prev_colour + 1, ne), hx, lx, hy,
-                             ly, hz, lz);
+      ext_field<SO>(d, i, group_start(g, prev_colour, ne), group_start(g, prev_colour + 1, ne), hx, lx, hy, ly, hz,
+                    lz);
     } else {
       hx = d.zee_f[0].x; lx = d.zee_f[0].y;
       hy = d.zee_f[1].x; ly = d.zee_f[1].y;
       hz = d.zee_f[2].x; lz = d.zee_f[2].y;
-      ext_field<SO, PERSIST>(d, i, __ldg(d.exin + i), ne, hx, lx, hy, ly, hz, lz);
+      ext_field<SO>(d, i, __ldg(d.exin + i), ne, hx, lx, hy, ly, hz, lz);
     }
     Fx[3 * t] = D2(acc_done(hx, lx));
     Fx[3 * t + 1] = D2(acc_done(hy, ly));
@@ -478,7 +452,7 @@ __device__ __forceinline__ void sweep_item(const SlDev& d, int colour, int backw
   } else if (pout >= 0) {
     // precompute the next pass's partial external field (all neighbours not
     // of this pass's colour) for block b's sectors of the next colour
-    const int nq0 = next_colour * s8 + (PERSIST ? blk : blockIdx.x) * SW_SPB;
+    const int nq0 = next_colour * s8 + blockIdx.x * SW_SPB;
     const int nq1 = min(nq0 + SW_SPB, (next_colour + 1) * s8);
     const int n0 = d.sec_start[nq0], n1 = d.sec_start[nq1];
     float2* Q = d.hpart[pout];
@@ -490,8 +464,8 @@ __device__ __forceinline__ void sweep_item(const SlDev& d, int colour, int backw
       // every other-sector neighbour not of this pass's colour: two ranges
       const int ne = __ldg(d.exn + i);
       const uint2 g = __ldg(d.exc + i);
-      ext_field<SO, PERSIST>(d, i, __ldg(d.exin + i), group_start(g, colour, ne), hx, lx, hy, ly, hz, lz);
-      ext_field<SO, PERSIST>(d, i, group_start(g, colour + 1, ne), ne, hx, lx, hy, ly, hz, lz);
+      ext_field<SO>(d, i, __ldg(d.exin + i), group_start(g, colour, ne), hx, lx, hy, ly, hz, lz);
+      ext_field<SO>(d, i, group_start(g, colour + 1, ne), ne, hx, lx, hy, ly, hz, lz);
       Q[3 * (size_t)i] = make_float2(hx, lx);
       Q[3 * (size_t)i + 1] = make_float2(hy, ly);
       Q[3 * (size_t)i + 2] = make_float2(hz, lz);
@@ -502,129 +476,13 @@ __device__ __forceinline__ void sweep_item(const SlDev& d, int colour, int backw
   // phase 3
   for (int t = threadIdx.x; t < na; t += blockDim.x) {
     const int i = a0 + t;
-    double4_32a s = PERSIST ? ld_cg_d4(d.s + i) : d.s[i];
+    double4_32a s = d.s[i];
     s.x += df_to_double(F2(H[3 * t]));
     s.y += df_to_double(F2(H[3 * t + 1]));
     s.z += df_to_double(F2(H[3 * t + 2]));
     d.s[i] = s;
     store_spin_split(d, i, s);
   }
-}
-
-// SW_RES: threads per SM the register budget is cut for (768: 80 registers;
-// 1024: 64, no spills for the plain instance).
-template <int SW_SPB, int SW_THREADS, bool SO, int SW_RES = 768>
-__global__ void __launch_bounds__(SW_THREADS, SW_RES / SW_THREADS)
-k_sweep_pass(SlDev d, int colour, int backward, int subpass, int prev_colour, int next_colour, int pin, int pout) {
-  sweep_item<SW_SPB, SW_THREADS, SO, false>(d, colour, backward, subpass, prev_colour, next_colour, pin, pout,
-                                            blockIdx.x);
-}
-
-// ---------------------------------------------------------------------------
-// Dataflow half-op: one launch runs the 15 colour passes, one thread block
-// per item (pass p, block b); a block takes its item from a ticket counter
-// when it starts running, so items are taken in increasing order; an item
-// waits only until the previous pass's blocks whose 2x2x2 super-cells touch
-// b's are done (done flags, release/acquire at GPU scope), then runs the
-// pass body.  Block b of every colour covers the same super-cells, and the
-// neighbour relation holds b itself, so by induction an item starts after
-// every earlier pass of its neighbourhood: it reads final spins and no
-// earlier reader of the spins it writes is still running.  Every item waits
-// only for items of lower index, which blocks that are already running have
-// taken, so the launch cannot deadlock whatever number of blocks is
-// resident.  (One item per block, not a loop over items: a loop would hold
-// the kernel's loop-invariant parameter loads in registers and spill.)  A wait gives up after SL_SWEEP_WAIT_NS (an error in a block
-// that never finishes), sets SL_ERR_TIMEOUT and the abort word, and every
-// block then leaves.
-// ---------------------------------------------------------------------------
-constexpr unsigned long long SL_SWEEP_WAIT_NS = 1000000000ull;   // one second
-
-// Colour of pass p of a half-op (0 .. 6 forward, 7 fused, 6 .. 0 backward)
-// and its direction (0 forward, 2 fused, 1 backward).
-__device__ __forceinline__ int sw_colour(int p) { return p < 7 ? p : (p == 7 ? 7 : 14 - p); }
-__device__ __forceinline__ int sw_dir(int p) { return p < 7 ? 0 : (p == 7 ? 2 : 1); }
-
-__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_gpu(int* p, int v) {
-  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long sl_gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Warp-wide: true once F[list[k]] != 0 for every k in [k0, k1) (the lanes
-// split the list); false if *abort is set or limit_ns pass first.
-__device__ __forceinline__ bool wait_flags(const int* F, const int* list, int k0, int k1, const int* abort,
-                                           unsigned long long limit_ns) {
-  const unsigned long long t0 = sl_gtimer();
-  bool ok = true;
-  for (int k = k0 + (int)(threadIdx.x & 31); k < k1 && ok; k += 32) {
-    const int* f = F + list[k];
-    while (ld_acquire_gpu(f) == 0) {
-      if (ld_acquire_gpu(abort) != 0 || sl_gtimer() - t0 > limit_ns) {
-        ok = false;
-        break;
-      }
-      __nanosleep(100);
-    }
-  }
-  return __all_sync(0xffffffffu, ok);
-}
-
-template <int SPB, int THREADS, bool SO, int RES>
-__global__ void __launch_bounds__(THREADS, RES / THREADS) k_sweep_persist(SlDev d, int subpass0, int cls) {
-  __shared__ int s_item, s_ok;
-  const int nblk = (d.s8 + SPB - 1) / SPB;
-  int* abort = d.sw_sync + 1;
-  int* done = d.sw_sync + 2;
-  // the item: the next ticket, taken when this block starts running
-  if (threadIdx.x == 0) s_item = atomicAdd(d.sw_sync, 1);
-  __syncthreads();
-  const int item = s_item;
-  const int p = item / nblk, b = item - p * nblk;
-  if (threadIdx.x < 32) {
-    const bool ok = p == 0 || wait_flags(done + (p - 1) * nblk, d.swnb_list[cls], d.swnb_start[cls][b],
-                                         d.swnb_start[cls][b + 1], abort, SL_SWEEP_WAIT_NS);
-    if (threadIdx.x == 0) {
-      s_ok = ok;
-      if (!ok) {
-        atomicExch(abort, 1);
-        sl_set_error(d.ctrl, SL_ERR_TIMEOUT);
-      }
-    }
-  }
-  __syncthreads();
-  if (!s_ok) return;
-  const int dir = sw_dir(p);
-  sweep_item<SPB, THREADS, SO, true>(d, sw_colour(p), dir, subpass0 + (dir == 1), p > 0 ? sw_colour(p - 1) : -1,
-                                     p < SL_SWEEP_PASSES - 1 ? sw_colour(p + 1) : -1, p > 0 ? (p - 1) & 1 : -1,
-                                     p < SL_SWEEP_PASSES - 1 ? p & 1 : -1, b);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    st_release_gpu(done + item, 1);
-  }
-}
-
-// The dataflow pass's wait, on its own: one warp waits for 40 done flags that
-// are all set (set = 1) or that nothing sets (set = 0).
-__device__ int g_fw_flags[40], g_fw_list[40], g_fw_abort, g_fw_status;
-__global__ void k_check_sweep_wait(unsigned long long limit_ns, int set) {
-  for (int k = threadIdx.x; k < 40; k += 32) {
-    g_fw_flags[k] = set;
-    g_fw_list[k] = 39 - k;
-  }
-  if (threadIdx.x == 0) g_fw_abort = 0;
-  __threadfence();
-  __syncwarp();
-  const bool ok = wait_flags(g_fw_flags, g_fw_list, 0, 40, &g_fw_abort, limit_ns);
-  if (threadIdx.x == 0) g_fw_status = ok ? SL_OK : SL_ERR_TIMEOUT;
 }
 
 // ---------------------------------------------------------------------------
@@ -1240,6 +1098,7 @@ int launch_tables(const SlDev& d, int grid, int block, cudaStream_t st) {
 // backward in one fused pass (nothing of another colour turns between the
 // two), colours 6..0 backward.  Pass p reads the partial field written by
 // pass p - 1 (none for p = 0) and precomputes the next pass's.
+constexpr int SL_SWEEP_PASSES = 15;
 // Launch with programmatic stream serialization (pdl = true): the kernel may
 // start while the previous one finishes; it waits for it with
 // griddepcontrol.wait.  The first pass of a half-op is launched plainly: the
@@ -1279,27 +1138,8 @@ void launch_half_op_t(const SlDev& d, cudaStream_t st, int subpass0) {
   }
 }
 
-// The dataflow half-op (variants 10, 11): the done flags and the ticket
-// start at zero (one memset node), then one launch of one block per item.
-template <int SPB, int THREADS, bool SO, int RES>
-void launch_half_op_persist_t(const SlDev& d, cudaStream_t st, int subpass0, int cls) {
-  const int nblk = (d.s8 + SPB - 1) / SPB;
-  cudaMemsetAsync(d.sw_sync, 0, sizeof(int) * (2 + (size_t)SL_SWEEP_PASSES * nblk), st);
-  // the fused pass's layout is the largest: every item may be that pass
-  const size_t sm = sweep_smem_bytes(d.any_noise != 0, 12 * SPB, true, true);
-  k_sweep_persist<SPB, THREADS, SO, RES><<<SL_SWEEP_PASSES * nblk, THREADS, sm, st>>>(d, subpass0, cls);
-}
-
 template <bool SO>
 void launch_half_op_so(const SlDev& d, cudaStream_t st, int subpass0) {
-  if (d.tune_sweep == 10) {
-    launch_half_op_persist_t<16, 128, SO, 1024>(d, st, subpass0, 0);
-    return;
-  }
-  if (d.tune_sweep == 11) {
-    launch_half_op_persist_t<8, 128, SO, 768>(d, st, subpass0, 1);
-    return;
-  }
   switch (d.tune_sweep % 5) {
     case 1: launch_half_op_t<32, 256, SO>(d, st, subpass0); break;
     case 2: launch_half_op_t<16, 128, SO>(d, st, subpass0); break;
@@ -1407,10 +1247,6 @@ bool prepare_sweep() {
   ok &= cudaFuncSetAttribute(k_sweep_pass<16, 128, SO, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sweep_smem_bytes(true, 12 * 16, true, true)) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_sweep_pass<8, 128, SO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 8, true, true)) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_sweep_persist<16, 128, SO, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sweep_smem_bytes(true, 12 * 16, true, true)) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_sweep_persist<8, 128, SO, 768>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sweep_smem_bytes(true, 12 * 8, true, true)) == cudaSuccess;
   return ok;
 }
@@ -1540,19 +1376,4 @@ int sl_launch_step(const SlDev& d, cudaStream_t st, SlPhaseMark mark, void* user
 int sl_launch_omega_all(const SlDev& d, double* out, cudaStream_t st) {
   k_omega_all<<<grid_for(d.n), SL_BLOCK, 0, st>>>(d, out);
   return cudaPeekAtLastError() == cudaSuccess ? SL_OK : SL_ERR_CUDA;
-}
-
-extern "C" int sl_check_sweep_wait(int64_t limit_ns, int32_t set, int32_t* status) {
-  if (!status || limit_ns < 0 || limit_ns > 2000000000LL) return SL_ERR_ARG;
-  cudaStream_t st = nullptr;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SL_ERR_CUDA;
-  int rc = SL_OK;
-  int v = SL_ERR_CUDA;
-  k_check_sweep_wait<<<1, 32, 0, st>>>((unsigned long long)limit_ns, set ? 1 : 0);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess ||
-      cudaMemcpyFromSymbol(&v, g_fw_status, sizeof(int)) != cudaSuccess)
-    rc = SL_ERR_CUDA;
-  cudaStreamDestroy(st);
-  if (rc == SL_OK) *status = v;
-  return rc;
 }

@@ -56,22 +56,3 @@ def test_bounds_are_checked_on_the_host(lib):
     assert L.sl_check_bounded_wait(-1, 0, ctypes.byref(st)) == lib.SL_ERR_ARG
     assert L.sl_check_bounded_wait(3_000_000_000, 0, ctypes.byref(st)) == lib.SL_ERR_ARG
     assert L.sl_check_bounded_wait(1000, 0, None) == lib.SL_ERR_ARG
-
-
-def test_the_dataflow_pass_wait_times_out_and_the_gpu_stays_usable(lib):
-    """The wait of the dataflow colour pass (items waiting for their
-    neighbour blocks' done flags) on flags nothing sets ends with
-    SL_ERR_TIMEOUT after its bound; on set flags it returns SL_OK."""
-    L = lib.load()
-    st = ctypes.c_int32(-100)
-    t0 = time.perf_counter()
-    assert L.sl_check_sweep_wait(2_000_000, 0, ctypes.byref(st)) == 0 and st.value == lib.SL_ERR_TIMEOUT
-    assert time.perf_counter() - t0 < 5.0
-    assert L.sl_check_sweep_wait(2_000_000, 1, ctypes.byref(st)) == 0 and st.value == lib.SL_OK
-    from paper_1801_10233_gb300 import System
-    p, r, v, s = inputs.bcc_fe_system(6, 72, T=200.0)
-    g = System(p, r, v, s)
-    g.set_launch_shape(10, 128)
-    g.step(3)
-    assert g.status() == 0
-    assert np.isfinite(g.energy()[4])

@@ -34,8 +34,7 @@ def test_every_shape_is_bitwise_identical(batch):
     else:
         p, r, v, s = inputs.bcc_fe_system(12, 5, T=300.0, spins="uniform", rebuild_every=4)
     ref, _ = run(p, r, v, s, 8)
-    for shape in [(1, 64), (2, 256), (3, 128), (4, 64), (0, 256), (5, 128), (6, 64), (7, 256), (8, 128), (9, 64),
-                  (10, 128), (11, 64)]:
+    for shape in [(1, 64), (2, 256), (3, 128), (4, 64), (0, 256), (5, 128), (6, 64), (7, 256), (8, 128), (9, 64)]:
         got, _ = run(p, r, v, s, 8, shape=shape)
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), shape
@@ -45,7 +44,7 @@ def test_autotune_keeps_state_and_results():
     p, r, v, s = inputs.bcc_fe_system(12, 6, T=300.0, spins="uniform", rebuild_every=4)
     ref, _ = run(p, r, v, s, 8)
     got, info = run(p, r, v, s, 8, tune=True)
-    assert info["candidates"] == 36 and info["ns_per_step"] > 0 and info["default_ns_per_step"] > 0
+    assert info["candidates"] == 30 and info["ns_per_step"] > 0 and info["default_ns_per_step"] > 0
     assert info["ns_per_step"] <= info["default_ns_per_step"]
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
@@ -59,45 +58,6 @@ def test_autotune_rejects_small_scratch():
     scratch = torch.empty(1024, dtype=torch.uint8, device="cuda")
     out = (ctypes.c_int64 * 8)()
     assert g._L.sl_autotune(g._h, scratch.data_ptr(), 1024, 2, out) == _lib.SL_ERR_WORKSPACE
-    assert g._L.sl_set_launch_shape(g._h, 12, 128) == _lib.SL_ERR_ARG
+    assert g._L.sl_set_launch_shape(g._h, 10, 128) == _lib.SL_ERR_ARG
     assert g._L.sl_set_launch_shape(g._h, 0, 96) == _lib.SL_ERR_ARG
     g.close()
-
-
-DATAFLOW = [(10, 3), (11, 4)]   # dataflow variant, the pipelined variant of the same tile
-
-
-@pytest.mark.parametrize("variant,same", DATAFLOW)
-@pytest.mark.parametrize("case", ["spins_only", "langevin", "spin_orbit", "ragged_batch"])
-def test_dataflow_pass_is_bitwise_the_pipelined_pass(case, variant, same):
-    """The dataflow half-op (one launch, items waiting on their neighbour
-    blocks of the previous pass) gives the bits of the pipelined pass with the
-    same tile: spins only (consecutive half-ops turn the same colour back to
-    back), the spin bath, the spin-orbit terms, and a batch of uneven
-    replicas (blocks spanning replicas)."""
-    if case == "spins_only":
-        p, r, v, s = inputs.bcc_fe_system(14, 41, T=300.0, spins="uniform", fix_lattice=1)
-    elif case == "langevin":
-        p, r, v, s = inputs.bcc_fe_system(14, 42, T=300.0, spins="uniform")
-        p = dict(p, **{"lambda": 0.05, "temperature_K": 400.0, "seed": 97531, "replica": 1})
-    elif case == "spin_orbit":
-        p, r, v, s = inputs.bcc_fe_system(12, 43, T=300.0, spins="uniform", aniso_K_eV=0.003, aniso_axis=[0.6, 0.0, 0.8],
-                                          neel_alpha_eV=0.01, neel_gamma=0.1, neel_delta_A=1.7, dmi_alpha_eV=0.008,
-                                          dmi_gamma=0.3, dmi_delta_A=1.9)
-    else:
-        p, r, v, s = inputs.replica_systems([8, 13, 6, 11], [100.0, 600.0, 300.0, 1100.0], 44)
-    ref, _ = run(p, r, v, s, 6, shape=(same, 128))
-    got, _ = run(p, r, v, s, 6, shape=(variant, 128))
-    for a, b in zip(got, ref):
-        assert np.array_equal(a, b)
-
-
-@pytest.mark.parametrize("variant,same", DATAFLOW)
-def test_dataflow_pass_full_size(variant, same):
-    """524,288 atoms (12,960 items of 16 sectors per half-op, thousands in
-    flight at once): ten steps bitwise equal to the pipelined pass."""
-    p, r, v, s = inputs.workload("fe_bcc_64x64x64_nve")
-    ref, _ = run(p, r, v, s, 10, shape=(same, 128))
-    got, _ = run(p, r, v, s, 10, shape=(variant, 128))
-    for a, b in zip(got, ref):
-        assert np.array_equal(a, b)
