@@ -197,10 +197,13 @@ __device__ __forceinline__ void sweep_rotate(const SlDev& d, int i, int a0, bool
       acc_prod(hz, lz, J0, F2(S[3 * u0 + 2]));
     }
   }
+  // the two running sums (each kept normalised by acc_prod) combined with
+  // the sloppy sum: they are partial fields, not nearly opposite ones, and
+  // this sits on the dependent chain of the in-sector rotations
   df3 w;
-  w.x = df_mul(df_add(acc_done(hx, lx), acc_done(gx, kx)), ih);
-  w.y = df_mul(df_add(acc_done(hy, ly), acc_done(gy, ky)), ih);
-  w.z = df_mul(df_add(acc_done(hz, lz), acc_done(gz, kz)), ih);
+  w.x = df_mul(df_add_sloppy(df_make(hx, lx), df_make(gx, kx)), ih);
+  w.y = df_mul(df_add_sloppy(df_make(hy, ly), df_make(gy, ky)), ih);
+  w.z = df_mul(df_add_sloppy(df_make(hz, lz), df_make(gz, kz)), ih);
   df3 s;
   s.x = F2(S[3 * t]); s.y = F2(S[3 * t + 1]); s.z = F2(S[3 * t + 2]);
   // uniaxial anisotropy: exact half turns about n before and after the
@@ -243,9 +246,12 @@ __device__ __forceinline__ void sweep_rotate(const SlDev& d, int i, int a0, bool
     inc.z = df_add(df_add(inc_a.z, inc.z), i2.z);
     S[3 * t] = D2(s.x); S[3 * t + 1] = D2(s.y); S[3 * t + 2] = D2(s.z);
   } else {
-    S[3 * t] = D2(df_add(s.x, inc.x));
-    S[3 * t + 1] = D2(df_add(s.y, inc.y));
-    S[3 * t + 2] = D2(df_add(s.z, inc.z));
+    // the turned spin for the later same-sector neighbours (the FP64 state
+    // takes the increment itself): |inc| is of order theta, so the sloppy
+    // sum's error stays below 2^-47 of a unit component
+    S[3 * t] = D2(df_add_sloppy(s.x, inc.x));
+    S[3 * t + 1] = D2(df_add_sloppy(s.y, inc.y));
+    S[3 * t + 2] = D2(df_add_sloppy(s.z, inc.z));
   }
   if (second) {   // the fused pass's second chain: total increment
     H[3 * t] = D2(df_add(F2(H[3 * t]), inc.x));
