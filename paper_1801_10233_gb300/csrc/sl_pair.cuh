@@ -70,8 +70,14 @@ __device__ __forceinline__ box3 load_box(const SlDev& d, const SlRep& R) {
 }
 
 // Minimum-image difference b - a in fixed point (|b - a| < 1.5 L before the shift).
+// A difference whose high word lies strictly inside (-H_hi, H_hi) is below H
+// in magnitude and needs no shift: one 32-bit test decides that for all but
+// the pairs across the box faces, which take the 64-bit comparisons (the
+// result is the same either way).
 __device__ __forceinline__ long long fx_diff(long long b, long long a, long long L, long long H) {
   long long D = b - a;
+  const int hi = (int)(D >> 32), hh = (int)(H >> 32);
+  if (hi > -hh && hi < hh) return D;
   D = D > H ? D - L : D;
   D = D < -H ? D + L : D;
   return D;
