@@ -71,11 +71,11 @@ STATE_BYTES_PER_ATOM_STEP = 144.0
 # reported as null (stale), never reused.
 PROFILED_DRAM = {
     ("fe_bcc_100x100x100_nve", "k_sweep_pass"): {
-        "dram_bytes_per_launch": 172.7e6, "sources_sha": "5748c2ce744de71b",
+        "dram_bytes_per_launch": 172.9e6, "sources_sha": "461ff7b982d6e9fe",
         "profile": "ncu dram__bytes_read.sum + dram__bytes_write.sum, --cache-control none, mean of 2 launches "
                    "of k_sweep_pass<16, 128, 0, 1024> (launch shape 3,128) inside 3-step runs"},
     ("fe_bcc_100x100x100_nve", "k_force"): {
-        "dram_bytes_per_launch": 2445.5e6, "sources_sha": "5748c2ce744de71b",
+        "dram_bytes_per_launch": 2412.4e6, "sources_sha": "461ff7b982d6e9fe",
         "profile": "ncu dram__bytes_read.sum + dram__bytes_write.sum, --cache-control none, mean of 2 launches "
                    "of k_force<0, 0> (launch shape 3,128) inside 3-step runs"},
 }
