@@ -71,15 +71,16 @@ STATE_BYTES_PER_ATOM_STEP = 144.0
 # reported as null (stale), never reused.
 PROFILED_DRAM = {
     ("fe_bcc_100x100x100_nve", "k_sweep_pass"): {
-        "dram_bytes_per_launch": 172.9e6, "sources_sha": "461ff7b982d6e9fe",
+        "dram_bytes_per_launch": 172.7e6, "sources_sha": "0258bccf97492cd8",
         "profile": "ncu dram__bytes_read.sum + dram__bytes_write.sum, --cache-control none, mean of 2 launches "
                    "of k_sweep_pass<16, 128, 0, 1024> (launch shape 3,128) inside 3-step runs"},
     ("fe_bcc_100x100x100_nve", "k_force"): {
-        "dram_bytes_per_launch": 2412.4e6, "sources_sha": "461ff7b982d6e9fe",
+        "dram_bytes_per_launch": 2415.1e6, "sources_sha": "0258bccf97492cd8",
         "profile": "ncu dram__bytes_read.sum + dram__bytes_write.sum, --cache-control none, mean of 2 launches "
                    "of k_force<0, 0> (launch shape 3,128) inside 3-step runs"},
 }
-PROFILED_SOURCES = ("sl_step.cu", "sl_pair.cuh", "sl_df64.cuh", "sl_internal.cuh", "sl_build.cu", "sl_api.cu")
+PROFILED_SOURCES = ("sl_step.cu", "sl_sweep.cuh", "sl_sweep.cu", "sl_sweep_so.cu", "sl_pair.cuh", "sl_df64.cuh",
+                    "sl_internal.cuh", "sl_build.cu", "sl_api.cu")
 
 
 def kernel_sources_sha():

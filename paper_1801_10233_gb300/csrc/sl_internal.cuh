@@ -266,6 +266,19 @@ int sl_launch_rebuild(const SlDev& d, cudaStream_t st);
 int sl_launch_pairs_and_forces(const SlDev& d, cudaStream_t st, int kick);
 int sl_launch_split(const SlDev& d, cudaStream_t st, int only_if_rebuild);
 int sl_prepare_kernels();
+// The spin half-op: its 15 colour passes in the context's tile shape, noise
+// sub-passes from subpass0 (sl_sweep.cu for the plain Hamiltonian,
+// sl_sweep_so.cu with the spin-orbit terms); the pass kernels'
+// shared-memory limits.
+#define SL_SWEEP_PASSES 15
+void sl_launch_half_op_plain(const SlDev& d, cudaStream_t st, int subpass0);
+void sl_launch_half_op_so(const SlDev& d, cudaStream_t st, int subpass0);
+int sl_prepare_sweep_plain();
+int sl_prepare_sweep_so();
+inline void sl_launch_half_op(const SlDev& d, cudaStream_t st, int subpass0) {
+  if (d.so) sl_launch_half_op_so(d, st, subpass0);
+  else sl_launch_half_op_plain(d, st, subpass0);
+}
 // Phases of one step, for optional event timing.
 enum { SL_PHASE_KICK = 0, SL_PHASE_SPIN1 = 1, SL_PHASE_DRIFT = 2, SL_PHASE_JTABLE = 3, SL_PHASE_SPIN2 = 4,
        SL_PHASE_FORCE = 5, SL_NPHASE = 6 };
